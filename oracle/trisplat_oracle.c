@@ -1,0 +1,896 @@
+/*
+ * FP64 CPU oracle for the differentiable triangle-splat rasterizer of
+ * "Triangle Splatting for Real-Time Radiance Field Rendering" (arXiv 2505.19175).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+ * CPU-baseline / reference leg may load this library. It shares no code, header,
+ * constant table or helper with the CUDA path, and nothing in the product calls it.
+ *
+ * What it computes is the plain definition of the rendered image, not the tiled
+ * method that reaches it faster:
+ *   - pinhole projection of each vertex (Sec. 3.1, "Differentiable rasterization";
+ *     the printed q = K(Rv + t) omits the perspective divide, read here as the
+ *     standard u = fx x/z + cx, v = fy y/z + cy);
+ *   - the 2D signed distance field phi(p) = max_i (n_i . p + d_i) with outward unit
+ *     edge normals, its minimum at the incenter s, phi(s) = -inradius (Sec. 3.1,
+ *     "A new window function");
+ *   - the window I(p) = ReLU(phi(p)/phi(s))^sigma (Sec. 3.1, Eq. indicator1);
+ *   - alpha = min(ALPHA_MAX, o I), kept when alpha >= ALPHA_MIN, composited front to
+ *     back in order of camera-space centroid depth (ties: triangle id), stopping
+ *     before a fragment that would drop transmittance below T_EPS (Sec. 3.1: the
+ *     rendering equation of prior splatting work; depth sort by triangle centre,
+ *     Supp. "Depth sorting");
+ *   - view-dependent colour from real spherical harmonics up to degree 3
+ *     (Sec. 4: 48 colour floats per triangle), rgb = max(0, sum Y_lm c_lm + 0.5);
+ *   - the tight screen rectangle of Supp. "Tile assignment": edges moved inward by
+ *     d = r (tau/o)^(1/sigma), i.e. the triangle scaled about its incenter by
+ *     f = 1 - (tau/o)^(1/sigma), tau = ALPHA_MIN.
+ * Every pixel is tested against every triangle (brute force) or, in "fast" mode,
+ * every triangle visits only the pixels of its padded vertex bounding box; the two
+ * evaluate the identical per-(pixel, triangle) arithmetic and are bit-identical.
+ *
+ * The adjoint differentiates that definition: per pixel, reverse-mode through the
+ * compositing sum, and forward-mode dual numbers for alpha and rgb as functions of
+ * the 9 vertex coordinates, o and sigma; SH coefficients enter linearly.
+ *
+ * For comparisons against an FP32 implementation it also classifies each pixel whose
+ * value FP32 arithmetic cannot resolve to the image tolerance: a discontinuous
+ * decision (alpha vs ALPHA_MIN, the T_EPS stop, depth order, culling) that lies within
+ * an FP32 error band, or a first-order error estimate above a quarter of 1e-4.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------ */
+/* constants and camera, passed as flat double arrays                  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double alpha_max, alpha_min, t_eps, z_near, r_min, tile, rect_pad;
+} consts_t;
+
+typedef struct {
+    double R[9], t[3], fx, fy, cx, cy;
+    int W, H;
+    double bg[3];
+} cam_t;
+
+static consts_t load_consts(const double *c) {
+    consts_t k;
+    k.alpha_max = c[0]; k.alpha_min = c[1]; k.t_eps = c[2]; k.z_near = c[3];
+    k.r_min = c[4]; k.tile = c[5]; k.rect_pad = c[6];
+    return k;
+}
+
+static cam_t load_cam(const double *c) {
+    cam_t m;
+    for (int i = 0; i < 9; ++i) m.R[i] = c[i];
+    for (int i = 0; i < 3; ++i) m.t[i] = c[9 + i];
+    m.fx = c[12]; m.fy = c[13]; m.cx = c[14]; m.cy = c[15];
+    m.W = (int)c[16]; m.H = (int)c[17];
+    for (int i = 0; i < 3; ++i) m.bg[i] = c[18 + i];
+    return m;
+}
+
+/* FP32 error model used only by the pixel classifier (not by the image). */
+#define EPS_LINE 9.5367431640625e-07   /* 2^-20: FP32 line-evaluation error per unit term */
+#define EPS_MUFU 9.5367431640625e-07   /* 2^-20: relative error of FP32 lg2/ex2 */
+#define EPS_ACC  1.1920928955078125e-07 /* 2^-23: one FP32 rounding */
+#define RECT_BAND 1.0e-3               /* px: FP32 error band of a rectangle bound */
+#define FLAG_TOL 2.5e-5                /* flag a pixel whose error estimate exceeds this */
+
+enum { AMB_SKIP = 1, AMB_STOP = 2, AMB_ORDER = 4, AMB_SENS = 8, AMB_CULL = 16 };
+
+/* ------------------------------------------------------------------ */
+/* real spherical harmonics, degree <= 3                               */
+/* ------------------------------------------------------------------ */
+/* Legendre polynomial coefficients P_l(z) = sum_j leg[l][j] z^j from Bonnet's
+ * recurrence (l+1) P_{l+1} = (2l+1) z P_l - l P_{l-1}. */
+static double leg[4][4];
+static double sh_K[4][4];   /* K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) */
+static int sh_ready = 0;
+
+static double fact(int n) { double f = 1; for (int i = 2; i <= n; ++i) f *= i; return f; }
+
+static void sh_init(void) {
+    if (sh_ready) return;
+    memset(leg, 0, sizeof leg);
+    leg[0][0] = 1.0;
+    leg[1][1] = 1.0;
+    for (int l = 1; l < 3; ++l)
+        for (int j = 0; j < 4; ++j) {
+            double v = -(double)l * leg[l - 1][j];
+            if (j > 0) v += (2.0 * l + 1.0) * leg[l][j - 1];
+            leg[l + 1][j] = v / (l + 1.0);
+        }
+    for (int l = 0; l < 4; ++l)
+        for (int m = 0; m <= l; ++m)
+            sh_K[l][m] = sqrt((2.0 * l + 1.0) / (4.0 * ORC_PI) * fact(l - m) / fact(l + m));
+    sh_ready = 1;
+}
+
+/* m-th derivative of P_l evaluated at z. */
+static double leg_deriv(int l, int m, double z) {
+    double acc = 0.0, zp = 1.0;
+    for (int j = m; j <= l; ++j) {
+        double c = leg[l][j];
+        for (int k = 0; k < m; ++k) c *= (double)(j - k);
+        acc += c * zp;
+        zp *= z;
+    }
+    return acc;
+}
+
+/* ------------------------------------------------------------------ */
+/* dual numbers: value + 11 partials (9 vertex coords, o, sigma)       */
+/* ------------------------------------------------------------------ */
+#define ND 11
+typedef struct { double v, d[ND]; } dual;
+
+static dual dcst(double v) { dual r; r.v = v; memset(r.d, 0, sizeof r.d); return r; }
+static dual dvar(double v, int i) { dual r = dcst(v); r.d[i] = 1.0; return r; }
+static dual dadd(dual a, dual b) { a.v += b.v; for (int i = 0; i < ND; ++i) a.d[i] += b.d[i]; return a; }
+static dual dsub(dual a, dual b) { a.v -= b.v; for (int i = 0; i < ND; ++i) a.d[i] -= b.d[i]; return a; }
+static dual dscale(dual a, double s) { a.v *= s; for (int i = 0; i < ND; ++i) a.d[i] *= s; return a; }
+static dual daddc(dual a, double c) { a.v += c; return a; }
+static dual dmul(dual a, dual b) {
+    dual r; r.v = a.v * b.v;
+    for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+    return r;
+}
+static dual ddiv(dual a, dual b) {
+    dual r; r.v = a.v / b.v;
+    for (int i = 0; i < ND; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+    return r;
+}
+static dual dsqrt(dual a) {
+    dual r; r.v = sqrt(a.v);
+    for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] / (2.0 * r.v);
+    return r;
+}
+/* a^b for a > 0, both dual */
+static dual dpow(dual a, dual b) {
+    dual r; r.v = pow(a.v, b.v);
+    double la = log(a.v);
+    for (int i = 0; i < ND; ++i) r.d[i] = r.v * (b.v * a.d[i] / a.v + la * b.d[i]);
+    return r;
+}
+
+/* Y_k(dir) for k < (deg+1)^2, dual version (dir is a unit vector of duals). */
+static void sh_eval_dual(int deg, const dual dir[3], dual *out) {
+    sh_init();
+    /* (x + i y)^m for m = 0..3 */
+    dual re[4], im[4];
+    re[0] = dcst(1.0); im[0] = dcst(0.0);
+    for (int m = 1; m <= 3; ++m) {
+        re[m] = dsub(dmul(re[m - 1], dir[0]), dmul(im[m - 1], dir[1]));
+        im[m] = dadd(dmul(re[m - 1], dir[1]), dmul(im[m - 1], dir[0]));
+    }
+    for (int l = 0; l <= deg; ++l) {
+        for (int m = -l; m <= l; ++m) {
+            int am = m < 0 ? -m : m;
+            /* d^am P_l / dz^am at z, as a dual through dir[2] */
+            double pv = leg_deriv(l, am, dir[2].v);
+            double pd = (am < l) ? leg_deriv(l, am + 1, dir[2].v) : 0.0;
+            dual P = dscale(dir[2], pd);
+            P.v = pv;
+            dual y;
+            if (m == 0) y = dscale(P, sh_K[l][0]);
+            else if (m > 0) y = dscale(dmul(P, re[am]), sqrt(2.0) * sh_K[l][am]);
+            else y = dscale(dmul(P, im[am]), sqrt(2.0) * sh_K[l][am]);
+            out[l * l + l + m] = y;
+        }
+    }
+}
+
+static void sh_eval_val(int deg, const double dir[3], double *out) {
+    dual dd[3], y[16];
+    for (int i = 0; i < 3; ++i) dd[i] = dcst(dir[i]);
+    sh_eval_dual(deg, dd, y);
+    for (int k = 0; k < (deg + 1) * (deg + 1); ++k) out[k] = y[k].v;
+}
+
+/* ------------------------------------------------------------------ */
+/* 2D triangle: edges, outward normals, inradius, incenter             */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double q[3][2];
+    double ell[3];          /* side opposite vertex i */
+    double area2;           /* (q1-q0) x (q2-q0) */
+    double perim, r;        /* perimeter, inradius = |area2| / perim */
+    double s[2];            /* incenter */
+    double n[3][2], d[3];   /* L_i(p) = n_i . p + d_i, n_i outward unit normal of side i */
+} tri2d_t;
+
+static void tri2d_setup(const double q[3][2], tri2d_t *T) {
+    memcpy(T->q, q, sizeof T->q);
+    double ex[3], ey[3];
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3, k = (i + 2) % 3;
+        ex[i] = q[k][0] - q[j][0];
+        ey[i] = q[k][1] - q[j][1];
+        T->ell[i] = hypot(ex[i], ey[i]);
+    }
+    T->area2 = (q[1][0] - q[0][0]) * (q[2][1] - q[0][1]) - (q[1][1] - q[0][1]) * (q[2][0] - q[0][0]);
+    T->perim = T->ell[0] + T->ell[1] + T->ell[2];
+    T->r = T->perim > 0 ? fabs(T->area2) / T->perim : 0.0;
+    if (T->perim > 0) {
+        T->s[0] = (T->ell[0] * q[0][0] + T->ell[1] * q[1][0] + T->ell[2] * q[2][0]) / T->perim;
+        T->s[1] = (T->ell[0] * q[0][1] + T->ell[1] * q[1][1] + T->ell[2] * q[2][1]) / T->perim;
+    } else {
+        T->s[0] = q[0][0]; T->s[1] = q[0][1];
+    }
+    double sg = T->area2 >= 0 ? 1.0 : -1.0;
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3;
+        double l = T->ell[i] > 0 ? T->ell[i] : 1.0;
+        /* edge i runs q_j -> q_k; (ey, -ex) is its right-hand normal, outward for a
+         * counter-clockwise triangle, hence the sign of the signed area. */
+        T->n[i][0] = sg * ey[i] / l;
+        T->n[i][1] = -sg * ex[i] / l;
+        T->d[i] = -(T->n[i][0] * q[j][0] + T->n[i][1] * q[j][1]);
+    }
+}
+
+/* phi(p)/phi(s) with phi(s) = -r; also returns the arg-max edge (lowest index on ties) */
+static double tri2d_ratio(const tri2d_t *T, double px, double py, int *amax) {
+    double phi = -INFINITY;
+    int am = 0;
+    for (int i = 0; i < 3; ++i) {
+        double L = T->n[i][0] * px + T->n[i][1] * py + T->d[i];
+        if (L > phi) { phi = L; am = i; }
+    }
+    if (amax) *amax = am;
+    return phi / (-T->r);
+}
+
+/* ------------------------------------------------------------------ */
+/* per-triangle setup                                                  */
+/* ------------------------------------------------------------------ */
+enum { CULL_NONE = 0, CULL_NEAR = 1, CULL_DEGENERATE = 2 };
+enum { RECT_OK = 0, RECT_LOW_OPACITY = 1, RECT_EMPTY = 2 };
+
+typedef struct {
+    int cull;               /* CULL_* : removes the triangle from the image */
+    int amb_cull;           /* a cull decision within the FP32 band */
+    double z[3], depth;
+    tri2d_t g;
+    double o, sigma;
+    double dir[3], rgb_raw[3], rgb[3];
+    double bbox[4];         /* vertex bbox (xmin, ymin, xmax, ymax) */
+    /* tight rectangle */
+    int rect_state;
+    double f, rect[4];
+    int pix[4], tiles[4], ntiles;
+    int amb_rect;
+} tri_t;
+
+static void cam_center(const cam_t *C, double cp[3]) {
+    for (int j = 0; j < 3; ++j)
+        cp[j] = -(C->R[0 * 3 + j] * C->t[0] + C->R[1 * 3 + j] * C->t[1] + C->R[2 * 3 + j] * C->t[2]);
+}
+
+/* pixel range whose centres x + 0.5 lie in [lo, hi], clamped to [0, n-1] */
+static void pix_range(double lo, double hi, int n, int *a, int *b) {
+    if (lo < -2.0) lo = -2.0;
+    if (hi > n + 2.0) hi = n + 2.0;
+    if (hi < -2.0) hi = -2.0;
+    if (lo > n + 2.0) lo = n + 2.0;
+    int x0 = (int)ceil(lo - 0.5), x1 = (int)floor(hi - 0.5);
+    if (x0 < 0) x0 = 0;
+    if (x1 > n - 1) x1 = n - 1;
+    *a = x0; *b = x1;
+}
+
+static void rect_tiles(const double rect[4], double pad, const cam_t *C, int tile, int pix[4], int tiles[4], int *ntiles) {
+    pix_range(rect[0] - pad, rect[2] + pad, C->W, &pix[0], &pix[2]);
+    pix_range(rect[1] - pad, rect[3] + pad, C->H, &pix[1], &pix[3]);
+    if (pix[0] > pix[2] || pix[1] > pix[3]) {
+        tiles[0] = tiles[1] = 0; tiles[2] = tiles[3] = -1; *ntiles = 0;
+        return;
+    }
+    tiles[0] = pix[0] / tile; tiles[1] = pix[1] / tile;
+    tiles[2] = pix[2] / tile; tiles[3] = pix[3] / tile;
+    *ntiles = (tiles[2] - tiles[0] + 1) * (tiles[3] - tiles[1] + 1);
+}
+
+static void tri_setup(int id, const double *verts, const double *sh, int sh_deg,
+                      const double *opac, const double *sigma, const cam_t *C,
+                      const consts_t *K, tri_t *T) {
+    memset(T, 0, sizeof *T);
+    const double *v = verts + 9 * (size_t)id;
+    double q[3][2];
+    int near = 0, near_amb = 0;
+    for (int i = 0; i < 3; ++i) {
+        double X = v[3 * i], Y = v[3 * i + 1], Z = v[3 * i + 2];
+        double xc = C->R[0] * X + C->R[1] * Y + C->R[2] * Z + C->t[0];
+        double yc = C->R[3] * X + C->R[4] * Y + C->R[5] * Z + C->t[1];
+        double zc = C->R[6] * X + C->R[7] * Y + C->R[8] * Z + C->t[2];
+        T->z[i] = zc;
+        if (zc < K->z_near) near = 1;
+        if (fabs(zc - K->z_near) <= 1e-5 * (1.0 + fabs(K->z_near))) near_amb = 1;
+        if (zc > 0) {
+            q[i][0] = C->fx * xc / zc + C->cx;
+            q[i][1] = C->fy * yc / zc + C->cy;
+        } else {
+            q[i][0] = q[i][1] = 0.0;
+        }
+    }
+    T->depth = (T->z[0] + T->z[1] + T->z[2]) / 3.0;
+    T->o = opac[id];
+    T->sigma = sigma[id];
+    T->bbox[0] = fmin(q[0][0], fmin(q[1][0], q[2][0]));
+    T->bbox[1] = fmin(q[0][1], fmin(q[1][1], q[2][1]));
+    T->bbox[2] = fmax(q[0][0], fmax(q[1][0], q[2][0]));
+    T->bbox[3] = fmax(q[0][1], fmax(q[1][1], q[2][1]));
+    T->tiles[2] = T->tiles[3] = -1;
+    T->amb_cull = near_amb;
+    tri2d_setup((const double (*)[2])q, &T->g);
+    if (fabs(T->g.r - K->r_min) <= 0.01 * K->r_min) T->amb_cull = 1;
+    if (near) { T->cull = CULL_NEAR; T->rect_state = RECT_EMPTY; return; }
+    if (!(T->g.r >= K->r_min)) { T->cull = CULL_DEGENERATE; T->rect_state = RECT_EMPTY; return; }
+
+    /* colour: direction from the camera centre to the world-space centroid */
+    double cp[3], m[3], w2 = 0.0;
+    cam_center(C, cp);
+    for (int j = 0; j < 3; ++j) {
+        m[j] = (v[j] + v[3 + j] + v[6 + j]) / 3.0;
+        T->dir[j] = m[j] - cp[j];
+        w2 += T->dir[j] * T->dir[j];
+    }
+    double wn = sqrt(w2);
+    for (int j = 0; j < 3; ++j) T->dir[j] /= wn;
+    double Y[16];
+    int nk = (sh_deg + 1) * (sh_deg + 1);
+    sh_eval_val(sh_deg, T->dir, Y);
+    const double *c = sh + (size_t)id * nk * 3;
+    for (int ch = 0; ch < 3; ++ch) {
+        double acc = 0.5;
+        for (int k = 0; k < nk; ++k) acc += Y[k] * c[k * 3 + ch];
+        T->rgb_raw[ch] = acc;
+        T->rgb[ch] = acc > 0 ? acc : 0.0;
+    }
+
+    /* tight rectangle: triangle scaled about its incenter by f */
+    T->f = 1.0 - pow(K->alpha_min / T->o, 1.0 / T->sigma);
+    if (fabs(T->f) <= 1e-5) T->amb_rect = 1;
+    if (!(T->f > 0)) {
+        T->rect_state = RECT_LOW_OPACITY;
+        T->tiles[2] = T->tiles[3] = -1;
+        return;
+    }
+    double w[3][2];
+    for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 2; ++a) w[i][a] = T->g.s[a] + T->f * (q[i][a] - T->g.s[a]);
+    T->rect[0] = fmin(w[0][0], fmin(w[1][0], w[2][0]));
+    T->rect[1] = fmin(w[0][1], fmin(w[1][1], w[2][1]));
+    T->rect[2] = fmax(w[0][0], fmax(w[1][0], w[2][0]));
+    T->rect[3] = fmax(w[0][1], fmax(w[1][1], w[2][1]));
+    int tile = (int)K->tile;
+    rect_tiles(T->rect, K->rect_pad, C, tile, T->pix, T->tiles, &T->ntiles);
+    T->rect_state = T->ntiles > 0 ? RECT_OK : RECT_EMPTY;
+    /* a bound within the FP32 band of a boundary that changes the tile set */
+    int pp[4], tt[4], nn;
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+        rect_tiles(T->rect, K->rect_pad + sgn * RECT_BAND, C, tile, pp, tt, &nn);
+        if (nn != T->ntiles || (nn > 0 && memcmp(tt, T->tiles, sizeof tt) != 0)) T->amb_rect = 1;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* dual setup of one triangle (only for the adjoint)                   */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    dual n[3][2], d[3], r, o, sigma, rgb_raw[3];
+    double Y[16];
+} tri_dual_t;
+
+static void tri_dual_setup(int id, const double *verts, const double *sh, int sh_deg,
+                           const cam_t *C, const tri_t *T, tri_dual_t *D) {
+    const double *v = verts + 9 * (size_t)id;
+    dual V[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) V[i][a] = dvar(v[3 * i + a], 3 * i + a);
+    dual q[3][2];
+    for (int i = 0; i < 3; ++i) {
+        dual xc = daddc(dadd(dadd(dscale(V[i][0], C->R[0]), dscale(V[i][1], C->R[1])), dscale(V[i][2], C->R[2])), C->t[0]);
+        dual yc = daddc(dadd(dadd(dscale(V[i][0], C->R[3]), dscale(V[i][1], C->R[4])), dscale(V[i][2], C->R[5])), C->t[1]);
+        dual zc = daddc(dadd(dadd(dscale(V[i][0], C->R[6]), dscale(V[i][1], C->R[7])), dscale(V[i][2], C->R[8])), C->t[2]);
+        q[i][0] = daddc(dscale(ddiv(xc, zc), C->fx), C->cx);
+        q[i][1] = daddc(dscale(ddiv(yc, zc), C->fy), C->cy);
+    }
+    dual ex[3], ey[3], ell[3];
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3, k = (i + 2) % 3;
+        ex[i] = dsub(q[k][0], q[j][0]);
+        ey[i] = dsub(q[k][1], q[j][1]);
+        ell[i] = dsqrt(dadd(dmul(ex[i], ex[i]), dmul(ey[i], ey[i])));
+    }
+    dual area2 = dsub(dmul(dsub(q[1][0], q[0][0]), dsub(q[2][1], q[0][1])),
+                      dmul(dsub(q[1][1], q[0][1]), dsub(q[2][0], q[0][0])));
+    double sg = T->g.area2 >= 0 ? 1.0 : -1.0;
+    dual perim = dadd(dadd(ell[0], ell[1]), ell[2]);
+    D->r = ddiv(dscale(area2, sg), perim);
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3;
+        D->n[i][0] = dscale(ddiv(ey[i], ell[i]), sg);
+        D->n[i][1] = dscale(ddiv(ex[i], ell[i]), -sg);
+        D->d[i] = dscale(dadd(dmul(D->n[i][0], q[j][0]), dmul(D->n[i][1], q[j][1])), -1.0);
+    }
+    D->o = dvar(T->o, 9);
+    D->sigma = dvar(T->sigma, 10);
+    /* colour */
+    double cp[3];
+    cam_center(C, cp);
+    dual w[3], w2 = dcst(0.0);
+    for (int a = 0; a < 3; ++a) {
+        w[a] = daddc(dscale(dadd(dadd(V[0][a], V[1][a]), V[2][a]), 1.0 / 3.0), -cp[a]);
+        w2 = dadd(w2, dmul(w[a], w[a]));
+    }
+    dual wn = dsqrt(w2), dir[3];
+    for (int a = 0; a < 3; ++a) dir[a] = ddiv(w[a], wn);
+    dual Y[16];
+    int nk = (sh_deg + 1) * (sh_deg + 1);
+    sh_eval_dual(sh_deg, dir, Y);
+    const double *c = sh + (size_t)id * nk * 3;
+    for (int ch = 0; ch < 3; ++ch) {
+        dual acc = dcst(0.5);
+        for (int k = 0; k < nk; ++k) acc = dadd(acc, dscale(Y[k], c[k * 3 + ch]));
+        D->rgb_raw[ch] = acc;
+    }
+    for (int k = 0; k < nk; ++k) D->Y[k] = Y[k].v;
+}
+
+/* alpha at pixel p as a dual (same formula and arg-max rule as the value path) */
+static dual frag_alpha_dual(const tri_dual_t *D, double px, double py, const consts_t *K) {
+    dual phi = dcst(-INFINITY);
+    for (int i = 0; i < 3; ++i) {
+        dual L = dadd(dadd(dscale(D->n[i][0], px), dscale(D->n[i][1], py)), D->d[i]);
+        if (L.v > phi.v) phi = L;
+    }
+    dual ratio = ddiv(dscale(phi, -1.0), D->r);
+    dual I = dpow(ratio, D->sigma);
+    dual a = dmul(D->o, I);
+    if (a.v > K->alpha_max) a = dcst(K->alpha_max);
+    return a;
+}
+
+/* ------------------------------------------------------------------ */
+/* rendering                                                           */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int pix, id;
+    double depth, alpha, ratio;
+    int kept;       /* alpha >= ALPHA_MIN */
+    int argmax;
+} ent_t;
+
+static int ent_cmp(const void *a, const void *b) {
+    const ent_t *x = (const ent_t *)a, *y = (const ent_t *)b;
+    if (x->pix != y->pix) return x->pix < y->pix ? -1 : 1;
+    if (x->depth != y->depth) return x->depth < y->depth ? -1 : 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+typedef struct { ent_t *e; size_t n, cap; } vec_t;
+
+static void vec_push(vec_t *v, ent_t x) {
+    if (v->n == v->cap) {
+        v->cap = v->cap ? 2 * v->cap : 1024;
+        v->e = (ent_t *)realloc(v->e, v->cap * sizeof(ent_t));
+    }
+    v->e[v->n++] = x;
+}
+
+static double ulp32(double x) {
+    int e;
+    frexp(fabs(x), &e);   /* x = m 2^e, m in [0.5, 1) */
+    return ldexp(1.0, e - 24);
+}
+
+/* FP32 error band of the window ratio at p (classifier only) */
+static double ratio_band(const tri2d_t *g, int am, double px, double py) {
+    double ax = fabs(g->n[am][0] * (px - g->s[0])) / g->r;
+    double ay = fabs(g->n[am][1] * (py - g->s[1])) / g->r;
+    return EPS_LINE * (1.0 + ax + ay);
+}
+
+typedef struct {
+    int n, sh_deg, nk;
+    const double *verts, *sh, *opac, *sigma;
+    cam_t C;
+    consts_t K;
+    tri_t *tris;
+    int brute;
+    const uint8_t *pix_mask;
+    /* forward outputs (nullable) */
+    double *image, *T_final;
+    int32_t *n_kept;
+    uint8_t *flags;
+    double *err_est;
+    /* adjoint (nullable) */
+    const double *dL;
+    const int32_t *track;        /* triangle id -> dual slot, or -1 */
+    const tri_dual_t *duals;
+    double *dverts, *dsh, *dopac, *dsigma;
+} job_t;
+
+#define BAND 8
+
+static void atomic_add(double *p, double v) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+    *p += v;
+}
+
+/* composite one pixel's sorted entries [e0, e1) */
+static void shade_pixel(const job_t *J, const ent_t *e, size_t cnt, int x, int y) {
+    const consts_t *K = &J->K;
+    const int W = J->C.W, H = J->C.H;
+    const size_t pix = (size_t)y * W + x;
+    double px = x + 0.5, py = y + 0.5;
+    double T = 1.0, C[3] = {0, 0, 0};
+    int amb = 0, nk = 0;
+    double dTrel = 0.0;
+    /* kept fragments, for the suffix pass */
+    enum { MAXK = 4096 };
+    static __thread int kid[MAXK];
+    static __thread double ka[MAXK], kT[MAXK], kda[MAXK];
+    double prev_depth = NAN;
+    for (size_t i = 0; i < cnt; ++i) {
+        const ent_t *f = &e[i];
+        const tri_t *t = &J->tris[f->id];
+        if (f->kept < 0) { amb |= AMB_CULL; continue; }
+        double band = ratio_band(&t->g, f->argmax, px, py);
+        double ahi = t->o * pow(f->ratio + band, t->sigma) * (1.0 + EPS_MUFU * (1.0 + t->sigma * fabs(log2(fmax(f->ratio, 1e-300)))));
+        double rlo = f->ratio - band;
+        double alo = rlo > 0 ? t->o * pow(rlo, t->sigma) * (1.0 - EPS_MUFU * (1.0 + t->sigma * fabs(log2(fmax(f->ratio, 1e-300))))) : 0.0;
+        if (!f->kept) {
+            if (ahi >= K->alpha_min) amb |= AMB_SKIP;
+            continue;
+        }
+        if (alo < K->alpha_min) amb |= AMB_SKIP;
+        double a = f->alpha;
+        double da;
+        if (alo >= K->alpha_max) da = 0.0;
+        else da = fmax(fmin(ahi, K->alpha_max) - a, a - alo);
+        if (!isnan(prev_depth) && fabs(f->depth - prev_depth) <= 4.0 * ulp32(f->depth)) amb |= AMB_ORDER;
+        prev_depth = f->depth;
+        double test = T * (1.0 - a);
+        if (K->t_eps > 0) {
+            double rel = dTrel + da / (1.0 - a) + (nk + 1) * EPS_ACC;
+            if (fabs(test - K->t_eps) <= 2.0 * test * rel) amb |= AMB_STOP;
+        }
+        if (test < K->t_eps) break;
+        for (int c = 0; c < 3; ++c) C[c] += t->rgb[c] * a * T;
+        if (nk < MAXK) { kid[nk] = f->id; ka[nk] = a; kT[nk] = T; kda[nk] = da; }
+        T = test;
+        dTrel += da / (1.0 - a);
+        ++nk;
+    }
+    if (nk > MAXK) nk = MAXK;  /* never reached at the sizes used */
+    for (int c = 0; c < 3; ++c) C[c] += T * J->C.bg[c];
+    if (J->image)
+        for (int c = 0; c < 3; ++c) J->image[(size_t)c * W * H + pix] = C[c];
+    if (J->T_final) J->T_final[pix] = T;
+    if (J->n_kept) J->n_kept[pix] = nk;
+
+    /* suffix pass: B = colour from fragment k+1 on, plus the background term */
+    double B[3];
+    for (int c = 0; c < 3; ++c) B[c] = T * J->C.bg[c];
+    double E = 0.0;
+    const double *g = J->dL ? J->dL : NULL;
+    for (int k = nk - 1; k >= 0; --k) {
+        const tri_t *t = &J->tris[kid[k]];
+        double a = ka[k], Tk = kT[k];
+        double dCda = 0.0, gal = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double dc = t->rgb[c] * Tk - B[c] / (1.0 - a);
+            if (fabs(dc) > dCda) dCda = fabs(dc);
+            if (g) gal += g[(size_t)c * W * H + pix] * dc;
+        }
+        E += dCda * kda[k] + a * Tk * 1e-6 * (1.0 + fabs(t->rgb[0]) + fabs(t->rgb[1]) + fabs(t->rgb[2]));
+        if (g && J->track && J->track[kid[k]] >= 0) {
+            const tri_dual_t *D = &J->duals[J->track[kid[k]]];
+            dual ad = frag_alpha_dual(D, px, py, K);
+            int id = kid[k];
+            double grgb[3];
+            for (int c = 0; c < 3; ++c)
+                grgb[c] = (D->rgb_raw[c].v > 0) ? g[(size_t)c * W * H + pix] * a * Tk : 0.0;
+            for (int j = 0; j < 9; ++j) {
+                double acc = gal * ad.d[j];
+                for (int c = 0; c < 3; ++c) acc += grgb[c] * D->rgb_raw[c].d[j];
+                atomic_add(&J->dverts[(size_t)id * 9 + j], acc);
+            }
+            atomic_add(&J->dopac[id], gal * ad.d[9]);
+            atomic_add(&J->dsigma[id], gal * ad.d[10]);
+            for (int kk = 0; kk < J->nk; ++kk)
+                for (int c = 0; c < 3; ++c)
+                    if (grgb[c] != 0.0) atomic_add(&J->dsh[((size_t)id * J->nk + kk) * 3 + c], grgb[c] * D->Y[kk]);
+        }
+        for (int c = 0; c < 3; ++c) B[c] += t->rgb[c] * a * Tk;
+    }
+    E += nk * 4.0 * EPS_ACC;
+    if (E > FLAG_TOL) amb |= AMB_SENS;
+    if (J->flags) J->flags[pix] = (uint8_t)amb;
+    if (J->err_est) J->err_est[pix] = E;
+}
+
+static void render_band(const job_t *J, int y0, int y1, const int *cand, int ncand) {
+    const int W = J->C.W;
+    const consts_t *K = &J->K;
+    vec_t v = {0};
+    int want_flags = J->flags != NULL || J->err_est != NULL;
+    for (int ci = 0; ci < ncand; ++ci) {
+        int id = cand[ci];
+        const tri_t *t = &J->tris[id];
+        if (t->cull) {
+            /* a culled triangle whose cull decision is within the FP32 band: its
+             * pixels are marked, provided its projection exists (all z > 0) */
+            if (!(want_flags && t->amb_cull && t->z[0] > 0 && t->z[1] > 0 && t->z[2] > 0)) continue;
+        }
+        int xa, xb, ya, yb;
+        if (J->brute) { xa = 0; xb = W - 1; ya = y0; yb = y1 - 1; }
+        else {
+            pix_range(t->bbox[0] - 1.0, t->bbox[2] + 1.0, W, &xa, &xb);
+            pix_range(t->bbox[1] - 1.0, t->bbox[3] + 1.0, J->C.H, &ya, &yb);
+            if (ya < y0) ya = y0;
+            if (yb > y1 - 1) yb = y1 - 1;
+        }
+        for (int y = ya; y <= yb; ++y)
+            for (int x = xa; x <= xb; ++x) {
+                size_t pix = (size_t)y * W + x;
+                if (J->pix_mask && !J->pix_mask[pix]) continue;
+                double px = x + 0.5, py = y + 0.5;
+                if (t->cull) {
+                    /* ambiguous degenerate triangle: mark the pixels around it */
+                    if (px >= t->bbox[0] - 1 && px <= t->bbox[2] + 1 && py >= t->bbox[1] - 1 && py <= t->bbox[3] + 1) {
+                        ent_t e = {(int)pix, id, t->depth, 0.0, 0.0, -1, 0};
+                        vec_push(&v, e);
+                    }
+                    continue;
+                }
+                int am;
+                double ratio = tri2d_ratio(&t->g, px, py, &am);
+                double araw = ratio > 0 ? t->o * pow(ratio, t->sigma) : 0.0;
+                /* a fragment needs a positive window (ratio > 0) and alpha >= ALPHA_MIN */
+                int kept = ratio > 0 && araw >= K->alpha_min;
+                if (!kept) {
+                    if (!want_flags) continue;
+                    double band = ratio_band(&t->g, am, px, py);
+                    if (ratio + band <= 0) continue;
+                    double ahi = t->o * pow(ratio + band, t->sigma) * (1.0 + 4.0 * EPS_MUFU);
+                    if (ahi < K->alpha_min) continue;
+                }
+                ent_t e;
+                e.pix = (int)pix; e.id = id; e.depth = t->depth;
+                e.alpha = araw < K->alpha_max ? araw : K->alpha_max;
+                e.ratio = ratio; e.kept = kept; e.argmax = am;
+                vec_push(&v, e);
+                if (t->amb_cull && want_flags) {
+                    ent_t m = e; m.kept = -1;
+                    vec_push(&v, m);
+                }
+            }
+    }
+    qsort(v.e, v.n, sizeof(ent_t), ent_cmp);
+    /* every pixel of the band gets written, with or without fragments */
+    size_t i = 0;
+    for (int y = y0; y < y1; ++y)
+        for (int x = 0; x < W; ++x) {
+            int pix = y * W + x;
+            size_t j = i;
+            while (j < v.n && v.e[j].pix == pix) ++j;
+            if (!J->pix_mask || J->pix_mask[pix]) shade_pixel(J, v.e + i, j - i, x, y);
+            i = j;
+        }
+    free(v.e);
+}
+
+static void run_job(job_t *J) {
+    const int H = J->C.H;
+    int nb = (H + BAND - 1) / BAND;
+    /* candidate lists per band */
+    int *cnt = (int *)calloc((size_t)nb + 1, sizeof(int));
+    int *all = NULL;
+    if (!J->brute) {
+        for (int id = 0; id < J->n; ++id) {
+            const tri_t *t = &J->tris[id];
+            if (t->cull && !t->amb_cull) continue;
+            int ya, yb;
+            pix_range(t->bbox[1] - 1.0, t->bbox[3] + 1.0, H, &ya, &yb);
+            if (ya > yb) continue;
+            for (int b = ya / BAND; b <= yb / BAND; ++b) cnt[b + 1]++;
+        }
+        for (int b = 0; b < nb; ++b) cnt[b + 1] += cnt[b];
+        all = (int *)malloc(sizeof(int) * ((size_t)cnt[nb] + 1));
+        int *fill = (int *)calloc((size_t)nb, sizeof(int));
+        for (int id = 0; id < J->n; ++id) {
+            const tri_t *t = &J->tris[id];
+            if (t->cull && !t->amb_cull) continue;
+            int ya, yb;
+            pix_range(t->bbox[1] - 1.0, t->bbox[3] + 1.0, H, &ya, &yb);
+            if (ya > yb) continue;
+            for (int b = ya / BAND; b <= yb / BAND; ++b) all[cnt[b] + fill[b]++] = id;
+        }
+        free(fill);
+    } else {
+        all = (int *)malloc(sizeof(int) * ((size_t)J->n + 1));
+        for (int id = 0; id < J->n; ++id) all[id] = id;
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int b = 0; b < nb; ++b) {
+        int y0 = b * BAND, y1 = y0 + BAND < H ? y0 + BAND : H;
+        if (J->pix_mask) {
+            int any = 0;
+            for (size_t p = (size_t)y0 * J->C.W; p < (size_t)y1 * J->C.W && !any; ++p) any = J->pix_mask[p];
+            if (!any) continue;
+        }
+        if (J->brute) render_band(J, y0, y1, all, J->n);
+        else render_band(J, y0, y1, all + cnt[b], cnt[b + 1] - cnt[b]);
+    }
+    free(all);
+    free(cnt);
+}
+
+static tri_t *setup_all(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
+                        const double *sigma, const cam_t *C, const consts_t *K) {
+    tri_t *tris = (tri_t *)malloc(sizeof(tri_t) * (size_t)(n > 0 ? n : 1));
+    sh_init();
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int id = 0; id < n; ++id) tri_setup(id, verts, sh, sh_deg, opac, sigma, C, K, &tris[id]);
+    return tris;
+}
+
+/* ------------------------------------------------------------------ */
+/* exported API (ctypes)                                               */
+/* ------------------------------------------------------------------ */
+int orc_version(void) { return 1; }
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Forward render. image [3,H,W], T_final [H,W], n_kept [H,W]; flags / err_est nullable. */
+int orc_render(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
+               const double *sigma, const double *cam, const double *consts, int brute,
+               const uint8_t *pix_mask, double *image, double *T_final, int32_t *n_kept,
+               uint8_t *flags, double *err_est) {
+    if (n < 0 || sh_deg < 0 || sh_deg > 3) return 1;
+    job_t J;
+    memset(&J, 0, sizeof J);
+    J.n = n; J.sh_deg = sh_deg; J.nk = (sh_deg + 1) * (sh_deg + 1);
+    J.verts = verts; J.sh = sh; J.opac = opac; J.sigma = sigma;
+    J.C = load_cam(cam); J.K = load_consts(consts);
+    J.brute = brute; J.pix_mask = pix_mask;
+    J.image = image; J.T_final = T_final; J.n_kept = n_kept; J.flags = flags; J.err_est = err_est;
+    J.tris = setup_all(n, verts, sh, sh_deg, opac, sigma, &J.C, &J.K);
+    run_job(&J);
+    free(J.tris);
+    return 0;
+}
+
+/* Adjoint: given dL/dimage [3,H,W], accumulate parameter gradients of the triangles
+ * with tri_mask[id] != 0 (all when NULL) from the pixels with pix_mask != 0 (all when
+ * NULL). Outputs are overwritten: dverts [n,9], dsh [n,K,3], dopac [n], dsigma [n]. */
+int orc_render_grad(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
+                    const double *sigma, const double *cam, const double *consts,
+                    const double *dL_dimage, const uint8_t *pix_mask, const uint8_t *tri_mask,
+                    double *dverts, double *dsh, double *dopac, double *dsigma) {
+    if (n < 0 || sh_deg < 0 || sh_deg > 3) return 1;
+    job_t J;
+    memset(&J, 0, sizeof J);
+    J.n = n; J.sh_deg = sh_deg; J.nk = (sh_deg + 1) * (sh_deg + 1);
+    J.verts = verts; J.sh = sh; J.opac = opac; J.sigma = sigma;
+    J.C = load_cam(cam); J.K = load_consts(consts);
+    J.brute = 0; J.pix_mask = pix_mask;
+    J.dL = dL_dimage;
+    J.dverts = dverts; J.dsh = dsh; J.dopac = dopac; J.dsigma = dsigma;
+    memset(dverts, 0, sizeof(double) * 9 * (size_t)n);
+    memset(dsh, 0, sizeof(double) * 3 * (size_t)J.nk * n);
+    memset(dopac, 0, sizeof(double) * (size_t)n);
+    memset(dsigma, 0, sizeof(double) * (size_t)n);
+    J.tris = setup_all(n, verts, sh, sh_deg, opac, sigma, &J.C, &J.K);
+    int32_t *track = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int nt = 0;
+    for (int id = 0; id < n; ++id) {
+        int want = (!tri_mask || tri_mask[id]) && J.tris[id].cull == CULL_NONE;
+        track[id] = want ? nt++ : -1;
+    }
+    tri_dual_t *duals = (tri_dual_t *)malloc(sizeof(tri_dual_t) * (size_t)(nt > 0 ? nt : 1));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int id = 0; id < n; ++id)
+        if (track[id] >= 0) tri_dual_setup(id, verts, sh, sh_deg, &J.C, &J.tris[id], &duals[track[id]]);
+    J.track = track;
+    J.duals = duals;
+    run_job(&J);
+    free(duals);
+    free(track);
+    free(J.tris);
+    return 0;
+}
+
+/* Per-triangle quantities.
+ * f64 [n, 24]: q (6), z (3), depth, s (2), r, f, rect (4), rgb (3), dir (3)
+ * i32 [n, 12]: cull, rect_state, pix (4), tiles (4), amb (bit0 cull band, bit1 rect band), ntiles */
+int orc_tri_info(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
+                 const double *sigma, const double *cam, const double *consts,
+                 double *out_f, int32_t *out_i) {
+    if (n < 0 || sh_deg < 0 || sh_deg > 3) return 1;
+    cam_t C = load_cam(cam);
+    consts_t K = load_consts(consts);
+    tri_t *tris = setup_all(n, verts, sh, sh_deg, opac, sigma, &C, &K);
+    for (int id = 0; id < n; ++id) {
+        const tri_t *t = &tris[id];
+        double *f = out_f + 24 * (size_t)id;
+        int32_t *o = out_i + 12 * (size_t)id;
+        for (int i = 0; i < 3; ++i) { f[2 * i] = t->g.q[i][0]; f[2 * i + 1] = t->g.q[i][1]; }
+        for (int i = 0; i < 3; ++i) f[6 + i] = t->z[i];
+        f[9] = t->depth; f[10] = t->g.s[0]; f[11] = t->g.s[1]; f[12] = t->g.r; f[13] = t->f;
+        for (int i = 0; i < 4; ++i) f[14 + i] = t->rect[i];
+        for (int i = 0; i < 3; ++i) { f[18 + i] = t->rgb[i]; f[21 + i] = t->dir[i]; }
+        o[0] = t->cull; o[1] = t->rect_state;
+        for (int i = 0; i < 4; ++i) { o[2 + i] = t->pix[i]; o[6 + i] = t->tiles[i]; }
+        o[10] = (t->amb_cull ? 1 : 0) | (t->amb_rect ? 2 : 0);
+        o[11] = (t->cull == CULL_NONE && t->rect_state == RECT_OK) ? t->ntiles : 0;
+    }
+    free(tris);
+    return 0;
+}
+
+/* 2D triangle geometry. out [15]: n (6), d (3), s (2), r, ell (3) */
+int orc_tri2d(const double *q6, double *out) {
+    double q[3][2] = {{q6[0], q6[1]}, {q6[2], q6[3]}, {q6[4], q6[5]}};
+    tri2d_t T;
+    tri2d_setup(q, &T);
+    for (int i = 0; i < 3; ++i) { out[2 * i] = T.n[i][0]; out[2 * i + 1] = T.n[i][1]; out[6 + i] = T.d[i]; }
+    out[9] = T.s[0]; out[10] = T.s[1]; out[11] = T.r;
+    for (int i = 0; i < 3; ++i) out[12 + i] = T.ell[i];
+    return 0;
+}
+
+/* Window at points: ratio = phi(p)/phi(s), I = ReLU(ratio)^sigma. */
+int orc_window(const double *q6, double sigma, int npts, const double *pts, double *ratio, double *I) {
+    double q[3][2] = {{q6[0], q6[1]}, {q6[2], q6[3]}, {q6[4], q6[5]}};
+    tri2d_t T;
+    tri2d_setup(q, &T);
+    for (int i = 0; i < npts; ++i) {
+        double r = tri2d_ratio(&T, pts[2 * i], pts[2 * i + 1], NULL);
+        if (ratio) ratio[i] = r;
+        if (I) I[i] = r > 0 ? pow(r, sigma) : 0.0;
+    }
+    return 0;
+}
+
+/* Real SH basis at unit directions: out [ndir, (deg+1)^2]. */
+int orc_sh_eval(int deg, int ndir, const double *dirs, double *out) {
+    if (deg < 0 || deg > 3) return 1;
+    int nk = (deg + 1) * (deg + 1);
+    for (int i = 0; i < ndir; ++i) sh_eval_val(deg, dirs + 3 * i, out + (size_t)nk * i);
+    return 0;
+}
