@@ -1,0 +1,361 @@
+"""Benchmark of the differentiable triangle-splat rasterizer on one GB300.
+
+Default workload (one step = the whole hot path once): 500,000 triangles clustered on
+200 planar patches, SH degree 3, one camera at 1297x840, fp32:
+    preprocess -> depth sort -> pair emission -> tile sort -> ranges -> render forward
+    -> L1 loss against a seeded target -> render backward -> preprocess backward.
+The metric is forward+backward iterations per second (device time, CUDA events on the
+launching stream, L2 flushed between timed steps); the JSON line also carries the
+forward frames per second, the per-stage breakdown, the roofline of the dominant
+kernel, an end-to-end number through host buffers, and the FP64 CPU oracle timed on a
+bounded sample of the same workload.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun (N > 1) every rank renders its own replica (no collective on the data
+path); the value is the sum over ranks of the steps divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd FPS & fwd+bwd it/s at 1297×840, 500k–3M tris; serving p99 ms vs unbatched"
+WORKLOAD = "500k tris on 200 planar patches, SH3, 1297x840, 1 view, fwd+bwd with L1 loss"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP32 lanes per SM per clock on the FMA pipe of sm_10x
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_workload():
+    from paper_2505_19175_gb300 import synth
+    scene, _, _ = synth.scene_patches()
+    cam = synth.camera_patches()
+    target = synth.target_image(cam.H, cam.W)
+    return scene, cam, target
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle: baseline and reference arm
+# ---------------------------------------------------------------------------------------
+def oracle_sample(scene, cam, target, rows: int):
+    """One oracle fwd+bwd over a band of `rows` pixel rows in the image centre;
+    returns (seconds, fraction of the frame, threads)."""
+    import oracle as O
+    mask = np.zeros((cam.H, cam.W), np.uint8)
+    y0 = cam.H // 2 - rows // 2
+    mask[y0:y0 + rows] = 1
+    t0 = time.perf_counter()
+    ref = O.render(scene, cam, pix_mask=mask)
+    g = np.sign(ref["image"] - target) / ref["image"].size * mask[None]
+    O.render_grad(scene, cam, g, pix_mask=mask)
+    dt = time.perf_counter() - t0
+    return dt, rows / cam.H, O.max_threads()
+
+
+def cpu_baseline(scene, cam, target, budget_s: float = 20.0):
+    rows = 16
+    dt, frac, threads = oracle_sample(scene, cam, target, rows)
+    if dt < budget_s / 4:
+        rows = int(min(cam.H, max(rows, rows * (budget_s / 2) / max(dt, 1e-3))))
+        dt, frac, threads = oracle_sample(scene, cam, target, rows)
+    its = frac / dt
+    return {"value": its, "unit": "it/s", "cores": threads, "kind": "oracle",
+            "sample": f"FP64 oracle fwd+bwd over {rows} of {cam.H} pixel rows (centre band) of the same "
+                      f"workload, {dt:.2f} s, extrapolated to the full frame"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    scene, cam, target = make_workload()
+    rows = 8
+    for _ in range(max(args.warmup, 0) and 1):
+        oracle_sample(scene, cam, target, rows)
+    times, fracs, threads = [], [], 1
+    for _ in range(args.steps):
+        dt, frac, threads = oracle_sample(scene, cam, target, rows)
+        times.append(dt)
+        fracs.append(frac)
+    its = sum(fracs) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": its, "unit": "it/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / its, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_rows_per_step": rows},
+            "cpu_baseline": {"value": its, "unit": "it/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{rows} of {cam.H} pixel rows per step, fwd+bwd, extrapolated"},
+            "e2e": {"value": its, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+STAGES = ("preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd")
+KERNELS_PER_STEP_BASE = 1 + 4 + 1 + 1 + 1 + 1 + 1 + 1  # + tile passes
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2505_19175_gb300 import native as N
+    from paper_2505_19175_gb300.renderer import Context, SceneTensors, new_images
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    scene, cam, target = make_workload()
+    st = SceneTensors.from_numpy(scene)
+    tgt = torch.as_tensor(target).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = Context(dev)
+    ctx.preprocess(st, [cam])
+    n_pairs = ctx.bin_sort(sync=True)
+    ctx.reserve(int(n_pairs * 1.25) + 1024)
+    imgs = new_images([cam])
+    grad = torch.empty_like(imgs[0])
+    loss = torch.empty((), device="cuda")
+    dv, dsh = torch.empty_like(st.verts), torch.empty_like(st.sh)
+    do, ds = torch.empty_like(st.opacity), torch.empty_like(st.sigma)
+    L = N.lib()
+    sh = int(stream.cuda_stream)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record()
+        ctx.preprocess(st, [cam])
+        if ev:
+            ev[1].record()
+        ctx.bin_sort(sync=False)
+        if ev:
+            ev[2].record()
+        ctx.render_fwd(imgs)
+        if ev:
+            ev[3].record()
+        N.check(L.tri_loss_l1(imgs[0].data_ptr(), tgt.data_ptr(), imgs[0].numel(), grad.data_ptr(),
+                              loss.data_ptr(), sh))
+        if ev:
+            ev[4].record()
+        ctx.render_bwd([grad])
+        if ev:
+            ev[5].record()
+        ctx.preprocess_bwd(dv, dsh, do, ds)
+        if ev:
+            ev[6].record()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MB > 129 MB L2
+    for _ in range(args.warmup):
+        step()
+    info = ctx.check()
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            step(evs[k])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    info = ctx.check()
+    stage_ms = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(6)] for k in range(args.steps)])
+    step_ms = stage_ms.sum(1)
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # forward-only frames per second (preprocess + sort + render), same protocol
+    fwd_ms = float((stage_ms[:, 0] + stage_ms[:, 1] + stage_ms[:, 2]).sum())
+    fps = args.steps / (fwd_ms / 1000.0)
+
+    # end to end through the C ABI with host buffers: H2D of the scene and target from
+    # pinned memory, the step, D2H of the loss and the parameter gradients
+    host = {k: v.cpu().pin_memory() for k, v in (("verts", st.verts), ("sh", st.sh), ("opacity", st.opacity),
+                                                  ("sigma", st.sigma), ("target", tgt))}
+    hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in
+            (("dv", dv), ("dsh", dsh), ("do", do), ("ds", ds), ("loss", loss))}
+    h2d = sum(v.numel() * 4 for v in host.values())
+    d2h = sum(v.numel() * 4 for v in hout.values())
+
+    def e2e_step():
+        st.verts.copy_(host["verts"], non_blocking=True)
+        st.sh.copy_(host["sh"], non_blocking=True)
+        st.opacity.copy_(host["opacity"], non_blocking=True)
+        st.sigma.copy_(host["sigma"], non_blocking=True)
+        tgt.copy_(host["target"], non_blocking=True)
+        step()
+        hout["dv"].copy_(dv, non_blocking=True)
+        hout["dsh"].copy_(dsh, non_blocking=True)
+        hout["do"].copy_(do, non_blocking=True)
+        hout["ds"].copy_(ds, non_blocking=True)
+        hout["loss"].copy_(loss, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "it/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    peaks, peak_src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    med = np.median(stage_ms, axis=0)
+    breakdown = {s: round(float(m), 4) for s, m in zip(STAGES, med)}
+    dom = STAGES[int(np.argmax(med))]
+    # roofline of the dominant stage
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12          # T lane-ops/s
+    roof = None
+    F_eval, F_kept = int(info.frag_evaluated), int(info.frag_composited)
+    if dom in ("render_fwd", "render_bwd"):
+        # FP32-pipe operations per evaluated (pixel, entry) pair: 2 FADD + 6 FFMA + 2 FMNMX
+        # + compare; per composited fragment 10 more (alpha, clamp, T, 3 colour FMAs ...).
+        ops = F_eval * 11 + F_kept * 10
+        if dom == "render_bwd":
+            ops = F_eval * 11 + F_kept * 45   # + ~35 FP32 ops of the adjoint per fragment
+        ach = ops / (med[STAGES.index(dom)] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 3), "peak": round(fp32_peak, 3),
+                "unit": "T FP32-lane-ops/s", "frac": round(ach / fp32_peak, 4), "traffic": None,
+                "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} lanes x {clock_mhz:.0f} MHz ({peak_src} max clock)"}
+    else:
+        hbm = float(peaks["hbm_gbs"])
+        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None}
+    tile_passes = 2
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "it/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "triangles": int(st.n), "width": cam.W, "height": cam.H, "views": 1,
+                   "sh_degree": 3, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "fwd_fps": round(fps, 2),
+        "stage_ms_median": breakdown,
+        "workload_stats": {"pairs": int(info.n_pairs), "visible": int(info.n_visible),
+                           "frag_evaluated": F_eval, "frag_composited": F_kept},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": (KERNELS_PER_STEP_BASE + tile_passes) * args.steps,
+        "clocks": clocks,
+        "wall_s_timed": round(t_wall, 4),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(scene, cam, target, args.cpu_budget)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

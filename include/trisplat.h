@@ -1,0 +1,251 @@
+/*
+ * trisplat.h — C ABI of the GB300 (sm_103a) differentiable triangle-splat rasterizer.
+ *
+ * The renderer follows "Triangle Splatting for Real-Time Radiance Field Rendering"
+ * (arXiv 2505.19175). A scene is a soup of 3D triangles, each with three vertices
+ * v_i, a spherical-harmonic colour c (degree <= 3, 48 floats at degree 3), a
+ * smoothness sigma > 0 and an opacity o (Sec. 3.1 "Differentiable rasterization";
+ * Sec. 4 counts 59 parameters per triangle). A pinhole camera K, R, t maps it to an
+ * image; image gradients map back to parameter gradients (Sec. 3.3 "Optimization").
+ *
+ * Pipeline (one call each, all stream-ordered, none synchronises unless stated):
+ *   tri_preprocess      project, build the signed-distance window, colour, depth and
+ *                       tight tile rectangle of every (view, triangle) item
+ *                       (Sec. 3.1, Eq. indicator1; Supp. "Tile assignment");
+ *   tri_bin_sort        depth sort of visible items by centroid depth, duplication of
+ *                       each item into the tiles of its rectangle, stable radix sort
+ *                       by tile, per-tile ranges (Supp. "Tile assignment", "Depth
+ *                       sorting");
+ *   tri_render_fwd      per-pixel front-to-back compositing with alpha = o I (Sec. 3.1:
+ *                       the rendering equation of prior splatting work);
+ *   tri_render_bwd      back-to-front recomputation and per-item gradients;
+ *   tri_preprocess_bwd  chain rule to vertices, SH, opacity and sigma.
+ *
+ * Conventions.
+ *   Alignment: verts and sh must start on a 16-byte boundary (they are read with
+ *     16-byte vector loads); any fresh cudaMalloc / torch allocation satisfies this.
+ *   Device pointers: every float / int pointer below, unless marked host, is device
+ *     memory of the context's device, fp32 / int32, contiguous, caller-owned. The
+ *     library never frees caller memory.
+ *   Workspace: each context owns its device workspace (cudaMalloc'd on demand, grown
+ *     as needed, freed by tri_ctx_destroy). tri_workspace_query reports its size.
+ *   Layouts: verts [n][3][3] (vertex-major xyz), sh [n][(deg+1)^2][3] (coefficient
+ *     k = l*l + l + m, m = -l..l; channel innermost), opacity [n], sigma [n]; images
+ *     [3][H][W] planar per view; per-pixel buffers [H][W].
+ *   Camera: R row-major world->camera, t, OpenCV axes (+x right, +y down, +z
+ *     forward); pixel (x, y) is sampled at (x + 0.5, y + 0.5).
+ *   Errors: every call returns a tri_status and never aborts; tri_last_error gives a
+ *     message. Device-side checks (bounded spins, capacity) set a status word that
+ *     tri_ctx_check reads back (that call synchronises the stream).
+ *   Threads: a context is not thread-safe; use one per host thread.
+ *   Streams: cudaStream_t values are passed as void* (0 = legacy default stream).
+ */
+#ifndef TRISPLAT_H
+#define TRISPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TRI_OK = 0,
+    TRI_ERR_INVALID_ARG = 1,   /* null pointer, n < 0, sh_degree not in 0..3, W/H <= 0, ... */
+    TRI_ERR_OOM = 2,           /* cudaMalloc failed */
+    TRI_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in tri_last_error) */
+    TRI_ERR_CAPACITY = 4,      /* pair list or memory budget exceeded */
+    TRI_ERR_TIMEOUT = 5,       /* a bounded device wait or a request deadline ran out */
+    TRI_ERR_DEVICE_CHECK = 6,  /* a device-side check set the status word */
+    TRI_ERR_STATE = 7          /* calls out of order (e.g. render before bin_sort) */
+} tri_status;
+
+/* Pinhole camera of one view (Sec. 3.1: q = K(R v + t) with the perspective divide). */
+typedef struct {
+    float R[9];        /* world -> camera rotation, row-major */
+    float t[3];        /* world -> camera translation */
+    float fx, fy;      /* focal lengths in pixels */
+    float cx, cy;      /* principal point in pixels */
+    int32_t width, height;
+    float bg[3];       /* background colour added with the final transmittance */
+} tri_camera;
+
+/* Triangle soup (Sec. 3.1; 59 floats per triangle at SH degree 3, Sec. 4).
+ * opacity is the activated o in (0, 1], sigma the activated sigma > 0. */
+typedef struct {
+    const float *verts;    /* [n][3][3] */
+    const float *sh;       /* [n][(sh_degree+1)^2][3] */
+    const float *opacity;  /* [n] */
+    const float *sigma;    /* [n] */
+    int64_t n;
+    int32_t sh_degree;     /* 0..3 */
+} tri_scene;
+
+typedef struct tri_ctx tri_ctx;
+
+/* Counters of the last pipeline run (tri_ctx_check fills them). */
+typedef struct {
+    int64_t n_items;       /* views x triangles */
+    int64_t n_visible;     /* items with a non-empty tile rectangle */
+    int64_t n_pairs;       /* (tile, item) pairs, may exceed pair_capacity */
+    int64_t pair_capacity;
+    int32_t overflow;      /* 1 when n_pairs > pair_capacity (pairs were dropped) */
+    int32_t device_error;  /* bit 0: a bounded spin gave up; bit 1: index check failed */
+    int32_t n_views, total_tiles;
+    int64_t frag_evaluated;   /* last forward: (pixel, list entry) window evaluations */
+    int64_t frag_composited;  /* last forward: fragments composited */
+} tri_ctx_info;
+
+/* Create a context on CUDA device `device`. Allocates nothing until first use.
+ * Returns TRI_ERR_INVALID_ARG for a null `out`, TRI_ERR_CUDA for a bad device. */
+tri_status tri_ctx_create(tri_ctx **out, int device);
+
+/* Free the context and all its device workspace. Null is ignored. */
+void tri_ctx_destroy(tri_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none). Never null. */
+const char *tri_last_error(const tri_ctx *ctx);
+
+/* Device bytes a context holds to render `nviews` views of an n-triangle scene with
+ * room for `pair_capacity` (tile, item) pairs (<= 0: the library's default estimate).
+ * Pure host arithmetic; `cams` is a host array of nviews cameras. */
+tri_status tri_workspace_query(const tri_scene *scene, const tri_camera *cams, int nviews,
+                               int64_t pair_capacity, size_t *bytes);
+
+/* Reserve room for at least `pair_capacity` pairs now (optional; bin_sort grows it
+ * when it synchronises). Allocates with cudaMalloc. */
+tri_status tri_reserve(tri_ctx *ctx, int64_t pair_capacity);
+
+/* Step 1 (Sec. 3.1; Supp. "Tile assignment"): for every (view, triangle) item, project
+ * the vertices (vertex 0 in double-float precision, the others relative to it), cull
+ * items with a vertex nearer than z = 0.2 or an inradius below 1e-4 px, build the three
+ * normalised edge lines (m_i = 1 at the incenter, 0 on edge i), the SH colour for the
+ * direction camera -> centroid, the centroid depth and the tile rectangle of the
+ * triangle shrunk about its incenter by f = 1 - (1/255 / o)^(1/sigma); and compact the
+ * visible items in index order. `scene` device pointers must stay valid until
+ * tri_preprocess_bwd. `cams` is a host array of `nviews` cameras (views may differ in
+ * resolution). */
+tri_status tri_preprocess(tri_ctx *ctx, const tri_scene *scene, const tri_camera *cams,
+                          int nviews, void *stream);
+
+/* Step 2 (Supp. "Depth sorting", "Tile assignment"): stable LSD radix sort of the
+ * visible items by 32-bit centroid-depth key, duplication of each item into the tiles
+ * of its rectangle (in depth order), stable LSD radix sort of the pairs by tile id, and
+ * per-tile [start, end) ranges. The result equals a stable sort of the 64-bit keys
+ * (tile << 32 | depth bits) emitted in item order.
+ * If `num_pairs_out` is non-null the call synchronises, returns the pair count there,
+ * and re-runs the duplication with a larger pair buffer when it overflowed. If null,
+ * nothing synchronises; an overflow drops pairs, sets the status word, and
+ * tri_ctx_check reports TRI_ERR_CAPACITY. */
+tri_status tri_bin_sort(tri_ctx *ctx, int64_t *num_pairs_out, void *stream);
+
+/* Step 3 (Sec. 3.1): per pixel, in sorted order: ratio = min_i m_i(p); skip if ratio <= 0;
+ * I = ratio^sigma; alpha = o I; skip if alpha < 1/255; alpha = min(alpha, 0.99); stop
+ * before a fragment that would take the transmittance T below 1e-4; C += rgb alpha T;
+ * T *= 1 - alpha. Output C + T bg.
+ * `images` is a host array of nviews device pointers, each [3][H_v][W_v].
+ * `T_final` / `n_contrib` (host arrays of nviews device pointers to [H_v][W_v], or null
+ * arrays) receive the final transmittance and the 1-based index, within the tile's
+ * list, of the last composited entry; the context keeps its own copies for the
+ * backward pass either way. */
+tri_status tri_render_fwd(tri_ctx *ctx, float *const *images, float *const *T_final,
+                          int32_t *const *n_contrib, void *stream);
+
+/* Step 4 (gradient of step 3): per pixel, back to front from its last composited
+ * entry, recompute alpha and T_k = T_{k+1} / (1 - alpha_k), and accumulate per item
+ * the gradients of the incenter, the six edge-line slopes, o, sigma and rgb (warp
+ * reduction, then one vector atomic per item and tile). `dL_dimages` is a host array of
+ * nviews device pointers [3][H_v][W_v]. Requires tri_render_fwd on the same context. */
+tri_status tri_render_bwd(tri_ctx *ctx, const float *const *dL_dimages, void *stream);
+
+/* Step 5 (chain rule of step 1): gradients of the loss with respect to the scene,
+ * summed over views: dverts [n][3][3], dsh [n][(deg+1)^2][3], dopacity [n],
+ * dsigma [n]. With accumulate = 0 the outputs are overwritten, else added to. Any
+ * output pointer may be null to skip it. */
+tri_status tri_preprocess_bwd(tri_ctx *ctx, float *dverts, float *dsh, float *dopacity,
+                              float *dsigma, int accumulate, void *stream);
+
+/* Synchronise `stream`, read the context's counters and device status word.
+ * Returns TRI_ERR_CAPACITY on a pair overflow, TRI_ERR_DEVICE_CHECK / TRI_ERR_TIMEOUT on
+ * a device-side check, else TRI_OK. `info` may be null. */
+tri_status tri_ctx_check(tri_ctx *ctx, tri_ctx_info *info, void *stream);
+
+/* Internal buffers, for tests and diagnostics: copies buffer `which` to host memory
+ * `dst` (at most `max_bytes`), synchronously; `*bytes` receives the byte count used.
+ *   0: sorted pair tile keys (uint32 [n_pairs])   1: sorted pair item ids (uint32)
+ *   2: tile ranges (uint32 [total_tiles][2])       3: item depth keys (uint32 [n_items])
+ *   4: item tile rectangles (uint16 [n_items][4])  5: item tile counts (uint32 [n_items])
+ *   6: depth-sorted visible item ids (uint32 [n_visible])
+ *   7: per-item render records (float [n_items][16])
+ *   8: per-item 2D gradients (float [n_items][16]) */
+tri_status tri_debug_copy(tri_ctx *ctx, int which, void *dst, size_t max_bytes, size_t *bytes);
+
+/* L1 photometric loss helper (Sec. 3.3 lists L1 among the loss terms): loss = mean
+ * |image - target| over n values, written to the device scalar `loss` (may be null),
+ * and dL/dimage = sign(image - target) / n into `dL_dimage`. */
+tri_status tri_loss_l1(const float *image, const float *target, int64_t n, float *dL_dimage,
+                       float *loss, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * Serving: resident scenes, admission by device memory, continuous batching of camera
+ * requests of mixed resolutions into batched launches (one batched preprocess + sort
+ * and one persistent render over all (request, tile) work items per batch), completion
+ * by CUDA event, p50/p99 latency.
+ * --------------------------------------------------------------------------------- */
+typedef struct tri_serve tri_serve;
+
+typedef struct {
+    size_t mem_budget_bytes;   /* scenes + batch workspaces; 0 = 80 % of free memory */
+    int32_t max_batch;         /* views per batch (>= 1) */
+    int32_t max_width, max_height;
+    int32_t slots;             /* batches in flight (>= 1); each has its own stream */
+    int32_t timeout_ms;        /* per-request deadline (0 = none) */
+    int32_t use_graphs;        /* capture each slot's launch sequence in a CUDA graph */
+    int32_t batch_window_us;   /* wait this long for more requests before launching */
+} tri_serve_opts;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, timed_out, batches;
+    double p50_ms, p99_ms, max_ms, mean_ms;
+    double fps;                /* completed frames per second of wall time */
+    double mean_batch;         /* views per batch */
+    size_t bytes_resident;     /* scene bytes held */
+    size_t bytes_workspace;    /* batch workspaces held */
+} tri_serve_stats_t;
+
+/* Create a server on `device`. Starts one dispatcher thread. */
+tri_status tri_serve_create(tri_serve **out, const tri_serve_opts *opts, int device);
+
+/* Copy a scene into server-owned device memory (the scene's pointers may be host or
+ * device memory). Returns TRI_ERR_CAPACITY when it does not fit the budget. */
+tri_status tri_serve_add_scene(tri_serve *srv, const tri_scene *scene, int32_t *scene_id);
+
+/* Drop a scene once no queued or running request uses it. */
+tri_status tri_serve_remove_scene(tri_serve *srv, int32_t scene_id);
+
+/* Queue a request: render `cam` of `scene_id` into device buffer `out_image`
+ * [3][H][W] (caller-owned, must stay valid until the ticket completes). Never blocks
+ * on the GPU. Returns TRI_ERR_CAPACITY when the resolution exceeds max_width/height. */
+tri_status tri_serve_submit(tri_serve *srv, int32_t scene_id, const tri_camera *cam,
+                            float *out_image, uint64_t *ticket);
+
+/* Finished tickets since the last poll (up to max); the status of each is in
+ * `status` (may be null): TRI_OK or TRI_ERR_TIMEOUT. */
+tri_status tri_serve_poll(tri_serve *srv, uint64_t *done, int32_t *status, int32_t max,
+                          int32_t *ndone);
+
+/* Block the host until `ticket` completes or `timeout_ms` passes (TRI_ERR_TIMEOUT). */
+tri_status tri_serve_wait(tri_serve *srv, uint64_t ticket, int32_t timeout_ms);
+
+/* Latency percentiles and counters over completed requests. */
+tri_status tri_serve_stats(tri_serve *srv, tri_serve_stats_t *stats);
+
+/* Stop the dispatcher after the queued work drains, free everything. */
+void tri_serve_destroy(tri_serve *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRISPLAT_H */

@@ -36,7 +36,7 @@
  * For comparisons against an FP32 implementation it also classifies each pixel whose
  * value FP32 arithmetic cannot resolve to the image tolerance: a discontinuous
  * decision (alpha vs ALPHA_MIN, the T_EPS stop, depth order, culling) that lies within
- * an FP32 error band, or a first-order error estimate above a quarter of 1e-4.
+ * an FP32 error band, or a first-order error estimate above half of 1e-4.
  */
 #include <math.h>
 #include <stdint.h>
@@ -79,11 +79,11 @@ static cam_t load_cam(const double *c) {
 }
 
 /* FP32 error model used only by the pixel classifier (not by the image). */
-#define EPS_LINE 9.5367431640625e-07   /* 2^-20: FP32 line-evaluation error per unit term */
+#define EPS_LINE 2.384185791015625e-07 /* 2^-22: FP32 line-evaluation error per unit term */
 #define EPS_MUFU 9.5367431640625e-07   /* 2^-20: relative error of FP32 lg2/ex2 */
 #define EPS_ACC  1.1920928955078125e-07 /* 2^-23: one FP32 rounding */
 #define RECT_BAND 1.0e-3               /* px: FP32 error band of a rectangle bound */
-#define FLAG_TOL 2.5e-5                /* flag a pixel whose error estimate exceeds this */
+#define FLAG_TOL 5.0e-5                /* flag a pixel whose error estimate exceeds this */
 
 enum { AMB_SKIP = 1, AMB_STOP = 2, AMB_ORDER = 4, AMB_SENS = 8, AMB_CULL = 16 };
 

@@ -1,0 +1,576 @@
+// C ABI of the triangle-splat renderer: contexts, workspace, pipeline sequencing.
+// Declarations and contracts: include/trisplat.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "trisplat.h"
+
+using namespace ts;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct tri_ctx {
+    int device = 0;
+    int sms = 0;
+    std::string err;
+    tri_scene scene{};
+    int nviews = 0;
+    std::vector<ViewDev> views;
+    int64_t n_items = 0;
+    int total_tiles = 0;
+    int64_t total_pix = 0;
+    int tile_passes = 1;
+    int64_t pair_cap = 0;
+    int stage = 0;  // 1 preprocessed, 2 sorted, 3 rendered, 4 backward rendered
+    int pair_final = 0;
+    DevBuf views_d, outs_fwd, outs_bwd, ctl, recs, ntiles, rects, dkeys, ck[2], cv[2], pk[2], pv[2], ranges,
+        tile_max, Tfin, ncontrib, grad2d, st_pre, st_emit, st_depth, st_pairs;
+    std::vector<DevBuf *> all() {
+        return {&views_d, &outs_fwd, &outs_bwd, &ctl, &recs, &ntiles, &rects, &dkeys, &ck[0], &ck[1], &cv[0],
+                &cv[1], &pk[0], &pk[1], &pv[0], &pv[1], &ranges, &tile_max, &Tfin, &ncontrib, &grad2d,
+                &st_pre, &st_emit, &st_depth, &st_pairs};
+    }
+};
+
+namespace {
+
+constexpr int64_t MAX_PAIRS = (int64_t)LB_MASK;  // look-back words carry 30-bit counts
+
+tri_status fail(tri_ctx *c, tri_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+tri_status cuda_fail(tri_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? TRI_ERR_OOM : TRI_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+// Grow `b` to at least `bytes` (never shrinks). Synchronises the device before
+// freeing the old allocation, since queued work may still use it.
+tri_status ensure(tri_ctx *c, DevBuf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return TRI_OK;
+    if (b.p) {
+        CK(cudaDeviceSynchronize());
+        CK(cudaFree(b.p));
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    want = (want + 255) & ~(size_t)255;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return cuda_fail(c, e, "cudaMalloc");
+    }
+    b.bytes = want;
+    return TRI_OK;
+}
+
+#define ENSURE(buf, n)                          \
+    do {                                        \
+        tri_status s_ = ensure(c, (buf), (n));  \
+        if (s_ != TRI_OK) return s_;            \
+    } while (0)
+
+template <class T>
+T *P(DevBuf &b) {
+    return reinterpret_cast<T *>(b.p);
+}
+
+Ctl *ctl_of(tri_ctx *c) { return P<Ctl>(c->ctl); }
+
+tri_status set_device(tri_ctx *c) {
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != c->device) CK(cudaSetDevice(c->device));
+    return TRI_OK;
+}
+
+int tile_digits(int total_tiles) {
+    int bits = 0;
+    while (bits < 31 && (1ll << bits) < (int64_t)total_tiles) ++bits;
+    int d = (bits + 7) / 8;
+    return d < 1 ? 1 : d;
+}
+
+int64_t default_pair_cap(int64_t n_items) {
+    int64_t cap = 4 * n_items;
+    if (cap < (1 << 20)) cap = 1 << 20;
+    if (cap > MAX_PAIRS) cap = MAX_PAIRS;
+    return cap;
+}
+
+tri_status validate_scene(tri_ctx *c, const tri_scene *s) {
+    if (!s) return fail(c, TRI_ERR_INVALID_ARG, "scene is null");
+    if (s->n < 0) return fail(c, TRI_ERR_INVALID_ARG, "scene n < 0");
+    if (s->sh_degree < 0 || s->sh_degree > 3) return fail(c, TRI_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (s->n > 0 && (!s->verts || !s->sh || !s->opacity || !s->sigma))
+        return fail(c, TRI_ERR_INVALID_ARG, "scene pointer is null");
+    // vertices and SH are staged with 16-byte vector loads
+    if (((uintptr_t)s->verts & 15) || ((uintptr_t)s->sh & 15) || ((uintptr_t)s->opacity & 3) ||
+        ((uintptr_t)s->sigma & 3))
+        return fail(c, TRI_ERR_INVALID_ARG, "verts and sh must be 16-byte aligned");
+    return TRI_OK;
+}
+
+tri_status build_views(tri_ctx *c, const tri_camera *cams, int nviews, std::vector<ViewDev> &out, int &tiles,
+                       int64_t &pix) {
+    if (!cams || nviews <= 0 || nviews > MAX_VIEWS)
+        return fail(c, TRI_ERR_INVALID_ARG, "need 1.." + std::to_string(MAX_VIEWS) + " cameras");
+    out.resize(nviews);
+    int64_t tb = 0, pb = 0;
+    for (int v = 0; v < nviews; ++v) {
+        const tri_camera &k = cams[v];
+        if (k.width <= 0 || k.height <= 0 || k.width > 65535 * TILE || k.height > 65535 * TILE)
+            return fail(c, TRI_ERR_INVALID_ARG, "camera width/height out of range");
+        ViewDev &d = out[v];
+        memcpy(d.R, k.R, sizeof d.R);
+        memcpy(d.t, k.t, sizeof d.t);
+        d.fx = k.fx; d.fy = k.fy; d.cx = k.cx; d.cy = k.cy;
+        memcpy(d.bg, k.bg, sizeof d.bg);
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int i = 0; i < 3; ++i) acc -= (double)k.R[i * 3 + j] * (double)k.t[i];
+            d.campos[j] = (float)acc;
+        }
+        d.W = k.width; d.H = k.height;
+        d.tiles_x = (k.width + TILE - 1) / TILE;
+        d.tiles_y = (k.height + TILE - 1) / TILE;
+        d.tile_base = (int)tb;
+        d.pix_base = (int)pb;
+        tb += (int64_t)d.tiles_x * d.tiles_y;
+        pb += (int64_t)k.width * k.height;
+        if (tb > (1ll << 30) || pb > (1ll << 31) - 1) return fail(c, TRI_ERR_INVALID_ARG, "views too large");
+    }
+    tiles = (int)tb;
+    pix = pb;
+    return TRI_OK;
+}
+
+size_t sort_status_words(int64_t cap) { return (size_t)((cap + SORT_TILE - 1) / SORT_TILE) * 256; }
+
+tri_status launch_check(tri_ctx *c, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    return TRI_OK;
+}
+
+tri_status emit_pairs(tri_ctx *c, cudaStream_t st) {
+    Ctl *ctl = ctl_of(c);
+    const int64_t M = c->n_items;
+    CK(cudaMemsetAsync(P<char>(c->st_emit), 0, sizeof(uint32_t) * ((M + 255) / 256 + 1), st));
+    CK(cudaMemsetAsync(P<char>(c->ranges), 0, sizeof(uint2) * (size_t)c->total_tiles, st));
+    EmitArgs e;
+    e.sorted_items = P<uint32_t>(c->cv[0]);
+    e.ntiles = P<uint32_t>(c->ntiles);
+    e.rects = P<ushort4>(c->rects);
+    e.views = P<ViewDev>(c->views_d);
+    e.nviews = c->nviews;
+    e.n = c->scene.n;
+    e.pkeys = P<uint32_t>(c->pk[0]);
+    e.pvals = P<uint32_t>(c->pv[0]);
+    e.cap = (uint32_t)c->pair_cap;
+    e.tile_passes = c->tile_passes;
+    e.lb_status = P<uint32_t>(c->st_emit);
+    e.ctl = ctl;
+    launch_emit(e, M, st);
+    return launch_check(c, "emit_kernel");
+}
+
+}  // namespace
+
+extern "C" {
+
+tri_status tri_ctx_create(tri_ctx **out, int device) {
+    if (!out) return TRI_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return TRI_ERR_CUDA;
+    }
+    tri_ctx *c = new tri_ctx();
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return TRI_ERR_CUDA;
+    }
+    *out = c;
+    return TRI_OK;
+}
+
+void tri_ctx_destroy(tri_ctx *c) {
+    if (!c) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != c->device) cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (DevBuf *b : c->all())
+        if (b->p) cudaFree(b->p);
+    if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
+    delete c;
+}
+
+const char *tri_last_error(const tri_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+tri_status tri_workspace_query(const tri_scene *scene, const tri_camera *cams, int nviews, int64_t pair_capacity,
+                               size_t *bytes) {
+    if (!bytes) return TRI_ERR_INVALID_ARG;
+    tri_status s = validate_scene(nullptr, scene);
+    if (s != TRI_OK) return s;
+    std::vector<ViewDev> v;
+    int tiles = 0;
+    int64_t pix = 0;
+    s = build_views(nullptr, cams, nviews, v, tiles, pix);
+    if (s != TRI_OK) return s;
+    const int64_t M = scene->n * nviews;
+    const int64_t cap = pair_capacity > 0 ? pair_capacity : default_pair_cap(M);
+    size_t b = 0;
+    b += (size_t)M * (sizeof(Rec) + 4 + 8 + 4 + 16 + GRAD_FIELDS * 4);  // records, counts, rects, keys, 2x2 lists, grads
+    b += (size_t)cap * 16;                                            // 2 x (key, value) pair buffers
+    b += (size_t)tiles * (8 + 4) + (size_t)pix * 8;
+    b += sizeof(uint32_t) * (sort_status_words(M) * 4 + sort_status_words(cap) * 3 + (M + 255) / 256 * 2);
+    b += sizeof(Ctl) + nviews * (sizeof(ViewDev) + 2 * sizeof(ViewOut));
+    *bytes = b;
+    return TRI_OK;
+}
+
+tri_status tri_reserve(tri_ctx *c, int64_t pair_capacity) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    if (pair_capacity <= 0 || pair_capacity > MAX_PAIRS)
+        return fail(c, TRI_ERR_INVALID_ARG, "pair_capacity out of range");
+    tri_status s = set_device(c);
+    if (s != TRI_OK) return s;
+    if (pair_capacity > c->pair_cap) c->pair_cap = pair_capacity;
+    for (int k = 0; k < 2; ++k) {
+        ENSURE(c->pk[k], sizeof(uint32_t) * (size_t)c->pair_cap);
+        ENSURE(c->pv[k], sizeof(uint32_t) * (size_t)c->pair_cap);
+    }
+    return TRI_OK;
+}
+
+tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *cams, int nviews, void *stream) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    tri_status s = validate_scene(c, scene);
+    if (s != TRI_OK) return s;
+    if ((s = set_device(c)) != TRI_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<ViewDev> views;
+    int tiles = 0;
+    int64_t pix = 0;
+    if ((s = build_views(c, cams, nviews, views, tiles, pix)) != TRI_OK) return s;
+    const int64_t M = scene->n * (int64_t)nviews;
+    if (M > (int64_t)LB_MASK) return fail(c, TRI_ERR_INVALID_ARG, "too many (view, triangle) items");
+    c->scene = *scene;
+    c->nviews = nviews;
+    c->views = views;
+    c->n_items = M;
+    c->total_tiles = tiles;
+    c->total_pix = pix;
+    c->tile_passes = tile_digits(tiles);
+    c->stage = 0;
+    ENSURE(c->ctl, sizeof(Ctl));
+    ENSURE(c->views_d, sizeof(ViewDev) * nviews);
+    ENSURE(c->outs_fwd, sizeof(ViewOut) * nviews);
+    ENSURE(c->outs_bwd, sizeof(ViewOut) * nviews);
+    ENSURE(c->recs, sizeof(Rec) * (size_t)M);
+    ENSURE(c->ntiles, 4 * (size_t)M);
+    ENSURE(c->rects, 8 * (size_t)M);
+    ENSURE(c->dkeys, 4 * (size_t)M);
+    for (int k = 0; k < 2; ++k) {
+        ENSURE(c->ck[k], 4 * (size_t)M);
+        ENSURE(c->cv[k], 4 * (size_t)M);
+    }
+    ENSURE(c->ranges, sizeof(uint2) * (size_t)tiles);
+    ENSURE(c->tile_max, 4 * (size_t)tiles);
+    ENSURE(c->Tfin, 4 * (size_t)pix);
+    ENSURE(c->ncontrib, 4 * (size_t)pix);
+    const int64_t pre_ctas = (scene->n + 127) / 128;
+    ENSURE(c->st_pre, 4 * (size_t)(pre_ctas + 1));
+    CK(cudaMemcpyAsync(c->views_d.p, views.data(), sizeof(ViewDev) * nviews, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(c->ctl.p, 0, sizeof(Ctl), st));
+    CK(cudaMemsetAsync(c->st_pre.p, 0, 4 * (size_t)(pre_ctas + 1), st));
+    if (M > 0) {
+        PreArgs a;
+        a.verts = scene->verts;
+        a.sh = scene->sh;
+        a.opacity = scene->opacity;
+        a.sigma = scene->sigma;
+        a.n = scene->n;
+        a.sh_degree = scene->sh_degree;
+        a.views = P<ViewDev>(c->views_d);
+        a.nviews = nviews;
+        a.recs = P<Rec>(c->recs);
+        a.ntiles = P<uint32_t>(c->ntiles);
+        a.rects = P<ushort4>(c->rects);
+        a.dkeys = P<uint32_t>(c->dkeys);
+        a.ckeys = P<uint32_t>(c->ck[0]);
+        a.cvals = P<uint32_t>(c->cv[0]);
+        a.lb_status = P<uint32_t>(c->st_pre);
+        a.ctl = ctl_of(c);
+        launch_preprocess_fwd(a, st);
+        if ((s = launch_check(c, "preprocess_fwd_kernel")) != TRI_OK) return s;
+    }
+    c->stage = 1;
+    return TRI_OK;
+}
+
+tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    if (c->stage < 1) return fail(c, TRI_ERR_STATE, "tri_bin_sort before tri_preprocess");
+    tri_status s = set_device(c);
+    if (s != TRI_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    Ctl *ctl = ctl_of(c);
+    const int64_t M = c->n_items;
+    // counters owned by this step (the depth histograms come from tri_preprocess)
+    CK(cudaMemsetAsync(&ctl->n_pairs, 0, 3 * 4, st));  // n_pairs, n_pairs_used, overflow
+    CK(cudaMemsetAsync(&ctl->cta_counter[1], 0, 4, st));
+    CK(cudaMemsetAsync(&ctl->pass_counter[0], 0, sizeof(ctl->pass_counter), st));
+    CK(cudaMemsetAsync(&ctl->tile_hist[0][0], 0, sizeof(ctl->tile_hist), st));
+    // 1. depth sort of the visible items (4 x 8-bit passes)
+    const size_t dwords = sort_status_words(M);
+    ENSURE(c->st_depth, 4 * dwords * 4);
+    CK(cudaMemsetAsync(c->st_depth.p, 0, 4 * dwords * 4, st));
+    const int gd = onesweep_grid(c->sms, (uint32_t)(M > 0 ? M : 1));
+    int cur = 0;
+    for (int p = 0; p < 4; ++p) {
+        launch_onesweep_pass(P<uint32_t>(c->ck[cur]), P<uint32_t>(c->cv[cur]), P<uint32_t>(c->ck[cur ^ 1]),
+                             P<uint32_t>(c->cv[cur ^ 1]), &ctl->n_visible, (uint32_t)M, ctl->depth_hist[p],
+                             P<uint32_t>(c->st_depth) + p * dwords, &ctl->pass_counter[p], 8 * p, &ctl->error, gd, st);
+        cur ^= 1;
+    }
+    if ((s = launch_check(c, "onesweep (depth)")) != TRI_OK) return s;
+    // 2. emission (result of the depth sort is back in ck[0] / cv[0])
+    if (c->pair_cap <= 0) c->pair_cap = default_pair_cap(M);
+    for (int k = 0; k < 2; ++k) {
+        ENSURE(c->pk[k], sizeof(uint32_t) * (size_t)c->pair_cap);
+        ENSURE(c->pv[k], sizeof(uint32_t) * (size_t)c->pair_cap);
+    }
+    ENSURE(c->st_emit, sizeof(uint32_t) * ((M + 255) / 256 + 1));
+    if ((s = emit_pairs(c, st)) != TRI_OK) return s;
+    if (num_pairs_out) {
+        uint32_t np = 0;
+        CK(cudaMemcpyAsync(&np, &ctl->n_pairs, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if ((int64_t)np > c->pair_cap) {
+            if ((int64_t)np > MAX_PAIRS) return fail(c, TRI_ERR_CAPACITY, "more than 2^30 pairs");
+            int64_t cap = (int64_t)np + (int64_t)np / 4;
+            if (cap > MAX_PAIRS) cap = MAX_PAIRS;
+            c->pair_cap = cap;
+            for (int k = 0; k < 2; ++k) {
+                ENSURE(c->pk[k], sizeof(uint32_t) * (size_t)c->pair_cap);
+                ENSURE(c->pv[k], sizeof(uint32_t) * (size_t)c->pair_cap);
+            }
+            // redo the emission with the larger buffer
+            CK(cudaMemsetAsync(&ctl->n_pairs, 0, 4 * 4, st));  // n_pairs, n_pairs_used, overflow, error
+            CK(cudaMemsetAsync(&ctl->cta_counter[1], 0, 4, st));
+            CK(cudaMemsetAsync(&ctl->tile_hist[0][0], 0, sizeof(ctl->tile_hist), st));
+            if ((s = emit_pairs(c, st)) != TRI_OK) return s;
+        }
+        *num_pairs_out = np;
+    }
+    // 3. tile sort of the pairs
+    const size_t pwords = sort_status_words(c->pair_cap);
+    ENSURE(c->st_pairs, 4 * pwords * c->tile_passes);
+    CK(cudaMemsetAsync(c->st_pairs.p, 0, 4 * pwords * c->tile_passes, st));
+    const int gp = onesweep_grid(c->sms, (uint32_t)c->pair_cap);
+    cur = 0;
+    for (int p = 0; p < c->tile_passes; ++p) {
+        launch_onesweep_pass(P<uint32_t>(c->pk[cur]), P<uint32_t>(c->pv[cur]), P<uint32_t>(c->pk[cur ^ 1]),
+                             P<uint32_t>(c->pv[cur ^ 1]), &ctl->n_pairs_used, (uint32_t)c->pair_cap,
+                             ctl->tile_hist[p], P<uint32_t>(c->st_pairs) + p * pwords, &ctl->pass_counter[4 + p],
+                             8 * p, &ctl->error, gp, st);
+        cur ^= 1;
+    }
+    c->pair_final = cur;
+    // 4. ranges
+    launch_ranges(P<uint32_t>(c->pk[cur]), &ctl->n_pairs_used, P<uint2>(c->ranges), (uint32_t)c->total_tiles,
+                  &ctl->error, c->sms * 8, st);
+    if ((s = launch_check(c, "onesweep (tiles) / ranges")) != TRI_OK) return s;
+    c->stage = 2;
+    return TRI_OK;
+}
+
+static RenderArgs render_args(tri_ctx *c, DevBuf &outs) {
+    RenderArgs r;
+    r.views = P<ViewDev>(c->views_d);
+    r.outs = P<ViewOut>(outs);
+    r.nviews = c->nviews;
+    r.total_tiles = c->total_tiles;
+    r.ranges = P<uint2>(c->ranges);
+    r.items = P<uint32_t>(c->pv[c->pair_final]);
+    r.recs = P<Rec>(c->recs);
+    r.T_final = P<float>(c->Tfin);
+    r.n_contrib = P<int32_t>(c->ncontrib);
+    r.tile_max = P<uint32_t>(c->tile_max);
+    r.grad2d = P<float>(c->grad2d);
+    r.n_items = (uint32_t)c->n_items;
+    r.ctl = ctl_of(c);
+    return r;
+}
+
+tri_status tri_render_fwd(tri_ctx *c, float *const *images, float *const *T_final, int32_t *const *n_contrib,
+                          void *stream) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    if (c->stage < 2) return fail(c, TRI_ERR_STATE, "tri_render_fwd before tri_bin_sort");
+    if (!images) return fail(c, TRI_ERR_INVALID_ARG, "images is null");
+    for (int v = 0; v < c->nviews; ++v)
+        if (!images[v]) return fail(c, TRI_ERR_INVALID_ARG, "image pointer is null");
+    tri_status s = set_device(c);
+    if (s != TRI_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<ViewOut> outs(c->nviews);
+    for (int v = 0; v < c->nviews; ++v) outs[v] = ViewOut{images[v], nullptr};
+    CK(cudaMemcpyAsync(c->outs_fwd.p, outs.data(), sizeof(ViewOut) * c->nviews, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(&ctl_of(c)->work_counter[0], 0, 4, st));
+    CK(cudaMemsetAsync(&ctl_of(c)->frag_eval, 0, 16, st));
+    launch_render_fwd(render_args(c, c->outs_fwd), c->sms, st);
+    if ((s = launch_check(c, "render_fwd_kernel")) != TRI_OK) return s;
+    for (int v = 0; v < c->nviews; ++v) {
+        const ViewDev &V = c->views[v];
+        const size_t np = (size_t)V.W * V.H;
+        if (T_final && T_final[v])
+            CK(cudaMemcpyAsync(T_final[v], P<float>(c->Tfin) + V.pix_base, 4 * np, cudaMemcpyDeviceToDevice, st));
+        if (n_contrib && n_contrib[v])
+            CK(cudaMemcpyAsync(n_contrib[v], P<int32_t>(c->ncontrib) + V.pix_base, 4 * np, cudaMemcpyDeviceToDevice,
+                               st));
+    }
+    c->stage = 3;
+    return TRI_OK;
+}
+
+tri_status tri_render_bwd(tri_ctx *c, const float *const *dL, void *stream) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    if (c->stage < 3) return fail(c, TRI_ERR_STATE, "tri_render_bwd before tri_render_fwd");
+    if (!dL) return fail(c, TRI_ERR_INVALID_ARG, "dL_dimages is null");
+    for (int v = 0; v < c->nviews; ++v)
+        if (!dL[v]) return fail(c, TRI_ERR_INVALID_ARG, "dL_dimage pointer is null");
+    tri_status s = set_device(c);
+    if (s != TRI_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<ViewOut> outs(c->nviews);
+    for (int v = 0; v < c->nviews; ++v) outs[v] = ViewOut{nullptr, dL[v]};
+    ENSURE(c->grad2d, sizeof(float) * GRAD_FIELDS * (size_t)c->n_items);
+    CK(cudaMemcpyAsync(c->outs_bwd.p, outs.data(), sizeof(ViewOut) * c->nviews, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(c->grad2d.p, 0, sizeof(float) * GRAD_FIELDS * (size_t)c->n_items, st));
+    CK(cudaMemsetAsync(&ctl_of(c)->work_counter[1], 0, 4, st));
+    launch_render_bwd(render_args(c, c->outs_bwd), c->sms, st);
+    if ((s = launch_check(c, "render_bwd_kernel")) != TRI_OK) return s;
+    c->stage = 4;
+    return TRI_OK;
+}
+
+tri_status tri_preprocess_bwd(tri_ctx *c, float *dverts, float *dsh, float *dopacity, float *dsigma, int accumulate,
+                              void *stream) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    if (c->stage < 4) return fail(c, TRI_ERR_STATE, "tri_preprocess_bwd before tri_render_bwd");
+    tri_status s = set_device(c);
+    if (s != TRI_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    PreBwdArgs a;
+    a.verts = c->scene.verts;
+    a.sh = c->scene.sh;
+    a.n = c->scene.n;
+    a.sh_degree = c->scene.sh_degree;
+    a.views = P<ViewDev>(c->views_d);
+    a.nviews = c->nviews;
+    a.ntiles = P<uint32_t>(c->ntiles);
+    a.grad2d = P<float>(c->grad2d);
+    a.dverts = dverts;
+    a.dsh = dsh;
+    a.dopacity = dopacity;
+    a.dsigma = dsigma;
+    a.accumulate = accumulate;
+    launch_preprocess_bwd(a, st);
+    return launch_check(c, "preprocess_bwd_kernel");
+}
+
+tri_status tri_ctx_check(tri_ctx *c, tri_ctx_info *info, void *stream) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    tri_status s = set_device(c);
+    if (s != TRI_OK) return s;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    Ctl h;
+    memset(&h, 0, sizeof h);
+    if (c->ctl.p) CK(cudaMemcpy(&h, c->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    if (info) {
+        info->n_items = c->n_items;
+        info->n_visible = h.n_visible;
+        info->n_pairs = h.n_pairs;
+        info->pair_capacity = c->pair_cap;
+        info->overflow = (int32_t)h.overflow;
+        info->device_error = (int32_t)h.error;
+        info->n_views = c->nviews;
+        info->total_tiles = c->total_tiles;
+        info->frag_evaluated = (int64_t)h.frag_eval;
+        info->frag_composited = (int64_t)h.frag_kept;
+    }
+    if (h.error & ERR_SPIN) return fail(c, TRI_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (h.error) return fail(c, TRI_ERR_DEVICE_CHECK, "device-side check failed");
+    if (h.overflow) return fail(c, TRI_ERR_CAPACITY, "pair buffer overflow");
+    return TRI_OK;
+}
+
+tri_status tri_debug_copy(tri_ctx *c, int which, void *dst, size_t max_bytes, size_t *bytes) {
+    if (!c || !dst) return TRI_ERR_INVALID_ARG;
+    tri_status s = set_device(c);
+    if (s != TRI_OK) return s;
+    CK(cudaDeviceSynchronize());
+    Ctl h;
+    memset(&h, 0, sizeof h);
+    if (c->ctl.p) CK(cudaMemcpy(&h, c->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    const void *src = nullptr;
+    size_t n = 0;
+    const size_t M = (size_t)c->n_items;
+    const size_t np = (size_t)(h.n_pairs_used);
+    switch (which) {
+        case 0: src = c->pk[c->pair_final].p; n = 4 * np; break;
+        case 1: src = c->pv[c->pair_final].p; n = 4 * np; break;
+        case 2: src = c->ranges.p; n = sizeof(uint2) * (size_t)c->total_tiles; break;
+        case 3: src = c->dkeys.p; n = 4 * M; break;
+        case 4: src = c->rects.p; n = 8 * M; break;
+        case 5: src = c->ntiles.p; n = 4 * M; break;
+        case 6: src = c->cv[0].p; n = 4 * (size_t)h.n_visible; break;
+        case 7: src = c->recs.p; n = sizeof(Rec) * M; break;
+        case 8: src = c->grad2d.p; n = sizeof(float) * GRAD_FIELDS * M; break;
+        default: return fail(c, TRI_ERR_INVALID_ARG, "unknown buffer");
+    }
+    if (n > max_bytes) return fail(c, TRI_ERR_CAPACITY, "destination too small");
+    if (bytes) *bytes = n;
+    if (n == 0) return TRI_OK;
+    if (!src) return fail(c, TRI_ERR_STATE, "buffer not allocated");
+    CK(cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost));
+    return TRI_OK;
+}
+
+tri_status tri_loss_l1(const float *image, const float *target, int64_t n, float *dL_dimage, float *loss,
+                       void *stream) {
+    if (!image || !target || !dL_dimage || n < 0) return TRI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (loss && cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess) return TRI_ERR_CUDA;
+    launch_loss_l1(image, target, n, dL_dimage, loss, st);
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+}
+
+}  // extern "C"

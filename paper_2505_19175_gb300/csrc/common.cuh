@@ -1,0 +1,214 @@
+// Internal device definitions of the triangle-splat renderer (sm_103a).
+//
+// Constants are this library's readings of values the paper leaves to prior
+// splatting work (Sec. 3.1: "the rendering equation is the same as ...") or leaves
+// unset (Supp. "Tile assignment": tau_cutoff).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ts {
+
+constexpr int TILE = 16;                 // 16 x 16 pixel tiles
+constexpr int TILE_PIX = TILE * TILE;    // one CTA of 256 threads per tile
+constexpr float ALPHA_MAX = 0.99f;       // alpha clamp
+constexpr float ALPHA_MIN = 1.0f / 255.0f;  // skip threshold; also tau_cutoff of the rectangle
+constexpr float T_EPS = 1e-4f;           // stop before transmittance drops below this
+constexpr float Z_NEAR = 0.2f;           // cull a triangle with a vertex nearer than this
+constexpr float R_MIN = 1e-4f;           // cull a triangle whose inradius (px) is below this
+constexpr float RECT_PAD = 1.0f / 512.0f;  // px added around the tight rectangle (FP32 slack)
+constexpr int MAX_VIEWS = 64;            // views per preprocess call
+
+// Status words of the decoupled look-back scans: 2 flag bits over a 30-bit count.
+constexpr uint32_t LB_AGG = 1u << 30;
+constexpr uint32_t LB_PREFIX = 2u << 30;
+constexpr uint32_t LB_MASK = (1u << 30) - 1;
+
+// bits of Ctl::error
+constexpr uint32_t ERR_SPIN = 1u;        // a bounded look-back wait gave up
+constexpr uint32_t ERR_INDEX = 2u;       // an index check failed
+
+// One view as the kernels see it.
+struct ViewDev {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float bg[3];
+    float campos[3];       // camera centre -R^T t in world space
+    int W, H;
+    int tiles_x, tiles_y;
+    int tile_base;         // first global tile id of this view
+    int pix_base;          // first pixel of this view in the per-pixel buffers
+};
+
+// Per-view output pointers of one render call.
+struct ViewOut {
+    float *image;          // [3][H][W]
+    const float *dL;       // [3][H][W] (backward)
+};
+
+// Device control block: counters, histograms and work queues of one pipeline run.
+struct Ctl {
+    uint32_t n_visible;        // visible items after preprocess
+    uint32_t n_pairs;          // pairs emitted (may exceed capacity)
+    uint32_t n_pairs_used;     // min(n_pairs, capacity)
+    uint32_t overflow;
+    uint32_t error;
+    uint32_t cta_counter[8];   // dynamic CTA ids of the single-pass scans
+    uint32_t pass_counter[8];  // dynamic tile ids of the radix passes
+    uint32_t work_counter[4];  // render work queues
+    unsigned long long frag_eval;   // forward: (pixel, entry) evaluations
+    unsigned long long frag_kept;   // forward: composited fragments
+    uint32_t depth_hist[4][256];
+    uint32_t tile_hist[4][256];
+};
+
+// Render record of one item: 16 floats = 4 x float4 (64 B).
+//   a = (s_hi.x, s_hi.y, A0, B0)   b = (C0, A1, B1, C1)
+//   c = (A2, B2, C2, o)             d = (sigma, r, g, b)
+// Edge line i is m_i(p) = C_i + A_i (p.x - s_hi.x) + B_i (p.y - s_hi.y); m_i = 1 at the
+// incenter, 0 on edge i, and the window ratio phi(p)/phi(s) = min_i m_i(p).
+struct __align__(16) Rec {
+    float4 a, b, c, d;
+};
+
+// Per-item gradient record, same 16-float footprint:
+//   (g_sx, g_sy, gA0, gB0, gA1, gB1, gA2, gB2, g_o, g_sigma, g_r, g_g, g_b, 0, 0, 0)
+constexpr int GRAD_FIELDS = 16;
+
+// ---------------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+                 "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Wait for a look-back predecessor's status word to leave 0, for at most ~1 s of
+// device time; on timeout set ERR_SPIN and return 0 (the result is then invalid but
+// the kernel finishes). Waiting stops at once when an error is already set.
+__device__ __forceinline__ uint32_t wait_status(const uint32_t *p, uint32_t *err) {
+    uint32_t s = ld_relaxed(p);
+    if (s != 0) return s;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        s = ld_relaxed(p);
+        if (s != 0) return s;
+        if ((it & 63) == 63) {
+            if (ld_relaxed(err) != 0 || global_ns() - t0 > 1000000000ull) {
+                atomicOr(err, ERR_SPIN);
+                return LB_PREFIX;  // pretend a zero prefix so the chain ends
+            }
+            __nanosleep(100);
+        }
+    }
+}
+
+// Fragment evaluation shared by the forward and backward kernels, so that both take
+// bitwise identical decisions: edge values, window ratio and unclamped alpha.
+struct Frag {
+    float dx, dy, m0, m1, m2, ratio;
+};
+
+__device__ __forceinline__ Frag eval_lines(const float4 a, const float4 b, const float4 c, float px,
+                                           float py) {
+    Frag f;
+    f.dx = __fsub_rn(px, a.x);
+    f.dy = __fsub_rn(py, a.y);
+    f.m0 = fmaf(a.z, f.dx, fmaf(a.w, f.dy, b.x));
+    f.m1 = fmaf(b.y, f.dx, fmaf(b.z, f.dy, b.w));
+    f.m2 = fmaf(c.x, f.dx, fmaf(c.y, f.dy, c.z));
+    f.ratio = fminf(f.m0, fminf(f.m1, f.m2));
+    return f;
+}
+
+// I = ratio^sigma for ratio > 0
+__device__ __forceinline__ float window_pow(float ratio, float sigma) {
+    return ex2_approx(__fmul_rn(sigma, lg2_approx(ratio)));
+}
+
+// Exclusive scan across the CTA of one value per thread (blockDim.x <= 1024).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_sums, uint32_t &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < nw ? warp_sums[lane] : 0u;
+        uint32_t t = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_sums[lane] = t - s;
+        if (lane == nw - 1) warp_sums[32] = t;
+    }
+    __syncthreads();
+    total = warp_sums[32];
+    uint32_t r = warp_sums[w] + x - v;
+    __syncthreads();
+    return r;
+}
+
+// Single-word decoupled look-back: exclusive prefix of `agg` over CTAs 0..idx-1.
+__device__ __forceinline__ uint32_t lookback_excl(uint32_t *status, uint32_t idx, uint32_t agg, uint32_t *err) {
+    if (idx == 0) {
+        st_relaxed(&status[0], LB_PREFIX | agg);
+        return 0;
+    }
+    st_relaxed(&status[idx], LB_AGG | agg);
+    uint32_t excl = 0;
+    int k = (int)idx - 1;
+    while (true) {
+        uint32_t s = wait_status(&status[k], err);
+        excl += s & LB_MASK;
+        if ((s >> 30) == 2u) break;
+        --k;
+    }
+    st_relaxed(&status[idx], LB_PREFIX | ((excl + agg) & LB_MASK));
+    return excl;
+}
+
+}  // namespace ts

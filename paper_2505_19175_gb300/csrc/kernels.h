@@ -1,0 +1,90 @@
+// Launch interfaces between the host-side API (api.cu) and the kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace ts {
+
+struct PreArgs {
+    const float *verts, *sh, *opacity, *sigma;
+    int64_t n;
+    int sh_degree;
+    const ViewDev *views;
+    int nviews;
+    Rec *recs;
+    uint32_t *ntiles;
+    ushort4 *rects;
+    uint32_t *dkeys;
+    uint32_t *ckeys, *cvals;   // compacted (depth key, item id) of visible items
+    uint32_t *lb_status;       // one word per CTA, zeroed
+    Ctl *ctl;
+};
+
+struct PreBwdArgs {
+    const float *verts, *sh;
+    int64_t n;
+    int sh_degree;
+    const ViewDev *views;
+    int nviews;
+    const uint32_t *ntiles;
+    const float *grad2d;       // [items][16]
+    float *dverts, *dsh, *dopacity, *dsigma;
+    int accumulate;
+};
+
+void launch_preprocess_fwd(const PreArgs &a, cudaStream_t st);
+void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st);
+
+// ---- sorting ----
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_IPT = 15;                          // keys per thread
+constexpr int SORT_TILE = SORT_THREADS * SORT_IPT;    // keys per CTA tile
+
+// One stable 8-bit LSD pass over (key, value) pairs. `count` lives on the device and
+// is clamped to `cap`; `hist` is this digit's 256-bin histogram over all keys;
+// `status` has room for ceil(cap / SORT_TILE) x 256 words and is zeroed.
+void launch_onesweep_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+                          const uint32_t *count, uint32_t cap, const uint32_t *hist, uint32_t *status,
+                          uint32_t *tile_counter, int shift, uint32_t *err, int grid, cudaStream_t st);
+int onesweep_grid(int sm_count, uint32_t cap);
+
+struct EmitArgs {
+    const uint32_t *sorted_items;   // depth-sorted visible items
+    const uint32_t *ntiles;
+    const ushort4 *rects;
+    const ViewDev *views;
+    int nviews;
+    int64_t n;                      // triangles per view
+    uint32_t *pkeys, *pvals;        // pair output
+    uint32_t cap;
+    int tile_passes;                // digits of the tile key
+    uint32_t *lb_status;            // one word per CTA, zeroed
+    Ctl *ctl;
+};
+void launch_emit(const EmitArgs &a, int64_t max_items, cudaStream_t st);
+
+void launch_ranges(const uint32_t *keys, const uint32_t *count, uint2 *ranges, uint32_t total_tiles, uint32_t *err,
+                   int grid, cudaStream_t st);
+
+// ---- rendering ----
+struct RenderArgs {
+    const ViewDev *views;
+    const ViewOut *outs;
+    int nviews;
+    int total_tiles;
+    const uint2 *ranges;
+    const uint32_t *items;          // sorted pair item ids
+    const Rec *recs;
+    float *T_final;                 // [total pixels]
+    int32_t *n_contrib;             // [total pixels]
+    uint32_t *tile_max;             // [total tiles]
+    float *grad2d;                  // backward: [items][16]
+    uint32_t n_items;               // bound of the item ids in `items`
+    Ctl *ctl;
+};
+void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st);
+void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st);
+
+void launch_loss_l1(const float *img, const float *tgt, int64_t n, float *grad, float *loss, cudaStream_t st);
+
+}  // namespace ts

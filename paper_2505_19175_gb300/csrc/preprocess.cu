@@ -1,0 +1,333 @@
+// Preprocess (forward and backward) of the triangle-splat renderer.
+//
+// Forward, one thread per triangle looping over views so that the triangle's
+// parameters (36 B of vertices, up to 192 B of SH, o, sigma) are read from HBM once
+// per call, staged through shared memory with coalesced float4 loads:
+//   - projection, culling, normalised edge lines and incenter (Sec. 3.1);
+//   - SH colour for the direction camera centre -> centroid (Sec. 4: degree 3);
+//   - tight rectangle of the triangle shrunk about its incenter by
+//     f = 1 - (tau/o)^(1/sigma), tau = ALPHA_MIN (Supp. "Tile assignment");
+//   - order-preserving compaction of the visible items (single-pass decoupled
+//     look-back scan) and the digit histograms of their 32-bit depth keys.
+// Backward: the chain rule of all of the above from the per-item gradient record.
+#include "geometry.cuh"
+#include "kernels.h"
+
+namespace ts {
+
+constexpr int PRE_THREADS = 128;
+
+// Stage `count` floats starting at `src` (16-byte aligned) into shared memory.
+__device__ __forceinline__ void stage_floats(float *dst, const float *src, int count) {
+    const int n4 = count >> 2;
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (int k = threadIdx.x; k < n4; k += blockDim.x) d4[k] = __ldg(s4 + k);
+    for (int k = (n4 << 2) + threadIdx.x; k < count; k += blockDim.x) dst[k] = __ldg(src + k);
+}
+
+__device__ __forceinline__ int clamp_pix(float v, int n) {
+    v = fminf(fmaxf(v, -2.0f), (float)n + 2.0f);
+    return (int)v;
+}
+
+__global__ void __launch_bounds__(PRE_THREADS)
+preprocess_fwd_kernel(PreArgs a) {
+    __shared__ __align__(16) float s_v[PRE_THREADS * 9];
+    __shared__ __align__(16) float s_sh[PRE_THREADS * 48];
+    __shared__ uint32_t s_hist[4][256];
+    __shared__ uint32_t s_scan[33];
+    __shared__ uint32_t s_cta, s_base;
+    __shared__ ViewDev s_view[MAX_VIEWS];
+
+    const int tid = threadIdx.x;
+    if (tid == 0) s_cta = atomicAdd(&a.ctl->cta_counter[0], 1u);
+    for (int k = tid; k < 4 * 256; k += PRE_THREADS) (&s_hist[0][0])[k] = 0u;
+    for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += PRE_THREADS)
+        reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
+    __syncthreads();
+    const uint32_t cta = s_cta;
+    const int64_t i0 = (int64_t)cta * PRE_THREADS;
+    const int cnt = (int)(a.n - i0 < PRE_THREADS ? a.n - i0 : PRE_THREADS);
+    const int nk = (a.sh_degree + 1) * (a.sh_degree + 1);
+    stage_floats(s_v, a.verts + i0 * 9, cnt * 9);
+    stage_floats(s_sh, a.sh + i0 * nk * 3, cnt * nk * 3);
+    __syncthreads();
+
+    const int64_t i = i0 + tid;
+    const bool alive = tid < cnt;
+    float v[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = s_v[tid * 9 + k];
+    const float o = alive ? __ldg(a.opacity + i) : 1.0f;
+    const float sig = alive ? __ldg(a.sigma + i) : 1.0f;
+    const float *shp = s_sh + tid * nk * 3;
+    // shrink factor of the tight rectangle (Supp. "Tile assignment")
+    const float fshrink = 1.0f - powf(ALPHA_MIN / o, 1.0f / sig);
+    const float cen[3] = {(v[0] + v[3] + v[6]) * (1.0f / 3.0f), (v[1] + v[4] + v[7]) * (1.0f / 3.0f),
+                          (v[2] + v[5] + v[8]) * (1.0f / 3.0f)};
+
+    uint64_t vis = 0;
+    uint32_t nvis = 0;
+    for (int vw = 0; vw < a.nviews; ++vw) {
+        if (!alive) break;
+        const ViewDev &V = s_view[vw];
+        const int64_t m = (int64_t)vw * a.n + i;
+        Geom g;
+        int cull = item_geometry(v, V, g);
+        uint32_t nt = 0;
+        ushort4 rect = make_ushort4(0, 0, 0, 0);
+        Rec rec;
+        rec.a = rec.b = rec.c = rec.d = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (cull == CULL_NONE && fshrink > 0.0f) {
+            // shrunk triangle: S + f (Q_k - S), Q_0 = 0
+            const float wx0 = g.S.x - fshrink * g.S.x, wy0 = g.S.y - fshrink * g.S.y;
+            const float wx1 = fmaf(fshrink, g.Q1.x - g.S.x, g.S.x), wy1 = fmaf(fshrink, g.Q1.y - g.S.y, g.S.y);
+            const float wx2 = fmaf(fshrink, g.Q2.x - g.S.x, g.S.x), wy2 = fmaf(fshrink, g.Q2.y - g.S.y, g.S.y);
+            const float xmin = g.u0.hi + fminf(wx0, fminf(wx1, wx2)) - RECT_PAD;
+            const float xmax = g.u0.hi + fmaxf(wx0, fmaxf(wx1, wx2)) + RECT_PAD;
+            const float ymin = g.v0.hi + fminf(wy0, fminf(wy1, wy2)) - RECT_PAD;
+            const float ymax = g.v0.hi + fmaxf(wy0, fmaxf(wy1, wy2)) + RECT_PAD;
+            // pixels whose centres x + 0.5 lie in [min, max]
+            int px0 = max(clamp_pix(ceilf(fminf(fmaxf(xmin, -2.f), V.W + 2.f) - 0.5f), V.W), 0);
+            int px1 = min(clamp_pix(floorf(fminf(fmaxf(xmax, -2.f), V.W + 2.f) - 0.5f), V.W), V.W - 1);
+            int py0 = max(clamp_pix(ceilf(fminf(fmaxf(ymin, -2.f), V.H + 2.f) - 0.5f), V.H), 0);
+            int py1 = min(clamp_pix(floorf(fminf(fmaxf(ymax, -2.f), V.H + 2.f) - 0.5f), V.H), V.H - 1);
+            if (px0 <= px1 && py0 <= py1) {
+                rect = make_ushort4(px0 / TILE, py0 / TILE, px1 / TILE, py1 / TILE);
+                nt = (uint32_t)(rect.z - rect.x + 1) * (uint32_t)(rect.w - rect.y + 1);
+            }
+        }
+        if (nt > 0) {
+            // incenter s = q0 + S in double-float; lines re-based on s_hi
+            ff sx = two_sum(g.u0.hi, g.S.x);
+            ff sy = two_sum(g.v0.hi, g.S.y);
+            const float slx = sx.lo + g.u0.lo, sly = sy.lo + g.v0.lo;
+            float C[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) C[k] = fmaf(-g.A[k], slx, fmaf(-g.B[k], sly, 1.0f));
+            // colour
+            float w0 = cen[0] - V.campos[0], w1 = cen[1] - V.campos[1], w2 = cen[2] - V.campos[2];
+            float inv = rsqrtf(fmaf(w0, w0, fmaf(w1, w1, w2 * w2)));
+            float Y[16];
+            sh_basis(a.sh_degree, w0 * inv, w1 * inv, w2 * inv, Y);
+            float col[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                if (k < nk) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) col[c] = fmaf(Y[k], shp[k * 3 + c], col[c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c], 0.0f);
+            rec.a = make_float4(sx.hi, sy.hi, g.A[0], g.B[0]);
+            rec.b = make_float4(C[0], g.A[1], g.B[1], C[1]);
+            rec.c = make_float4(g.A[2], g.B[2], C[2], o);
+            rec.d = make_float4(sig, col[0], col[1], col[2]);
+            vis |= 1ull << vw;
+            ++nvis;
+        }
+        a.recs[m] = rec;
+        a.ntiles[m] = nt;
+        a.rects[m] = rect;
+        a.dkeys[m] = __float_as_uint(g.depth);
+    }
+
+    // order-preserving compaction: (triangle, view) order, hence by triangle within a view
+    uint32_t total;
+    uint32_t local = block_excl_scan(nvis, s_scan, total);
+    if (tid == 0) s_base = lookback_excl(a.lb_status, cta, total, &a.ctl->error);
+    __syncthreads();
+    uint32_t pos = s_base + local;
+    for (int vw = 0; vw < a.nviews; ++vw) {
+        if (!((vis >> vw) & 1ull)) continue;
+        const int64_t m = (int64_t)vw * a.n + i;
+        const uint32_t key = a.dkeys[m];
+        if ((int64_t)pos >= a.n * a.nviews) {
+            atomicOr(&a.ctl->error, ERR_INDEX);
+            break;
+        }
+        a.ckeys[pos] = key;
+        a.cvals[pos] = (uint32_t)m;
+        ++pos;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int k = tid; k < 4 * 256; k += PRE_THREADS) {
+        uint32_t c = (&s_hist[0][0])[k];
+        if (c) atomicAdd(&(&a.ctl->depth_hist[0][0])[k], c);
+    }
+    if (tid == 0 && cta == gridDim.x - 1) a.ctl->n_visible = s_base + total;
+}
+
+__global__ void __launch_bounds__(PRE_THREADS)
+preprocess_bwd_kernel(PreBwdArgs a) {
+    __shared__ __align__(16) float s_v[PRE_THREADS * 9];
+    __shared__ __align__(16) float s_sh[PRE_THREADS * 48];
+    __shared__ ViewDev s_view[MAX_VIEWS];
+    const int tid = threadIdx.x;
+    for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += PRE_THREADS)
+        reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
+    const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
+    const int cnt = (int)(a.n - i0 < PRE_THREADS ? a.n - i0 : PRE_THREADS);
+    const int nk = (a.sh_degree + 1) * (a.sh_degree + 1);
+    stage_floats(s_v, a.verts + i0 * 9, cnt * 9);
+    stage_floats(s_sh, a.sh + i0 * nk * 3, cnt * nk * 3);
+    __syncthreads();
+    const int64_t i = i0 + tid;
+    const bool alive = tid < cnt;
+    float v[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = s_v[tid * 9 + k];
+    float *shp = s_sh + tid * nk * 3;
+    const float cen[3] = {(v[0] + v[3] + v[6]) * (1.0f / 3.0f), (v[1] + v[4] + v[7]) * (1.0f / 3.0f),
+                          (v[2] + v[5] + v[8]) * (1.0f / 3.0f)};
+    float gv[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) gv[k] = 0.f;
+    float go = 0.f, gsig = 0.f;
+    float gsh[48];
+#pragma unroll
+    for (int k = 0; k < 48; ++k) gsh[k] = 0.f;
+
+    for (int vw = 0; vw < a.nviews && alive; ++vw) {
+        const int64_t m = (int64_t)vw * a.n + i;
+        if (a.ntiles[m] == 0) continue;
+        const float4 *gp = reinterpret_cast<const float4 *>(a.grad2d + m * GRAD_FIELDS);
+        const float4 G0 = gp[0], G1 = gp[1], G2 = gp[2], G3 = gp[3];
+        const ViewDev &V = s_view[vw];
+        Geom g;
+        item_geometry(v, V, g);
+        go += G2.x;
+        gsig += G2.y;
+        // s = q0 + S
+        const float gsx = G0.x, gsy = G0.y;
+        const float gA[3] = {G0.z, G1.x, G1.z}, gB[3] = {G0.w, G1.y, G1.w};
+        float gq0x = gsx, gq0y = gsy;
+        float gQ1x = 0.f, gQ1y = 0.f, gQ2x = 0.f, gQ2y = 0.f;
+        float gell[3] = {0.f, 0.f, 0.f};
+        float gP = 0.f, gA2 = 0.f;
+        const float P = g.perim, iP = 1.0f / P;
+        // S = (ell1 Q1 + ell2 Q2) / P
+        gQ1x += gsx * g.ell[1] * iP; gQ1y += gsy * g.ell[1] * iP;
+        gQ2x += gsx * g.ell[2] * iP; gQ2y += gsy * g.ell[2] * iP;
+        gell[1] += (gsx * g.Q1.x + gsy * g.Q1.y) * iP;
+        gell[2] += (gsx * g.Q2.x + gsy * g.Q2.y) * iP;
+        gP -= (gsx * g.S.x + gsy * g.S.y) * iP;
+        // A_i = -E_i.y k_i, B_i = E_i.x k_i, k_i = P / (ell_i area2)
+        const float Ex[3] = {g.Q2.x - g.Q1.x, -g.Q2.x, g.Q1.x};
+        const float Ey[3] = {g.Q2.y - g.Q1.y, -g.Q2.y, g.Q1.y};
+        float gEx[3], gEy[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float kk = P / (g.ell[k] * g.area2);
+            const float gk = -gA[k] * Ey[k] + gB[k] * Ex[k];
+            gEx[k] = gB[k] * kk;
+            gEy[k] = -gA[k] * kk;
+            gP += gk * kk * iP;
+            gell[k] -= gk * kk / g.ell[k];
+            gA2 -= gk * kk / g.area2;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float gl = gell[k] + gP;
+            gEx[k] += gl * Ex[k] / g.ell[k];
+            gEy[k] += gl * Ey[k] / g.ell[k];
+        }
+        // E0 = Q2 - Q1, E1 = -Q2, E2 = Q1
+        gQ2x += gEx[0] - gEx[1]; gQ2y += gEy[0] - gEy[1];
+        gQ1x += gEx[2] - gEx[0]; gQ1y += gEy[2] - gEy[0];
+        // area2 = Q1.x Q2.y - Q1.y Q2.x
+        gQ1x += gA2 * g.Q2.y; gQ1y -= gA2 * g.Q2.x;
+        gQ2x -= gA2 * g.Q1.y; gQ2y += gA2 * g.Q1.x;
+        // Q_k = q_k - q_0
+        gq0x -= gQ1x + gQ2x; gq0y -= gQ1y + gQ2y;
+        const float gqx[3] = {gq0x, gQ1x, gQ2x}, gqy[3] = {gq0y, gQ1y, gQ2y};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float iz = 1.0f / g.xc[k].z;
+            const float gx = gqx[k] * V.fx * iz;
+            const float gy = gqy[k] * V.fy * iz;
+            const float gz = -(gx * g.xc[k].x + gy * g.xc[k].y) * iz;
+            // x_k = R v_k + t
+            gv[3 * k + 0] += V.R[0] * gx + V.R[3] * gy + V.R[6] * gz;
+            gv[3 * k + 1] += V.R[1] * gx + V.R[4] * gy + V.R[7] * gz;
+            gv[3 * k + 2] += V.R[2] * gx + V.R[5] * gy + V.R[8] * gz;
+        }
+        // colour: rgb = max(0, 0.5 + sum Y_k sh_k)
+        float w0 = cen[0] - V.campos[0], w1 = cen[1] - V.campos[1], w2 = cen[2] - V.campos[2];
+        const float inv = rsqrtf(fmaf(w0, w0, fmaf(w1, w1, w2 * w2)));
+        const float dx = w0 * inv, dy = w1 * inv, dz = w2 * inv;
+        float Y[16];
+        sh_basis(a.sh_degree, dx, dy, dz, Y);
+        const float grgb[3] = {G2.z, G2.w, G3.x};
+        float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (k < nk) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) raw[c] = fmaf(Y[k], shp[k * 3 + c], raw[c]);
+            }
+        }
+        float graw[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) graw[c] = raw[c] > 0.0f ? grgb[c] : 0.0f;
+        float gY[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (k < nk) {
+                gsh[k * 3 + 0] += graw[0] * Y[k];
+                gsh[k * 3 + 1] += graw[1] * Y[k];
+                gsh[k * 3 + 2] += graw[2] * Y[k];
+                gY[k] = graw[0] * shp[k * 3] + graw[1] * shp[k * 3 + 1] + graw[2] * shp[k * 3 + 2];
+            } else {
+                gY[k] = 0.f;
+            }
+        }
+        if (a.sh_degree > 0) {
+            const float3 gd = sh_basis_vjp(a.sh_degree, dx, dy, dz, gY);
+            const float dd = gd.x * dx + gd.y * dy + gd.z * dz;
+            const float gwx = (gd.x - dx * dd) * inv, gwy = (gd.y - dy * dd) * inv, gwz = (gd.z - dz * dd) * inv;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gv[3 * k + 0] += gwx * (1.0f / 3.0f);
+                gv[3 * k + 1] += gwy * (1.0f / 3.0f);
+                gv[3 * k + 2] += gwz * (1.0f / 3.0f);
+            }
+        }
+    }
+    __syncthreads();
+    // stage and write (coalesced): vertices, then SH
+    if (alive) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s_v[tid * 9 + k] = gv[k];
+#pragma unroll
+        for (int k = 0; k < 48; ++k)
+            if (k < nk * 3) shp[k] = gsh[k];
+        if (a.dopacity) a.dopacity[i] = a.accumulate ? a.dopacity[i] + go : go;
+        if (a.dsigma) a.dsigma[i] = a.accumulate ? a.dsigma[i] + gsig : gsig;
+    }
+    __syncthreads();
+    if (a.dverts) {
+        float *dst = a.dverts + i0 * 9;
+        for (int k = tid; k < cnt * 9; k += PRE_THREADS) dst[k] = a.accumulate ? dst[k] + s_v[k] : s_v[k];
+    }
+    if (a.dsh) {
+        float *dst = a.dsh + i0 * nk * 3;
+        for (int k = tid; k < cnt * nk * 3; k += PRE_THREADS) dst[k] = a.accumulate ? dst[k] + s_sh[k] : s_sh[k];
+    }
+}
+
+void launch_preprocess_fwd(const PreArgs &a, cudaStream_t st) {
+    const int grid = (int)((a.n + PRE_THREADS - 1) / PRE_THREADS);
+    if (grid > 0) preprocess_fwd_kernel<<<grid, PRE_THREADS, 0, st>>>(a);
+}
+
+void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st) {
+    const int grid = (int)((a.n + PRE_THREADS - 1) / PRE_THREADS);
+    if (grid > 0) preprocess_bwd_kernel<<<grid, PRE_THREADS, 0, st>>>(a);
+}
+
+}  // namespace ts

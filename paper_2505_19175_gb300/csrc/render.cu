@@ -1,0 +1,351 @@
+// Tile rendering of the triangle-splat renderer, forward and backward.
+//
+// One CTA of 256 threads renders one 16x16 tile (one thread per pixel; each warp
+// covers an 8x4 block so that small triangles touch few warps). Tiles are taken from
+// a device work queue by a persistent grid, so a launch serves any mix of views and
+// resolutions. The tile's depth-sorted records are staged through shared memory 256
+// at a time (64 B each, one coalesced float4 x 4 gather per thread).
+//
+// Forward (Sec. 3.1, the rendering equation of prior splatting work): per pixel,
+// ratio = min_i m_i(p) (phi(p)/phi(s) of Eq. indicator1), I = ratio^sigma, alpha = o I,
+// skip below 1/255, clamp at 0.99, stop before T drops below 1e-4, C += rgb alpha T.
+// The CTA leaves a tile as soon as every pixel has stopped (__syncthreads_count).
+//
+// Backward: per pixel, from its last composited entry back to the first,
+// T_k = T_{k+1} / (1 - alpha_k), dL/dalpha_k = sum_c g_c (rgb_c T_k - B_c / (1 - alpha_k))
+// with B the colour behind fragment k plus T_final bg; gradients of the record
+// fields are reduced across the warp with a transposed butterfly (16 shuffles for 16
+// fields), summed per record in shared memory, and added to the per-item gradient
+// record with four 16-byte vector atomics per (item, tile).
+#include "kernels.h"
+
+namespace ts {
+
+constexpr int REN_THREADS = TILE_PIX;
+
+__device__ __forceinline__ int find_view(const ViewDev *vs, int nviews, int tile) {
+    int v = 0;
+    for (int k = 1; k < nviews; ++k)
+        if (vs[k].tile_base <= tile) v = k;
+    return v;
+}
+
+__device__ __forceinline__ void pixel_of(int tid, int &lx, int &ly) {
+    const int w = tid >> 5, lane = tid & 31;
+    lx = ((w & 1) << 3) | (lane & 7);
+    ly = ((w >> 1) << 2) | (lane >> 3);
+}
+
+__global__ void __launch_bounds__(REN_THREADS)
+render_fwd_kernel(RenderArgs a) {
+    __shared__ Rec s_rec[REN_THREADS];
+    __shared__ ViewDev s_view[MAX_VIEWS];
+    __shared__ uint32_t s_red[REN_THREADS / 32];
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += REN_THREADS)
+        reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
+    int lx, ly;
+    pixel_of(tid, lx, ly);
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&a.ctl->work_counter[0], 1u);
+        __syncthreads();
+        const int tile = (int)s_tile;
+        if (tile >= a.total_tiles) break;
+        const int vw = find_view(s_view, a.nviews, tile);
+        const ViewDev &V = s_view[vw];
+        const int lt = tile - V.tile_base;
+        const int x = (lt % V.tiles_x) * TILE + lx, y = (lt / V.tiles_x) * TILE + ly;
+        const bool inside = x < V.W && y < V.H;
+        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+        const uint2 rg = a.ranges[tile];
+        const uint32_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
+        float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        uint32_t last = 0, n_eval = 0, n_kept = 0;
+        bool done = !inside;
+        for (uint32_t b0 = start; b0 < end; b0 += REN_THREADS) {
+            if (__syncthreads_count(done) == REN_THREADS) break;
+            const uint32_t idx = b0 + tid;
+            if (idx < end) {
+                uint32_t it = a.items[idx];
+                if (it >= a.n_items) {
+                    atomicOr(&a.ctl->error, ERR_INDEX);
+                    it = 0;
+                }
+                s_rec[tid] = a.recs[it];
+            }
+            __syncthreads();
+            const int nb = (int)min((uint32_t)REN_THREADS, end - b0);
+            if (!done) {
+                int j = 0;
+                for (; j < nb; ++j) {
+                    const float4 ra = s_rec[j].a, rb = s_rec[j].b, rc = s_rec[j].c;
+                    const Frag f = eval_lines(ra, rb, rc, px, py);
+                    if (f.ratio <= 0.0f) continue;
+                    const float4 rd = s_rec[j].d;
+                    const float I = window_pow(f.ratio, rd.x);
+                    float al = __fmul_rn(rc.w, I);
+                    if (al < ALPHA_MIN) continue;
+                    al = fminf(al, ALPHA_MAX);
+                    const float tT = __fmul_rn(T, __fsub_rn(1.0f, al));
+                    if (tT < T_EPS) {
+                        done = true;
+                        ++j;
+                        break;
+                    }
+                    const float wgt = __fmul_rn(al, T);
+                    C0 = fmaf(rd.y, wgt, C0);
+                    C1 = fmaf(rd.z, wgt, C1);
+                    C2 = fmaf(rd.w, wgt, C2);
+                    T = tT;
+                    last = b0 - start + (uint32_t)j + 1u;
+                    ++n_kept;
+                }
+                n_eval += (uint32_t)j;
+            }
+        }
+        if (inside) {
+            const int64_t HW = (int64_t)V.W * V.H;
+            const int64_t pix = (int64_t)y * V.W + x;
+            float *img = a.outs[vw].image;
+            img[pix] = fmaf(T, V.bg[0], C0);
+            img[HW + pix] = fmaf(T, V.bg[1], C1);
+            img[2 * HW + pix] = fmaf(T, V.bg[2], C2);
+            a.T_final[V.pix_base + pix] = T;
+            a.n_contrib[V.pix_base + pix] = (int32_t)last;
+        }
+        const uint32_t wm = __reduce_max_sync(0xffffffffu, last);
+        const uint32_t we = __reduce_add_sync(0xffffffffu, n_eval);
+        const uint32_t wk = __reduce_add_sync(0xffffffffu, n_kept);
+        if (lane == 0) {
+            s_red[w] = wm;
+            atomicAdd(&a.ctl->frag_eval, (unsigned long long)we);
+            atomicAdd(&a.ctl->frag_kept, (unsigned long long)wk);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t m = 0;
+#pragma unroll
+            for (int k = 0; k < REN_THREADS / 32; ++k) m = max(m, s_red[k]);
+            a.tile_max[tile] = m;
+        }
+        __syncthreads();
+    }
+}
+
+// Sum 16 per-lane values across the warp; lane l ends with field (l >> 1).
+__device__ __forceinline__ float warp_reduce16(float (&v)[16], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float send = b4 ? v[i] : v[i + 8];
+        const float keep = b4 ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b3 ? v[i] : v[i + 4];
+        const float keep = b3 ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b2 ? v[i] : v[i + 2];
+        const float keep = b2 ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const float send = b1 ? v[0] : v[1];
+        const float keep = b1 ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__global__ void __launch_bounds__(REN_THREADS)
+render_bwd_kernel(RenderArgs a) {
+    __shared__ Rec s_rec[REN_THREADS];
+    __shared__ uint32_t s_item[REN_THREADS];
+    __shared__ __align__(16) float s_acc[REN_THREADS][GRAD_FIELDS];
+    __shared__ ViewDev s_view[MAX_VIEWS];
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += REN_THREADS)
+        reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
+    int lx, ly;
+    pixel_of(tid, lx, ly);
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&a.ctl->work_counter[1], 1u);
+        __syncthreads();
+        const int tile = (int)s_tile;
+        if (tile >= a.total_tiles) break;
+        const int vw = find_view(s_view, a.nviews, tile);
+        const ViewDev &V = s_view[vw];
+        const int lt = tile - V.tile_base;
+        const int x = (lt % V.tiles_x) * TILE + lx, y = (lt / V.tiles_x) * TILE + ly;
+        const bool inside = x < V.W && y < V.H;
+        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+        const uint32_t start = a.ranges[tile].x;
+        const uint32_t maxc = a.tile_max[tile];
+        float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
+        uint32_t last = 0;
+        if (inside) {
+            const int64_t HW = (int64_t)V.W * V.H;
+            const int64_t pix = (int64_t)y * V.W + x;
+            T = a.T_final[V.pix_base + pix];
+            last = (uint32_t)a.n_contrib[V.pix_base + pix];
+            const float *dL = a.outs[vw].dL;
+            g0 = dL[pix];
+            g1 = dL[HW + pix];
+            g2 = dL[2 * HW + pix];
+            B0 = T * V.bg[0];
+            B1 = T * V.bg[1];
+            B2 = T * V.bg[2];
+        }
+        for (int bend = (int)maxc; bend > 0; bend -= REN_THREADS) {
+            const int bstart = max(0, bend - REN_THREADS);
+            const int nb = bend - bstart;
+            __syncthreads();
+            if (tid < nb) {
+                uint32_t it = a.items[start + bstart + tid];
+                if (it >= a.n_items) {
+                    atomicOr(&a.ctl->error, ERR_INDEX);
+                    it = 0;
+                }
+                s_item[tid] = it;
+                s_rec[tid] = a.recs[it];
+            }
+            {
+                float4 *acc4 = reinterpret_cast<float4 *>(&s_acc[tid][0]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncthreads();
+            for (int j = nb - 1; j >= 0; --j) {
+                float gv[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) gv[k] = 0.f;
+                bool kept = false;
+                if ((uint32_t)(bstart + j) < last) {
+                    const float4 ra = s_rec[j].a, rb = s_rec[j].b, rc = s_rec[j].c;
+                    const Frag f = eval_lines(ra, rb, rc, px, py);
+                    if (f.ratio > 0.0f) {
+                        const float4 rd = s_rec[j].d;
+                        const float lg = lg2_approx(f.ratio);
+                        const float I = ex2_approx(__fmul_rn(rd.x, lg));
+                        const float araw = __fmul_rn(rc.w, I);
+                        if (araw >= ALPHA_MIN) {
+                            kept = true;
+                            const float al = fminf(araw, ALPHA_MAX);
+                            const float om = __fsub_rn(1.0f, al);
+                            T = __fdiv_rn(T, om);
+                            const float wgt = al * T;
+                            gv[10] = g0 * wgt;
+                            gv[11] = g1 * wgt;
+                            gv[12] = g2 * wgt;
+                            const float iom = 1.0f / om;
+                            const float galpha = g0 * (rd.y * T - B0 * iom) + g1 * (rd.z * T - B1 * iom) +
+                                                 g2 * (rd.w * T - B2 * iom);
+                            B0 = fmaf(rd.y, wgt, B0);
+                            B1 = fmaf(rd.z, wgt, B1);
+                            B2 = fmaf(rd.w, wgt, B2);
+                            if (araw <= ALPHA_MAX) {
+                                const float gI = galpha * rc.w;
+                                gv[8] = galpha * I;                               // d/do
+                                gv[9] = gI * I * lg * 0.69314718055994531f;       // d/dsigma: I ln(ratio)
+                                const float gr = gI * rd.x * I / f.ratio;         // d/dratio
+                                // the active line: lowest index among the minima
+                                const int ia = (f.m0 <= f.m1 && f.m0 <= f.m2) ? 0 : (f.m1 <= f.m2 ? 1 : 2);
+                                const float Aa = ia == 0 ? ra.z : (ia == 1 ? rb.y : rc.x);
+                                const float Ba = ia == 0 ? ra.w : (ia == 1 ? rb.z : rc.y);
+                                gv[0] = -gr * Aa;
+                                gv[1] = -gr * Ba;
+                                const float gA = gr * f.dx, gB = gr * f.dy;
+                                gv[2] = ia == 0 ? gA : 0.f;
+                                gv[3] = ia == 0 ? gB : 0.f;
+                                gv[4] = ia == 1 ? gA : 0.f;
+                                gv[5] = ia == 1 ? gB : 0.f;
+                                gv[6] = ia == 2 ? gA : 0.f;
+                                gv[7] = ia == 2 ? gB : 0.f;
+                            }
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, kept)) {
+                    const float s = warp_reduce16(gv, lane);
+                    if (!(lane & 1)) atomicAdd(&s_acc[j][lane >> 1], s);
+                }
+            }
+            __syncthreads();
+            if (tid < nb) {
+                const float4 *acc4 = reinterpret_cast<const float4 *>(&s_acc[tid][0]);
+                const float4 q0 = acc4[0], q1 = acc4[1], q2 = acc4[2], q3 = acc4[3];
+                const bool nz = (q0.x != 0.f) | (q0.y != 0.f) | (q0.z != 0.f) | (q0.w != 0.f) | (q1.x != 0.f) |
+                                (q1.y != 0.f) | (q1.z != 0.f) | (q1.w != 0.f) | (q2.x != 0.f) | (q2.y != 0.f) |
+                                (q2.z != 0.f) | (q2.w != 0.f) | (q3.x != 0.f) | (q3.y != 0.f) | (q3.z != 0.f);
+                if (nz) {
+                    float *dst = a.grad2d + (size_t)s_item[tid] * GRAD_FIELDS;
+                    red_add_v4(dst, q0.x, q0.y, q0.z, q0.w);
+                    red_add_v4(dst + 4, q1.x, q1.y, q1.z, q1.w);
+                    red_add_v4(dst + 8, q2.x, q2.y, q2.z, q2.w);
+                    red_add_v4(dst + 12, q3.x, q3.y, q3.z, q3.w);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+static int occupancy(const void *fn, int threads) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0) != cudaSuccess || occ < 1) occ = 1;
+    return occ;
+}
+
+void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st) {
+    static int occ = occupancy((const void *)render_fwd_kernel, REN_THREADS);
+    int g = grid > 0 ? grid * occ : occ;
+    if (g > a.total_tiles) g = a.total_tiles;
+    if (g > 0) render_fwd_kernel<<<g, REN_THREADS, 0, st>>>(a);
+}
+
+void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st) {
+    static int occ = occupancy((const void *)render_bwd_kernel, REN_THREADS);
+    int g = grid > 0 ? grid * occ : occ;
+    if (g > a.total_tiles) g = a.total_tiles;
+    if (g > 0) render_bwd_kernel<<<g, REN_THREADS, 0, st>>>(a);
+}
+
+// ---------------------------------------------------------------------------------
+// L1 loss: mean |image - target| and its gradient sign(image - target) / n
+// ---------------------------------------------------------------------------------
+__global__ void loss_l1_kernel(const float *__restrict__ img, const float *__restrict__ tgt, int64_t n,
+                               float *__restrict__ grad, float *loss) {
+    const float inv = 1.0f / (float)n;
+    float acc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = img[i] - tgt[i];
+        acc += fabsf(d);
+        grad[i] = d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
+    }
+    if (loss) {
+        __shared__ float s_part[32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_part[k];
+            atomicAdd(loss, t * inv);
+        }
+    }
+}
+
+void launch_loss_l1(const float *img, const float *tgt, int64_t n, float *grad, float *loss, cudaStream_t st) {
+    int64_t g = (n + 255) / 256;
+    if (g > 1216) g = 1216;  // 8 CTAs per SM on 152 SMs: one atomic per CTA
+    if (g > 0) loss_l1_kernel<<<(unsigned)g, 256, 0, st>>>(img, tgt, n, grad, loss);
+}
+
+}  // namespace ts

@@ -1,0 +1,111 @@
+"""GPU backward parity against the FP64 oracle adjoint (gradients within 1e-3
+relative, norm-wise per tensor and element-wise against 1e-3 of the tensor's rms)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2505_19175_gb300 import synth
+from gpu_util import gpu_backward, gpu_forward
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-3
+
+
+def _check_grads(got, want, names=("verts", "sh", "opacity", "sigma")):
+    for k in names:
+        g, w = got[k], want[k]
+        nw = np.linalg.norm(w)
+        assert nw > 0, k
+        rel = np.linalg.norm(g - w) / nw
+        assert rel <= RTOL, f"{k}: relative error {rel:.3e}"
+        rms = np.sqrt(np.mean(w ** 2))
+        bad = np.abs(g - w) > RTOL * np.abs(w) + RTOL * rms
+        assert bad.mean() <= 1e-3, f"{k}: {bad.sum()} elements outside the element-wise bound"
+
+
+def _masked_grad(ref, seed, shape):
+    """Random dL/dimage, zero on pixels whose FP32 value is ill-conditioned."""
+    g = np.random.default_rng(seed).standard_normal(shape)
+    return g * (ref["flags"] == 0)[None]
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_backward_random_scene(seed):
+    scene = synth.random_scene(600, seed=20 + seed, deg=3, sigma=(0.4, 2.5))
+    cam = synth.camera_identity(96, 80)
+    imgs, T, nc, ctx, st = gpu_forward(scene, [cam])
+    ref = O.render(scene, cam, flags=True)
+    g = _masked_grad(ref, seed, (3, cam.H, cam.W))
+    got = gpu_backward(ctx, st, [g])
+    want = O.render_grad(scene, cam, g)
+    _check_grads(got, want)
+
+
+@pytest.mark.slow
+def test_backward_patch_crop_2k_triangles():
+    """The 2,000 triangles nearest one patch of the 500k-triangle workload, in a
+    128x128 window; L1 loss against a seeded target."""
+    scene, centres, _ = synth.scene_patches()
+    crop, cam, _ = synth.crop_around(scene, synth.camera_patches(), centres[0])
+    imgs, T, nc, ctx, st = gpu_forward(crop, [cam])
+    ref = O.render(crop, cam, flags=True)
+    tgt = synth.target_image(cam.H, cam.W, seed=5)
+    g = np.sign(imgs[0] - tgt) / imgs[0].size * (ref["flags"] == 0)[None]
+    got = gpu_backward(ctx, st, [g])
+    want = O.render_grad(crop, cam, g)
+    _check_grads(got, want)
+
+
+def test_multiview_gradients_sum_over_views():
+    scene = synth.random_scene(300, seed=30, deg=2)
+    cams = [synth.camera_look_at((0.2 * k - 0.2, 0.0, -0.3), (0, 0, 3.5), 64, 48) for k in range(3)]
+    imgs, T, nc, ctx, st = gpu_forward(scene, cams)
+    gs, total = [], None
+    for k, c in enumerate(cams):
+        ref = O.render(scene, c, flags=True)
+        gs.append(_masked_grad(ref, 40 + k, (3, c.H, c.W)))
+        w = O.render_grad(scene, c, gs[-1])
+        total = w if total is None else {n: total[n] + w[n] for n in w}
+    got = gpu_backward(ctx, st, gs)
+    _check_grads(got, total)
+
+
+def test_autograd_function_matches_direct_calls():
+    import torch
+    from paper_2505_19175_gb300.autograd import rasterize
+    scene = synth.random_scene(400, seed=31, deg=1)
+    cam = synth.camera_identity(80, 64)
+    p = [torch.tensor(np.asarray(x, np.float32), device="cuda", requires_grad=True)
+         for x in (scene.verts, scene.sh, scene.opacity, scene.sigma)]
+    (img,) = rasterize(p[0], p[1], p[2], p[3], scene.sh_degree, [cam])
+    tgt = torch.as_tensor(synth.target_image(cam.H, cam.W, seed=1), device="cuda")
+    loss = (img - tgt).abs().mean()
+    loss.backward()
+    imgs, T, nc, ctx, st = gpu_forward(scene, [cam])
+    np.testing.assert_array_equal(img.detach().cpu().numpy(), imgs[0].astype(np.float32))
+    g = (np.sign(imgs[0] - synth.target_image(cam.H, cam.W, seed=1)) / imgs[0].size)
+    got = gpu_backward(ctx, st, [g])
+    for k, t in zip(("verts", "sh", "opacity", "sigma"), p):
+        np.testing.assert_allclose(t.grad.cpu().numpy(), got[k], rtol=1e-4, atol=1e-7 * np.abs(got[k]).max())
+
+
+def test_fp32_directional_finite_difference():
+    """d/de L(theta + e u) by central differences of the GPU forward matches <grad, u>."""
+    import torch
+    from paper_2505_19175_gb300.renderer import Context, SceneTensors, new_images
+    scene = synth.random_scene(200, seed=32, deg=1, sigma=(1.5, 2.5), opacity=(0.2, 0.6))
+    cam = synth.camera_identity(64, 48)
+    g = np.random.default_rng(3).standard_normal((3, cam.H, cam.W))
+    imgs, T, nc, ctx, st = gpu_forward(scene, [cam])
+    grads = gpu_backward(ctx, st, [g])
+    rng = np.random.default_rng(4)
+    for key, scale in (("opacity", 1e-2), ("sigma", 1e-2), ("sh", 1e-2), ("verts", 1e-3)):
+        u = rng.standard_normal(getattr(scene, key).shape)
+        def L(eps):
+            s = synth.Scene(scene.verts.copy(), scene.sh.copy(), scene.opacity.copy(), scene.sigma.copy(), 1)
+            setattr(s, key, (getattr(scene, key) + eps * u).astype(np.float32))
+            im, _, _, _, _ = gpu_forward(s, [cam])
+            return float(np.sum(im[0] * g))
+        fd = (L(scale) - L(-scale)) / (2 * scale)
+        an = float(np.sum(grads[key] * u))
+        assert abs(fd - an) <= 2e-2 * (abs(an) + abs(fd)) + 1e-3, (key, fd, an)
