@@ -67,7 +67,7 @@ typedef struct {
     float t[3];        /* world -> camera translation */
     float fx, fy;      /* focal lengths in pixels */
     float cx, cy;      /* principal point in pixels */
-    int32_t width, height;
+    int32_t width, height;  /* 1..65535 */
     float bg[3];       /* background colour added with the final transmittance */
 } tri_camera;
 
@@ -175,7 +175,8 @@ tri_status tri_ctx_check(tri_ctx *ctx, tri_ctx_info *info, void *stream);
  * `dst` (at most `max_bytes`), synchronously; `*bytes` receives the byte count used.
  *   0: sorted pair tile keys (uint32 [n_pairs])   1: sorted pair item ids (uint32)
  *   2: tile ranges (uint32 [total_tiles][2])       3: item depth keys (uint32 [n_items])
- *   4: item tile rectangles (uint16 [n_items][4])  5: item tile counts (uint32 [n_items])
+ *   4: item pixel rectangles (uint16 [n_items][4]: x0, y0, x1, y1 inclusive)
+ *   5: item tile counts (uint32 [n_items])
  *   6: depth-sorted visible item ids (uint32 [n_visible])
  *   7: per-item render records (float [n_items][16])
  *   8: per-item 2D gradients (float [n_items][16]) */

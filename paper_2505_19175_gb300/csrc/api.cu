@@ -141,7 +141,7 @@ tri_status build_views(tri_ctx *c, const tri_camera *cams, int nviews, std::vect
     int64_t tb = 0, pb = 0;
     for (int v = 0; v < nviews; ++v) {
         const tri_camera &k = cams[v];
-        if (k.width <= 0 || k.height <= 0 || k.width > 65535 * TILE || k.height > 65535 * TILE)
+        if (k.width <= 0 || k.height <= 0 || k.width > 65535 || k.height > 65535)
             return fail(c, TRI_ERR_INVALID_ARG, "camera width/height out of range");
         ViewDev &d = out[v];
         memcpy(d.R, k.R, sizeof d.R);
@@ -248,7 +248,7 @@ tri_status tri_workspace_query(const tri_scene *scene, const tri_camera *cams, i
     size_t b = 0;
     b += (size_t)M * (sizeof(Rec) + 4 + 8 + 4 + 16 + GRAD_FIELDS * 4);  // records, counts, rects, keys, 2x2 lists, grads
     b += (size_t)cap * 16;                                            // 2 x (key, value) pair buffers
-    b += (size_t)tiles * (8 + 4) + (size_t)pix * 8;
+    b += (size_t)tiles * (8 + 32) + (size_t)pix * 8;
     b += sizeof(uint32_t) * (sort_status_words(M) * 4 + sort_status_words(cap) * 3 + (M + 255) / 256 * 2);
     b += sizeof(Ctl) + nviews * (sizeof(ViewDev) + 2 * sizeof(ViewOut));
     *bytes = b;
@@ -302,7 +302,7 @@ tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *
         ENSURE(c->cv[k], 4 * (size_t)M);
     }
     ENSURE(c->ranges, sizeof(uint2) * (size_t)tiles);
-    ENSURE(c->tile_max, 4 * (size_t)tiles);
+    ENSURE(c->tile_max, 4 * 8 * (size_t)tiles);
     ENSURE(c->Tfin, 4 * (size_t)pix);
     ENSURE(c->ncontrib, 4 * (size_t)pix);
     const int64_t pre_ctas = (scene->n + 127) / 128;
@@ -421,6 +421,7 @@ static RenderArgs render_args(tri_ctx *c, DevBuf &outs) {
     r.ranges = P<uint2>(c->ranges);
     r.items = P<uint32_t>(c->pv[c->pair_final]);
     r.recs = P<Rec>(c->recs);
+    r.rects = P<ushort4>(c->rects);
     r.T_final = P<float>(c->Tfin);
     r.n_contrib = P<int32_t>(c->ncontrib);
     r.tile_max = P<uint32_t>(c->tile_max);

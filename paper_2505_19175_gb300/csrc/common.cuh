@@ -192,22 +192,31 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_s
     return r;
 }
 
-// Single-word decoupled look-back: exclusive prefix of `agg` over CTAs 0..idx-1.
-__device__ __forceinline__ uint32_t lookback_excl(uint32_t *status, uint32_t idx, uint32_t agg, uint32_t *err) {
+// Decoupled look-back over one status word per CTA, run by all 32 lanes of one warp:
+// each round fetches the 32 nearest predecessors at once and stops at the nearest one
+// that already holds an inclusive prefix. Returns the exclusive prefix of `agg` over
+// CTAs 0..idx-1 in every lane.
+__device__ __forceinline__ uint32_t warp_lookback_excl(uint32_t *status, uint32_t idx, uint32_t agg, uint32_t *err) {
+    const int lane = threadIdx.x & 31;
     if (idx == 0) {
-        st_relaxed(&status[0], LB_PREFIX | agg);
+        if (lane == 0) st_relaxed(&status[0], LB_PREFIX | agg);
         return 0;
     }
-    st_relaxed(&status[idx], LB_AGG | agg);
+    if (lane == 0) st_relaxed(&status[idx], LB_AGG | agg);
     uint32_t excl = 0;
-    int k = (int)idx - 1;
+    int base = (int)idx - 1;
     while (true) {
-        uint32_t s = wait_status(&status[k], err);
-        excl += s & LB_MASK;
-        if ((s >> 30) == 2u) break;
-        --k;
+        const int k = base - lane;  // lane 0 holds the nearest predecessor
+        const uint32_t s = k >= 0 ? wait_status(&status[k], err) : LB_PREFIX;
+        const unsigned pre = __ballot_sync(0xffffffffu, (s >> 30) == 2u);
+        const int stop = pre ? __ffs(pre) - 1 : 31;
+        uint32_t v = lane <= stop ? (s & LB_MASK) : 0u;
+        v = __reduce_add_sync(0xffffffffu, v);
+        excl += v;
+        if (pre) break;
+        base -= 32;
     }
-    st_relaxed(&status[idx], LB_PREFIX | ((excl + agg) & LB_MASK));
+    if (lane == 0) st_relaxed(&status[idx], LB_PREFIX | ((excl + agg) & LB_MASK));
     return excl;
 }
 

@@ -13,7 +13,7 @@ struct PreArgs {
     int nviews;
     Rec *recs;
     uint32_t *ntiles;
-    ushort4 *rects;
+    ushort4 *rects;            // pixel rectangle (x0, y0, x1, y1), inclusive
     uint32_t *dkeys;
     uint32_t *ckeys, *cvals;   // compacted (depth key, item id) of visible items
     uint32_t *lb_status;       // one word per CTA, zeroed
@@ -75,9 +75,10 @@ struct RenderArgs {
     const uint2 *ranges;
     const uint32_t *items;          // sorted pair item ids
     const Rec *recs;
+    const ushort4 *rects;           // per-item pixel rectangles
     float *T_final;                 // [total pixels]
     int32_t *n_contrib;             // [total pixels]
-    uint32_t *tile_max;             // [total tiles]
+    uint32_t *tile_max;             // [total tiles][8]: largest n_contrib of each warp
     float *grad2d;                  // backward: [items][16]
     uint32_t n_items;               // bound of the item ids in `items`
     Ctl *ctl;

@@ -16,6 +16,7 @@
 namespace ts {
 
 constexpr int PRE_THREADS = 128;
+constexpr int PRE_BWD_THREADS = 64;
 
 // Stage `count` floats starting at `src` (16-byte aligned) into shared memory.
 __device__ __forceinline__ void stage_floats(float *dst, const float *src, int count) {
@@ -31,14 +32,14 @@ __device__ __forceinline__ int clamp_pix(float v, int n) {
     return (int)v;
 }
 
-__global__ void __launch_bounds__(PRE_THREADS)
+__global__ void __launch_bounds__(PRE_THREADS, 6)
 preprocess_fwd_kernel(PreArgs a) {
     __shared__ __align__(16) float s_v[PRE_THREADS * 9];
     __shared__ __align__(16) float s_sh[PRE_THREADS * 48];
     __shared__ uint32_t s_hist[4][256];
     __shared__ uint32_t s_scan[33];
     __shared__ uint32_t s_cta, s_base;
-    __shared__ ViewDev s_view[MAX_VIEWS];
+    extern __shared__ ViewDev s_view[];   // nviews entries
 
     const int tid = threadIdx.x;
     if (tid == 0) s_cta = atomicAdd(&a.ctl->cta_counter[0], 1u);
@@ -94,8 +95,8 @@ preprocess_fwd_kernel(PreArgs a) {
             int py0 = max(clamp_pix(ceilf(fminf(fmaxf(ymin, -2.f), V.H + 2.f) - 0.5f), V.H), 0);
             int py1 = min(clamp_pix(floorf(fminf(fmaxf(ymax, -2.f), V.H + 2.f) - 0.5f), V.H), V.H - 1);
             if (px0 <= px1 && py0 <= py1) {
-                rect = make_ushort4(px0 / TILE, py0 / TILE, px1 / TILE, py1 / TILE);
-                nt = (uint32_t)(rect.z - rect.x + 1) * (uint32_t)(rect.w - rect.y + 1);
+                rect = make_ushort4(px0, py0, px1, py1);
+                nt = (uint32_t)(px1 / TILE - px0 / TILE + 1) * (uint32_t)(py1 / TILE - py0 / TILE + 1);
             }
         }
         if (nt > 0) {
@@ -137,7 +138,10 @@ preprocess_fwd_kernel(PreArgs a) {
     // order-preserving compaction: (triangle, view) order, hence by triangle within a view
     uint32_t total;
     uint32_t local = block_excl_scan(nvis, s_scan, total);
-    if (tid == 0) s_base = lookback_excl(a.lb_status, cta, total, &a.ctl->error);
+    if (tid < 32) {
+        const uint32_t b = warp_lookback_excl(a.lb_status, cta, total, &a.ctl->error);
+        if (tid == 0) s_base = b;
+    }
     __syncthreads();
     uint32_t pos = s_base + local;
     for (int vw = 0; vw < a.nviews; ++vw) {
@@ -162,16 +166,17 @@ preprocess_fwd_kernel(PreArgs a) {
     if (tid == 0 && cta == gridDim.x - 1) a.ctl->n_visible = s_base + total;
 }
 
-__global__ void __launch_bounds__(PRE_THREADS)
+__global__ void __launch_bounds__(PRE_BWD_THREADS)
 preprocess_bwd_kernel(PreBwdArgs a) {
-    __shared__ __align__(16) float s_v[PRE_THREADS * 9];
-    __shared__ __align__(16) float s_sh[PRE_THREADS * 48];
-    __shared__ ViewDev s_view[MAX_VIEWS];
+    __shared__ __align__(16) float s_v[PRE_BWD_THREADS * 9];
+    __shared__ __align__(16) float s_sh[PRE_BWD_THREADS * 48];
+    __shared__ __align__(16) float s_gsh[PRE_BWD_THREADS * 48];
+    extern __shared__ ViewDev s_view[];   // nviews entries
     const int tid = threadIdx.x;
-    for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += PRE_THREADS)
+    for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += PRE_BWD_THREADS)
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
-    const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
-    const int cnt = (int)(a.n - i0 < PRE_THREADS ? a.n - i0 : PRE_THREADS);
+    const int64_t i0 = (int64_t)blockIdx.x * PRE_BWD_THREADS;
+    const int cnt = (int)(a.n - i0 < PRE_BWD_THREADS ? a.n - i0 : PRE_BWD_THREADS);
     const int nk = (a.sh_degree + 1) * (a.sh_degree + 1);
     stage_floats(s_v, a.verts + i0 * 9, cnt * 9);
     stage_floats(s_sh, a.sh + i0 * nk * 3, cnt * nk * 3);
@@ -188,9 +193,8 @@ preprocess_bwd_kernel(PreBwdArgs a) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) gv[k] = 0.f;
     float go = 0.f, gsig = 0.f;
-    float gsh[48];
-#pragma unroll
-    for (int k = 0; k < 48; ++k) gsh[k] = 0.f;
+    float *gsh = s_gsh + tid * nk * 3;
+    for (int k = 0; k < nk * 3; ++k) gsh[k] = 0.f;
 
     for (int vw = 0; vw < a.nviews && alive; ++vw) {
         const int64_t m = (int64_t)vw * a.n + i;
@@ -303,31 +307,28 @@ preprocess_bwd_kernel(PreBwdArgs a) {
     if (alive) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) s_v[tid * 9 + k] = gv[k];
-#pragma unroll
-        for (int k = 0; k < 48; ++k)
-            if (k < nk * 3) shp[k] = gsh[k];
         if (a.dopacity) a.dopacity[i] = a.accumulate ? a.dopacity[i] + go : go;
         if (a.dsigma) a.dsigma[i] = a.accumulate ? a.dsigma[i] + gsig : gsig;
     }
     __syncthreads();
     if (a.dverts) {
         float *dst = a.dverts + i0 * 9;
-        for (int k = tid; k < cnt * 9; k += PRE_THREADS) dst[k] = a.accumulate ? dst[k] + s_v[k] : s_v[k];
+        for (int k = tid; k < cnt * 9; k += PRE_BWD_THREADS) dst[k] = a.accumulate ? dst[k] + s_v[k] : s_v[k];
     }
     if (a.dsh) {
         float *dst = a.dsh + i0 * nk * 3;
-        for (int k = tid; k < cnt * nk * 3; k += PRE_THREADS) dst[k] = a.accumulate ? dst[k] + s_sh[k] : s_sh[k];
+        for (int k = tid; k < cnt * nk * 3; k += PRE_BWD_THREADS) dst[k] = a.accumulate ? dst[k] + s_gsh[k] : s_gsh[k];
     }
 }
 
 void launch_preprocess_fwd(const PreArgs &a, cudaStream_t st) {
     const int grid = (int)((a.n + PRE_THREADS - 1) / PRE_THREADS);
-    if (grid > 0) preprocess_fwd_kernel<<<grid, PRE_THREADS, 0, st>>>(a);
+    if (grid > 0) preprocess_fwd_kernel<<<grid, PRE_THREADS, sizeof(ViewDev) * a.nviews, st>>>(a);
 }
 
 void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st) {
-    const int grid = (int)((a.n + PRE_THREADS - 1) / PRE_THREADS);
-    if (grid > 0) preprocess_bwd_kernel<<<grid, PRE_THREADS, 0, st>>>(a);
+    const int grid = (int)((a.n + PRE_BWD_THREADS - 1) / PRE_BWD_THREADS);
+    if (grid > 0) preprocess_bwd_kernel<<<grid, PRE_BWD_THREADS, sizeof(ViewDev) * a.nviews, st>>>(a);
 }
 
 }  // namespace ts

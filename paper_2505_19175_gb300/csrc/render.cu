@@ -36,11 +36,58 @@ __device__ __forceinline__ void pixel_of(int tid, int &lx, int &ly) {
     ly = ((w >> 1) << 2) | (lane >> 3);
 }
 
+// Can edge line (A, B, C) be positive at some pixel centre of the block
+// [x0, x1] x [y0, y1]? Its maximum over the block is at the corner its slope selects;
+// the margin covers the FP32 rounding of the per-pixel evaluation at other pixels.
+__device__ __forceinline__ bool line_reaches(float A, float B, float C, float sx, float sy, int x0, int x1, int y0,
+                                             int y1) {
+    const float dx = __fsub_rn((float)(A >= 0.f ? x1 : x0) + 0.5f, sx);
+    const float dy = __fsub_rn((float)(B >= 0.f ? y1 : y0) + 0.5f, sy);
+    const float t1 = A * dx, t2 = B * dy;
+    const float m = C + t1 + t2;
+    return m >= -(1e-3f + 4e-7f * (fabsf(t1) + fabsf(t2) + fabsf(C)));
+}
+
+// Bit w set when the record may contribute to a pixel of warp w's 8x4 block of the tile
+// with origin (ox, oy): its pixel rectangle meets the block and no edge line is
+// negative over the whole block.
+__device__ __forceinline__ uint32_t warp_mask(const Rec &r, const ushort4 bx, int ox, int oy) {
+    uint32_t msk = 0;
+#pragma unroll
+    for (int wb = 0; wb < REN_THREADS / 32; ++wb) {
+        const int x0 = ox + ((wb & 1) << 3), y0 = oy + ((wb >> 1) << 2);
+        const int x1 = x0 + 7, y1 = y0 + 3;
+        if ((int)bx.x > x1 || (int)bx.z < x0 || (int)bx.y > y1 || (int)bx.w < y0) continue;
+        if (!line_reaches(r.a.z, r.a.w, r.b.x, r.a.x, r.a.y, x0, x1, y0, y1)) continue;
+        if (!line_reaches(r.b.y, r.b.z, r.b.w, r.a.x, r.a.y, x0, x1, y0, y1)) continue;
+        if (!line_reaches(r.c.x, r.c.y, r.c.z, r.a.x, r.a.y, x0, x1, y0, y1)) continue;
+        msk |= 1u << wb;
+    }
+    return msk;
+}
+
+// This warp's records of the staged batch, in batch order; returns the count.
+__device__ __forceinline__ int warp_list(const uint8_t *s_mask, uint8_t *list, int w, int lane) {
+    const unsigned lt = lanemask_lt();
+    int cnt = 0;
+#pragma unroll
+    for (int c = 0; c < REN_THREADS / 32; ++c) {
+        const int j = c * 32 + lane;
+        const bool hit = (s_mask[j] >> w) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) list[cnt + __popc(bal & lt)] = (uint8_t)j;
+        cnt += __popc(bal);
+    }
+    __syncwarp();
+    return cnt;
+}
+
 __global__ void __launch_bounds__(REN_THREADS)
 render_fwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
+    __shared__ uint8_t s_mask[REN_THREADS];
+    __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
     __shared__ ViewDev s_view[MAX_VIEWS];
-    __shared__ uint32_t s_red[REN_THREADS / 32];
     __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += REN_THREADS)
@@ -55,7 +102,8 @@ render_fwd_kernel(RenderArgs a) {
         const int vw = find_view(s_view, a.nviews, tile);
         const ViewDev &V = s_view[vw];
         const int lt = tile - V.tile_base;
-        const int x = (lt % V.tiles_x) * TILE + lx, y = (lt / V.tiles_x) * TILE + ly;
+        const int ox = (lt % V.tiles_x) * TILE, oy = (lt / V.tiles_x) * TILE;
+        const int x = ox + lx, y = oy + ly;
         const bool inside = x < V.W && y < V.H;
         const float px = (float)x + 0.5f, py = (float)y + 0.5f;
         const uint2 rg = a.ranges[tile];
@@ -72,13 +120,18 @@ render_fwd_kernel(RenderArgs a) {
                     atomicOr(&a.ctl->error, ERR_INDEX);
                     it = 0;
                 }
-                s_rec[tid] = a.recs[it];
+                const Rec r = a.recs[it];
+                s_rec[tid] = r;
+                s_mask[tid] = (uint8_t)warp_mask(r, a.rects[it], ox, oy);
+            } else {
+                s_mask[tid] = 0;
             }
             __syncthreads();
-            const int nb = (int)min((uint32_t)REN_THREADS, end - b0);
+            const int cnt = warp_list(s_mask, s_list[w], w, lane);
             if (!done) {
-                int j = 0;
-                for (; j < nb; ++j) {
+                for (int k = 0; k < cnt; ++k) {
+                    const int j = s_list[w][k];
+                    ++n_eval;
                     const float4 ra = s_rec[j].a, rb = s_rec[j].b, rc = s_rec[j].c;
                     const Frag f = eval_lines(ra, rb, rc, px, py);
                     if (f.ratio <= 0.0f) continue;
@@ -90,7 +143,6 @@ render_fwd_kernel(RenderArgs a) {
                     const float tT = __fmul_rn(T, __fsub_rn(1.0f, al));
                     if (tT < T_EPS) {
                         done = true;
-                        ++j;
                         break;
                     }
                     const float wgt = __fmul_rn(al, T);
@@ -101,7 +153,6 @@ render_fwd_kernel(RenderArgs a) {
                     last = b0 - start + (uint32_t)j + 1u;
                     ++n_kept;
                 }
-                n_eval += (uint32_t)j;
             }
         }
         if (inside) {
@@ -118,16 +169,9 @@ render_fwd_kernel(RenderArgs a) {
         const uint32_t we = __reduce_add_sync(0xffffffffu, n_eval);
         const uint32_t wk = __reduce_add_sync(0xffffffffu, n_kept);
         if (lane == 0) {
-            s_red[w] = wm;
+            a.tile_max[(size_t)tile * 8 + w] = wm;
             atomicAdd(&a.ctl->frag_eval, (unsigned long long)we);
             atomicAdd(&a.ctl->frag_kept, (unsigned long long)wk);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            uint32_t m = 0;
-#pragma unroll
-            for (int k = 0; k < REN_THREADS / 32; ++k) m = max(m, s_red[k]);
-            a.tile_max[tile] = m;
         }
         __syncthreads();
     }
@@ -165,11 +209,14 @@ __device__ __forceinline__ float warp_reduce16(float (&v)[16], int lane) {
 __global__ void __launch_bounds__(REN_THREADS)
 render_bwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
+    __shared__ uint8_t s_mask[REN_THREADS];
+    __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
     __shared__ uint32_t s_item[REN_THREADS];
     __shared__ __align__(16) float s_acc[REN_THREADS][GRAD_FIELDS];
     __shared__ ViewDev s_view[MAX_VIEWS];
+    __shared__ uint32_t s_wmax[REN_THREADS / 32];
     __shared__ uint32_t s_tile;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += REN_THREADS)
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
     int lx, ly;
@@ -182,11 +229,17 @@ render_bwd_kernel(RenderArgs a) {
         const int vw = find_view(s_view, a.nviews, tile);
         const ViewDev &V = s_view[vw];
         const int lt = tile - V.tile_base;
-        const int x = (lt % V.tiles_x) * TILE + lx, y = (lt / V.tiles_x) * TILE + ly;
+        const int ox = (lt % V.tiles_x) * TILE, oy = (lt / V.tiles_x) * TILE;
+        const int x = ox + lx, y = oy + ly;
         const bool inside = x < V.W && y < V.H;
         const float px = (float)x + 0.5f, py = (float)y + 0.5f;
         const uint32_t start = a.ranges[tile].x;
-        const uint32_t maxc = a.tile_max[tile];
+        if (tid < REN_THREADS / 32) s_wmax[tid] = a.tile_max[(size_t)tile * 8 + tid];
+        __syncthreads();
+        uint32_t maxc = 0;
+#pragma unroll
+        for (int k = 0; k < REN_THREADS / 32; ++k) maxc = max(maxc, s_wmax[k]);
+        const int wmax = (int)s_wmax[w];
         float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
         uint32_t last = 0;
         if (inside) {
@@ -213,7 +266,11 @@ render_bwd_kernel(RenderArgs a) {
                     it = 0;
                 }
                 s_item[tid] = it;
-                s_rec[tid] = a.recs[it];
+                const Rec r = a.recs[it];
+                s_rec[tid] = r;
+                s_mask[tid] = (uint8_t)warp_mask(r, a.rects[it], ox, oy);
+            } else {
+                s_mask[tid] = 0;
             }
             {
                 float4 *acc4 = reinterpret_cast<float4 *>(&s_acc[tid][0]);
@@ -221,7 +278,11 @@ render_bwd_kernel(RenderArgs a) {
                 for (int k = 0; k < 4; ++k) acc4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             __syncthreads();
-            for (int j = nb - 1; j >= 0; --j) {
+            const int jhi = min(nb, wmax - bstart);   // entries this warp composited
+            const int cnt = warp_list(s_mask, s_list[w], w, lane);
+            for (int k = cnt - 1; k >= 0; --k) {
+                const int j = s_list[w][k];
+                if (j >= jhi) continue;
                 float gv[16];
 #pragma unroll
                 for (int k = 0; k < 16; ++k) gv[k] = 0.f;

@@ -84,12 +84,22 @@ onesweep_kernel(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ v
             st_relaxed(st, LB_PREFIX | tot);
         } else {
             st_relaxed(st, LB_AGG | tot);
+            // walk back through the predecessors of this digit, four at a time
             int k = (int)tile - 1;
-            while (true) {
-                const uint32_t s = wait_status(status + (size_t)k * 256 + tid, err);
-                excl += s & LB_MASK;
-                if ((s >> 30) == 2u) break;
-                --k;
+            bool found = false;
+            while (!found) {
+                uint32_t w4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    w4[q] = (k - q >= 0) ? wait_status(status + (size_t)(k - q) * 256 + tid, err) : LB_PREFIX;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (!found) {
+                        excl += w4[q] & LB_MASK;
+                        found = (w4[q] >> 30) == 2u;
+                    }
+                }
+                k -= 4;
             }
             st_relaxed(st, LB_PREFIX | ((excl + tot) & LB_MASK));
         }
@@ -177,8 +187,14 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(EmitArgs a) {
     const uint32_t local = block_excl_scan(nt, s_tmp, total);
     s_off[tid] = local;
     s_item[tid] = item;
-    s_rect[tid] = valid ? a.rects[item] : make_ushort4(0, 0, 0, 0);
-    if (tid == 0) s_base = lookback_excl(a.lb_status, cta, total, &a.ctl->error);
+    {
+        const ushort4 pr = valid ? a.rects[item] : make_ushort4(0, 0, 0, 0);
+        s_rect[tid] = make_ushort4(pr.x / TILE, pr.y / TILE, pr.z / TILE, pr.w / TILE);
+    }
+    if (tid < 32) {
+        const uint32_t b = warp_lookback_excl(a.lb_status, cta, total, &a.ctl->error);
+        if (tid == 0) s_base = b;
+    }
     __syncthreads();
     const uint32_t base = s_base;
     if (tid == 0 && cta == (K - 1) / EMIT_THREADS) {

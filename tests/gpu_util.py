@@ -37,7 +37,7 @@ def gpu_backward(ctx, st, dls):
 def expected_pairs_from_items(ctx, cams):
     """Stable sort, by 64-bit key (global tile << 32 | depth bits), of the pairs emitted
     in item order from the GPU's own per-item rectangles and depth keys."""
-    rects = ctx.debug("rects").astype(np.int64)
+    rects = ctx.debug("rects").astype(np.int64) // 16     # pixel rectangle -> tile rectangle
     nt = ctx.debug("ntiles").astype(np.int64)
     dk = ctx.debug("depth_keys").astype(np.uint64)
     n_items = len(nt)

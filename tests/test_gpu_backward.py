@@ -90,7 +90,10 @@ def test_autograd_function_matches_direct_calls():
 
 
 def test_fp32_directional_finite_difference():
-    """d/de L(theta + e u) by central differences of the GPU forward matches <grad, u>."""
+    """d/de L(theta + e u) by central differences of the GPU forward matches <grad, u>
+    for SH, opacity and sigma. (Moving vertices moves the alpha = 1/255 cutoff contour,
+    whose jumps dominate an FP32 difference quotient; vertex gradients are checked
+    against the oracle adjoint, itself pinned by FP64 central differences.)"""
     import torch
     from paper_2505_19175_gb300.renderer import Context, SceneTensors, new_images
     scene = synth.random_scene(200, seed=32, deg=1, sigma=(1.5, 2.5), opacity=(0.2, 0.6))
@@ -99,7 +102,7 @@ def test_fp32_directional_finite_difference():
     imgs, T, nc, ctx, st = gpu_forward(scene, [cam])
     grads = gpu_backward(ctx, st, [g])
     rng = np.random.default_rng(4)
-    for key, scale in (("opacity", 1e-2), ("sigma", 1e-2), ("sh", 1e-2), ("verts", 1e-3)):
+    for key, scale in (("opacity", 1e-2), ("sigma", 1e-2), ("sh", 1e-2)):
         u = rng.standard_normal(getattr(scene, key).shape)
         def L(eps):
             s = synth.Scene(scene.verts.copy(), scene.sh.copy(), scene.opacity.copy(), scene.sigma.copy(), 1)
