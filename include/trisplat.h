@@ -39,6 +39,12 @@
  *     tri_ctx_check reads back (that call synchronises the stream).
  *   Threads: a context is not thread-safe; use one per host thread.
  *   Streams: cudaStream_t values are passed as void* (0 = legacy default stream).
+ *   CUDA graphs: tri_preprocess, tri_bin_sort (with num_pairs_out = NULL),
+ *     tri_render_fwd, tri_render_bwd, tri_preprocess_bwd and tri_loss_l1 may be
+ *     captured once the context's buffers are sized by an eager run of the same
+ *     workload (a capture allocates nothing). A replay re-reads the context's pinned
+ *     copies of its camera and output-pointer tables, written by its most recent
+ *     captured call of each kind (eager calls do not touch them).
  */
 #ifndef TRISPLAT_H
 #define TRISPLAT_H

@@ -34,12 +34,15 @@ struct tri_ctx {
     int64_t pair_cap = 0;
     int stage = 0;  // 1 preprocessed, 2 sorted, 3 rendered, 4 backward rendered
     int pair_final = 0;
+    // pinned copies of the small per-call tables, used while the stream is captured
+    ViewDev *h_views = nullptr;
+    ViewOut *h_outs_fwd = nullptr, *h_outs_bwd = nullptr;
     DevBuf views_d, outs_fwd, outs_bwd, ctl, recs, ntiles, rects, dkeys, ck[2], cv[2], pk[2], pv[2], ranges,
-        tile_max, Tfin, ncontrib, grad2d, st_pre, st_emit, st_depth, st_pairs;
+        tile_max, Tfin, ncontrib, grad2d, st_emit, st_depth, st_pairs;
     std::vector<DevBuf *> all() {
         return {&views_d, &outs_fwd, &outs_bwd, &ctl, &recs, &ntiles, &rects, &dkeys, &ck[0], &ck[1], &cv[0],
                 &cv[1], &pk[0], &pk[1], &pv[0], &pv[1], &ranges, &tile_max, &Tfin, &ncontrib, &grad2d,
-                &st_pre, &st_emit, &st_depth, &st_pairs};
+                &st_emit, &st_depth, &st_pairs};
     }
 };
 
@@ -169,6 +172,22 @@ tri_status build_views(tri_ctx *c, const tri_camera *cams, int nviews, std::vect
 
 size_t sort_status_words(int64_t cap) { return (size_t)((cap + SORT_TILE - 1) / SORT_TILE) * 256; }
 
+// Host -> device copy of a small per-call table. Outside stream capture the driver
+// stages the pageable source, so the caller may reuse it at once. Under capture the
+// copy node must read memory that outlives the call: the context's pinned buffer,
+// which a replay re-reads (the tables of the most recent captured call of this kind).
+tri_status upload(tri_ctx *c, void *dst, const void *src, size_t bytes, void *pinned, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusActive) {
+        memcpy(pinned, src, bytes);
+        CK(cudaMemcpyAsync(dst, pinned, bytes, cudaMemcpyHostToDevice, st));
+    } else {
+        CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    }
+    return TRI_OK;
+}
+
 tri_status launch_check(tri_ctx *c, const char *what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, what);
@@ -211,7 +230,19 @@ tri_status tri_ctx_create(tri_ctx **out, int device) {
     }
     tri_ctx *c = new tri_ctx();
     c->device = device;
-    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != device) cudaSetDevice(device);
+    bool ok = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
+              cudaMallocHost((void **)&c->h_views, sizeof(ViewDev) * MAX_VIEWS) == cudaSuccess &&
+              cudaMallocHost((void **)&c->h_outs_fwd, sizeof(ViewOut) * MAX_VIEWS) == cudaSuccess &&
+              cudaMallocHost((void **)&c->h_outs_bwd, sizeof(ViewOut) * MAX_VIEWS) == cudaSuccess;
+    if (cur >= 0 && cur != device) cudaSetDevice(cur);
+    if (!ok) {
+        cudaGetLastError();
+        if (c->h_views) cudaFreeHost(c->h_views);
+        if (c->h_outs_fwd) cudaFreeHost(c->h_outs_fwd);
+        if (c->h_outs_bwd) cudaFreeHost(c->h_outs_bwd);
         delete c;
         return TRI_ERR_CUDA;
     }
@@ -227,6 +258,9 @@ void tri_ctx_destroy(tri_ctx *c) {
     cudaDeviceSynchronize();
     for (DevBuf *b : c->all())
         if (b->p) cudaFree(b->p);
+    if (c->h_views) cudaFreeHost(c->h_views);
+    if (c->h_outs_fwd) cudaFreeHost(c->h_outs_fwd);
+    if (c->h_outs_bwd) cudaFreeHost(c->h_outs_bwd);
     if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
     delete c;
 }
@@ -305,11 +339,8 @@ tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *
     ENSURE(c->tile_max, 4 * 8 * (size_t)tiles);
     ENSURE(c->Tfin, 4 * (size_t)pix);
     ENSURE(c->ncontrib, 4 * (size_t)pix);
-    const int64_t pre_ctas = (scene->n + 127) / 128;
-    ENSURE(c->st_pre, 4 * (size_t)(pre_ctas + 1));
-    CK(cudaMemcpyAsync(c->views_d.p, views.data(), sizeof(ViewDev) * nviews, cudaMemcpyHostToDevice, st));
+    if ((s = upload(c, c->views_d.p, views.data(), sizeof(ViewDev) * nviews, c->h_views, st)) != TRI_OK) return s;
     CK(cudaMemsetAsync(c->ctl.p, 0, sizeof(Ctl), st));
-    CK(cudaMemsetAsync(c->st_pre.p, 0, 4 * (size_t)(pre_ctas + 1), st));
     if (M > 0) {
         PreArgs a;
         a.verts = scene->verts;
@@ -324,9 +355,6 @@ tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *
         a.ntiles = P<uint32_t>(c->ntiles);
         a.rects = P<ushort4>(c->rects);
         a.dkeys = P<uint32_t>(c->dkeys);
-        a.ckeys = P<uint32_t>(c->ck[0]);
-        a.cvals = P<uint32_t>(c->cv[0]);
-        a.lb_status = P<uint32_t>(c->st_pre);
         a.ctl = ctl_of(c);
         launch_preprocess_fwd(a, st);
         if ((s = launch_check(c, "preprocess_fwd_kernel")) != TRI_OK) return s;
@@ -353,11 +381,15 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
     ENSURE(c->st_depth, 4 * dwords * 4);
     CK(cudaMemsetAsync(c->st_depth.p, 0, 4 * dwords * 4, st));
     const int gd = onesweep_grid(c->sms, (uint32_t)(M > 0 ? M : 1));
-    int cur = 0;
+    // all items take part (invisible ones carry the largest key and end up last), so
+    // the first pass reads the per-item keys and numbers the values itself
+    int cur = 1;
     for (int p = 0; p < 4; ++p) {
-        launch_onesweep_pass(P<uint32_t>(c->ck[cur]), P<uint32_t>(c->cv[cur]), P<uint32_t>(c->ck[cur ^ 1]),
-                             P<uint32_t>(c->cv[cur ^ 1]), &ctl->n_visible, (uint32_t)M, ctl->depth_hist[p],
-                             P<uint32_t>(c->st_depth) + p * dwords, &ctl->pass_counter[p], 8 * p, &ctl->error, gd, st);
+        const uint32_t *kin = p == 0 ? P<uint32_t>(c->dkeys) : P<uint32_t>(c->ck[cur ^ 1]);
+        const uint32_t *vin = p == 0 ? nullptr : P<uint32_t>(c->cv[cur ^ 1]);
+        launch_onesweep_pass(kin, vin, P<uint32_t>(c->ck[cur]), P<uint32_t>(c->cv[cur]), nullptr, (uint32_t)M,
+                             ctl->depth_hist[p], P<uint32_t>(c->st_depth) + p * dwords, &ctl->pass_counter[p],
+                             8 * p, &ctl->error, gd, st);
         cur ^= 1;
     }
     if ((s = launch_check(c, "onesweep (depth)")) != TRI_OK) return s;
@@ -443,7 +475,8 @@ tri_status tri_render_fwd(tri_ctx *c, float *const *images, float *const *T_fina
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<ViewOut> outs(c->nviews);
     for (int v = 0; v < c->nviews; ++v) outs[v] = ViewOut{images[v], nullptr};
-    CK(cudaMemcpyAsync(c->outs_fwd.p, outs.data(), sizeof(ViewOut) * c->nviews, cudaMemcpyHostToDevice, st));
+    if ((s = upload(c, c->outs_fwd.p, outs.data(), sizeof(ViewOut) * c->nviews, c->h_outs_fwd, st)) != TRI_OK)
+        return s;
     CK(cudaMemsetAsync(&ctl_of(c)->work_counter[0], 0, 4, st));
     CK(cudaMemsetAsync(&ctl_of(c)->frag_eval, 0, 16, st));
     launch_render_fwd(render_args(c, c->outs_fwd), c->sms, st);
@@ -473,7 +506,8 @@ tri_status tri_render_bwd(tri_ctx *c, const float *const *dL, void *stream) {
     std::vector<ViewOut> outs(c->nviews);
     for (int v = 0; v < c->nviews; ++v) outs[v] = ViewOut{nullptr, dL[v]};
     ENSURE(c->grad2d, sizeof(float) * GRAD_FIELDS * (size_t)c->n_items);
-    CK(cudaMemcpyAsync(c->outs_bwd.p, outs.data(), sizeof(ViewOut) * c->nviews, cudaMemcpyHostToDevice, st));
+    if ((s = upload(c, c->outs_bwd.p, outs.data(), sizeof(ViewOut) * c->nviews, c->h_outs_bwd, st)) != TRI_OK)
+        return s;
     CK(cudaMemsetAsync(c->grad2d.p, 0, sizeof(float) * GRAD_FIELDS * (size_t)c->n_items, st));
     CK(cudaMemsetAsync(&ctl_of(c)->work_counter[1], 0, 4, st));
     launch_render_bwd(render_args(c, c->outs_bwd), c->sms, st);

@@ -14,9 +14,7 @@ struct PreArgs {
     Rec *recs;
     uint32_t *ntiles;
     ushort4 *rects;            // pixel rectangle (x0, y0, x1, y1), inclusive
-    uint32_t *dkeys;
-    uint32_t *ckeys, *cvals;   // compacted (depth key, item id) of visible items
-    uint32_t *lb_status;       // one word per CTA, zeroed
+    uint32_t *dkeys;           // depth key per item; 0xffffffff for items with no tile
     Ctl *ctl;
 };
 
@@ -41,7 +39,8 @@ constexpr int SORT_IPT = 15;                          // keys per thread
 constexpr int SORT_TILE = SORT_THREADS * SORT_IPT;    // keys per CTA tile
 
 // One stable 8-bit LSD pass over (key, value) pairs. `count` lives on the device and
-// is clamped to `cap`; `hist` is this digit's 256-bin histogram over all keys;
+// is clamped to `cap` (null: `cap` keys); `vin` null means value = index;
+// `hist` is this digit's 256-bin histogram over all keys;
 // `status` has room for ceil(cap / SORT_TILE) x 256 words and is zeroed.
 void launch_onesweep_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                           const uint32_t *count, uint32_t cap, const uint32_t *hist, uint32_t *status,

@@ -27,6 +27,33 @@ __device__ __forceinline__ void stage_floats(float *dst, const float *src, int c
     for (int k = (n4 << 2) + threadIdx.x; k < count; k += blockDim.x) dst[k] = __ldg(src + k);
 }
 
+// Per-thread stride in shared memory for records of `len` floats: odd, so that the 32
+// lanes reading element k of their own record hit 32 different banks.
+__host__ __device__ __forceinline__ int odd_stride(int len) { return len | 1; }
+
+// Stage records of `len` floats (count of them, contiguous in global memory) into
+// shared memory at stride odd_stride(len), with coalesced float4 global loads.
+__device__ __forceinline__ void stage_records(float *dst, const float *src, int count, int len) {
+    const int stride = odd_stride(len);
+    const int total = count * len;
+    const int n4 = total >> 2;
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    for (int k = threadIdx.x; k < n4; k += blockDim.x) {
+        const float4 v = __ldg(s4 + k);
+        const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int f = 4 * k + q;
+            const int r = f / len;
+            dst[r * stride + (f - r * len)] = e[q];
+        }
+    }
+    for (int f = (n4 << 2) + threadIdx.x; f < total; f += blockDim.x) {
+        const int r = f / len;
+        dst[r * stride + (f - r * len)] = __ldg(src + f);
+    }
+}
+
 __device__ __forceinline__ int clamp_pix(float v, int n) {
     v = fminf(fmaxf(v, -2.0f), (float)n + 2.0f);
     return (int)v;
@@ -35,24 +62,21 @@ __device__ __forceinline__ int clamp_pix(float v, int n) {
 __global__ void __launch_bounds__(PRE_THREADS, 6)
 preprocess_fwd_kernel(PreArgs a) {
     __shared__ __align__(16) float s_v[PRE_THREADS * 9];
-    __shared__ __align__(16) float s_sh[PRE_THREADS * 48];
+    __shared__ __align__(16) float s_sh[PRE_THREADS * 49];
     __shared__ uint32_t s_hist[4][256];
-    __shared__ uint32_t s_scan[33];
-    __shared__ uint32_t s_cta, s_base;
+    __shared__ uint32_t s_nvis;
     extern __shared__ ViewDev s_view[];   // nviews entries
 
     const int tid = threadIdx.x;
-    if (tid == 0) s_cta = atomicAdd(&a.ctl->cta_counter[0], 1u);
     for (int k = tid; k < 4 * 256; k += PRE_THREADS) (&s_hist[0][0])[k] = 0u;
+    if (tid == 0) s_nvis = 0;
     for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += PRE_THREADS)
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
-    __syncthreads();
-    const uint32_t cta = s_cta;
-    const int64_t i0 = (int64_t)cta * PRE_THREADS;
+    const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
     const int cnt = (int)(a.n - i0 < PRE_THREADS ? a.n - i0 : PRE_THREADS);
     const int nk = (a.sh_degree + 1) * (a.sh_degree + 1);
     stage_floats(s_v, a.verts + i0 * 9, cnt * 9);
-    stage_floats(s_sh, a.sh + i0 * nk * 3, cnt * nk * 3);
+    stage_records(s_sh, a.sh + i0 * nk * 3, cnt, nk * 3);
     __syncthreads();
 
     const int64_t i = i0 + tid;
@@ -62,13 +86,12 @@ preprocess_fwd_kernel(PreArgs a) {
     for (int k = 0; k < 9; ++k) v[k] = s_v[tid * 9 + k];
     const float o = alive ? __ldg(a.opacity + i) : 1.0f;
     const float sig = alive ? __ldg(a.sigma + i) : 1.0f;
-    const float *shp = s_sh + tid * nk * 3;
+    const float *shp = s_sh + tid * odd_stride(nk * 3);
     // shrink factor of the tight rectangle (Supp. "Tile assignment")
     const float fshrink = 1.0f - powf(ALPHA_MIN / o, 1.0f / sig);
     const float cen[3] = {(v[0] + v[3] + v[6]) * (1.0f / 3.0f), (v[1] + v[4] + v[7]) * (1.0f / 3.0f),
                           (v[2] + v[5] + v[8]) * (1.0f / 3.0f)};
 
-    uint64_t vis = 0;
     uint32_t nvis = 0;
     for (int vw = 0; vw < a.nviews; ++vw) {
         if (!alive) break;
@@ -99,6 +122,7 @@ preprocess_fwd_kernel(PreArgs a) {
                 nt = (uint32_t)(px1 / TILE - px0 / TILE + 1) * (uint32_t)(py1 / TILE - py0 / TILE + 1);
             }
         }
+        uint32_t key = 0xffffffffu;   // invisible items sort after every depth
         if (nt > 0) {
             // incenter s = q0 + S in double-float; lines re-based on s_hi
             ff sx = two_sum(g.u0.hi, g.S.x);
@@ -126,51 +150,31 @@ preprocess_fwd_kernel(PreArgs a) {
             rec.b = make_float4(C[0], g.A[1], g.B[1], C[1]);
             rec.c = make_float4(g.A[2], g.B[2], C[2], o);
             rec.d = make_float4(sig, col[0], col[1], col[2]);
-            vis |= 1ull << vw;
+            key = __float_as_uint(g.depth);
             ++nvis;
         }
         a.recs[m] = rec;
         a.ntiles[m] = nt;
         a.rects[m] = rect;
-        a.dkeys[m] = __float_as_uint(g.depth);
-    }
-
-    // order-preserving compaction: (triangle, view) order, hence by triangle within a view
-    uint32_t total;
-    uint32_t local = block_excl_scan(nvis, s_scan, total);
-    if (tid < 32) {
-        const uint32_t b = warp_lookback_excl(a.lb_status, cta, total, &a.ctl->error);
-        if (tid == 0) s_base = b;
-    }
-    __syncthreads();
-    uint32_t pos = s_base + local;
-    for (int vw = 0; vw < a.nviews; ++vw) {
-        if (!((vis >> vw) & 1ull)) continue;
-        const int64_t m = (int64_t)vw * a.n + i;
-        const uint32_t key = a.dkeys[m];
-        if ((int64_t)pos >= a.n * a.nviews) {
-            atomicOr(&a.ctl->error, ERR_INDEX);
-            break;
-        }
-        a.ckeys[pos] = key;
-        a.cvals[pos] = (uint32_t)m;
-        ++pos;
+        a.dkeys[m] = key;
 #pragma unroll
         for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
     }
+    const uint32_t wv = __reduce_add_sync(0xffffffffu, nvis);
+    if ((tid & 31) == 0 && wv) atomicAdd(&s_nvis, wv);
     __syncthreads();
     for (int k = tid; k < 4 * 256; k += PRE_THREADS) {
-        uint32_t c = (&s_hist[0][0])[k];
+        const uint32_t c = (&s_hist[0][0])[k];
         if (c) atomicAdd(&(&a.ctl->depth_hist[0][0])[k], c);
     }
-    if (tid == 0 && cta == gridDim.x - 1) a.ctl->n_visible = s_base + total;
+    if (tid == 0 && s_nvis) atomicAdd(&a.ctl->n_visible, s_nvis);
 }
 
 __global__ void __launch_bounds__(PRE_BWD_THREADS)
 preprocess_bwd_kernel(PreBwdArgs a) {
     __shared__ __align__(16) float s_v[PRE_BWD_THREADS * 9];
-    __shared__ __align__(16) float s_sh[PRE_BWD_THREADS * 48];
-    __shared__ __align__(16) float s_gsh[PRE_BWD_THREADS * 48];
+    __shared__ __align__(16) float s_sh[PRE_BWD_THREADS * 49];
+    __shared__ __align__(16) float s_gsh[PRE_BWD_THREADS * 49];
     extern __shared__ ViewDev s_view[];   // nviews entries
     const int tid = threadIdx.x;
     for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += PRE_BWD_THREADS)
@@ -179,21 +183,22 @@ preprocess_bwd_kernel(PreBwdArgs a) {
     const int cnt = (int)(a.n - i0 < PRE_BWD_THREADS ? a.n - i0 : PRE_BWD_THREADS);
     const int nk = (a.sh_degree + 1) * (a.sh_degree + 1);
     stage_floats(s_v, a.verts + i0 * 9, cnt * 9);
-    stage_floats(s_sh, a.sh + i0 * nk * 3, cnt * nk * 3);
+    stage_records(s_sh, a.sh + i0 * nk * 3, cnt, nk * 3);
     __syncthreads();
     const int64_t i = i0 + tid;
     const bool alive = tid < cnt;
     float v[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) v[k] = s_v[tid * 9 + k];
-    float *shp = s_sh + tid * nk * 3;
+    const int sstride = odd_stride(nk * 3);
+    float *shp = s_sh + tid * sstride;
     const float cen[3] = {(v[0] + v[3] + v[6]) * (1.0f / 3.0f), (v[1] + v[4] + v[7]) * (1.0f / 3.0f),
                           (v[2] + v[5] + v[8]) * (1.0f / 3.0f)};
     float gv[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) gv[k] = 0.f;
     float go = 0.f, gsig = 0.f;
-    float *gsh = s_gsh + tid * nk * 3;
+    float *gsh = s_gsh + tid * sstride;
     for (int k = 0; k < nk * 3; ++k) gsh[k] = 0.f;
 
     for (int vw = 0; vw < a.nviews && alive; ++vw) {
@@ -316,8 +321,13 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         for (int k = tid; k < cnt * 9; k += PRE_BWD_THREADS) dst[k] = a.accumulate ? dst[k] + s_v[k] : s_v[k];
     }
     if (a.dsh) {
-        float *dst = a.dsh + i0 * nk * 3;
-        for (int k = tid; k < cnt * nk * 3; k += PRE_BWD_THREADS) dst[k] = a.accumulate ? dst[k] + s_gsh[k] : s_gsh[k];
+        const int len = nk * 3;
+        float *dst = a.dsh + i0 * len;
+        for (int f = tid; f < cnt * len; f += PRE_BWD_THREADS) {
+            const int r = f / len;
+            const float g = s_gsh[r * sstride + (f - r * len)];
+            dst[f] = a.accumulate ? dst[f] + g : g;
+        }
     }
 }
 

@@ -206,7 +206,7 @@ __device__ __forceinline__ float warp_reduce16(float (&v)[16], int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-__global__ void __launch_bounds__(REN_THREADS)
+__global__ void __launch_bounds__(REN_THREADS, 4)
 render_bwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
     __shared__ uint8_t s_mask[REN_THREADS];
@@ -299,12 +299,12 @@ render_bwd_kernel(RenderArgs a) {
                             kept = true;
                             const float al = fminf(araw, ALPHA_MAX);
                             const float om = __fsub_rn(1.0f, al);
-                            T = __fdiv_rn(T, om);
+                            const float iom = rcp_approx(om);
+                            T = T * iom;
                             const float wgt = al * T;
                             gv[10] = g0 * wgt;
                             gv[11] = g1 * wgt;
                             gv[12] = g2 * wgt;
-                            const float iom = 1.0f / om;
                             const float galpha = g0 * (rd.y * T - B0 * iom) + g1 * (rd.z * T - B1 * iom) +
                                                  g2 * (rd.w * T - B2 * iom);
                             B0 = fmaf(rd.y, wgt, B0);
@@ -314,7 +314,7 @@ render_bwd_kernel(RenderArgs a) {
                                 const float gI = galpha * rc.w;
                                 gv[8] = galpha * I;                               // d/do
                                 gv[9] = gI * I * lg * 0.69314718055994531f;       // d/dsigma: I ln(ratio)
-                                const float gr = gI * rd.x * I / f.ratio;         // d/dratio
+                                const float gr = gI * rd.x * I * rcp_approx(f.ratio);  // d/dratio
                                 // the active line: lowest index among the minima
                                 const int ia = (f.m0 <= f.m1 && f.m0 <= f.m2) ? 0 : (f.m1 <= f.m2 ? 1 : 2);
                                 const float Aa = ia == 0 ? ra.z : (ia == 1 ? rb.y : rc.x);

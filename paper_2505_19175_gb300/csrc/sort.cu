@@ -33,7 +33,7 @@ onesweep_kernel(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ v
     __shared__ uint32_t s_tile;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const uint32_t n = min(*count_ptr, cap);
+    const uint32_t n = count_ptr ? min(*count_ptr, cap) : cap;
     const uint32_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
     {
         uint32_t tot;
@@ -54,7 +54,7 @@ onesweep_kernel(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ v
             const uint32_t idx = wbase + j * 32 + lane;
             const bool valid = idx < n;
             const uint32_t key = valid ? kin[idx] : 0u;
-            const uint32_t val = valid ? vin[idx] : 0u;
+            const uint32_t val = valid ? (vin ? vin[idx] : idx) : 0u;
             const uint32_t d = valid ? (key >> shift) & 255u : 256u;
             const unsigned peers = __match_any_sync(0xffffffffu, d);
             const int leader = __ffs(peers) - 1;
