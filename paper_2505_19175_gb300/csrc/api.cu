@@ -170,7 +170,7 @@ tri_status build_views(tri_ctx *c, const tri_camera *cams, int nviews, std::vect
     return TRI_OK;
 }
 
-size_t sort_status_words(int64_t cap) { return (size_t)((cap + SORT_TILE - 1) / SORT_TILE) * 256; }
+size_t sort_status_words(int64_t cap, int tile) { return (size_t)((cap + tile - 1) / tile) * 256; }
 
 // Host -> device copy of a small per-call table. Outside stream capture the driver
 // stages the pageable source, so the caller may reuse it at once. Under capture the
@@ -283,7 +283,7 @@ tri_status tri_workspace_query(const tri_scene *scene, const tri_camera *cams, i
     b += (size_t)M * (sizeof(Rec) + 4 + 8 + 4 + 16 + GRAD_FIELDS * 4);  // records, counts, rects, keys, 2x2 lists, grads
     b += (size_t)cap * 16;                                            // 2 x (key, value) pair buffers
     b += (size_t)tiles * (8 + 32) + (size_t)pix * 8;
-    b += sizeof(uint32_t) * (sort_status_words(M) * 4 + sort_status_words(cap) * 3 + (M + 255) / 256 * 2);
+    b += sizeof(uint32_t) * (sort_status_words(M, 1024) * 4 + sort_status_words(cap, 1024) * 3 + (M + 255) / 256 * 2);
     b += sizeof(Ctl) + nviews * (sizeof(ViewDev) + 2 * sizeof(ViewOut));
     *bytes = b;
     return TRI_OK;
@@ -377,10 +377,10 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
     CK(cudaMemsetAsync(&ctl->pass_counter[0], 0, sizeof(ctl->pass_counter), st));
     CK(cudaMemsetAsync(&ctl->tile_hist[0][0], 0, sizeof(ctl->tile_hist), st));
     // 1. depth sort of the visible items (4 x 8-bit passes)
-    const size_t dwords = sort_status_words(M);
+    const int dtile = onesweep_tile((uint32_t)M, c->sms);
+    const size_t dwords = sort_status_words(M, dtile);
     ENSURE(c->st_depth, 4 * dwords * 4);
     CK(cudaMemsetAsync(c->st_depth.p, 0, 4 * dwords * 4, st));
-    const int gd = onesweep_grid(c->sms, (uint32_t)(M > 0 ? M : 1));
     // all items take part (invisible ones carry the largest key and end up last), so
     // the first pass reads the per-item keys and numbers the values itself
     int cur = 1;
@@ -389,7 +389,7 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
         const uint32_t *vin = p == 0 ? nullptr : P<uint32_t>(c->cv[cur ^ 1]);
         launch_onesweep_pass(kin, vin, P<uint32_t>(c->ck[cur]), P<uint32_t>(c->cv[cur]), nullptr, (uint32_t)M,
                              ctl->depth_hist[p], P<uint32_t>(c->st_depth) + p * dwords, &ctl->pass_counter[p],
-                             8 * p, &ctl->error, gd, st);
+                             8 * p, &ctl->error, dtile, c->sms, st);
         cur ^= 1;
     }
     if ((s = launch_check(c, "onesweep (depth)")) != TRI_OK) return s;
@@ -423,16 +423,16 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
         *num_pairs_out = np;
     }
     // 3. tile sort of the pairs
-    const size_t pwords = sort_status_words(c->pair_cap);
+    const int ptile = onesweep_tile((uint32_t)c->pair_cap, c->sms);
+    const size_t pwords = sort_status_words(c->pair_cap, ptile);
     ENSURE(c->st_pairs, 4 * pwords * c->tile_passes);
     CK(cudaMemsetAsync(c->st_pairs.p, 0, 4 * pwords * c->tile_passes, st));
-    const int gp = onesweep_grid(c->sms, (uint32_t)c->pair_cap);
     cur = 0;
     for (int p = 0; p < c->tile_passes; ++p) {
         launch_onesweep_pass(P<uint32_t>(c->pk[cur]), P<uint32_t>(c->pv[cur]), P<uint32_t>(c->pk[cur ^ 1]),
                              P<uint32_t>(c->pv[cur ^ 1]), &ctl->n_pairs_used, (uint32_t)c->pair_cap,
                              ctl->tile_hist[p], P<uint32_t>(c->st_pairs) + p * pwords, &ctl->pass_counter[4 + p],
-                             8 * p, &ctl->error, gp, st);
+                             8 * p, &ctl->error, ptile, c->sms, st);
         cur ^= 1;
     }
     c->pair_final = cur;

@@ -35,17 +35,20 @@ void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st);
 
 // ---- sorting ----
 constexpr int SORT_THREADS = 256;
-constexpr int SORT_IPT = 15;                          // keys per thread
-constexpr int SORT_TILE = SORT_THREADS * SORT_IPT;    // keys per CTA tile
+constexpr int SORT_IPT_MAX = 15;                      // keys per thread, large sorts
+
+// Keys per CTA tile used for a sort of at most `cap` keys: 256 x {4, 8, 15}, so that
+// small sorts still spread over every SM.
+int onesweep_tile(uint32_t cap, int sm_count);
 
 // One stable 8-bit LSD pass over (key, value) pairs. `count` lives on the device and
 // is clamped to `cap` (null: `cap` keys); `vin` null means value = index;
 // `hist` is this digit's 256-bin histogram over all keys;
-// `status` has room for ceil(cap / SORT_TILE) x 256 words and is zeroed.
+// `status` has room for ceil(cap / tile) x 256 words and is zeroed.
 void launch_onesweep_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                           const uint32_t *count, uint32_t cap, const uint32_t *hist, uint32_t *status,
-                          uint32_t *tile_counter, int shift, uint32_t *err, int grid, cudaStream_t st);
-int onesweep_grid(int sm_count, uint32_t cap);
+                          uint32_t *tile_counter, int shift, uint32_t *err, int tile, int sm_count,
+                          cudaStream_t st);
 
 struct EmitArgs {
     const uint32_t *sorted_items;   // depth-sorted visible items

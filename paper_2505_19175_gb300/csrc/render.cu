@@ -40,27 +40,29 @@ __device__ __forceinline__ void pixel_of(int tid, int &lx, int &ly) {
 // [x0, x1] x [y0, y1]? Its maximum over the block is at the corner its slope selects;
 // the margin covers the FP32 rounding of the per-pixel evaluation at other pixels.
 __device__ __forceinline__ bool line_reaches(float A, float B, float C, float sx, float sy, int x0, int x1, int y0,
-                                             int y1) {
+                                             int y1, float thr) {
     const float dx = __fsub_rn((float)(A >= 0.f ? x1 : x0) + 0.5f, sx);
     const float dy = __fsub_rn((float)(B >= 0.f ? y1 : y0) + 0.5f, sy);
     const float t1 = A * dx, t2 = B * dy;
     const float m = C + t1 + t2;
-    return m >= -(1e-3f + 4e-7f * (fabsf(t1) + fabsf(t2) + fabsf(C)));
+    return m >= thr - (1e-3f + 4e-7f * (fabsf(t1) + fabsf(t2) + fabsf(C)));
 }
 
-// Bit w set when the record may contribute to a pixel of warp w's 8x4 block of the tile
-// with origin (ox, oy): its pixel rectangle meets the block and no edge line is
-// negative over the whole block.
+// Bit w set when the record may composite at a pixel of warp w's 8x4 block of the tile
+// with origin (ox, oy): its pixel rectangle meets the block, and every edge line can
+// reach the record's cutoff ratio (1/255 / o)^(1/sigma), below which alpha < 1/255
+// (taken 0.1 % low, far beyond the error of the approximate lg2 / ex2).
 __device__ __forceinline__ uint32_t warp_mask(const Rec &r, const ushort4 bx, int ox, int oy) {
+    const float thr = 0.999f * ex2_approx(lg2_approx(ALPHA_MIN / r.c.w) * rcp_approx(r.d.x));
     uint32_t msk = 0;
 #pragma unroll
     for (int wb = 0; wb < REN_THREADS / 32; ++wb) {
         const int x0 = ox + ((wb & 1) << 3), y0 = oy + ((wb >> 1) << 2);
         const int x1 = x0 + 7, y1 = y0 + 3;
         if ((int)bx.x > x1 || (int)bx.z < x0 || (int)bx.y > y1 || (int)bx.w < y0) continue;
-        if (!line_reaches(r.a.z, r.a.w, r.b.x, r.a.x, r.a.y, x0, x1, y0, y1)) continue;
-        if (!line_reaches(r.b.y, r.b.z, r.b.w, r.a.x, r.a.y, x0, x1, y0, y1)) continue;
-        if (!line_reaches(r.c.x, r.c.y, r.c.z, r.a.x, r.a.y, x0, x1, y0, y1)) continue;
+        if (!line_reaches(r.a.z, r.a.w, r.b.x, r.a.x, r.a.y, x0, x1, y0, y1, thr)) continue;
+        if (!line_reaches(r.b.y, r.b.z, r.b.w, r.a.x, r.a.y, x0, x1, y0, y1, thr)) continue;
+        if (!line_reaches(r.c.x, r.c.y, r.c.z, r.a.x, r.a.y, x0, x1, y0, y1, thr)) continue;
         msk |= 1u << wb;
     }
     return msk;
@@ -305,8 +307,9 @@ render_bwd_kernel(RenderArgs a) {
                             gv[10] = g0 * wgt;
                             gv[11] = g1 * wgt;
                             gv[12] = g2 * wgt;
-                            const float galpha = g0 * (rd.y * T - B0 * iom) + g1 * (rd.z * T - B1 * iom) +
-                                                 g2 * (rd.w * T - B2 * iom);
+                            const float gc = fmaf(g0, rd.y, fmaf(g1, rd.z, g2 * rd.w));
+                            const float gb = fmaf(g0, B0, fmaf(g1, B1, g2 * B2));
+                            const float galpha = T * gc - iom * gb;
                             B0 = fmaf(rd.y, wgt, B0);
                             B1 = fmaf(rd.z, wgt, B1);
                             B2 = fmaf(rd.w, wgt, B2);

@@ -19,10 +19,12 @@
 
 namespace ts {
 
+template <int SORT_IPT>
 __global__ void __launch_bounds__(SORT_THREADS)
 onesweep_kernel(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
                 uint32_t *__restrict__ vout, const uint32_t *count_ptr, uint32_t cap, const uint32_t *hist,
                 uint32_t *status, uint32_t *tile_counter, int shift, uint32_t *err) {
+    constexpr int SORT_TILE = SORT_THREADS * SORT_IPT;
     __shared__ uint32_t s_keys[SORT_TILE];
     __shared__ uint32_t s_vals[SORT_TILE];
     __shared__ uint32_t s_whist[SORT_THREADS / 32][256];
@@ -134,23 +136,42 @@ onesweep_kernel(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ v
     }
 }
 
-int onesweep_grid(int sm_count, uint32_t cap) {
+int onesweep_tile(uint32_t cap, int sm_count) {
+    const uint64_t target = (uint64_t)sm_count * 4;   // tiles wanted for a full machine
+    if ((uint64_t)cap >= target * SORT_THREADS * SORT_IPT_MAX) return SORT_THREADS * SORT_IPT_MAX;
+    if ((uint64_t)cap >= target * SORT_THREADS * 8) return SORT_THREADS * 8;
+    return SORT_THREADS * 4;
+}
+
+template <int IPT>
+static void launch_ipt(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+                       const uint32_t *count, uint32_t cap, const uint32_t *hist, uint32_t *status,
+                       uint32_t *tile_counter, int shift, uint32_t *err, int sm_count, cudaStream_t st) {
     static int occ = -1;
     if (occ < 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, onesweep_kernel, SORT_THREADS, 0) != cudaSuccess || occ < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, onesweep_kernel<IPT>, SORT_THREADS, 0) !=
+                cudaSuccess ||
+            occ < 1)
             occ = 1;
     }
-    int64_t tiles = ((int64_t)cap + SORT_TILE - 1) / SORT_TILE;
+    const int64_t tiles = ((int64_t)cap + SORT_THREADS * IPT - 1) / (SORT_THREADS * IPT);
     int64_t g = (int64_t)sm_count * occ;
     if (tiles < g) g = tiles;
-    return (int)(g < 1 ? 1 : g);
+    if (g < 1) g = 1;
+    onesweep_kernel<IPT><<<(unsigned)g, SORT_THREADS, 0, st>>>(kin, vin, kout, vout, count, cap, hist, status,
+                                                               tile_counter, shift, err);
 }
 
 void launch_onesweep_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                           const uint32_t *count, uint32_t cap, const uint32_t *hist, uint32_t *status,
-                          uint32_t *tile_counter, int shift, uint32_t *err, int grid, cudaStream_t st) {
-    onesweep_kernel<<<grid, SORT_THREADS, 0, st>>>(kin, vin, kout, vout, count, cap, hist, status, tile_counter,
-                                                   shift, err);
+                          uint32_t *tile_counter, int shift, uint32_t *err, int tile, int sm_count,
+                          cudaStream_t st) {
+    if (tile == SORT_THREADS * SORT_IPT_MAX)
+        launch_ipt<SORT_IPT_MAX>(kin, vin, kout, vout, count, cap, hist, status, tile_counter, shift, err, sm_count, st);
+    else if (tile == SORT_THREADS * 8)
+        launch_ipt<8>(kin, vin, kout, vout, count, cap, hist, status, tile_counter, shift, err, sm_count, st);
+    else
+        launch_ipt<4>(kin, vin, kout, vout, count, cap, hist, status, tile_counter, shift, err, sm_count, st);
 }
 
 // ---------------------------------------------------------------------------------
@@ -161,7 +182,9 @@ constexpr int EMIT_THREADS = 256;
 __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(EmitArgs a) {
     __shared__ uint32_t s_off[EMIT_THREADS];
     __shared__ uint32_t s_item[EMIT_THREADS];
-    __shared__ ushort4 s_rect[EMIT_THREADS];
+    __shared__ uint32_t s_base_tile[EMIT_THREADS];   // global id of the rectangle's first tile
+    __shared__ uint32_t s_wx[EMIT_THREADS];          // (rect width in tiles, view tiles_x)
+    __shared__ float s_iw[EMIT_THREADS];             // 1 / rect width
     __shared__ uint32_t s_hist[3][256];
     __shared__ uint32_t s_tmp[33];
     __shared__ uint32_t s_cta, s_base;
@@ -189,7 +212,11 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(EmitArgs a) {
     s_item[tid] = item;
     {
         const ushort4 pr = valid ? a.rects[item] : make_ushort4(0, 0, 0, 0);
-        s_rect[tid] = make_ushort4(pr.x / TILE, pr.y / TILE, pr.z / TILE, pr.w / TILE);
+        const uint32_t tx0 = pr.x / TILE, ty0 = pr.y / TILE, wdt = pr.z / TILE - tx0 + 1;
+        const int2 vt = s_vt[a.nviews > 1 ? (int)(item / (uint32_t)a.n) : 0];
+        s_base_tile[tid] = (uint32_t)vt.y + ty0 * (uint32_t)vt.x + tx0;
+        s_wx[tid] = (wdt << 16) | (uint32_t)vt.x;
+        s_iw[tid] = 1.0f / (float)wdt;
     }
     if (tid < 32) {
         const uint32_t b = warp_lookback_excl(a.lb_status, cta, total, &a.ctl->error);
@@ -203,7 +230,6 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(EmitArgs a) {
         a.ctl->n_pairs_used = (uint32_t)(np < a.cap ? np : a.cap);
         a.ctl->overflow = np > a.cap ? 1u : 0u;
     }
-    const uint32_t n32 = (uint32_t)a.n;
     for (uint32_t o = tid; o < total; o += EMIT_THREADS) {
         // owner: the last thread whose offset is <= o
         int lo = 0, hi = EMIT_THREADS - 1;
@@ -213,13 +239,12 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(EmitArgs a) {
             else hi = mid - 1;
         }
         const uint32_t k = o - s_off[lo];
-        const ushort4 r = s_rect[lo];
-        const uint32_t wdt = (uint32_t)(r.z - r.x + 1);
-        const uint32_t tx = r.x + k % wdt, ty = r.y + k / wdt;
+        const uint32_t wx = s_wx[lo], wdt = wx >> 16, tiles_x = wx & 0xffffu;
+        // row = k / wdt: exact in FP32 (k < 2^24, the quotient's fraction >= 1 / (2 wdt))
+        const uint32_t row = (uint32_t)(((float)k + 0.5f) * s_iw[lo]);
+        const uint32_t col = k - row * wdt;
         const uint32_t it = s_item[lo];
-        const uint32_t vw = it / n32;
-        const int2 vt = s_vt[vw];
-        const uint32_t tile = (uint32_t)vt.y + ty * (uint32_t)vt.x + tx;
+        const uint32_t tile = s_base_tile[lo] + row * tiles_x + col;
         const uint32_t pos = base + o;
         if (pos < a.cap) {
             a.pkeys[pos] = tile;
