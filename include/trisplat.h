@@ -195,6 +195,32 @@ tri_status tri_loss_l1(const float *image, const float *target, int64_t n, float
                        float *loss, void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * Allocation-free forward render. The paper has no counterpart: this is a deployment
+ * aid for callers that cannot allocate device memory (a plugin inside an application
+ * that owns the device allocator, a real-time loop that reserved every byte up front).
+ * It runs the steps of tri_preprocess + tri_bin_sort + tri_render_fwd for one view with
+ * all workspace carved from one fixed array in device global memory declared by the
+ * library (about 33 MB, held by every GPU that loads the library until the process
+ * exits); it calls no cudaMalloc, cudaFree or other allocating routine.
+ * Limits: scene->n <= TRI_NOALLOC_MAX_TRIANGLES and width * height <=
+ * TRI_NOALLOC_MAX_PIXELS (else TRI_ERR_CAPACITY, nothing runs); pairs beyond
+ * TRI_NOALLOC_MAX_PAIRS are dropped and reported in *device_status.
+ * Outputs: image [3][H][W]; T_final / n_contrib [H][W] (nullable); device_status (a
+ * device int32, nullable) receives bit 0 = a bounded wait gave up, bit 1 = an index
+ * check failed, bit 2 = pair overflow. Asynchronous on `stream`.
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture. All
+ * calls share the array and it keeps the last call's contents: each call clears what
+ * must start at zero, and calls that overlap on the GPU (other streams or threads)
+ * race on it. */
+#define TRI_NOALLOC_MAX_TRIANGLES 65536
+#define TRI_NOALLOC_MAX_PAIRS 524288
+#define TRI_NOALLOC_MAX_PIXELS (2048 * 1088)
+tri_status tri_render_fwd_noalloc(const tri_scene *scene, const tri_camera *cam, float *image,
+                                  float *T_final, int32_t *n_contrib, int32_t *device_status,
+                                  void *stream);
+
+/* ---------------------------------------------------------------------------------
  * Serving: resident scenes, admission by device memory, continuous batching of camera
  * requests of mixed resolutions into batched launches (one batched preprocess + sort
  * and one persistent render over all (request, tile) work items per batch), completion
