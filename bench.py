@@ -357,9 +357,66 @@ def run_ours(args, rank, world):
         "clocks": clocks,
         "wall_s_timed": round(t_wall, 4),
     }
+    if not args.no_serving:
+        line["serving"] = run_serving(args.serve_requests, 2000.0, 1_000_000)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(scene, cam, target, args.cpu_budget)
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# serving: open-loop replay of a Poisson trace against one resident scene
+# ---------------------------------------------------------------------------------------
+def replay(srv, sid, trace, max_time_s=60.0):
+    """Submit each request at its arrival time; returns wall seconds."""
+    import torch
+    free = {}
+    pending = {}
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(trace) or pending:
+        now = time.perf_counter() - t0
+        while i < len(trace) and trace[i][0] <= now:
+            cam = trace[i][2]
+            key = (cam.H, cam.W)
+            buf = free.get(key, [])
+            out = buf.pop() if buf else torch.empty((3, cam.H, cam.W), device="cuda")
+            t, _ = srv.submit(sid, cam, out)
+            pending[t] = (key, out)
+            i += 1
+        for t, _st in srv.poll():
+            key, out = pending.pop(t)
+            free.setdefault(key, []).append(out)
+        if now > max_time_s:
+            break
+        time.sleep(0.0001)
+    return time.perf_counter() - t0
+
+
+def run_serving(n_req: int, rate_hz: float, n_tris: int):
+    import torch
+    from paper_2505_19175_gb300 import synth
+    from paper_2505_19175_gb300.renderer import SceneTensors
+    from paper_2505_19175_gb300.serve import Server
+    scene = SceneTensors.from_numpy(synth.scene_shells(n_tris, seed=1004))
+    trace = synth.serve_requests(n_req, seed=1004, rate_hz=rate_hz)
+    out = {"workload": f"{n_tris} tris SH3 shells, {n_req} requests, Poisson {rate_hz:.0f} req/s, "
+                       "640x360 : 1280x720 : 1920x1080 = 2:2:1, open-loop"}
+    for name, kw in (("batched", dict(max_batch=16, slots=4)), ("one_request_per_launch", dict(max_batch=1, slots=1))):
+        srv = Server(max_width=1920, max_height=1080, use_graphs=True, **kw)
+        sid = srv.add_scene(scene)
+        # warm-up on another trace of the same mix: grows workspaces, captures graphs
+        replay(srv, sid, synth.serve_requests(512, seed=999, rate_hz=rate_hz))
+        torch.cuda.synchronize()
+        srv.reset_stats()
+        wall = replay(srv, sid, trace)
+        st = srv.stats()
+        srv.close()
+        out[name] = {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                     "max_ms": round(st["max_ms"], 3), "fps": round(st["fps"], 1),
+                     "completed": int(st["completed"]), "mean_batch": round(st["mean_batch"], 2),
+                     "wall_s": round(wall, 3), **kw}
+    return out
 
 
 def main():
@@ -370,6 +427,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=4096)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

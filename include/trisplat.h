@@ -274,6 +274,10 @@ tri_status tri_serve_wait(tri_serve *srv, uint64_t ticket, int32_t timeout_ms);
 /* Latency percentiles and counters over completed requests. */
 tri_status tri_serve_stats(tri_serve *srv, tri_serve_stats_t *stats);
 
+/* Start a new statistics window: clears latencies and counters (requests in flight
+ * still complete normally and count in the new window). */
+tri_status tri_serve_reset_stats(tri_serve *srv);
+
 /* Stop the dispatcher after the queued work drains, free everything. */
 void tri_serve_destroy(tri_serve *srv);
 

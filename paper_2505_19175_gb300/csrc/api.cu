@@ -11,40 +11,7 @@
 
 using namespace ts;
 
-namespace {
-
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
-
-}  // namespace
-
-struct tri_ctx {
-    int device = 0;
-    int sms = 0;
-    std::string err;
-    tri_scene scene{};
-    int nviews = 0;
-    std::vector<ViewDev> views;
-    int64_t n_items = 0;
-    int total_tiles = 0;
-    int64_t total_pix = 0;
-    int tile_passes = 1;
-    int64_t pair_cap = 0;
-    int stage = 0;  // 1 preprocessed, 2 sorted, 3 rendered, 4 backward rendered
-    int pair_final = 0;
-    // pinned copies of the small per-call tables, used while the stream is captured
-    ViewDev *h_views = nullptr;
-    ViewOut *h_outs_fwd = nullptr, *h_outs_bwd = nullptr;
-    DevBuf views_d, outs_fwd, outs_bwd, ctl, recs, ntiles, rects, dkeys, ck[2], cv[2], pk[2], pv[2], ranges,
-        tile_max, Tfin, ncontrib, grad2d, st_emit, st_depth, st_pairs;
-    std::vector<DevBuf *> all() {
-        return {&views_d, &outs_fwd, &outs_bwd, &ctl, &recs, &ntiles, &rects, &dkeys, &ck[0], &ck[1], &cv[0],
-                &cv[1], &pk[0], &pk[1], &pv[0], &pv[1], &ranges, &tile_max, &Tfin, &ncontrib, &grad2d,
-                &st_emit, &st_depth, &st_pairs};
-    }
-};
+#include "ctx.h"
 
 namespace {
 
@@ -68,7 +35,7 @@ tri_status cuda_fail(tri_ctx *c, cudaError_t e, const char *what) {
 
 // Grow `b` to at least `bytes` (never shrinks). Synchronises the device before
 // freeing the old allocation, since queued work may still use it.
-tri_status ensure(tri_ctx *c, DevBuf &b, size_t bytes) {
+tri_status ensure(tri_ctx *c, TsDevBuf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return TRI_OK;
     if (b.p) {
@@ -86,6 +53,7 @@ tri_status ensure(tri_ctx *c, DevBuf &b, size_t bytes) {
         return cuda_fail(c, e, "cudaMalloc");
     }
     b.bytes = want;
+    ++c->realloc_gen;
     return TRI_OK;
 }
 
@@ -96,7 +64,7 @@ tri_status ensure(tri_ctx *c, DevBuf &b, size_t bytes) {
     } while (0)
 
 template <class T>
-T *P(DevBuf &b) {
+T *P(TsDevBuf &b) {
     return reinterpret_cast<T *>(b.p);
 }
 
@@ -136,8 +104,10 @@ tri_status validate_scene(tri_ctx *c, const tri_scene *s) {
     return TRI_OK;
 }
 
-tri_status build_views(tri_ctx *c, const tri_camera *cams, int nviews, std::vector<ViewDev> &out, int &tiles,
-                       int64_t &pix) {
+}  // namespace
+
+tri_status ts_build_views(tri_ctx *c, const tri_camera *cams, int nviews, std::vector<ViewDev> &out, int &tiles,
+                          int64_t &pix) {
     if (!cams || nviews <= 0 || nviews > MAX_VIEWS)
         return fail(c, TRI_ERR_INVALID_ARG, "need 1.." + std::to_string(MAX_VIEWS) + " cameras");
     out.resize(nviews);
@@ -169,6 +139,8 @@ tri_status build_views(tri_ctx *c, const tri_camera *cams, int nviews, std::vect
     pix = pb;
     return TRI_OK;
 }
+
+namespace {
 
 size_t sort_status_words(int64_t cap, int tile) { return (size_t)((cap + tile - 1) / tile) * 256; }
 
@@ -256,7 +228,7 @@ void tri_ctx_destroy(tri_ctx *c) {
     cudaGetDevice(&cur);
     if (cur != c->device) cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    for (DevBuf *b : c->all())
+    for (TsDevBuf *b : c->all())
         if (b->p) cudaFree(b->p);
     if (c->h_views) cudaFreeHost(c->h_views);
     if (c->h_outs_fwd) cudaFreeHost(c->h_outs_fwd);
@@ -275,7 +247,7 @@ tri_status tri_workspace_query(const tri_scene *scene, const tri_camera *cams, i
     std::vector<ViewDev> v;
     int tiles = 0;
     int64_t pix = 0;
-    s = build_views(nullptr, cams, nviews, v, tiles, pix);
+    s = ts_build_views(nullptr, cams, nviews, v, tiles, pix);
     if (s != TRI_OK) return s;
     const int64_t M = scene->n * nviews;
     const int64_t cap = pair_capacity > 0 ? pair_capacity : default_pair_cap(M);
@@ -312,7 +284,7 @@ tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *
     std::vector<ViewDev> views;
     int tiles = 0;
     int64_t pix = 0;
-    if ((s = build_views(c, cams, nviews, views, tiles, pix)) != TRI_OK) return s;
+    if ((s = ts_build_views(c, cams, nviews, views, tiles, pix)) != TRI_OK) return s;
     const int64_t M = scene->n * (int64_t)nviews;
     if (M > (int64_t)LB_MASK) return fail(c, TRI_ERR_INVALID_ARG, "too many (view, triangle) items");
     c->scene = *scene;
@@ -444,7 +416,7 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
     return TRI_OK;
 }
 
-static RenderArgs render_args(tri_ctx *c, DevBuf &outs) {
+static RenderArgs render_args(tri_ctx *c, TsDevBuf &outs) {
     RenderArgs r;
     r.views = P<ViewDev>(c->views_d);
     r.outs = P<ViewOut>(outs);

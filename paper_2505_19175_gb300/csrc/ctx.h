@@ -1,0 +1,44 @@
+// Internal definition of the renderer context (shared by api.cu, serve.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "trisplat.h"
+
+struct TsDevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct tri_ctx {
+    int device = 0;
+    int sms = 0;
+    std::string err;
+    tri_scene scene{};
+    int nviews = 0;
+    std::vector<ts::ViewDev> views;
+    int64_t n_items = 0;
+    int total_tiles = 0;
+    int64_t total_pix = 0;
+    int tile_passes = 1;
+    int64_t pair_cap = 0;
+    int stage = 0;  // 1 preprocessed, 2 sorted, 3 rendered, 4 backward rendered
+    int pair_final = 0;
+    uint64_t realloc_gen = 0;   // bumped whenever a device buffer is reallocated
+    // pinned copies of the small per-call tables, used while the stream is captured
+    ts::ViewDev *h_views = nullptr;
+    ts::ViewOut *h_outs_fwd = nullptr, *h_outs_bwd = nullptr;
+    TsDevBuf views_d, outs_fwd, outs_bwd, ctl, recs, ntiles, rects, dkeys, ck[2], cv[2], pk[2], pv[2], ranges,
+        tile_max, Tfin, ncontrib, grad2d, st_emit, st_depth, st_pairs;
+    std::vector<TsDevBuf *> all() {
+        return {&views_d, &outs_fwd, &outs_bwd, &ctl, &recs, &ntiles, &rects, &dkeys, &ck[0], &ck[1], &cv[0],
+                &cv[1], &pk[0], &pk[1], &pv[0], &pv[1], &ranges, &tile_max, &Tfin, &ncontrib, &grad2d,
+                &st_emit, &st_depth, &st_pairs};
+    }
+};
+
+// Device view table of `cams` (validated); tiles / pixels of all views.
+tri_status ts_build_views(tri_ctx *c, const tri_camera *cams, int nviews, std::vector<ts::ViewDev> &out, int &tiles,
+                          int64_t &pix);

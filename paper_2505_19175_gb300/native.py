@@ -95,6 +95,7 @@ def lib():
                 _sig(L, "tri_serve_poll", [vp, P(C.c_uint64), P(i32), i32, P(i32)])
                 _sig(L, "tri_serve_wait", [vp, C.c_uint64, i32])
                 _sig(L, "tri_serve_stats", [vp, P(tri_serve_stats_t)])
+                _sig(L, "tri_serve_reset_stats", [vp])
                 _sig(L, "tri_serve_destroy", [vp], None)
             _lib = L
     return _lib
