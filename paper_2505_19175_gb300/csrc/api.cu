@@ -33,13 +33,21 @@ tri_status cuda_fail(tri_ctx *c, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
     } while (0)
 
-// Grow `b` to at least `bytes` (never shrinks). Synchronises the device before
-// freeing the old allocation, since queued work may still use it.
+// Record the stream of a call (see ensure).
+void begin_call(tri_ctx *c, cudaStream_t st) {
+    c->prev_stream = c->last_stream;
+    c->last_stream = st;
+}
+
+// Grow `b` to at least `bytes` (never shrinks). Before freeing the old allocation it
+// waits for the streams of this call and of the previous one, the only work of this
+// context that can still use it.
 tri_status ensure(tri_ctx *c, TsDevBuf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return TRI_OK;
     if (b.p) {
-        CK(cudaDeviceSynchronize());
+        CK(cudaStreamSynchronize(c->prev_stream));
+        if (c->last_stream != c->prev_stream) CK(cudaStreamSynchronize(c->last_stream));
         CK(cudaFree(b.p));
         b.p = nullptr;
         b.bytes = 0;
@@ -281,6 +289,7 @@ tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *
     if (s != TRI_OK) return s;
     if ((s = set_device(c)) != TRI_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    begin_call(c, st);
     std::vector<ViewDev> views;
     int tiles = 0;
     int64_t pix = 0;
@@ -341,6 +350,7 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
     tri_status s = set_device(c);
     if (s != TRI_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    begin_call(c, st);
     Ctl *ctl = ctl_of(c);
     const int64_t M = c->n_items;
     // counters owned by this step (the depth histograms come from tri_preprocess)
@@ -445,6 +455,7 @@ tri_status tri_render_fwd(tri_ctx *c, float *const *images, float *const *T_fina
     tri_status s = set_device(c);
     if (s != TRI_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    begin_call(c, st);
     std::vector<ViewOut> outs(c->nviews);
     for (int v = 0; v < c->nviews; ++v) outs[v] = ViewOut{images[v], nullptr};
     if ((s = upload(c, c->outs_fwd.p, outs.data(), sizeof(ViewOut) * c->nviews, c->h_outs_fwd, st)) != TRI_OK)
@@ -475,6 +486,7 @@ tri_status tri_render_bwd(tri_ctx *c, const float *const *dL, void *stream) {
     tri_status s = set_device(c);
     if (s != TRI_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    begin_call(c, st);
     std::vector<ViewOut> outs(c->nviews);
     for (int v = 0; v < c->nviews; ++v) outs[v] = ViewOut{nullptr, dL[v]};
     ENSURE(c->grad2d, sizeof(float) * GRAD_FIELDS * (size_t)c->n_items);

@@ -27,6 +27,9 @@ struct tri_ctx {
     int stage = 0;  // 1 preprocessed, 2 sorted, 3 rendered, 4 backward rendered
     int pair_final = 0;
     uint64_t realloc_gen = 0;   // bumped whenever a device buffer is reallocated
+    // streams of the previous and the current call: a reallocation waits for both,
+    // not for the whole device
+    cudaStream_t prev_stream = nullptr, last_stream = nullptr;
     // pinned copies of the small per-call tables, used while the stream is captured
     ts::ViewDev *h_views = nullptr;
     ts::ViewOut *h_outs_fwd = nullptr, *h_outs_bwd = nullptr;

@@ -256,7 +256,12 @@ bool take_batch(tri_serve *S, Slot &sl, double t) {
         }
         return false;
     }
-    std::sort(reqs.begin(), reqs.end(), [](const Req &a, const Req &b) { return a.ticket < b.ticket; });
+    // order by resolution, so that the graph cache keys on the multiset of resolutions
+    std::sort(reqs.begin(), reqs.end(), [](const Req &a, const Req &b) {
+        if (a.cam.width != b.cam.width) return a.cam.width < b.cam.width;
+        if (a.cam.height != b.cam.height) return a.cam.height < b.cam.height;
+        return a.ticket < b.ticket;
+    });
     sl.batch = std::move(reqs);
     sl.scene = sid;
     sl.attempts = 0;
