@@ -37,6 +37,25 @@ FALLBACK_HBM_GBS = 6800.0
 FP32_LANES_PER_SM = 128
 
 
+PROFILE_FILE = os.path.join(ROOT, "profiles", "kernels_patches_500k.md")
+
+
+def _profiled_traffic(kernel: str):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or None when
+    the kernel's source changed after the capture (the sha256 prefix no longer matches)."""
+    import hashlib
+    try:
+        for ln in open(PROFILE_FILE):
+            f = ln.split()
+            if len(f) == 5 and f[0] == "traffic" and f[1] == kernel:
+                with open(os.path.join(ROOT, f[3]), "rb") as src:
+                    if hashlib.sha256(src.read()).hexdigest()[:16] == f[4]:
+                        return int(f[2])
+    except OSError:
+        pass
+    return None
+
+
 def _peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -331,7 +350,8 @@ def run_ours(args, rank, world):
             ops = F_eval * 11 + F_kept * 45   # + ~35 FP32 ops of the adjoint per fragment
         ach = ops / (med[STAGES.index(dom)] / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 3), "peak": round(fp32_peak, 3),
-                "unit": "T FP32-lane-ops/s", "frac": round(ach / fp32_peak, 4), "traffic": None,
+                "unit": "T FP32-lane-ops/s", "frac": round(ach / fp32_peak, 4),
+                "traffic": _profiled_traffic(dom + "_kernel"), "traffic_unit": "DRAM bytes per launch (ncu)",
                 "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} lanes x {clock_mhz:.0f} MHz ({peak_src} max clock)"}
     else:
         hbm = float(peaks["hbm_gbs"])
