@@ -377,11 +377,82 @@ def run_ours(args, rank, world):
         "clocks": clocks,
         "wall_s_timed": round(t_wall, 4),
     }
+    if not args.no_multiview and world == 1:
+        del g_step, g_fwd
+        line["multiview_3m_16views"] = run_multiview(max(3, min(args.steps, 10)), 3)
     if not args.no_serving:
         line["serving"] = run_serving(args.serve_requests, 2000.0, 1_000_000)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(scene, cam, target, args.cpu_budget)
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# multi-view training step: 3M triangles on 16 shells, 16 ring views at 1558x1038
+# ---------------------------------------------------------------------------------------
+def run_multiview(steps: int, warmup: int, n_tris: int = 3_000_000, n_views: int = 16):
+    """fwd+bwd over all views per step, cameras re-drawn every step (seeded ring offset);
+    eager calls, since the cameras change between steps. Returns a dict for the JSON line."""
+    import torch
+    from paper_2505_19175_gb300 import native as N
+    from paper_2505_19175_gb300 import synth
+    from paper_2505_19175_gb300.renderer import Context, SceneTensors
+    st = SceneTensors.from_numpy(synth.scene_shells(n_tris, seed=1003))
+    rng = np.random.default_rng(1003)
+    offsets = rng.uniform(0.0, 2 * np.pi / n_views, warmup + 2 * steps + 1)
+    W, H = 1558, 1038
+    cams0 = synth.ring_cameras(n_views, W=W, H=H, offset=float(offsets[0]))
+    imgs = torch.empty((n_views, 3, H, W), device="cuda")
+    grad = torch.empty_like(imgs)
+    tgt = torch.as_tensor(np.random.default_rng(1003).random((n_views, 3, H, W), dtype=np.float32)).cuda()
+    loss = torch.empty((), device="cuda")
+    dv, dsh = torch.empty_like(st.verts), torch.empty_like(st.sh)
+    do, ds = torch.empty_like(st.opacity), torch.empty_like(st.sigma)
+    ctx = Context()
+    ctx.preprocess(st, cams0)
+    ctx.reserve(int(ctx.bin_sort(sync=True) * 1.5) + 4096)
+    L = N.lib()
+    views = [imgs[v] for v in range(n_views)]
+    grads = [grad[v] for v in range(n_views)]
+
+    def step(k, fwd_only=False):
+        cams = synth.ring_cameras(n_views, W=W, H=H, offset=float(offsets[k]))
+        ctx.preprocess(st, cams)
+        ctx.bin_sort(sync=False)
+        ctx.render_fwd(views)
+        if fwd_only:
+            return
+        N.check(L.tri_loss_l1(imgs.data_ptr(), tgt.data_ptr(), imgs.numel(), grad.data_ptr(), loss.data_ptr(),
+                              int(torch.cuda.current_stream().cuda_stream)))
+        ctx.render_bwd(grads)
+        ctx.preprocess_bwd(dv, dsh, do, ds)
+
+    for k in range(warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    def timed(k0, fwd_only):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            ev[i][0].record()
+            step(k0 + i, fwd_only)
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        return np.array([a.elapsed_time(b) for a, b in ev])
+
+    ms = timed(warmup, False)
+    info = ctx.check()
+    ms_fwd = timed(warmup + steps, True)
+    info_f = ctx.check()
+    return {"workload": f"{n_tris} tris SH3 on 16 shells, {n_views} ring views {W}x{H} per step, ring offset "
+                        "re-drawn every step, fwd+bwd with L1 loss; params 708 MB > L2",
+            "it_per_s": round(1000.0 * steps / float(ms.sum()), 3), "ms_per_step_median": round(float(np.median(ms)), 3),
+            "views_per_s": round(1000.0 * steps * n_views / float(ms.sum()), 2),
+            "fwd_fps_per_view": round(1000.0 * steps * n_views / float(ms_fwd.sum()), 2),
+            "pairs": int(info.n_pairs), "visible_items": int(info.n_visible),
+            "frag_evaluated": int(info.frag_evaluated), "frag_composited": int(info.frag_composited),
+            "overflow": bool(info.overflow or info_f.overflow), "steps": steps, "warmup": warmup,
+            "timing": "eager calls, CUDA events per step"}
 
 
 # ---------------------------------------------------------------------------------------
@@ -435,6 +506,10 @@ def run_serving(n_req: int, rate_hz: float, n_tris: int):
         out[name] = {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
                      "max_ms": round(st["max_ms"], 3), "fps": round(st["fps"], 1),
                      "completed": int(st["completed"]), "mean_batch": round(st["mean_batch"], 2),
+                     "queue_p99_ms": round(st["queue_p99_ms"], 3), "graph_replays": int(st["graph_replays"]),
+                     "graph_captures": int(st["graph_captures"]), "eager_batches": int(st["eager_batches"]),
+                     "reruns": int(st["reruns"]), "reallocs": int(st["reallocs"]),
+                     "capture_ms": round(st["capture_ms"], 2), "eager_ms": round(st["eager_ms"], 2),
                      "wall_s": round(wall, 3), **kw}
     return out
 
@@ -448,6 +523,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-multiview", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4096)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

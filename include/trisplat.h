@@ -236,6 +236,8 @@ typedef struct {
     int32_t timeout_ms;        /* per-request deadline (0 = none) */
     int32_t use_graphs;        /* capture each slot's launch sequence in a CUDA graph */
     int32_t batch_window_us;   /* wait this long for more requests before launching */
+    int32_t graph_after;       /* capture a composition's graph once it has run eagerly this
+                                  many times (<= 1: on its first run) */
 } tri_serve_opts;
 
 typedef struct {
@@ -245,6 +247,14 @@ typedef struct {
     double mean_batch;         /* views per batch */
     size_t bytes_resident;     /* scene bytes held */
     size_t bytes_workspace;    /* batch workspaces held */
+    uint64_t graph_replays;    /* batches launched by replaying a captured graph */
+    uint64_t graph_captures;   /* graphs captured and instantiated */
+    uint64_t eager_batches;    /* batches launched call by call */
+    uint64_t reruns;           /* batches run again after a pair-list overflow */
+    uint64_t reallocs;         /* workspace buffers (re)allocated by the slots */
+    double eager_ms;           /* dispatcher time spent launching eager batches */
+    double capture_ms;         /* dispatcher time spent capturing and instantiating */
+    double queue_p99_ms;       /* p99 of submit -> launch of the completed requests */
 } tri_serve_stats_t;
 
 /* Create a server on `device`. Starts one dispatcher thread. */

@@ -47,6 +47,7 @@ struct Req {
     float *out;
     double t_submit;
     double deadline;   // <= 0: none
+    double t_launch;
 };
 
 struct Slot {
@@ -59,6 +60,7 @@ struct Slot {
     int32_t scene = -1;
     int attempts = 0;
     std::map<std::vector<int>, cudaGraphExec_t> graphs;
+    std::map<std::vector<int>, int> eager_runs;   // eager runs per composition (capture policy)
     uint64_t graph_gen = 0;             // context realloc generation the graphs were captured at
     int64_t graph_cap = 0;              // pair capacity the graphs were captured at
 };
@@ -73,6 +75,13 @@ std::vector<int> graph_key(int32_t scene, const std::vector<Req> &reqs) {
     }
     return k;
 }
+
+// What one launch did, folded into the server's counters under its lock.
+struct LaunchInfo {
+    bool replayed = false, captured = false;
+    double eager_ms = 0.0, capture_ms = 0.0;
+    uint64_t reallocs = 0;
+};
 
 }  // namespace
 
@@ -90,10 +99,12 @@ struct tri_serve {
     bool stop = false;
     std::deque<std::pair<uint64_t, int32_t>> done_q;
     std::unordered_map<uint64_t, int32_t> done_map;
-    std::vector<double> lat_ms;
+    std::vector<double> lat_ms, queue_ms;
     std::vector<int32_t> drop_requests;   // scenes whose graphs the dispatcher must drop
     uint64_t drops_done = 0;              // drop requests served so far
     uint64_t submitted = 0, completed = 0, rejected = 0, timed_out = 0, batches = 0, views = 0;
+    uint64_t graph_replays = 0, graph_captures = 0, eager_batches = 0, reruns = 0, reallocs = 0;
+    double eager_ms = 0.0, capture_ms = 0.0;
     double t_first = -1.0, t_last = 0.0;
     size_t bytes_resident = 0;
 };
@@ -131,6 +142,7 @@ void finish(tri_serve *S, const Req &r, int32_t status, double t) {
     S->done_map[r.ticket] = status;
     if (status == TRI_OK) {
         S->lat_ms.push_back(t - r.t_submit);
+        S->queue_ms.push_back(r.t_launch - r.t_submit);
         ++S->completed;
         S->t_last = std::max(S->t_last, t);
     } else if (status == TRI_ERR_TIMEOUT) {
@@ -150,7 +162,14 @@ tri_status batch_calls(Slot &sl, const tri_scene &sc, const std::vector<tri_came
 }
 
 // Launch the slot's batch: replay its composition's graph, or run eagerly and capture.
-tri_status launch(tri_serve *S, Slot &sl, const tri_scene &sc) {
+tri_status launch(tri_serve *S, Slot &sl, const tri_scene &sc, LaunchInfo &li) {
+    const uint64_t gen0 = sl.ctx->realloc_gen;
+    struct Count {
+        const tri_ctx *c;
+        uint64_t g0;
+        LaunchInfo &li;
+        ~Count() { li.reallocs += c->realloc_gen - g0; }
+    } count{sl.ctx, gen0, li};
     std::vector<tri_camera> cams;
     std::vector<float *> outs;
     for (const Req &r : sl.batch) {
@@ -172,13 +191,19 @@ tri_status launch(tri_serve *S, Slot &sl, const tri_scene &sc) {
             cudaGetLastError();
             return TRI_ERR_CUDA;
         }
+        li.replayed = true;
     } else {
+        const double t0 = now_ms();
         tri_status st = batch_calls(sl, sc, cams, outs);
+        const double t1 = now_ms();
+        li.eager_ms += t1 - t0;
         if (st != TRI_OK) return st;
         // the eager run may have grown a buffer: every graph captured before it would
         // replay into freed memory
         if (sl.graph_gen != sl.ctx->realloc_gen || sl.graph_cap != sl.ctx->pair_cap) drop_graphs(sl);
-        if (S->opts.use_graphs && sl.ctx->pair_cap > 0) {
+        if (sl.eager_runs.size() > 4096) sl.eager_runs.clear();
+        const int runs = S->opts.use_graphs ? ++sl.eager_runs[key] : 0;
+        if (S->opts.use_graphs && sl.ctx->pair_cap > 0 && runs >= std::max(1, S->opts.graph_after)) {
             cudaGraph_t g = nullptr;
             bool ok = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
@@ -194,6 +219,8 @@ tri_status launch(tri_serve *S, Slot &sl, const tri_scene &sc) {
             }
             if (g) cudaGraphDestroy(g);
             cudaGetLastError();
+            li.captured = ex != nullptr;
+            li.capture_ms += now_ms() - t1;
         }
     }
     if (cudaMemcpyAsync(sl.h_ctl, sl.ctx->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
@@ -202,6 +229,15 @@ tri_status launch(tri_serve *S, Slot &sl, const tri_scene &sc) {
         return TRI_ERR_CUDA;
     }
     return TRI_OK;
+}
+
+void fold(tri_serve *S, const LaunchInfo &li) {
+    S->graph_replays += li.replayed;
+    S->graph_captures += li.captured;
+    S->eager_batches += !li.replayed;
+    S->reallocs += li.reallocs;
+    S->eager_ms += li.eager_ms;
+    S->capture_ms += li.capture_ms;
 }
 
 // Take the next batch for slot `sl` from the queue (lock held). Returns false if none.
@@ -262,6 +298,7 @@ bool take_batch(tri_serve *S, Slot &sl, double t) {
         if (a.cam.height != b.cam.height) return a.cam.height < b.cam.height;
         return a.ticket < b.ticket;
     });
+    for (Req &r : reqs) r.t_launch = t;
     sl.batch = std::move(reqs);
     sl.scene = sid;
     sl.attempts = 0;
@@ -297,10 +334,15 @@ void dispatcher(tri_serve *S) {
                 ++sl.attempts;
                 const int64_t want = (int64_t)h.n_pairs + (int64_t)h.n_pairs / 4 + 1024;
                 const tri_scene desc = sc.desc;
+                LaunchInfo li;
                 lk.unlock();
+                const uint64_t g0 = sl.ctx->realloc_gen;
                 tri_status st = tri_reserve(sl.ctx, want);
-                if (st == TRI_OK) st = launch(S, sl, desc);
+                li.reallocs += sl.ctx->realloc_gen - g0;
+                if (st == TRI_OK) st = launch(S, sl, desc, li);
                 lk.lock();
+                fold(S, li);
+                ++S->reruns;
                 if (st == TRI_OK) {
                     any_busy = true;
                     continue;
@@ -330,9 +372,11 @@ void dispatcher(tri_serve *S) {
             sl.busy = true;
             any_busy = true;
             const tri_scene desc = S->scenes[sl.scene].desc;
+            LaunchInfo li;
             lk.unlock();
-            tri_status st = launch(S, sl, desc);
+            tri_status st = launch(S, sl, desc, li);
             lk.lock();
+            fold(S, li);
             if (st != TRI_OK) {
                 const double tc = now_ms();
                 for (const Req &r : sl.batch) finish(S, r, st, tc);
@@ -490,6 +534,7 @@ tri_status tri_serve_submit(tri_serve *S, int32_t scene_id, const tri_camera *ca
     r.cam = *cam;
     r.out = out_image;
     r.t_submit = now_ms();
+    r.t_launch = r.t_submit;
     r.deadline = S->opts.timeout_ms > 0 ? r.t_submit + S->opts.timeout_ms : 0.0;
     if (S->t_first < 0) S->t_first = r.t_submit;
     S->queue.push_back(r);
@@ -534,6 +579,13 @@ tri_status tri_serve_stats(tri_serve *S, tri_serve_stats_t *out) {
     out->batches = S->batches;
     out->mean_batch = S->batches ? (double)S->views / (double)S->batches : 0.0;
     out->bytes_resident = S->bytes_resident;
+    out->graph_replays = S->graph_replays;
+    out->graph_captures = S->graph_captures;
+    out->eager_batches = S->eager_batches;
+    out->reruns = S->reruns;
+    out->reallocs = S->reallocs;
+    out->eager_ms = S->eager_ms;
+    out->capture_ms = S->capture_ms;
     for (const Slot &sl : S->slots) out->bytes_workspace += slot_bytes(sl);
     if (!S->lat_ms.empty()) {
         std::vector<double> v = S->lat_ms;
@@ -545,6 +597,9 @@ tri_status tri_serve_stats(tri_serve *S, tri_serve_stats_t *out) {
             return i + 1 < v.size() ? v[i] * (1 - f) + v[i + 1] * f : v[i];
         };
         out->p50_ms = pct(0.50);
+        std::vector<double> q = S->queue_ms;
+        std::sort(q.begin(), q.end());
+        if (!q.empty()) out->queue_p99_ms = q[(size_t)(0.99 * (double)(q.size() - 1))];
         out->p99_ms = pct(0.99);
         out->max_ms = v.back();
         double s = 0;
@@ -560,7 +615,10 @@ tri_status tri_serve_reset_stats(tri_serve *S) {
     if (!S) return TRI_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(S->mu);
     S->lat_ms.clear();
+    S->queue_ms.clear();
     S->submitted = S->completed = S->rejected = S->timed_out = S->batches = S->views = 0;
+    S->graph_replays = S->graph_captures = S->eager_batches = S->reruns = S->reallocs = 0;
+    S->eager_ms = S->capture_ms = 0.0;
     S->t_first = -1.0;
     S->t_last = 0.0;
     return TRI_OK;

@@ -45,14 +45,17 @@ class tri_ctx_info(C.Structure):
 class tri_serve_opts(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_batch", C.c_int32), ("max_width", C.c_int32),
                 ("max_height", C.c_int32), ("slots", C.c_int32), ("timeout_ms", C.c_int32),
-                ("use_graphs", C.c_int32), ("batch_window_us", C.c_int32)]
+                ("use_graphs", C.c_int32), ("batch_window_us", C.c_int32), ("graph_after", C.c_int32)]
 
 
 class tri_serve_stats_t(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
                 ("timed_out", C.c_uint64), ("batches", C.c_uint64), ("p50_ms", C.c_double),
                 ("p99_ms", C.c_double), ("max_ms", C.c_double), ("mean_ms", C.c_double), ("fps", C.c_double),
-                ("mean_batch", C.c_double), ("bytes_resident", C.c_size_t), ("bytes_workspace", C.c_size_t)]
+                ("mean_batch", C.c_double), ("bytes_resident", C.c_size_t), ("bytes_workspace", C.c_size_t),
+                ("graph_replays", C.c_uint64), ("graph_captures", C.c_uint64), ("eager_batches", C.c_uint64),
+                ("reruns", C.c_uint64), ("reallocs", C.c_uint64), ("eager_ms", C.c_double),
+                ("capture_ms", C.c_double), ("queue_p99_ms", C.c_double)]
 
 
 _lock = threading.Lock()

@@ -19,14 +19,14 @@ from . import native as N
 class Server:
     def __init__(self, mem_budget_bytes: int = 0, max_batch: int = 8, max_width: int = 1920,
                  max_height: int = 1080, slots: int = 2, timeout_ms: int = 0, use_graphs: bool = True,
-                 batch_window_us: int = 0, device: int | None = None):
+                 batch_window_us: int = 0, graph_after: int = 1, device: int | None = None):
         self._lib = N.lib()
         self.device = torch.cuda.current_device() if device is None else int(device)
         o = N.tri_serve_opts()
         o.mem_budget_bytes = int(mem_budget_bytes)
         o.max_batch, o.max_width, o.max_height = int(max_batch), int(max_width), int(max_height)
         o.slots, o.timeout_ms, o.use_graphs = int(slots), int(timeout_ms), int(bool(use_graphs))
-        o.batch_window_us = int(batch_window_us)
+        o.batch_window_us, o.graph_after = int(batch_window_us), int(graph_after)
         h = C.c_void_p()
         N.check(self._lib.tri_serve_create(C.byref(h), C.byref(o), self.device))
         self.h = h

@@ -141,3 +141,25 @@ def test_pair_overflow_reruns_the_batch():
     assert srv.wait(t) == 0
     np.testing.assert_array_equal(out.cpu().numpy(), _alone(scene, cam).astype(np.float32))
     srv.close()
+
+
+def test_graph_policy_counters():
+    """graph_after=2: a composition runs eagerly twice, is captured on its second run
+    and replayed from then on; every run gives the same image."""
+    from paper_2505_19175_gb300.serve import Server
+    scene = _scene(10000, 68)
+    cam = synth.camera_look_at((0.0, -0.5, -4.0), (0, 0, 0), 160, 96)
+    srv = Server(max_batch=1, slots=1, graph_after=2)
+    sid = srv.add_scene(scene)
+    outs = []
+    for _ in range(4):
+        t, o = srv.submit(sid, cam)
+        assert srv.wait(t) == 0
+        outs.append(o.cpu().numpy())
+    st = srv.stats()
+    assert st["eager_batches"] == 2 and st["graph_captures"] == 1 and st["graph_replays"] == 2
+    assert st["queue_p99_ms"] >= 0.0
+    ref = _alone(scene, cam).astype(np.float32)
+    for o in outs:
+        np.testing.assert_array_equal(o, ref)
+    srv.close()
