@@ -12,10 +12,9 @@
  *   tri_preprocess      project, build the signed-distance window, colour, depth and
  *                       tight tile rectangle of every (view, triangle) item
  *                       (Sec. 3.1, Eq. indicator1; Supp. "Tile assignment");
- *   tri_bin_sort        depth sort of visible items by centroid depth, duplication of
- *                       each item into the tiles of its rectangle, stable radix sort
- *                       by tile, per-tile ranges (Supp. "Tile assignment", "Depth
- *                       sorting");
+ *   tri_bin_sort        duplication of visible items into the tiles they touch,
+ *                       binned by tile into per-tile ranges, each range ordered by
+ *                       centroid depth (Supp. "Tile assignment", "Depth sorting");
  *   tri_render_fwd      per-pixel front-to-back compositing with alpha = o I (Sec. 3.1:
  *                       the rendering equation of prior splatting work);
  *   tri_render_bwd      back-to-front recomputation and per-item gradients;
@@ -135,13 +134,14 @@ tri_status tri_reserve(tri_ctx *ctx, int64_t pair_capacity);
 tri_status tri_preprocess(tri_ctx *ctx, const tri_scene *scene, const tri_camera *cams,
                           int nviews, void *stream);
 
-/* Step 2 (Supp. "Depth sorting", "Tile assignment"): stable LSD radix sort of the
- * visible items by 32-bit centroid-depth key, duplication of each item into the tiles
- * of its rectangle (in depth order), stable LSD radix sort of the pairs by tile id, and
- * per-tile [start, end) ranges. The result equals a stable sort of the 64-bit keys
- * (tile << 32 | depth bits) emitted in item order.
- * If `num_pairs_out` is non-null the call synchronises, returns the pair count there,
- * and re-runs the duplication with a larger pair buffer when it overflowed. If null,
+/* Step 2 (Supp. "Depth sorting", "Tile assignment"): duplication of every visible item
+ * into the tiles of its rectangle, binned by tile (per-tile counts, their scan into
+ * [start, end) ranges, a scatter into the ranges), then each tile's range sorted by
+ * (32-bit centroid-depth key, item id). The result equals a stable sort of the 64-bit
+ * keys (tile << 32 | depth bits) emitted in item order.
+ * If `num_pairs_out` is non-null the call synchronises after the counts, returns the
+ * pair count there, and grows the pair buffers before the scatter when they are too
+ * small. If null,
  * nothing synchronises; an overflow drops pairs, sets the status word, and
  * tri_ctx_check reports TRI_ERR_CAPACITY. */
 tri_status tri_bin_sort(tri_ctx *ctx, int64_t *num_pairs_out, void *stream);
@@ -183,7 +183,9 @@ tri_status tri_ctx_check(tri_ctx *ctx, tri_ctx_info *info, void *stream);
  *   2: tile ranges (uint32 [total_tiles][2])       3: item depth keys (uint32 [n_items])
  *   4: item pixel rectangles (uint16 [n_items][4]: x0, y0, x1, y1 inclusive)
  *   5: item tile counts (uint32 [n_items])
- *   6: depth-sorted visible item ids (uint32 [n_visible])
+ *   6: binned pairs (uint64 [n_pairs]: depth key << 32 | item id), grouped by tile;
+ *      within a tile in scatter order, except tiles of more than 2048 pairs, whose
+ *      ranges hold the sort's intermediate runs
  *   7: per-item render records (float [n_items][16])
  *   8: per-item 2D gradients (float [n_items][16]) */
 tri_status tri_debug_copy(tri_ctx *ctx, int which, void *dst, size_t max_bytes, size_t *bytes);

@@ -15,7 +15,7 @@ using namespace ts;
 
 namespace {
 
-constexpr int64_t MAX_PAIRS = (int64_t)LB_MASK;  // look-back words carry 30-bit counts
+constexpr int64_t MAX_PAIRS = (int64_t)LB_MASK;  // pair slots and item ids stay below 2^30
 
 tri_status fail(tri_ctx *c, tri_status s, const std::string &msg) {
     if (c) c->err = msg;
@@ -85,13 +85,6 @@ tri_status set_device(tri_ctx *c) {
     return TRI_OK;
 }
 
-int tile_digits(int total_tiles) {
-    int bits = 0;
-    while (bits < 31 && (1ll << bits) < (int64_t)total_tiles) ++bits;
-    int d = (bits + 7) / 8;
-    return d < 1 ? 1 : d;
-}
-
 int64_t default_pair_cap(int64_t n_items) {
     int64_t cap = 4 * n_items;
     if (cap < (1 << 20)) cap = 1 << 20;
@@ -150,7 +143,6 @@ tri_status ts_build_views(tri_ctx *c, const tri_camera *cams, int nviews, std::v
 
 namespace {
 
-size_t sort_status_words(int64_t cap, int tile) { return (size_t)((cap + tile - 1) / tile) * 256; }
 
 // Host -> device copy of a small per-call table. Outside stream capture the driver
 // stages the pageable source, so the caller may reuse it at once. Under capture the
@@ -168,32 +160,40 @@ tri_status upload(tri_ctx *c, void *dst, const void *src, size_t bytes, void *pi
     return TRI_OK;
 }
 
+// Pair buffers for the context's capacity: binned (depth key, item) words, the merge
+// buffer of long tile ranges, and the sorted item ids.
+tri_status ensure_pairs(tri_ctx *c) {
+    ENSURE(c->kv, 8 * (size_t)c->pair_cap);
+    ENSURE(c->kv_tmp, 8 * (size_t)c->pair_cap);
+    ENSURE(c->items, 4 * (size_t)c->pair_cap);
+    return TRI_OK;
+}
+
+BinArgs bin_args(tri_ctx *c) {
+    BinArgs b;
+    b.views = P<ViewDev>(c->views_d);
+    b.nviews = c->nviews;
+    b.n = c->scene.n;
+    b.n_items = c->n_items;
+    b.ntiles = P<uint32_t>(c->ntiles);
+    b.rects = P<ushort4>(c->rects);
+    b.dkeys = P<uint32_t>(c->dkeys);
+    b.tile_count = P<uint32_t>(c->tile_count);
+    b.tile_cursor = P<uint32_t>(c->tile_cursor);
+    b.ranges = P<uint2>(c->ranges);
+    b.kv = P<unsigned long long>(c->kv);
+    b.kv_tmp = P<unsigned long long>(c->kv_tmp);
+    b.items = P<uint32_t>(c->items);
+    b.cap = (uint32_t)c->pair_cap;
+    b.total_tiles = c->total_tiles;
+    b.ctl = ctl_of(c);
+    return b;
+}
+
 tri_status launch_check(tri_ctx *c, const char *what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, what);
     return TRI_OK;
-}
-
-tri_status emit_pairs(tri_ctx *c, cudaStream_t st) {
-    Ctl *ctl = ctl_of(c);
-    const int64_t M = c->n_items;
-    CK(cudaMemsetAsync(P<char>(c->st_emit), 0, sizeof(uint32_t) * ((M + 255) / 256 + 1), st));
-    CK(cudaMemsetAsync(P<char>(c->ranges), 0, sizeof(uint2) * (size_t)c->total_tiles, st));
-    EmitArgs e;
-    e.sorted_items = P<uint32_t>(c->cv[0]);
-    e.ntiles = P<uint32_t>(c->ntiles);
-    e.rects = P<ushort4>(c->rects);
-    e.views = P<ViewDev>(c->views_d);
-    e.nviews = c->nviews;
-    e.n = c->scene.n;
-    e.pkeys = P<uint32_t>(c->pk[0]);
-    e.pvals = P<uint32_t>(c->pv[0]);
-    e.cap = (uint32_t)c->pair_cap;
-    e.tile_passes = c->tile_passes;
-    e.lb_status = P<uint32_t>(c->st_emit);
-    e.ctl = ctl;
-    launch_emit(e, M, st);
-    return launch_check(c, "emit_kernel");
 }
 
 }  // namespace
@@ -260,11 +260,11 @@ tri_status tri_workspace_query(const tri_scene *scene, const tri_camera *cams, i
     const int64_t M = scene->n * nviews;
     const int64_t cap = pair_capacity > 0 ? pair_capacity : default_pair_cap(M);
     size_t b = 0;
-    b += (size_t)M * (sizeof(Rec) + 4 + 8 + 4 + 16 + GRAD_FIELDS * 4);  // records, counts, rects, keys, 2x2 lists, grads
-    b += (size_t)cap * 16;                                            // 2 x (key, value) pair buffers
-    b += (size_t)tiles * (8 + 32) + (size_t)pix * 8;
-    b += sizeof(uint32_t) * (sort_status_words(M, 1024) * 4 + sort_status_words(cap, 1024) * 3 + (M + 255) / 256 * 2);
+    b += (size_t)M * (sizeof(Rec) + 4 + 8 + 4 + GRAD_FIELDS * 4);    // records, counts, rects, keys, grads
+    b += (size_t)cap * (8 + 8 + 4);                                   // binned pairs, merge buffer, items
+    b += (size_t)tiles * (4 + 4 + 8 + 32) + (size_t)pix * 8;          // counts, cursors, ranges, maxima
     b += sizeof(Ctl) + nviews * (sizeof(ViewDev) + 2 * sizeof(ViewOut));
+    b += 256 * 18;                                                    // allocation rounding
     *bytes = b;
     return TRI_OK;
 }
@@ -276,11 +276,7 @@ tri_status tri_reserve(tri_ctx *c, int64_t pair_capacity) {
     tri_status s = set_device(c);
     if (s != TRI_OK) return s;
     if (pair_capacity > c->pair_cap) c->pair_cap = pair_capacity;
-    for (int k = 0; k < 2; ++k) {
-        ENSURE(c->pk[k], sizeof(uint32_t) * (size_t)c->pair_cap);
-        ENSURE(c->pv[k], sizeof(uint32_t) * (size_t)c->pair_cap);
-    }
-    return TRI_OK;
+    return ensure_pairs(c);
 }
 
 tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *cams, int nviews, void *stream) {
@@ -302,7 +298,6 @@ tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *
     c->n_items = M;
     c->total_tiles = tiles;
     c->total_pix = pix;
-    c->tile_passes = tile_digits(tiles);
     c->stage = 0;
     ENSURE(c->ctl, sizeof(Ctl));
     ENSURE(c->views_d, sizeof(ViewDev) * nviews);
@@ -312,10 +307,8 @@ tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *
     ENSURE(c->ntiles, 4 * (size_t)M);
     ENSURE(c->rects, 8 * (size_t)M);
     ENSURE(c->dkeys, 4 * (size_t)M);
-    for (int k = 0; k < 2; ++k) {
-        ENSURE(c->ck[k], 4 * (size_t)M);
-        ENSURE(c->cv[k], 4 * (size_t)M);
-    }
+    ENSURE(c->tile_count, 4 * (size_t)tiles);
+    ENSURE(c->tile_cursor, 4 * (size_t)tiles);
     ENSURE(c->ranges, sizeof(uint2) * (size_t)tiles);
     ENSURE(c->tile_max, 4 * 8 * (size_t)tiles);
     ENSURE(c->Tfin, 4 * (size_t)pix);
@@ -352,76 +345,38 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     begin_call(c, st);
     Ctl *ctl = ctl_of(c);
-    const int64_t M = c->n_items;
-    // counters owned by this step (the depth histograms come from tri_preprocess)
+    if (c->pair_cap <= 0) c->pair_cap = default_pair_cap(c->n_items);
+    if ((s = ensure_pairs(c)) != TRI_OK) return s;
+    // counters owned by this step
     CK(cudaMemsetAsync(&ctl->n_pairs, 0, 3 * 4, st));  // n_pairs, n_pairs_used, overflow
-    CK(cudaMemsetAsync(&ctl->cta_counter[1], 0, 4, st));
-    CK(cudaMemsetAsync(&ctl->pass_counter[0], 0, sizeof(ctl->pass_counter), st));
-    CK(cudaMemsetAsync(&ctl->tile_hist[0][0], 0, sizeof(ctl->tile_hist), st));
-    // 1. depth sort of the visible items (4 x 8-bit passes)
-    const int dtile = onesweep_tile((uint32_t)M, c->sms);
-    const size_t dwords = sort_status_words(M, dtile);
-    ENSURE(c->st_depth, 4 * dwords * 4);
-    CK(cudaMemsetAsync(c->st_depth.p, 0, 4 * dwords * 4, st));
-    // all items take part (invisible ones carry the largest key and end up last), so
-    // the first pass reads the per-item keys and numbers the values itself
-    int cur = 1;
-    for (int p = 0; p < 4; ++p) {
-        const uint32_t *kin = p == 0 ? P<uint32_t>(c->dkeys) : P<uint32_t>(c->ck[cur ^ 1]);
-        const uint32_t *vin = p == 0 ? nullptr : P<uint32_t>(c->cv[cur ^ 1]);
-        launch_onesweep_pass(kin, vin, P<uint32_t>(c->ck[cur]), P<uint32_t>(c->cv[cur]), nullptr, (uint32_t)M,
-                             ctl->depth_hist[p], P<uint32_t>(c->st_depth) + p * dwords, &ctl->pass_counter[p],
-                             8 * p, &ctl->error, dtile, c->sms, st);
-        cur ^= 1;
-    }
-    if ((s = launch_check(c, "onesweep (depth)")) != TRI_OK) return s;
-    // 2. emission (result of the depth sort is back in ck[0] / cv[0])
-    if (c->pair_cap <= 0) c->pair_cap = default_pair_cap(M);
-    for (int k = 0; k < 2; ++k) {
-        ENSURE(c->pk[k], sizeof(uint32_t) * (size_t)c->pair_cap);
-        ENSURE(c->pv[k], sizeof(uint32_t) * (size_t)c->pair_cap);
-    }
-    ENSURE(c->st_emit, sizeof(uint32_t) * ((M + 255) / 256 + 1));
-    if ((s = emit_pairs(c, st)) != TRI_OK) return s;
+    CK(cudaMemsetAsync(&ctl->work_counter[2], 0, 4, st));
+    CK(cudaMemsetAsync(c->tile_count.p, 0, 4 * (size_t)c->total_tiles, st));
+    BinArgs b = bin_args(c);
+    // 1. per-tile counts, 2. ranges
+    launch_bin_count(b, c->sms, st);
+    launch_bin_scan(b, st);
+    if ((s = launch_check(c, "bin_count / bin_scan")) != TRI_OK) return s;
     if (num_pairs_out) {
         uint32_t np = 0;
         CK(cudaMemcpyAsync(&np, &ctl->n_pairs, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if ((int64_t)np > c->pair_cap) {
+            // grow the pair buffers and redo the scan with the new capacity
             if ((int64_t)np > MAX_PAIRS) return fail(c, TRI_ERR_CAPACITY, "more than 2^30 pairs");
             int64_t cap = (int64_t)np + (int64_t)np / 4;
             if (cap > MAX_PAIRS) cap = MAX_PAIRS;
             c->pair_cap = cap;
-            for (int k = 0; k < 2; ++k) {
-                ENSURE(c->pk[k], sizeof(uint32_t) * (size_t)c->pair_cap);
-                ENSURE(c->pv[k], sizeof(uint32_t) * (size_t)c->pair_cap);
-            }
-            // redo the emission with the larger buffer
-            CK(cudaMemsetAsync(&ctl->n_pairs, 0, 4 * 4, st));  // n_pairs, n_pairs_used, overflow, error
-            CK(cudaMemsetAsync(&ctl->cta_counter[1], 0, 4, st));
-            CK(cudaMemsetAsync(&ctl->tile_hist[0][0], 0, sizeof(ctl->tile_hist), st));
-            if ((s = emit_pairs(c, st)) != TRI_OK) return s;
+            if ((s = ensure_pairs(c)) != TRI_OK) return s;
+            b = bin_args(c);
+            launch_bin_scan(b, st);
+            if ((s = launch_check(c, "bin_scan")) != TRI_OK) return s;
         }
         *num_pairs_out = np;
     }
-    // 3. tile sort of the pairs
-    const int ptile = onesweep_tile((uint32_t)c->pair_cap, c->sms);
-    const size_t pwords = sort_status_words(c->pair_cap, ptile);
-    ENSURE(c->st_pairs, 4 * pwords * c->tile_passes);
-    CK(cudaMemsetAsync(c->st_pairs.p, 0, 4 * pwords * c->tile_passes, st));
-    cur = 0;
-    for (int p = 0; p < c->tile_passes; ++p) {
-        launch_onesweep_pass(P<uint32_t>(c->pk[cur]), P<uint32_t>(c->pv[cur]), P<uint32_t>(c->pk[cur ^ 1]),
-                             P<uint32_t>(c->pv[cur ^ 1]), &ctl->n_pairs_used, (uint32_t)c->pair_cap,
-                             ctl->tile_hist[p], P<uint32_t>(c->st_pairs) + p * pwords, &ctl->pass_counter[4 + p],
-                             8 * p, &ctl->error, ptile, c->sms, st);
-        cur ^= 1;
-    }
-    c->pair_final = cur;
-    // 4. ranges
-    launch_ranges(P<uint32_t>(c->pk[cur]), &ctl->n_pairs_used, P<uint2>(c->ranges), (uint32_t)c->total_tiles,
-                  &ctl->error, c->sms * 8, st);
-    if ((s = launch_check(c, "onesweep (tiles) / ranges")) != TRI_OK) return s;
+    // 3. scatter into the tile ranges, 4. per-tile depth order
+    launch_bin_scatter(b, c->sms, st);
+    launch_tile_sort(b, c->sms, st);
+    if ((s = launch_check(c, "bin_scatter / tile_sort")) != TRI_OK) return s;
     c->stage = 2;
     return TRI_OK;
 }
@@ -433,7 +388,7 @@ static RenderArgs render_args(tri_ctx *c, TsDevBuf &outs) {
     r.nviews = c->nviews;
     r.total_tiles = c->total_tiles;
     r.ranges = P<uint2>(c->ranges);
-    r.items = P<uint32_t>(c->pv[c->pair_final]);
+    r.items = P<uint32_t>(c->items);
     r.recs = P<Rec>(c->recs);
     r.rects = P<ushort4>(c->rects);
     r.T_final = P<float>(c->Tfin);
@@ -564,13 +519,24 @@ tri_status tri_debug_copy(tri_ctx *c, int which, void *dst, size_t max_bytes, si
     const size_t M = (size_t)c->n_items;
     const size_t np = (size_t)(h.n_pairs_used);
     switch (which) {
-        case 0: src = c->pk[c->pair_final].p; n = 4 * np; break;
-        case 1: src = c->pv[c->pair_final].p; n = 4 * np; break;
+        case 0: {
+            // tile id of every sorted pair, expanded from the tile ranges
+            n = 4 * np;
+            if (n > max_bytes) return fail(c, TRI_ERR_CAPACITY, "destination too small");
+            std::vector<uint2> rg((size_t)c->total_tiles);
+            if (!rg.empty()) CK(cudaMemcpy(rg.data(), c->ranges.p, sizeof(uint2) * rg.size(), cudaMemcpyDeviceToHost));
+            uint32_t *out = (uint32_t *)dst;
+            for (size_t t = 0; t < rg.size(); ++t)
+                for (uint32_t k = rg[t].x; k < rg[t].y && k < np; ++k) out[k] = (uint32_t)t;
+            if (bytes) *bytes = n;
+            return TRI_OK;
+        }
+        case 1: src = c->items.p; n = 4 * np; break;
         case 2: src = c->ranges.p; n = sizeof(uint2) * (size_t)c->total_tiles; break;
         case 3: src = c->dkeys.p; n = 4 * M; break;
         case 4: src = c->rects.p; n = 8 * M; break;
         case 5: src = c->ntiles.p; n = 4 * M; break;
-        case 6: src = c->cv[0].p; n = 4 * (size_t)h.n_visible; break;
+        case 6: src = c->kv.p; n = 8 * np; break;
         case 7: src = c->recs.p; n = sizeof(Rec) * M; break;
         case 8: src = c->grad2d.p; n = sizeof(float) * GRAD_FIELDS * M; break;
         default: return fail(c, TRI_ERR_INVALID_ARG, "unknown buffer");

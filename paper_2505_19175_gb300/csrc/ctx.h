@@ -22,10 +22,8 @@ struct tri_ctx {
     int64_t n_items = 0;
     int total_tiles = 0;
     int64_t total_pix = 0;
-    int tile_passes = 1;
     int64_t pair_cap = 0;
     int stage = 0;  // 1 preprocessed, 2 sorted, 3 rendered, 4 backward rendered
-    int pair_final = 0;
     uint64_t realloc_gen = 0;   // bumped whenever a device buffer is reallocated
     // streams of the previous and the current call: a reallocation waits for both,
     // not for the whole device
@@ -33,12 +31,11 @@ struct tri_ctx {
     // pinned copies of the small per-call tables, used while the stream is captured
     ts::ViewDev *h_views = nullptr;
     ts::ViewOut *h_outs_fwd = nullptr, *h_outs_bwd = nullptr;
-    TsDevBuf views_d, outs_fwd, outs_bwd, ctl, recs, ntiles, rects, dkeys, ck[2], cv[2], pk[2], pv[2], ranges,
-        tile_max, Tfin, ncontrib, grad2d, st_emit, st_depth, st_pairs;
+    TsDevBuf views_d, outs_fwd, outs_bwd, ctl, recs, ntiles, rects, dkeys, tile_count, tile_cursor, kv, kv_tmp,
+        items, ranges, tile_max, Tfin, ncontrib, grad2d;
     std::vector<TsDevBuf *> all() {
-        return {&views_d, &outs_fwd, &outs_bwd, &ctl, &recs, &ntiles, &rects, &dkeys, &ck[0], &ck[1], &cv[0],
-                &cv[1], &pk[0], &pk[1], &pv[0], &pv[1], &ranges, &tile_max, &Tfin, &ncontrib, &grad2d,
-                &st_emit, &st_depth, &st_pairs};
+        return {&views_d, &outs_fwd, &outs_bwd, &ctl, &recs, &ntiles, &rects, &dkeys, &tile_count, &tile_cursor,
+                &kv, &kv_tmp, &items, &ranges, &tile_max, &Tfin, &ncontrib, &grad2d};
     }
 };
 

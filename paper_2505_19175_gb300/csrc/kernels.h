@@ -16,6 +16,7 @@ struct PreArgs {
     ushort4 *rects;            // pixel rectangle (x0, y0, x1, y1), inclusive
     uint32_t *dkeys;           // depth key per item; 0xffffffff for items with no tile
     Ctl *ctl;
+    int depth_hist = 0;        // also accumulate the 4 digit histograms of the depth keys
 };
 
 struct PreBwdArgs {
@@ -67,6 +68,30 @@ void launch_emit(const EmitArgs &a, int64_t max_items, cudaStream_t st);
 
 void launch_ranges(const uint32_t *keys, const uint32_t *count, uint2 *ranges, uint32_t total_tiles, uint32_t *err,
                    int grid, cudaStream_t st);
+
+// ---- tile binning (binning.cu) ----
+struct BinArgs {
+    const ViewDev *views;
+    int nviews;
+    int64_t n;                      // triangles per view
+    int64_t n_items;                // views x triangles
+    const uint32_t *ntiles;         // per item
+    const ushort4 *rects;           // per-item pixel rectangles
+    const uint32_t *dkeys;          // per-item depth keys
+    uint32_t *tile_count;           // [total_tiles], zeroed before bin_count
+    uint32_t *tile_cursor;          // [total_tiles]
+    uint2 *ranges;                  // [total_tiles]
+    unsigned long long *kv;         // [cap] (depth key << 32 | item), unsorted within tiles
+    unsigned long long *kv_tmp;     // [cap] merge buffer for ranges longer than one chunk
+    uint32_t *items;                // [cap] sorted item ids
+    uint32_t cap;
+    int total_tiles;
+    Ctl *ctl;                       // n_pairs / n_pairs_used / overflow, work_counter[2]
+};
+void launch_bin_count(const BinArgs &a, int sms, cudaStream_t st);
+void launch_bin_scan(const BinArgs &a, cudaStream_t st);
+void launch_bin_scatter(const BinArgs &a, int sms, cudaStream_t st);
+void launch_tile_sort(const BinArgs &a, int sms, cudaStream_t st);
 
 // ---- rendering ----
 struct RenderArgs {

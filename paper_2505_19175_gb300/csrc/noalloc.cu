@@ -188,6 +188,7 @@ extern "C" tri_status tri_render_fwd_noalloc(const tri_scene *scene, const tri_c
         a.n = M; a.sh_degree = scene->sh_degree;
         a.views = dview; a.nviews = 1;
         a.recs = recs; a.ntiles = ntiles; a.rects = rects; a.dkeys = dkeys; a.ctl = ctl;
+        a.depth_hist = 1;
         launch_preprocess_fwd(a, st);
         NA_CK(cudaGetLastError());
         // depth sort of all items (tile size fixed to the smallest, as the status area assumes)

@@ -7,8 +7,8 @@
 //   - SH colour for the direction camera centre -> centroid (Sec. 4: degree 3);
 //   - tight rectangle of the triangle shrunk about its incenter by
 //     f = 1 - (tau/o)^(1/sigma), tau = ALPHA_MIN (Supp. "Tile assignment");
-//   - order-preserving compaction of the visible items (single-pass decoupled
-//     look-back scan) and the digit histograms of their 32-bit depth keys.
+//   - the count of visible items and, on request (the global radix-sort path of the
+//     allocation-free render), the digit histograms of their 32-bit depth keys.
 // Backward: the chain rule of all of the above from the per-item gradient record.
 #include "geometry.cuh"
 #include "kernels.h"
@@ -158,14 +158,17 @@ preprocess_fwd_kernel(PreArgs a) {
         a.rects[m] = rect;
         a.dkeys[m] = key;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
+        for (int p = 0; p < 4; ++p)
+            if (a.depth_hist) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
     }
     const uint32_t wv = __reduce_add_sync(0xffffffffu, nvis);
     if ((tid & 31) == 0 && wv) atomicAdd(&s_nvis, wv);
     __syncthreads();
-    for (int k = tid; k < 4 * 256; k += PRE_THREADS) {
-        const uint32_t c = (&s_hist[0][0])[k];
-        if (c) atomicAdd(&(&a.ctl->depth_hist[0][0])[k], c);
+    if (a.depth_hist) {
+        for (int k = tid; k < 4 * 256; k += PRE_THREADS) {
+            const uint32_t c = (&s_hist[0][0])[k];
+            if (c) atomicAdd(&(&a.ctl->depth_hist[0][0])[k], c);
+        }
     }
     if (tid == 0 && s_nvis) atomicAdd(&a.ctl->n_visible, s_nvis);
 }

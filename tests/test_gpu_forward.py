@@ -54,6 +54,55 @@ def test_tile_lists_bit_exact_against_stable_sort():
         assert np.all(tiles[s:e] == t) and (s == 0 or tiles[s - 1] != t) and (e == len(tiles) or tiles[e] != t)
 
 
+def _crowded_scene(n, seed, W=64, H=48, px=(18.0, 30.0)):
+    """n small triangles whose centroids project inside one 16x16 tile (pixels 16..31)."""
+    rng = np.random.default_rng(seed)
+    cam = synth.camera_identity(W, H)
+    z = rng.uniform(2.0, 6.0, n)
+    u = rng.uniform(px[0], px[1], n)
+    v = rng.uniform(px[0], px[1], n)
+    c = np.stack([(u - cam.cx) / cam.fx * z, (v - cam.cy) / cam.fy * z, z], 1)
+    size = (3.0 / cam.fx) * z                                    # about 3 px across
+    verts = c[:, None, :] + size[:, None, None] * rng.standard_normal((n, 3, 3)) * np.array([1.0, 1.0, 0.05])
+    scene = synth.Scene(verts.astype(np.float32), (0.3 * rng.standard_normal((n, 1, 3))).astype(np.float32),
+                        rng.uniform(0.05, 0.6, n).astype(np.float32), rng.uniform(0.5, 2.0, n).astype(np.float32), 0)
+    return scene, cam
+
+
+@pytest.mark.parametrize("n", [2500, 9000])
+def test_crowded_tile_sorted_by_chunks_and_merges(n):
+    """A tile with more pairs than one shared-memory sort holds (2048) is sorted in
+    chunks and merged; the lists stay equal to the stable sort and the image to the
+    oracle."""
+    scene, cam = _crowded_scene(n, seed=20 + n)
+    imgs, T, _, ctx, _ = gpu_forward(scene, [cam])
+    rg = ctx.debug("ranges")
+    assert (rg[:, 1] - rg[:, 0]).max() > 2048
+    tiles = ctx.debug("pair_tiles").astype(np.uint64)
+    items = ctx.debug("pair_items").astype(np.uint64)
+    et, ei = expected_pairs_from_items(ctx, [cam])
+    np.testing.assert_array_equal(tiles, et)
+    np.testing.assert_array_equal(items, ei)
+    ref = O.render(scene, cam, flags=True)
+    _compare(imgs[0], T[0], ref, max_flagged=5e-2)
+
+
+def test_binned_pairs_hold_each_tiles_items():
+    """The scatter puts exactly the tile's items into its range; the sort only reorders."""
+    scene = synth.random_scene(1500, seed=21, deg=0, size=(0.05, 0.8))
+    cam = synth.camera_identity(160, 112)
+    _, _, _, ctx, _ = gpu_forward(scene, [cam])
+    binned = ctx.debug("binned")
+    items = ctx.debug("pair_items")
+    rg = ctx.debug("ranges")
+    dk = ctx.debug("depth_keys")
+    assert len(binned) == len(items) == rg[-1, 1]
+    for s, e in rg:
+        b = binned[s:e]
+        np.testing.assert_array_equal(np.sort(b) & np.uint64(0xffffffff), items[s:e].astype(np.uint64))
+        np.testing.assert_array_equal(b >> np.uint64(32), dk[(b & np.uint64(0xffffffff)).astype(np.int64)])
+
+
 def test_tile_lists_match_oracle_rectangles():
     scene = synth.random_scene(2000, seed=6, deg=0, size=(0.05, 0.8), sigma=(0.3, 3.0), opacity=(0.01, 0.99))
     cam = synth.camera_identity(200, 150)
