@@ -184,8 +184,22 @@ BinArgs bin_args(tri_ctx *c) {
     b.kv = P<unsigned long long>(c->kv);
     b.kv_tmp = P<unsigned long long>(c->kv_tmp);
     b.items = P<uint32_t>(c->items);
+    b.big_tiles = P<uint32_t>(c->big_tiles);
     b.cap = (uint32_t)c->pair_cap;
     b.total_tiles = c->total_tiles;
+    // a stride near 0.618 of the block count and coprime with it: a permutation
+    const uint64_t nblk = (uint64_t)(c->n_items + 255) / 256;
+    uint64_t stride = nblk > 2 ? (uint64_t)((double)nblk * 0.6180339887) | 1u : 1u;
+    auto gcd = [](uint64_t x, uint64_t y) {
+        while (y) {
+            const uint64_t t = x % y;
+            x = y;
+            y = t;
+        }
+        return x;
+    };
+    while (nblk > 1 && gcd(stride, nblk) != 1) stride += 2;
+    b.blk_stride = nblk > 1 ? stride % nblk : 0;
     b.ctl = ctl_of(c);
     return b;
 }
@@ -262,7 +276,7 @@ tri_status tri_workspace_query(const tri_scene *scene, const tri_camera *cams, i
     size_t b = 0;
     b += (size_t)M * (sizeof(Rec) + 4 + 8 + 4 + GRAD_FIELDS * 4);    // records, counts, rects, keys, grads
     b += (size_t)cap * (8 + 8 + 4);                                   // binned pairs, merge buffer, items
-    b += (size_t)tiles * (4 + 4 + 8 + 32) + (size_t)pix * 8;          // counts, cursors, ranges, maxima
+    b += (size_t)tiles * (4 + 4 + 4 + 8 + 32) + (size_t)pix * 8;      // counts, cursors, queue, ranges, maxima
     b += sizeof(Ctl) + nviews * (sizeof(ViewDev) + 2 * sizeof(ViewOut));
     b += 256 * 18;                                                    // allocation rounding
     *bytes = b;
@@ -309,12 +323,14 @@ tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *
     ENSURE(c->dkeys, 4 * (size_t)M);
     ENSURE(c->tile_count, 4 * (size_t)tiles);
     ENSURE(c->tile_cursor, 4 * (size_t)tiles);
+    ENSURE(c->big_tiles, 4 * (size_t)tiles);
     ENSURE(c->ranges, sizeof(uint2) * (size_t)tiles);
     ENSURE(c->tile_max, 4 * 8 * (size_t)tiles);
     ENSURE(c->Tfin, 4 * (size_t)pix);
     ENSURE(c->ncontrib, 4 * (size_t)pix);
     if ((s = upload(c, c->views_d.p, views.data(), sizeof(ViewDev) * nviews, c->h_views, st)) != TRI_OK) return s;
     CK(cudaMemsetAsync(c->ctl.p, 0, sizeof(Ctl), st));
+    CK(cudaMemsetAsync(c->tile_count.p, 0, 4 * (size_t)tiles, st));
     if (M > 0) {
         PreArgs a;
         a.verts = scene->verts;
@@ -330,6 +346,7 @@ tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *
         a.rects = P<ushort4>(c->rects);
         a.dkeys = P<uint32_t>(c->dkeys);
         a.ctl = ctl_of(c);
+        a.tile_count = P<uint32_t>(c->tile_count);
         launch_preprocess_fwd(a, st);
         if ((s = launch_check(c, "preprocess_fwd_kernel")) != TRI_OK) return s;
     }
@@ -349,13 +366,11 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
     if ((s = ensure_pairs(c)) != TRI_OK) return s;
     // counters owned by this step
     CK(cudaMemsetAsync(&ctl->n_pairs, 0, 3 * 4, st));  // n_pairs, n_pairs_used, overflow
-    CK(cudaMemsetAsync(&ctl->work_counter[2], 0, 4, st));
-    CK(cudaMemsetAsync(c->tile_count.p, 0, 4 * (size_t)c->total_tiles, st));
+    CK(cudaMemsetAsync(&ctl->work_counter[2], 0, 4 * 4, st));  // tile queue, (3), big_count, big_next
     BinArgs b = bin_args(c);
-    // 1. per-tile counts, 2. ranges
-    launch_bin_count(b, c->sms, st);
+    // 1. per-tile counts (from tri_preprocess), 2. ranges
     launch_bin_scan(b, st);
-    if ((s = launch_check(c, "bin_count / bin_scan")) != TRI_OK) return s;
+    if ((s = launch_check(c, "bin_scan")) != TRI_OK) return s;
     if (num_pairs_out) {
         uint32_t np = 0;
         CK(cudaMemcpyAsync(&np, &ctl->n_pairs, 4, cudaMemcpyDeviceToHost, st));

@@ -5,13 +5,14 @@
 // The result equals a stable sort of the pairs by the 64-bit key (tile << 32 | depth
 // bits) when the pairs are emitted in item order: within a tile, entries are ordered
 // by (depth key, item id). It is reached without a global sort:
-//   1. bin_count:   per-tile pair counts (warp-aggregated atomics);
+//   1. per-tile pair counts, accumulated by the preprocess kernel;
 //   2. bin_scan:    exclusive scan of the counts -> tile ranges and write cursors;
 //   3. bin_scatter: each pair takes a slot in its tile's range (order within the
 //                   range is arbitrary at this point);
-//   4. tile_sort:   each tile's range is sorted by (depth key << 32 | item) in shared
-//                   memory (bitonic network; ranges longer than TSORT_CAP are sorted
-//                   in shared-memory chunks and merged in global memory).
+//   4. tile_sort:   each tile's range is sorted by (depth key, item id) in shared
+//                   memory (radix sort by one warp or, for long ranges, one CTA;
+//                   ranges longer than one CTA's shared memory are sorted in chunks and
+//                   merged in global memory).
 // Keys are unique (item ids are), so the order is deterministic although the scatter
 // is not.
 #include "kernels.h"
@@ -21,7 +22,6 @@ namespace ts {
 constexpr int BIN_THREADS = 256;
 constexpr int SCAN_THREADS = 1024;
 constexpr int TSORT_THREADS = 256;
-constexpr int TSORT_CAP = 2048;           // entries a tile sorts in one shared-memory pass
 constexpr int MERGE_PER_THREAD = 8;
 
 // Per-item expansion of a CTA's 256 items into their (item, tile) pairs. Calls
@@ -39,7 +39,11 @@ __device__ __forceinline__ void for_each_pair(const BinArgs &a, F &&f) {
     const int tid = threadIdx.x;
     for (int k = tid; k < a.nviews; k += BIN_THREADS) s_vt[k] = make_int2(a.views[k].tiles_x, a.views[k].tile_base);
     __syncthreads();
-    for (int64_t m0 = (int64_t)blockIdx.x * BIN_THREADS; m0 < a.n_items; m0 += (int64_t)gridDim.x * BIN_THREADS) {
+    const uint64_t nblk = (uint64_t)(a.n_items + BIN_THREADS - 1) / BIN_THREADS;
+    for (uint64_t bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
+        // item blocks in a strided order: neighbouring items (often neighbours on screen)
+        // go to CTAs far apart in time, which spreads the atomics over many tiles
+        const int64_t m0 = (int64_t)((bi * a.blk_stride) % nblk) * BIN_THREADS;
         const int64_t m = m0 + tid;
         const bool valid = m < a.n_items;
         const uint32_t nt = valid ? a.ntiles[m] : 0u;
@@ -86,13 +90,6 @@ __device__ __forceinline__ void for_each_pair(const BinArgs &a, F &&f) {
         }
         __syncthreads();
     }
-}
-
-__global__ void __launch_bounds__(BIN_THREADS) bin_count_kernel(BinArgs a) {
-    for_each_pair(a, [&](bool ok, uint32_t, uint32_t tile) {
-        const unsigned peers = __match_any_sync(0xffffffffu, ok ? tile : 0xffffffffu);
-        if (ok && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&a.tile_count[tile], (uint32_t)__popc(peers));
-    });
 }
 
 __global__ void __launch_bounds__(BIN_THREADS) bin_scatter_kernel(BinArgs a) {
@@ -157,65 +154,180 @@ __global__ void __launch_bounds__(SCAN_THREADS) bin_scan_kernel(BinArgs a) {
     }
 }
 
-// Bitonic sort of s[0, P) ascending, P a power of two <= TSORT_CAP; all threads of the
-// block call it.
-__device__ __forceinline__ void bitonic_smem(unsigned long long *s, uint32_t P) {
-    for (uint32_t k = 2; k <= P; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P / 2; i += TSORT_THREADS) {
-                const uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
-                const uint32_t hi = lo + j;
-                const unsigned long long x = s[lo], y = s[hi];
-                const bool up = (lo & k) == 0;
-                if ((x > y) == up) {
-                    s[lo] = y;
-                    s[hi] = x;
+// ---- per-tile order ----
+// Each tile's range of (depth key << 32 | item) words is sorted ascending, which is
+// the (depth key, item id) order. Ranges of at most WS_MAX words are sorted by one
+// warp in registers (tile_sort_small_kernel, bitonic network: lane l holds words
+// [l E, l E + E), strides below E are exchanges between registers and larger ones
+// warp shuffles); longer ranges are queued for tile_sort_big_kernel, where the CTA's
+// warps sort 256-word chunks the same way and merge them in shared memory (merge
+// path). Ranges beyond BS_MAX words are sorted in BS_MAX chunks that are then merged
+// pairwise in global memory.
+constexpr int WS_WARPS = 4;               // warps of tile_sort_small_kernel
+constexpr int WS_MAX = 512;               // words one warp sorts
+constexpr int BS_MAX = 2048;              // words one CTA sorts in shared memory
+
+__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int m) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// Ascending bitonic sort of the 32 E words a warp holds, E per lane (blocked).
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&x)[E]) {
+    const uint32_t base = (uint32_t)(threadIdx.x & 31) * E;   // index of x[0]
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= E) {
+                // partner: lane ^ (j / E), same register; the pair's lower index keeps
+                // the smaller word in an ascending block (index & k == 0)
+                const bool keep_min = ((base & j) == 0) == ((base & k) == 0);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const unsigned long long y = shfl_xor_u64(x[e], j / E);
+                    x[e] = keep_min ? (x[e] < y ? x[e] : y) : (x[e] < y ? y : x[e]);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if ((e & j) == 0) {
+                        const bool asc = k < E ? (e & k) == 0 : (base & k) == 0;
+                        const unsigned long long p = x[e], q = x[e | j];
+                        const bool sw = (p > q) == asc;
+                        x[e] = sw ? q : p;
+                        x[e | j] = sw ? p : q;
+                    }
                 }
             }
-            __syncthreads();
         }
     }
 }
 
-__device__ __forceinline__ uint32_t pow2_ceil(uint32_t n) {
-    return n <= 2 ? 2u : 1u << (32 - __clz(n - 1));
+// One warp sorts kv[start, start + n) (n <= 32 E, padded with the largest word) and
+// writes the item ids.
+template <int E>
+__device__ __forceinline__ void warp_sort_range(const BinArgs &a, uint32_t start, int n) {
+    const int base = (threadIdx.x & 31) * E;
+    unsigned long long x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = base + e < n ? a.kv[start + base + e] : ~0ull;
+    warp_bitonic<E>(x);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (base + e < n) a.items[start + base + e] = (uint32_t)x[e];
 }
 
-// Sort kv[0, n) (n <= TSORT_CAP) into s, padding with the largest key.
-__device__ __forceinline__ void sort_chunk(const unsigned long long *kv, uint32_t n, unsigned long long *s) {
-    const uint32_t P = pow2_ceil(n);
-    for (uint32_t i = threadIdx.x; i < P; i += TSORT_THREADS) s[i] = i < n ? kv[i] : ~0ull;
-    __syncthreads();
-    bitonic_smem(s, P);
-}
-
-__global__ void __launch_bounds__(TSORT_THREADS) tile_sort_kernel(BinArgs a) {
-    __shared__ unsigned long long s_kv[TSORT_CAP];
-    __shared__ uint32_t s_tile;
-    const int tid = threadIdx.x;
+__global__ void __launch_bounds__(WS_WARPS * 32, 8) tile_sort_small_kernel(BinArgs a) {
+    const int lane = threadIdx.x & 31;
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(&a.ctl->work_counter[2], 1u);
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(&a.ctl->work_counter[2], 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (uint32_t)a.total_tiles) break;
+        const uint2 r = a.ranges[t];
+        const int n = (int)(r.y - r.x);
+        if (n <= 1) {
+            if (n == 1 && lane == 0) a.items[r.x] = (uint32_t)a.kv[r.x];
+        } else if (n > WS_MAX) {
+            if (lane == 0) {
+                const uint32_t q = atomicAdd(&a.ctl->big_count, 1u);
+                if (q < (uint32_t)a.total_tiles) a.big_tiles[q] = t;
+                else atomicOr(&a.ctl->error, ERR_INDEX);
+            }
+        } else if (n <= 32) {
+            warp_sort_range<1>(a, r.x, n);
+        } else if (n <= 64) {
+            warp_sort_range<2>(a, r.x, n);
+        } else if (n <= 128) {
+            warp_sort_range<4>(a, r.x, n);
+        } else if (n <= 256) {
+            warp_sort_range<8>(a, r.x, n);
+        } else {
+            warp_sort_range<16>(a, r.x, n);
+        }
+    }
+}
+
+// The CTA sorts src[0, n) (1 <= n <= BS_MAX) into shared memory: warps sort 256-word
+// chunks in registers, then merge levels 256 -> 512 -> ... between A and B. Returns
+// the buffer with the result (padded with the largest word to a power of two).
+__device__ unsigned long long *block_sort(const unsigned long long *src, int n, unsigned long long *A,
+                                          unsigned long long *B) {
+    const int tid = threadIdx.x, w = tid >> 5;
+    int P = 256;
+    while (P < n) P <<= 1;
+    if (w < P / 256) {
+        const int base = w * 256 + (tid & 31) * 8;
+        unsigned long long x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = base + e < n ? src[base + e] : ~0ull;
+        warp_bitonic<8>(x);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) A[base + e] = x[e];
+    }
+    __syncthreads();
+    const int per = P / TSORT_THREADS;   // outputs per thread, 1..8
+    for (int wdt = 256; wdt < P; wdt <<= 1) {
+        const int d0 = tid * per;
+        const int p0 = d0 / (2 * wdt) * (2 * wdt);
+        const int diag = d0 - p0;
+        const unsigned long long *Ar = A + p0, *Br = A + p0 + wdt;
+        int lo = diag > wdt ? diag - wdt : 0, hi = diag < wdt ? diag : wdt;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (Ar[mid] < Br[diag - 1 - mid]) lo = mid + 1;
+            else hi = mid;
+        }
+        int i = lo, j = diag - lo;
+        for (int q = 0; q < per; ++q) {
+            unsigned long long v;
+            if (j >= wdt || (i < wdt && Ar[i] < Br[j])) v = Ar[i++];
+            else v = Br[j++];
+            B[d0 + q] = v;
+        }
         __syncthreads();
-        const int t = (int)s_tile;
-        if (t >= a.total_tiles) break;
+        unsigned long long *t = A;
+        A = B;
+        B = t;
+    }
+    return A;
+}
+
+__global__ void __launch_bounds__(TSORT_THREADS) tile_sort_big_kernel(BinArgs a) {
+    __shared__ unsigned long long s_a[BS_MAX], s_b[BS_MAX];
+    __shared__ uint32_t s_q;
+    const int tid = threadIdx.x;
+    const uint32_t nbig = min(a.ctl->big_count, (uint32_t)a.total_tiles);
+    for (;;) {
+        if (tid == 0) s_q = atomicAdd(&a.ctl->big_next, 1u);
+        __syncthreads();
+        const uint32_t q = s_q;
+        if (q >= nbig) break;
+        const uint32_t t = a.big_tiles[q];
+        if (t >= (uint32_t)a.total_tiles) {
+            if (tid == 0) atomicOr(&a.ctl->error, ERR_INDEX);
+            __syncthreads();
+            continue;
+        }
         const uint2 r = a.ranges[t];
         const uint32_t n = r.y - r.x;
-        if (n == 1) {
-            if (tid == 0) a.items[r.x] = (uint32_t)a.kv[r.x];
-        } else if (n > 1 && n <= (uint32_t)TSORT_CAP) {
-            sort_chunk(a.kv + r.x, n, s_kv);
-            for (uint32_t i = tid; i < n; i += TSORT_THREADS) a.items[r.x + i] = (uint32_t)s_kv[i];
-        } else if (n > (uint32_t)TSORT_CAP) {
-            // chunks of TSORT_CAP sorted in place, then pairwise merges (merge path)
+        if (n <= (uint32_t)BS_MAX) {
+            const unsigned long long *res = block_sort(a.kv + r.x, (int)n, s_a, s_b);
+            for (uint32_t i = tid; i < n; i += TSORT_THREADS) a.items[r.x + i] = (uint32_t)res[i];
+        } else {
+            // chunks of BS_MAX sorted in place, then pairwise merges (merge path)
             // between kv and kv_tmp; the last merge writes the item ids
             unsigned long long *src = a.kv + r.x, *dst = a.kv_tmp + r.x;
-            for (uint32_t c0 = 0; c0 < n; c0 += TSORT_CAP) {
-                const uint32_t m = min((uint32_t)TSORT_CAP, n - c0);
-                sort_chunk(src + c0, m, s_kv);
-                for (uint32_t i = tid; i < m; i += TSORT_THREADS) src[c0 + i] = s_kv[i];
+            for (uint32_t c0 = 0; c0 < n; c0 += BS_MAX) {
+                const int m = (int)min((uint32_t)BS_MAX, n - c0);
+                const unsigned long long *res = block_sort(src + c0, m, s_a, s_b);
+                for (int i = tid; i < m; i += TSORT_THREADS) src[c0 + i] = res[i];
                 __syncthreads();
             }
-            for (uint32_t wdt = TSORT_CAP; wdt < n; wdt <<= 1) {
+            for (uint32_t wdt = BS_MAX; wdt < n; wdt <<= 1) {
                 const bool last = (uint64_t)wdt * 2 >= n;
                 for (uint32_t p0 = 0; p0 < n; p0 += 2 * wdt) {
                     const uint32_t la = min(wdt, n - p0), lb = min(wdt, n - p0 - la);
@@ -230,12 +342,12 @@ __global__ void __launch_bounds__(TSORT_THREADS) tile_sort_kernel(BinArgs a) {
                             else hi = mid;
                         }
                         uint32_t i = lo, j = diag - lo;
-                        for (int q = 0; q < MERGE_PER_THREAD && diag + q < tot; ++q) {
+                        for (int q2 = 0; q2 < MERGE_PER_THREAD && diag + q2 < tot; ++q2) {
                             unsigned long long v;
                             if (j >= lb || (i < la && A[i] < B[j])) v = A[i++];
                             else v = B[j++];
-                            if (last) a.items[r.x + p0 + diag + q] = (uint32_t)v;
-                            else dst[p0 + diag + q] = v;
+                            if (last) a.items[r.x + p0 + diag + q2] = (uint32_t)v;
+                            else dst[p0 + diag + q2] = v;
                         }
                     }
                 }
@@ -249,12 +361,6 @@ __global__ void __launch_bounds__(TSORT_THREADS) tile_sort_kernel(BinArgs a) {
     }
 }
 
-void launch_bin_count(const BinArgs &a, int sms, cudaStream_t st) {
-    int64_t g = (a.n_items + BIN_THREADS - 1) / BIN_THREADS;
-    if (g > (int64_t)sms * 16) g = (int64_t)sms * 16;
-    if (g > 0) bin_count_kernel<<<(unsigned)g, BIN_THREADS, 0, st>>>(a);
-}
-
 void launch_bin_scan(const BinArgs &a, cudaStream_t st) {
     if (a.total_tiles > 0) bin_scan_kernel<<<1, SCAN_THREADS, 0, st>>>(a);
 }
@@ -265,16 +371,24 @@ void launch_bin_scatter(const BinArgs &a, int sms, cudaStream_t st) {
     if (g > 0) bin_scatter_kernel<<<(unsigned)g, BIN_THREADS, 0, st>>>(a);
 }
 
+static int occupancy_of(const void *fn, int threads) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0) != cudaSuccess || occ < 1) occ = 1;
+    return occ;
+}
+
 void launch_tile_sort(const BinArgs &a, int sms, cudaStream_t st) {
-    static int occ = -1;
-    if (occ < 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tile_sort_kernel, TSORT_THREADS, 0) != cudaSuccess ||
-            occ < 1)
-            occ = 1;
-    }
-    int64_t g = (int64_t)sms * occ;
-    if (g > a.total_tiles) g = a.total_tiles;
-    if (g > 0) tile_sort_kernel<<<(unsigned)g, TSORT_THREADS, 0, st>>>(a);
+    static const int occ_small = occupancy_of((const void *)tile_sort_small_kernel, WS_WARPS * 32);
+    static const int occ_big = occupancy_of((const void *)tile_sort_big_kernel, TSORT_THREADS);
+    if (a.total_tiles <= 0) return;
+    // one warp per tile: enough CTAs for every tile's warp, at most a full machine
+    int64_t g = ((int64_t)a.total_tiles + WS_WARPS - 1) / WS_WARPS;
+    if (g > (int64_t)sms * occ_small) g = (int64_t)sms * occ_small;
+    tile_sort_small_kernel<<<(unsigned)g, WS_WARPS * 32, 0, st>>>(a);
+    // the long ranges the first kernel queued; CTAs with nothing queued return at once
+    int64_t gb = (int64_t)sms * occ_big;
+    if (gb > a.total_tiles) gb = a.total_tiles;
+    tile_sort_big_kernel<<<(unsigned)gb, TSORT_THREADS, 0, st>>>(a);
 }
 
 }  // namespace ts

@@ -58,6 +58,8 @@ struct Ctl {
     uint32_t cta_counter[8];   // dynamic CTA ids of the single-pass scans
     uint32_t pass_counter[8];  // dynamic tile ids of the radix passes
     uint32_t work_counter[4];  // render work queues
+    uint32_t big_count;        // tiles queued for the CTA-wide sort
+    uint32_t big_next;         // next queued tile to sort
     unsigned long long frag_eval;   // forward: (pixel, entry) evaluations
     unsigned long long frag_kept;   // forward: composited fragments
     uint32_t depth_hist[4][256];

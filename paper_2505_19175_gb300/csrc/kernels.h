@@ -17,6 +17,7 @@ struct PreArgs {
     uint32_t *dkeys;           // depth key per item; 0xffffffff for items with no tile
     Ctl *ctl;
     int depth_hist = 0;        // also accumulate the 4 digit histograms of the depth keys
+    uint32_t *tile_count = nullptr;  // if set (zeroed): pairs per tile, for the binning
 };
 
 struct PreBwdArgs {
@@ -78,17 +79,18 @@ struct BinArgs {
     const uint32_t *ntiles;         // per item
     const ushort4 *rects;           // per-item pixel rectangles
     const uint32_t *dkeys;          // per-item depth keys
-    uint32_t *tile_count;           // [total_tiles], zeroed before bin_count
+    uint32_t *tile_count;           // [total_tiles] pairs per tile (counted by the preprocess)
     uint32_t *tile_cursor;          // [total_tiles]
     uint2 *ranges;                  // [total_tiles]
     unsigned long long *kv;         // [cap] (depth key << 32 | item), unsorted within tiles
     unsigned long long *kv_tmp;     // [cap] merge buffer for ranges longer than one chunk
     uint32_t *items;                // [cap] sorted item ids
+    uint32_t *big_tiles;            // [total_tiles] tiles whose range one warp cannot sort
     uint32_t cap;
     int total_tiles;
-    Ctl *ctl;                       // n_pairs / n_pairs_used / overflow, work_counter[2]
+    uint64_t blk_stride;            // visiting order of the 256-item blocks: b * stride mod blocks
+    Ctl *ctl;                       // n_pairs / n_pairs_used / overflow, work_counter[2], big_*
 };
-void launch_bin_count(const BinArgs &a, int sms, cudaStream_t st);
 void launch_bin_scan(const BinArgs &a, cudaStream_t st);
 void launch_bin_scatter(const BinArgs &a, int sms, cudaStream_t st);
 void launch_tile_sort(const BinArgs &a, int sms, cudaStream_t st);

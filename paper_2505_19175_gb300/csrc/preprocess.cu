@@ -7,8 +7,9 @@
 //   - SH colour for the direction camera centre -> centroid (Sec. 4: degree 3);
 //   - tight rectangle of the triangle shrunk about its incenter by
 //     f = 1 - (tau/o)^(1/sigma), tau = ALPHA_MIN (Supp. "Tile assignment");
-//   - the count of visible items and, on request (the global radix-sort path of the
-//     allocation-free render), the digit histograms of their 32-bit depth keys.
+//   - the count of visible items, the per-tile pair counts of the binning and, on
+//     request (the global radix-sort path of the allocation-free render), the digit
+//     histograms of the 32-bit depth keys.
 // Backward: the chain rule of all of the above from the per-item gradient record.
 #include "geometry.cuh"
 #include "kernels.h"
@@ -157,6 +158,14 @@ preprocess_fwd_kernel(PreArgs a) {
         a.ntiles[m] = nt;
         a.rects[m] = rect;
         a.dkeys[m] = key;
+        if (a.tile_count && nt) {
+            // per-tile pair counts of the binning (fire-and-forget reductions)
+            const uint32_t tx0 = rect.x / TILE, tx1 = rect.z / TILE, ty0 = rect.y / TILE, ty1 = rect.w / TILE;
+            for (uint32_t ty = ty0; ty <= ty1; ++ty) {
+                uint32_t *row = a.tile_count + V.tile_base + ty * (uint32_t)V.tiles_x;
+                for (uint32_t tx = tx0; tx <= tx1; ++tx) atomicAdd(row + tx, 1u);
+            }
+        }
 #pragma unroll
         for (int p = 0; p < 4; ++p)
             if (a.depth_hist) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
