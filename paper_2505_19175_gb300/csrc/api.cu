@@ -166,6 +166,7 @@ tri_status ensure_pairs(tri_ctx *c) {
     ENSURE(c->kv, 8 * (size_t)c->pair_cap);
     ENSURE(c->kv_tmp, 8 * (size_t)c->pair_cap);
     ENSURE(c->items, 4 * (size_t)c->pair_cap);
+    ENSURE(c->kmask, (size_t)c->pair_cap);
     return TRI_OK;
 }
 
@@ -275,7 +276,7 @@ tri_status tri_workspace_query(const tri_scene *scene, const tri_camera *cams, i
     const int64_t cap = pair_capacity > 0 ? pair_capacity : default_pair_cap(M);
     size_t b = 0;
     b += (size_t)M * (sizeof(Rec) + 4 + 8 + 4 + GRAD_FIELDS * 4);    // records, counts, rects, keys, grads
-    b += (size_t)cap * (8 + 8 + 4);                                   // binned pairs, merge buffer, items
+    b += (size_t)cap * (8 + 8 + 4 + 1);                               // binned pairs, merge buffer, items, masks
     b += (size_t)tiles * (4 + 4 + 4 + 8 + 32) + (size_t)pix * 8;      // counts, cursors, queue, ranges, maxima
     b += sizeof(Ctl) + nviews * (sizeof(ViewDev) + 2 * sizeof(ViewOut));
     b += 256 * 18;                                                    // allocation rounding
@@ -410,6 +411,7 @@ static RenderArgs render_args(tri_ctx *c, TsDevBuf &outs) {
     r.n_contrib = P<int32_t>(c->ncontrib);
     r.tile_max = P<uint32_t>(c->tile_max);
     r.grad2d = P<float>(c->grad2d);
+    r.kmask = P<uint8_t>(c->kmask);
     r.n_items = (uint32_t)c->n_items;
     r.ctl = ctl_of(c);
     return r;

@@ -173,36 +173,44 @@ __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v,
     return ((unsigned long long)hi << 32) | lo;
 }
 
-// Ascending bitonic sort of the 32 E words a warp holds, E per lane (blocked).
-template <int E>
-__device__ __forceinline__ void warp_bitonic(unsigned long long (&x)[E]) {
-    const uint32_t base = (uint32_t)(threadIdx.x & 31) * E;   // index of x[0]
+// Register stages J, J/2, ..., 1 (those below the block size k) of a bitonic merge.
+template <int E, int J>
+__device__ __forceinline__ void reg_stages(unsigned long long (&x)[E], uint32_t base, uint32_t k) {
+    if constexpr (J >= 1) {
+        if ((uint32_t)J <= (k >> 1)) {
 #pragma unroll
-    for (int k = 2; k <= 32 * E; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= E) {
-                // partner: lane ^ (j / E), same register; the pair's lower index keeps
-                // the smaller word in an ascending block (index & k == 0)
-                const bool keep_min = ((base & j) == 0) == ((base & k) == 0);
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const unsigned long long y = shfl_xor_u64(x[e], j / E);
-                    x[e] = keep_min ? (x[e] < y ? x[e] : y) : (x[e] < y ? y : x[e]);
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    if ((e & j) == 0) {
-                        const bool asc = k < E ? (e & k) == 0 : (base & k) == 0;
-                        const unsigned long long p = x[e], q = x[e | j];
-                        const bool sw = (p > q) == asc;
-                        x[e] = sw ? q : p;
-                        x[e | j] = sw ? p : q;
-                    }
+            for (int e = 0; e < E; ++e) {
+                if ((e & J) == 0) {
+                    const bool asc = ((base + e) & k) == 0;
+                    const unsigned long long p = x[e], q = x[e | J];
+                    const bool sw = (p > q) == asc;
+                    x[e] = sw ? q : p;
+                    x[e | J] = sw ? p : q;
                 }
             }
         }
+        reg_stages<E, J / 2>(x, base, k);
+    }
+}
+
+// Ascending bitonic sort of the 32 E words a warp holds, E per lane (blocked: lane l
+// holds indices [l E, l E + E)). Strides of E and more are warp shuffles with lane
+// ^ (j / E); smaller strides are exchanges between a lane's registers. Loops over the
+// block sizes k keep the code small.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&x)[E]) {
+    const uint32_t base = (uint32_t)(threadIdx.x & 31) * E;   // index of x[0]
+    for (uint32_t k = 2; k <= 32u * E; k <<= 1) {
+        for (uint32_t j = k >> 1; j >= (uint32_t)E; j >>= 1) {
+            // the pair's lower index keeps the smaller word in an ascending block
+            const bool keep_min = ((base & j) == 0) == ((base & k) == 0);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const unsigned long long y = shfl_xor_u64(x[e], (int)(j / E));
+                x[e] = keep_min ? (x[e] < y ? x[e] : y) : (x[e] < y ? y : x[e]);
+            }
+        }
+        reg_stages<E, E / 2>(x, base, k);
     }
 }
 
@@ -220,7 +228,7 @@ __device__ __forceinline__ void warp_sort_range(const BinArgs &a, uint32_t start
         if (base + e < n) a.items[start + base + e] = (uint32_t)x[e];
 }
 
-__global__ void __launch_bounds__(WS_WARPS * 32, 8) tile_sort_small_kernel(BinArgs a) {
+__global__ void __launch_bounds__(WS_WARPS * 32, 6) tile_sort_small_kernel(BinArgs a) {
     const int lane = threadIdx.x & 31;
     for (;;) {
         uint32_t t = 0;

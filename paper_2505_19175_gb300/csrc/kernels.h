@@ -108,6 +108,8 @@ struct RenderArgs {
     float *T_final;                 // [total pixels]
     int32_t *n_contrib;             // [total pixels]
     uint32_t *tile_max;             // [total tiles][8]: largest n_contrib of each warp
+    uint8_t *kmask;                 // [pairs]: bit w = warp w composited the pair (forward
+                                    // writes it when set; the backward requires it)
     float *grad2d;                  // backward: [items][16]
     uint32_t n_items;               // bound of the item ids in `items`
     Ctl *ctl;

@@ -11,6 +11,9 @@
 // skip below 1/255, clamp at 0.99, stop before T drops below 1e-4, C += rgb alpha T.
 // The CTA leaves a tile as soon as every pixel has stopped (__syncthreads_count).
 //
+// The forward pass also records, per pair, which warps composited it (one byte of
+// warp bits); the backward walks only those (warp, pair) combinations.
+//
 // Backward: per pixel, from its last composited entry back to the first,
 // T_k = T_{k+1} / (1 - alpha_k), dL/dalpha_k = sum_c g_c (rgb_c T_k - B_c / (1 - alpha_k))
 // with B the colour behind fragment k plus T_final bg; gradients of the record
@@ -88,6 +91,7 @@ __global__ void __launch_bounds__(REN_THREADS)
 render_fwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
     __shared__ uint8_t s_mask[REN_THREADS];
+    __shared__ uint32_t s_km[REN_THREADS];   // warps that composited each staged record
     __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
     __shared__ ViewDev s_view[MAX_VIEWS];
     __shared__ uint32_t s_tile;
@@ -96,6 +100,7 @@ render_fwd_kernel(RenderArgs a) {
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
     int lx, ly;
     pixel_of(tid, lx, ly);
+    s_km[tid] = 0u;
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(&a.ctl->work_counter[0], 1u);
         __syncthreads();
@@ -130,8 +135,14 @@ render_fwd_kernel(RenderArgs a) {
             }
             __syncthreads();
             const int cnt = warp_list(s_mask, s_list[w], w, lane);
-            if (!done) {
-                for (int k = 0; k < cnt; ++k) {
+            // chunks of 32 list entries; bit k of `kept` marks the entries this lane
+            // composited, and the warp's OR of them marks the pairs for the backward
+            for (int c = 0; c < cnt; c += 32) {
+                if (__all_sync(0xffffffffu, done)) break;
+                const int kend = min(cnt, c + 32);
+                uint32_t kept = 0;
+                for (int k = c; k < kend; ++k) {
+                    if (done) break;
                     const int j = s_list[w][k];
                     ++n_eval;
                     const float4 ra = s_rec[j].a, rb = s_rec[j].b, rc = s_rec[j].c;
@@ -154,7 +165,17 @@ render_fwd_kernel(RenderArgs a) {
                     T = tT;
                     last = b0 - start + (uint32_t)j + 1u;
                     ++n_kept;
+                    kept |= 1u << (k - c);
                 }
+                if (a.kmask) {
+                    const uint32_t wk = __reduce_or_sync(0xffffffffu, kept);
+                    if ((wk >> lane) & 1u) atomicOr(&s_km[s_list[w][c + lane]], 1u << w);
+                }
+            }
+            if (a.kmask) {
+                __syncthreads();
+                if (idx < end) a.kmask[idx] = (uint8_t)s_km[tid];
+                s_km[tid] = 0u;
             }
         }
         if (inside) {
@@ -268,9 +289,9 @@ render_bwd_kernel(RenderArgs a) {
                     it = 0;
                 }
                 s_item[tid] = it;
-                const Rec r = a.recs[it];
-                s_rec[tid] = r;
-                s_mask[tid] = (uint8_t)warp_mask(r, a.rects[it], ox, oy);
+                s_rec[tid] = a.recs[it];
+                // the warps that composited this pair in the forward pass
+                s_mask[tid] = a.kmask[start + bstart + tid];
             } else {
                 s_mask[tid] = 0;
             }
