@@ -30,12 +30,14 @@ __device__ __forceinline__ void stage_floats(float *dst, const float *src, int c
 
 // Per-thread stride in shared memory for records of `len` floats: odd, so that the 32
 // lanes reading element k of their own record hit 32 different banks.
-__host__ __device__ __forceinline__ int odd_stride(int len) { return len | 1; }
+__host__ __device__ constexpr int odd_stride(int len) { return len | 1; }
 
 // Stage records of `len` floats (count of them, contiguous in global memory) into
-// shared memory at stride odd_stride(len), with coalesced float4 global loads.
-__device__ __forceinline__ void stage_records(float *dst, const float *src, int count, int len) {
-    const int stride = odd_stride(len);
+// shared memory at stride odd_stride(len), with coalesced float4 global loads. `len` is
+// a compile-time constant, so the divisions below are multiplications.
+template <int len>
+__device__ __forceinline__ void stage_records(float *dst, const float *src, int count) {
+    constexpr int stride = odd_stride(len);
     const int total = count * len;
     const int n4 = total >> 2;
     const float4 *s4 = reinterpret_cast<const float4 *>(src);
@@ -60,6 +62,7 @@ __device__ __forceinline__ int clamp_pix(float v, int n) {
     return (int)v;
 }
 
+template <int DEG>
 __global__ void __launch_bounds__(PRE_THREADS, 6)
 preprocess_fwd_kernel(PreArgs a) {
     __shared__ __align__(16) float s_v[PRE_THREADS * 9];
@@ -75,9 +78,9 @@ preprocess_fwd_kernel(PreArgs a) {
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
     const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
     const int cnt = (int)(a.n - i0 < PRE_THREADS ? a.n - i0 : PRE_THREADS);
-    const int nk = (a.sh_degree + 1) * (a.sh_degree + 1);
+    constexpr int nk = (DEG + 1) * (DEG + 1);
     stage_floats(s_v, a.verts + i0 * 9, cnt * 9);
-    stage_records(s_sh, a.sh + i0 * nk * 3, cnt, nk * 3);
+    stage_records<nk * 3>(s_sh, a.sh + i0 * nk * 3, cnt);
     __syncthreads();
 
     const int64_t i = i0 + tid;
@@ -136,7 +139,7 @@ preprocess_fwd_kernel(PreArgs a) {
             float w0 = cen[0] - V.campos[0], w1 = cen[1] - V.campos[1], w2 = cen[2] - V.campos[2];
             float inv = rsqrtf(fmaf(w0, w0, fmaf(w1, w1, w2 * w2)));
             float Y[16];
-            sh_basis(a.sh_degree, w0 * inv, w1 * inv, w2 * inv, Y);
+            sh_basis(DEG, w0 * inv, w1 * inv, w2 * inv, Y);
             float col[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -182,7 +185,8 @@ preprocess_fwd_kernel(PreArgs a) {
     if (tid == 0 && s_nvis) atomicAdd(&a.ctl->n_visible, s_nvis);
 }
 
-__global__ void __launch_bounds__(PRE_BWD_THREADS)
+template <int DEG>
+__global__ void __launch_bounds__(PRE_BWD_THREADS, 8)
 preprocess_bwd_kernel(PreBwdArgs a) {
     __shared__ __align__(16) float s_v[PRE_BWD_THREADS * 9];
     __shared__ __align__(16) float s_sh[PRE_BWD_THREADS * 49];
@@ -193,16 +197,16 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
     const int64_t i0 = (int64_t)blockIdx.x * PRE_BWD_THREADS;
     const int cnt = (int)(a.n - i0 < PRE_BWD_THREADS ? a.n - i0 : PRE_BWD_THREADS);
-    const int nk = (a.sh_degree + 1) * (a.sh_degree + 1);
+    constexpr int nk = (DEG + 1) * (DEG + 1);
     stage_floats(s_v, a.verts + i0 * 9, cnt * 9);
-    stage_records(s_sh, a.sh + i0 * nk * 3, cnt, nk * 3);
+    stage_records<nk * 3>(s_sh, a.sh + i0 * nk * 3, cnt);
     __syncthreads();
     const int64_t i = i0 + tid;
     const bool alive = tid < cnt;
     float v[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) v[k] = s_v[tid * 9 + k];
-    const int sstride = odd_stride(nk * 3);
+    constexpr int sstride = odd_stride(nk * 3);
     float *shp = s_sh + tid * sstride;
     const float cen[3] = {(v[0] + v[3] + v[6]) * (1.0f / 3.0f), (v[1] + v[4] + v[7]) * (1.0f / 3.0f),
                           (v[2] + v[5] + v[8]) * (1.0f / 3.0f)};
@@ -220,7 +224,7 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         const float4 G0 = gp[0], G1 = gp[1], G2 = gp[2], G3 = gp[3];
         const ViewDev &V = s_view[vw];
         Geom g;
-        item_geometry(v, V, g);
+        item_geometry<false>(v, V, g);
         go += G2.x;
         gsig += G2.y;
         // s = q0 + S
@@ -230,7 +234,7 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         float gQ1x = 0.f, gQ1y = 0.f, gQ2x = 0.f, gQ2y = 0.f;
         float gell[3] = {0.f, 0.f, 0.f};
         float gP = 0.f, gA2 = 0.f;
-        const float P = g.perim, iP = 1.0f / P;
+        const float P = g.perim, iP = rcp_approx(P);
         // S = (ell1 Q1 + ell2 Q2) / P
         gQ1x += gsx * g.ell[1] * iP; gQ1y += gsy * g.ell[1] * iP;
         gQ2x += gsx * g.ell[2] * iP; gQ2y += gsy * g.ell[2] * iP;
@@ -241,21 +245,25 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         const float Ex[3] = {g.Q2.x - g.Q1.x, -g.Q2.x, g.Q1.x};
         const float Ey[3] = {g.Q2.y - g.Q1.y, -g.Q2.y, g.Q1.y};
         float gEx[3], gEy[3];
+        const float ia2 = rcp_approx(g.area2);
+        float iell[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) iell[k] = rcp_approx(g.ell[k]);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float kk = P / (g.ell[k] * g.area2);
+            const float kk = P * iell[k] * ia2;
             const float gk = -gA[k] * Ey[k] + gB[k] * Ex[k];
             gEx[k] = gB[k] * kk;
             gEy[k] = -gA[k] * kk;
             gP += gk * kk * iP;
-            gell[k] -= gk * kk / g.ell[k];
-            gA2 -= gk * kk / g.area2;
+            gell[k] -= gk * kk * iell[k];
+            gA2 -= gk * kk * ia2;
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float gl = gell[k] + gP;
-            gEx[k] += gl * Ex[k] / g.ell[k];
-            gEy[k] += gl * Ey[k] / g.ell[k];
+            const float gl = (gell[k] + gP) * iell[k];
+            gEx[k] += gl * Ex[k];
+            gEy[k] += gl * Ey[k];
         }
         // E0 = Q2 - Q1, E1 = -Q2, E2 = Q1
         gQ2x += gEx[0] - gEx[1]; gQ2y += gEy[0] - gEy[1];
@@ -268,7 +276,7 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         const float gqx[3] = {gq0x, gQ1x, gQ2x}, gqy[3] = {gq0y, gQ1y, gQ2y};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float iz = 1.0f / g.xc[k].z;
+            const float iz = rcp_approx(g.xc[k].z);
             const float gx = gqx[k] * V.fx * iz;
             const float gy = gqy[k] * V.fy * iz;
             const float gz = -(gx * g.xc[k].x + gy * g.xc[k].y) * iz;
@@ -282,7 +290,7 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         const float inv = rsqrtf(fmaf(w0, w0, fmaf(w1, w1, w2 * w2)));
         const float dx = w0 * inv, dy = w1 * inv, dz = w2 * inv;
         float Y[16];
-        sh_basis(a.sh_degree, dx, dy, dz, Y);
+        sh_basis(DEG, dx, dy, dz, Y);
         const float grgb[3] = {G2.z, G2.w, G3.x};
         float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
@@ -307,8 +315,8 @@ preprocess_bwd_kernel(PreBwdArgs a) {
                 gY[k] = 0.f;
             }
         }
-        if (a.sh_degree > 0) {
-            const float3 gd = sh_basis_vjp(a.sh_degree, dx, dy, dz, gY);
+        if (DEG > 0) {
+            const float3 gd = sh_basis_vjp(DEG, dx, dy, dz, gY);
             const float dd = gd.x * dx + gd.y * dy + gd.z * dz;
             const float gwx = (gd.x - dx * dd) * inv, gwy = (gd.y - dy * dd) * inv, gwz = (gd.z - dz * dd) * inv;
 #pragma unroll
@@ -333,7 +341,7 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         for (int k = tid; k < cnt * 9; k += PRE_BWD_THREADS) dst[k] = a.accumulate ? dst[k] + s_v[k] : s_v[k];
     }
     if (a.dsh) {
-        const int len = nk * 3;
+        constexpr int len = nk * 3;
         float *dst = a.dsh + i0 * len;
         for (int f = tid; f < cnt * len; f += PRE_BWD_THREADS) {
             const int r = f / len;
@@ -345,12 +353,26 @@ preprocess_bwd_kernel(PreBwdArgs a) {
 
 void launch_preprocess_fwd(const PreArgs &a, cudaStream_t st) {
     const int grid = (int)((a.n + PRE_THREADS - 1) / PRE_THREADS);
-    if (grid > 0) preprocess_fwd_kernel<<<grid, PRE_THREADS, sizeof(ViewDev) * a.nviews, st>>>(a);
+    if (grid <= 0) return;
+    const size_t smem = sizeof(ViewDev) * a.nviews;
+    switch (a.sh_degree) {
+        case 0: preprocess_fwd_kernel<0><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        case 1: preprocess_fwd_kernel<1><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        case 2: preprocess_fwd_kernel<2><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        default: preprocess_fwd_kernel<3><<<grid, PRE_THREADS, smem, st>>>(a); break;
+    }
 }
 
 void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st) {
     const int grid = (int)((a.n + PRE_BWD_THREADS - 1) / PRE_BWD_THREADS);
-    if (grid > 0) preprocess_bwd_kernel<<<grid, PRE_BWD_THREADS, sizeof(ViewDev) * a.nviews, st>>>(a);
+    if (grid <= 0) return;
+    const size_t smem = sizeof(ViewDev) * a.nviews;
+    switch (a.sh_degree) {
+        case 0: preprocess_bwd_kernel<0><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+        case 1: preprocess_bwd_kernel<1><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+        case 2: preprocess_bwd_kernel<2><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+        default: preprocess_bwd_kernel<3><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+    }
 }
 
 }  // namespace ts
