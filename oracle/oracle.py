@@ -64,6 +64,7 @@ def _load():
                                        P, P, P, P, P, P]
             lib.orc_render_grad.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P,
                                             P, P, P, P, P, P, P]
+            lib.orc_render_stats.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P, P]
             lib.orc_tri_info.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P]
             lib.orc_tri2d.argtypes = [P, P]
             lib.orc_window.argtypes = [P, ctypes.c_double, ctypes.c_int, P, P, P]
@@ -141,6 +142,22 @@ def render(scene, cam, consts=None, brute: bool = False, pix_mask=None, flags: b
     if flags:
         out.update(flags=fl, err=err)
     return out
+
+
+def render_stats(scene, cam, consts=None):
+    """Pruning statistics per triangle (Sec. 3.3 "Pruning"): max_weight = largest T o
+    over the triangle's composited fragments, n_pix = pixels where it was composited,
+    amb = it took part in a pixel within the FP32 band."""
+    lib = _load()
+    n, verts, sh, opac, sig, deg = _scene_arrays(scene)
+    mw = np.zeros(n, dtype=np.float64)
+    npix = np.zeros(n, dtype=np.int32)
+    amb = np.zeros(n, dtype=np.uint8)
+    rc = lib.orc_render_stats(n, _ptr(verts), _ptr(sh), deg, _ptr(opac), _ptr(sig), _ptr(_cam_array(cam)),
+                              _ptr(_const_array(consts)), _ptr(mw), _ptr(npix), _ptr(amb))
+    if rc != 0:
+        raise ValueError(f"orc_render_stats failed ({rc})")
+    return dict(max_weight=mw, n_pix=npix, amb=amb)
 
 
 def render_grad(scene, cam, dL_dimage, consts=None, pix_mask=None, tri_mask=None):

@@ -514,6 +514,12 @@ typedef struct {
     int32_t *n_kept;
     uint8_t *flags;
     double *err_est;
+    /* pruning statistics per triangle (nullable, Sec. 3.3 "Pruning"): largest
+     * blending weight T o over its composited fragments, number of pixels where it
+     * was composited, and 1 when a pixel it took part in is flagged */
+    double *max_weight;
+    int32_t *n_pix;
+    uint8_t *tri_amb;
     /* adjoint (nullable) */
     const double *dL;
     const int32_t *track;        /* triangle id -> dual slot, or -1 */
@@ -569,6 +575,17 @@ static void shade_pixel(const job_t *J, const ent_t *e, size_t cnt, int x, int y
             if (fabs(test - K->t_eps) <= 2.0 * test * rel) amb |= AMB_STOP;
         }
         if (test < K->t_eps) break;
+        if (J->n_pix) {
+            const double wgt = T * t->o;
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+            J->n_pix[f->id] += 1;
+#ifdef _OPENMP
+#pragma omp critical(orc_max_weight)
+#endif
+            if (J->max_weight[f->id] < wgt) J->max_weight[f->id] = wgt;
+        }
         for (int c = 0; c < 3; ++c) C[c] += t->rgb[c] * a * T;
         if (nk < MAXK) { kid[nk] = f->id; ka[nk] = a; kT[nk] = T; kda[nk] = da; }
         T = test;
@@ -621,6 +638,8 @@ static void shade_pixel(const job_t *J, const ent_t *e, size_t cnt, int x, int y
     if (E > FLAG_TOL) amb |= AMB_SENS;
     if (J->flags) J->flags[pix] = (uint8_t)amb;
     if (J->err_est) J->err_est[pix] = E;
+    if (J->tri_amb && amb)
+        for (size_t i = 0; i < cnt; ++i) J->tri_amb[e[i].id] = 1;   /* benign race: all write 1 */
 }
 
 static void render_band(const job_t *J, int y0, int y1, const int *cand, int ncand) {
@@ -790,6 +809,31 @@ int orc_render(int n, const double *verts, const double *sh, int sh_deg, const d
     J.tris = setup_all(n, verts, sh, sh_deg, opac, sigma, &J.C, &J.K);
     run_job(&J);
     free(J.tris);
+    return 0;
+}
+
+/* Pruning statistics (Sec. 3.3 "Pruning"), per triangle: max_weight = largest T o over
+ * its composited fragments (0 if none), n_pix = number of pixels where it was
+ * composited, tri_amb = 1 if it took part in a pixel whose result is within the FP32
+ * band (flags != 0). Outputs are overwritten. */
+int orc_render_stats(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
+                     const double *sigma, const double *cam, const double *consts, double *max_weight,
+                     int32_t *n_pix, uint8_t *tri_amb) {
+    if (n < 0 || sh_deg < 0 || sh_deg > 3 || !max_weight || !n_pix || !tri_amb) return 1;
+    job_t J;
+    memset(&J, 0, sizeof J);
+    J.n = n; J.sh_deg = sh_deg; J.nk = (sh_deg + 1) * (sh_deg + 1);
+    J.verts = verts; J.sh = sh; J.opac = opac; J.sigma = sigma;
+    J.C = load_cam(cam); J.K = load_consts(consts);
+    for (int i = 0; i < n; ++i) { max_weight[i] = 0.0; n_pix[i] = 0; tri_amb[i] = 0; }
+    J.max_weight = max_weight; J.n_pix = n_pix; J.tri_amb = tri_amb;
+    /* flags are needed for tri_amb: a scratch image of flags */
+    uint8_t *fl = (uint8_t *)calloc((size_t)J.C.W * J.C.H, 1);
+    J.flags = fl;
+    J.tris = setup_all(n, verts, sh, sh_deg, opac, sigma, &J.C, &J.K);
+    run_job(&J);
+    free(J.tris);
+    free(fl);
     return 0;
 }
 
