@@ -245,10 +245,21 @@ def run_ours(args, rank, world):
         ctx.render_fwd(imgs)
 
     g_step = capture(step)
+    # forward with the pruning statistics of Sec. 3.3 (largest T o, composited pixels)
+    stat_w = torch.empty(st.n, device="cuda")
+    stat_n = torch.empty(st.n, dtype=torch.int32, device="cuda")
+
+    def fwd_stats():
+        ctx.preprocess(st, [cam])
+        ctx.bin_sort(sync=False)
+        ctx.render_fwd(imgs, stats=(stat_w, stat_n))
+
     g_fwd = capture(fwd_only)
+    g_fwd_stats = capture(fwd_stats)
     for _ in range(3):
         g_step.replay()
         g_fwd.replay()
+        g_fwd_stats.replay()
     torch.cuda.synchronize()
 
     def timed(graph, n):
@@ -271,6 +282,7 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     ev_fwd = timed(g_fwd, args.steps)
+    ev_fwd_stats = timed(g_fwd_stats, args.steps)
     torch.cuda.synchronize()
     info = ctx.check()
     step_ms = np.array([a.elapsed_time(b) for a, b in ev_step])
@@ -282,6 +294,7 @@ def run_ours(args, rank, world):
     value = world * args.steps / (total_ms / 1000.0)
     fwd_ms = float(sum(a.elapsed_time(b) for a, b in ev_fwd))
     fps = args.steps / (fwd_ms / 1000.0)
+    fps_stats = args.steps / (float(sum(a.elapsed_time(b) for a, b in ev_fwd_stats)) / 1000.0)
 
     # per-stage breakdown: eager steps with events between the calls (same stream)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
@@ -367,6 +380,7 @@ def run_ours(args, rank, world):
                    "sh_degree": 3, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "fwd_fps": round(fps, 2),
+        "fwd_fps_with_prune_stats": round(fps_stats, 2),
         "timing": "CUDA-graph replay of the whole step per timed iteration; stage_ms_median from eager "
                   "steps with events between the calls",
         "stage_ms_median": breakdown,
@@ -379,7 +393,7 @@ def run_ours(args, rank, world):
         "wall_s_timed": round(t_wall, 4),
     }
     if not args.no_multiview and world == 1:
-        del g_step, g_fwd
+        del g_step, g_fwd, g_fwd_stats
         line["multiview_3m_16views"] = run_multiview(max(3, min(args.steps, 10)), 3)
     if not args.no_serving:
         line["serving"] = run_serving(args.serve_requests, 2000.0, 1_000_000)

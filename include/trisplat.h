@@ -158,6 +158,19 @@ tri_status tri_bin_sort(tri_ctx *ctx, int64_t *num_pairs_out, void *stream);
 tri_status tri_render_fwd(tri_ctx *ctx, float *const *images, float *const *T_final,
                           int32_t *const *n_contrib, void *stream);
 
+/* Step 3 with the pruning statistics of Sec. 3.3 ("Pruning"): as tri_render_fwd, and
+ * for every (view, triangle) item m = v n + i, max_weight[m] = the largest blending
+ * weight T o over the pixels where the item was composited (T = transmittance in
+ * front of the fragment, o its opacity; 0 if none) and n_pixels[m] = the number of
+ * those pixels. Both are device arrays of n_items = nviews x n entries (float /
+ * int32), overwritten (zeroed first, on the stream). The pruning decisions across
+ * views (largest weight below tau_prune; fewer than two views with more than one
+ * pixel) are host-side reductions of these arrays. Same errors as tri_render_fwd;
+ * TRI_ERR_INVALID_ARG for a null output. */
+tri_status tri_render_fwd_stats(tri_ctx *ctx, float *const *images, float *const *T_final,
+                                int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels,
+                                void *stream);
+
 /* Step 4 (gradient of step 3): per pixel, back to front from its last composited
  * entry, recompute alpha and T_k = T_{k+1} / (1 - alpha_k), and accumulate per item
  * the gradients of the incenter, the six edge-line slopes, o, sigma and rgb (warp

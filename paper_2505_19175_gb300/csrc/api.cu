@@ -412,13 +412,14 @@ static RenderArgs render_args(tri_ctx *c, TsDevBuf &outs) {
     r.tile_max = P<uint32_t>(c->tile_max);
     r.grad2d = P<float>(c->grad2d);
     r.kmask = P<uint8_t>(c->kmask);
+    r.stat_w = r.stat_n = nullptr;
     r.n_items = (uint32_t)c->n_items;
     r.ctl = ctl_of(c);
     return r;
 }
 
-tri_status tri_render_fwd(tri_ctx *c, float *const *images, float *const *T_final, int32_t *const *n_contrib,
-                          void *stream) {
+static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const *T_final,
+                                  int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels, void *stream) {
     if (!c) return TRI_ERR_INVALID_ARG;
     if (c->stage < 2) return fail(c, TRI_ERR_STATE, "tri_render_fwd before tri_bin_sort");
     if (!images) return fail(c, TRI_ERR_INVALID_ARG, "images is null");
@@ -434,7 +435,14 @@ tri_status tri_render_fwd(tri_ctx *c, float *const *images, float *const *T_fina
         return s;
     CK(cudaMemsetAsync(&ctl_of(c)->work_counter[0], 0, 4, st));
     CK(cudaMemsetAsync(&ctl_of(c)->frag_eval, 0, 16, st));
-    launch_render_fwd(render_args(c, c->outs_fwd), c->sms, st);
+    RenderArgs r = render_args(c, c->outs_fwd);
+    if (max_weight && n_pixels) {
+        CK(cudaMemsetAsync(max_weight, 0, 4 * (size_t)c->n_items, st));
+        CK(cudaMemsetAsync(n_pixels, 0, 4 * (size_t)c->n_items, st));
+        r.stat_w = reinterpret_cast<uint32_t *>(max_weight);
+        r.stat_n = reinterpret_cast<uint32_t *>(n_pixels);
+    }
+    launch_render_fwd(r, c->sms, st);
     if ((s = launch_check(c, "render_fwd_kernel")) != TRI_OK) return s;
     for (int v = 0; v < c->nviews; ++v) {
         const ViewDev &V = c->views[v];
@@ -447,6 +455,17 @@ tri_status tri_render_fwd(tri_ctx *c, float *const *images, float *const *T_fina
     }
     c->stage = 3;
     return TRI_OK;
+}
+
+tri_status tri_render_fwd(tri_ctx *c, float *const *images, float *const *T_final, int32_t *const *n_contrib,
+                          void *stream) {
+    return render_fwd_impl(c, images, T_final, n_contrib, nullptr, nullptr, stream);
+}
+
+tri_status tri_render_fwd_stats(tri_ctx *c, float *const *images, float *const *T_final,
+                                int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels, void *stream) {
+    if (c && (!max_weight || !n_pixels)) return fail(c, TRI_ERR_INVALID_ARG, "statistics outputs are null");
+    return render_fwd_impl(c, images, T_final, n_contrib, max_weight, n_pixels, stream);
 }
 
 tri_status tri_render_bwd(tri_ctx *c, const float *const *dL, void *stream) {

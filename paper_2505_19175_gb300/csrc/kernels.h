@@ -108,6 +108,8 @@ struct RenderArgs {
     float *T_final;                 // [total pixels]
     int32_t *n_contrib;             // [total pixels]
     uint32_t *tile_max;             // [total tiles][8]: largest n_contrib of each warp
+    uint32_t *stat_w;               // [items] largest T o as float bits (null: no statistics)
+    uint32_t *stat_n;               // [items] pixels where the item was composited
     uint8_t *kmask;                 // [pairs]: bit w = warp w composited the pair (forward
                                     // writes it when set; the backward requires it)
     float *grad2d;                  // backward: [items][16]

@@ -218,14 +218,14 @@ extern "C" tri_status tri_render_fwd_noalloc(const tri_scene *scene, const tri_c
         RenderArgs r;
         r.views = dview; r.outs = dout; r.nviews = 1; r.total_tiles = tiles; r.ranges = ranges;
         r.items = pv[cur]; r.recs = recs; r.rects = rects; r.T_final = tfin; r.n_contrib = ncon; r.tile_max = tmax;
-        r.grad2d = nullptr; r.n_items = (uint32_t)M; r.ctl = ctl; r.kmask = nullptr;
+        r.grad2d = nullptr; r.n_items = (uint32_t)M; r.ctl = ctl; r.kmask = nullptr; r.stat_w = r.stat_n = nullptr;
         launch_render_fwd(r, sms, st);
     } else {
         // no triangles: one tile pass over zero pairs still renders the background
         RenderArgs r;
         r.views = dview; r.outs = dout; r.nviews = 1; r.total_tiles = tiles; r.ranges = ranges;
         r.items = pv[0]; r.recs = recs; r.rects = rects; r.T_final = tfin; r.n_contrib = ncon; r.tile_max = tmax;
-        r.grad2d = nullptr; r.n_items = 1; r.ctl = ctl; r.kmask = nullptr;
+        r.grad2d = nullptr; r.n_items = 1; r.ctl = ctl; r.kmask = nullptr; r.stat_w = r.stat_n = nullptr;
         launch_render_fwd(r, sms, st);
     }
     NA_CK(cudaGetLastError());

@@ -92,6 +92,8 @@ render_fwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
     __shared__ uint8_t s_mask[REN_THREADS];
     __shared__ uint32_t s_km[REN_THREADS];   // warps that composited each staged record
+    __shared__ uint32_t s_sw[REN_THREADS];   // pruning statistics of each staged record:
+    __shared__ uint32_t s_sn[REN_THREADS];   // largest T o (float bits), composited pixels
     __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
     __shared__ ViewDev s_view[MAX_VIEWS];
     __shared__ uint32_t s_tile;
@@ -101,6 +103,9 @@ render_fwd_kernel(RenderArgs a) {
     int lx, ly;
     pixel_of(tid, lx, ly);
     s_km[tid] = 0u;
+    s_sw[tid] = 0u;
+    s_sn[tid] = 0u;
+    const bool stats = a.stat_n != nullptr;
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(&a.ctl->work_counter[0], 1u);
         __syncthreads();
@@ -121,8 +126,9 @@ render_fwd_kernel(RenderArgs a) {
         for (uint32_t b0 = start; b0 < end; b0 += REN_THREADS) {
             if (__syncthreads_count(done) == REN_THREADS) break;
             const uint32_t idx = b0 + tid;
+            uint32_t it = 0;
             if (idx < end) {
-                uint32_t it = a.items[idx];
+                it = a.items[idx];
                 if (it >= a.n_items) {
                     atomicOr(&a.ctl->error, ERR_INDEX);
                     it = 0;
@@ -159,6 +165,11 @@ render_fwd_kernel(RenderArgs a) {
                         break;
                     }
                     const float wgt = __fmul_rn(al, T);
+                    if (stats) {
+                        // Sec. 3.3 "Pruning": blending weight T o of this fragment
+                        atomicMax(&s_sw[j], __float_as_uint(__fmul_rn(T, rc.w)));
+                        atomicAdd(&s_sn[j], 1u);
+                    }
                     C0 = fmaf(rd.y, wgt, C0);
                     C1 = fmaf(rd.z, wgt, C1);
                     C2 = fmaf(rd.w, wgt, C2);
@@ -172,10 +183,20 @@ render_fwd_kernel(RenderArgs a) {
                     if ((wk >> lane) & 1u) atomicOr(&s_km[s_list[w][c + lane]], 1u << w);
                 }
             }
-            if (a.kmask) {
+            if (a.kmask || stats) {
                 __syncthreads();
-                if (idx < end) a.kmask[idx] = (uint8_t)s_km[tid];
-                s_km[tid] = 0u;
+                if (a.kmask) {
+                    if (idx < end) a.kmask[idx] = (uint8_t)s_km[tid];
+                    s_km[tid] = 0u;
+                }
+                if (stats) {
+                    if (s_sn[tid]) {
+                        atomicAdd(&a.stat_n[it], s_sn[tid]);
+                        atomicMax(&a.stat_w[it], s_sw[tid]);
+                    }
+                    s_sn[tid] = 0u;
+                    s_sw[tid] = 0u;
+                }
             }
         }
         if (inside) {

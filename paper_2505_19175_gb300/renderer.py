@@ -100,11 +100,22 @@ class Context:
         self._ck(self._lib.tri_bin_sort(self.h, None, _stream_handle(stream)))
         return None
 
-    def render_fwd(self, images, T_final=None, n_contrib=None, stream=None) -> None:
+    def render_fwd(self, images, T_final=None, n_contrib=None, stream=None, stats=None) -> None:
+        """Composite the views into ``images``. With ``stats = (max_weight, n_pixels)``
+        (device float32 / int32 tensors of views x triangles entries, view-major) also
+        gather the pruning statistics of Sec. 3.3 (see ``prune``)."""
         ims = N.ptr_array([x.data_ptr() for x in images])
         tf = N.ptr_array([x.data_ptr() for x in T_final]) if T_final is not None else None
         nc = N.ptr_array([x.data_ptr() for x in n_contrib]) if n_contrib is not None else None
-        self._ck(self._lib.tri_render_fwd(self.h, ims, tf, nc, _stream_handle(stream)))
+        if stats is None:
+            self._ck(self._lib.tri_render_fwd(self.h, ims, tf, nc, _stream_handle(stream)))
+        else:
+            mw, npx = stats
+            n_items = len(self.cams) * self._scene.n
+            if mw.numel() < n_items or npx.numel() < n_items or mw.dtype != torch.float32 or npx.dtype != torch.int32:
+                raise ValueError("stats need float32 and int32 tensors of views x triangles entries")
+            self._ck(self._lib.tri_render_fwd_stats(self.h, ims, tf, nc, mw.data_ptr(), npx.data_ptr(),
+                                                    _stream_handle(stream)))
 
     def render_bwd(self, dL_dimages, stream=None) -> None:
         self._dl = [x.contiguous() for x in dL_dimages]
