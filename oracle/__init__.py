@@ -4,7 +4,7 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline / reference leg
 ``bench.py`` may import this package. The product path never does.
 """
 from .oracle import (  # noqa: F401
-    DEFAULT_CONSTS, EXACT_CONSTS, build, render, render_grad, render_stats, tri_info, tri2d,
+    DEFAULT_CONSTS, EXACT_CONSTS, build, render, render_grad, render_stats, render_solid, tri_info, tri2d,
     window, sh_eval, tile_pairs, set_threads, max_threads,
     AMB_SKIP, AMB_STOP, AMB_ORDER, AMB_SENS, AMB_CULL,
 )

@@ -64,6 +64,7 @@ def _load():
                                        P, P, P, P, P, P]
             lib.orc_render_grad.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P,
                                             P, P, P, P, P, P, P]
+            lib.orc_render_solid.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P, P]
             lib.orc_render_stats.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P, P]
             lib.orc_tri_info.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P]
             lib.orc_tri2d.argtypes = [P, P]
@@ -158,6 +159,22 @@ def render_stats(scene, cam, consts=None):
     if rc != 0:
         raise ValueError(f"orc_render_stats failed ({rc})")
     return dict(max_weight=mw, n_pix=npix, amb=amb)
+
+
+def render_solid(scene, cam, consts=None):
+    """Solid-triangle image [3,H,W], winning triangle id [H,W] (-1: background) and the
+    per-pixel FP32-band flags: the sigma -> 0, o = 1 limit of the splat render."""
+    lib = _load()
+    n, verts, sh, opac, sig, deg = _scene_arrays(scene)
+    W, H = int(_get(cam, "W")), int(_get(cam, "H"))
+    img = np.zeros((3, H, W), dtype=np.float64)
+    ids = np.zeros((H, W), dtype=np.int32)
+    fl = np.zeros((H, W), dtype=np.uint8)
+    rc = lib.orc_render_solid(n, _ptr(verts), _ptr(sh), deg, _ptr(opac), _ptr(sig), _ptr(_cam_array(cam)),
+                              _ptr(_const_array(consts)), _ptr(img), _ptr(ids), _ptr(fl))
+    if rc != 0:
+        raise ValueError(f"orc_render_solid failed ({rc})")
+    return dict(image=img, id=ids, flags=fl)
 
 
 def render_grad(scene, cam, dL_dimage, consts=None, pix_mask=None, tri_mask=None):

@@ -837,6 +837,66 @@ int orc_render_stats(int n, const double *verts, const double *sh, int sh_deg, c
     return 0;
 }
 
+/* Solid-triangle render: the limit of the splat render for sigma -> 0 and o = 1
+ * (Sec. 5 converts the soup into opaque triangles for game engines): every pixel
+ * takes the colour of the nearest triangle, by (centroid depth, id), whose window
+ * ratio at the pixel centre is positive, else the background. Opacity and sigma are
+ * ignored and only near-plane and degenerate triangles are culled. image [3,H,W],
+ * id [H,W] (-1: background). flags (nullable) marks pixels whose winner is within
+ * the FP32 band: a ratio within EPS_LINE of zero for the winner or a nearer
+ * triangle, or a depth within 4 FP32 ulps of the winner's. */
+int orc_render_solid(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
+                     const double *sigma, const double *cam, const double *consts, double *image,
+                     int32_t *id_out, uint8_t *flags) {
+    if (n < 0 || sh_deg < 0 || sh_deg > 3 || !image || !id_out) return 1;
+    cam_t C = load_cam(cam);
+    consts_t K = load_consts(consts);
+    tri_t *tris = setup_all(n, verts, sh, sh_deg, opac, sigma, &C, &K);
+    const int W = C.W, H = C.H;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int y = 0; y < H; ++y) {
+        const double py = y + 0.5;
+        for (int x = 0; x < W; ++x) {
+            const double px = x + 0.5;
+            int best = -1;
+            double bd = 0.0;
+            for (int id = 0; id < n; ++id) {
+                const tri_t *t = &tris[id];
+                if (t->cull) continue;
+                if (px < t->bbox[0] - 1.0 || px > t->bbox[2] + 1.0 || py < t->bbox[1] - 1.0 || py > t->bbox[3] + 1.0)
+                    continue;
+                if (tri2d_ratio(&t->g, px, py, NULL) <= 0.0) continue;
+                if (best < 0 || t->depth < bd || (t->depth == bd && id < best)) { best = id; bd = t->depth; }
+            }
+            const size_t pix = (size_t)y * W + x;
+            id_out[pix] = best;
+            for (int c = 0; c < 3; ++c)
+                image[(size_t)c * W * H + pix] = best >= 0 ? tris[best].rgb[c] : C.bg[c];
+            if (!flags) continue;
+            uint8_t amb = 0;
+            for (int id = 0; id < n; ++id) {
+                const tri_t *t = &tris[id];
+                if (t->cull) {
+                    if (t->amb_cull) amb |= AMB_CULL;
+                    continue;
+                }
+                if (px < t->bbox[0] - 1.0 || px > t->bbox[2] + 1.0 || py < t->bbox[1] - 1.0 || py > t->bbox[3] + 1.0)
+                    continue;
+                int am;
+                const double ratio = tri2d_ratio(&t->g, px, py, &am);
+                const int nearer = best < 0 || t->depth < bd || (t->depth == bd && id <= best);
+                if (nearer && fabs(ratio) <= ratio_band(&t->g, am, px, py)) amb |= AMB_SKIP;
+                if (best >= 0 && id != best && ratio > 0.0 && fabs(t->depth - bd) <= 4.0 * ulp32(bd)) amb |= AMB_ORDER;
+            }
+            flags[pix] = amb;
+        }
+    }
+    free(tris);
+    return 0;
+}
+
 /* Adjoint: given dL/dimage [3,H,W], accumulate parameter gradients of the triangles
  * with tri_mask[id] != 0 (all when NULL) from the pixels with pix_mask != 0 (all when
  * NULL). Outputs are overwritten: dverts [n,9], dsh [n,K,3], dopac [n], dsigma [n]. */
