@@ -395,6 +395,8 @@ def run_ours(args, rank, world):
     if not args.no_multiview and world == 1:
         del g_step, g_fwd, g_fwd_stats
         line["multiview_3m_16views"] = run_multiview(max(3, min(args.steps, 10)), 3)
+    if not args.no_solid and world == 1:
+        line["solid_2m"] = run_solid(max(3, min(args.steps, 20)))
     if not args.no_serving:
         line["serving"] = run_serving(args.serve_requests, 2000.0, 1_000_000)
     if not args.no_cpu_baseline and world == 1:
@@ -471,6 +473,50 @@ def run_multiview(steps: int, warmup: int, n_tris: int = 3_000_000, n_views: int
 
 
 # ---------------------------------------------------------------------------------------
+# opaque-triangle render of a 2M-triangle soup at 720p / 1080p / 4k
+# ---------------------------------------------------------------------------------------
+def run_solid(steps: int, n_tris: int = 2_000_000):
+    import torch
+    from paper_2505_19175_gb300 import synth
+    from paper_2505_19175_gb300.renderer import Context, SceneTensors, new_images
+    st = SceneTensors.from_numpy(synth.scene_shells(n_tris, seed=1005))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {"workload": f"{n_tris} tris SH3 on 16 shells, opaque render (sigma -> 0, o = 1 limit), camera at "
+                       "radius 4 looking at the centre; CUDA-graph replay of preprocess + binning + render; "
+                       "L2 flushed between frames"}
+    for W, H in ((1280, 720), (1920, 1080), (3840, 2160)):
+        cam = synth.ring_cameras(1, W=W, H=H)[0]
+        ctx = Context()
+        imgs = new_images([cam])
+        ids = [torch.empty((H, W), dtype=torch.int32, device="cuda")]
+        pairs = ctx.render_solid(st, [cam], imgs, ids, sync_pairs=True)
+        ctx.reserve(int(pairs * 1.25) + 1024)
+        for _ in range(3):
+            ctx.render_solid(st, [cam], imgs, ids, sync_pairs=False)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ctx.render_solid(st, [cam], imgs, ids, sync_pairs=False)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record()
+            g.replay()
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        info = ctx.check()
+        out[f"{W}x{H}"] = {"fps": round(1000.0 * steps / float(ms.sum()), 1),
+                           "ms_median": round(float(np.median(ms)), 4), "pairs": int(info.n_pairs),
+                           "visible": int(info.n_visible), "overflow": bool(info.overflow)}
+        del g
+    return out
+
+
+# ---------------------------------------------------------------------------------------
 # serving: open-loop replay of a Poisson trace against one resident scene
 # ---------------------------------------------------------------------------------------
 def replay(srv, sid, trace, max_time_s=60.0):
@@ -539,6 +585,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-multiview", action="store_true")
+    ap.add_argument("--no-solid", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4096)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

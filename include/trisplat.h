@@ -171,6 +171,20 @@ tri_status tri_render_fwd_stats(tri_ctx *ctx, float *const *images, float *const
                                 int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels,
                                 void *stream);
 
+/* Opaque-triangle render (Sec. 5 turns the optimised soup into solid triangles for
+ * game engines; this is the CUDA counterpart, the sigma -> 0, o = 1 limit of the splat
+ * render): tri_preprocess with every triangle taken whole and opaque (opacity and
+ * sigma ignored; near-plane and degenerate triangles culled), tri_bin_sort, then each
+ * pixel takes the colour of the nearest triangle by centroid depth (ties: lower
+ * index) whose window ratio at the pixel centre is positive, else the background.
+ * images [nviews] -> [3][H][W]; ids (nullable; entries nullable) -> [H][W] int32
+ * winning triangle index, -1 for background. num_pairs_out as in tri_bin_sort (null:
+ * no synchronisation). The context then holds no backward state: tri_render_bwd
+ * returns TRI_ERR_STATE until the next tri_preprocess. */
+tri_status tri_render_solid(tri_ctx *ctx, const tri_scene *scene, const tri_camera *cams, int nviews,
+                            float *const *images, int32_t *const *ids, int64_t *num_pairs_out,
+                            void *stream);
+
 /* Step 4 (gradient of step 3): per pixel, back to front from its last composited
  * entry, recompute alpha and T_k = T_{k+1} / (1 - alpha_k), and accumulate per item
  * the gradients of the incenter, the six edge-line slopes, o, sigma and rgb (warp

@@ -294,7 +294,8 @@ tri_status tri_reserve(tri_ctx *c, int64_t pair_capacity) {
     return ensure_pairs(c);
 }
 
-tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *cams, int nviews, void *stream) {
+static tri_status preprocess_impl(tri_ctx *c, const tri_scene *scene, const tri_camera *cams, int nviews,
+                                  bool solid, void *stream) {
     if (!c) return TRI_ERR_INVALID_ARG;
     tri_status s = validate_scene(c, scene);
     if (s != TRI_OK) return s;
@@ -348,11 +349,17 @@ tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *
         a.dkeys = P<uint32_t>(c->dkeys);
         a.ctl = ctl_of(c);
         a.tile_count = P<uint32_t>(c->tile_count);
+        a.solid = solid ? 1 : 0;
         launch_preprocess_fwd(a, st);
         if ((s = launch_check(c, "preprocess_fwd_kernel")) != TRI_OK) return s;
     }
     c->stage = 1;
+    c->solid = solid;
     return TRI_OK;
+}
+
+tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *cams, int nviews, void *stream) {
+    return preprocess_impl(c, scene, cams, nviews, false, stream);
 }
 
 tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
@@ -413,13 +420,15 @@ static RenderArgs render_args(tri_ctx *c, TsDevBuf &outs) {
     r.grad2d = P<float>(c->grad2d);
     r.kmask = P<uint8_t>(c->kmask);
     r.stat_w = r.stat_n = nullptr;
+    r.n_per_view = c->scene.n;
     r.n_items = (uint32_t)c->n_items;
     r.ctl = ctl_of(c);
     return r;
 }
 
 static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const *T_final,
-                                  int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels, void *stream) {
+                                  int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels, void *stream,
+                                  int32_t *const *ids = nullptr) {
     if (!c) return TRI_ERR_INVALID_ARG;
     if (c->stage < 2) return fail(c, TRI_ERR_STATE, "tri_render_fwd before tri_bin_sort");
     if (!images) return fail(c, TRI_ERR_INVALID_ARG, "images is null");
@@ -436,13 +445,20 @@ static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const
     CK(cudaMemsetAsync(&ctl_of(c)->work_counter[0], 0, 4, st));
     CK(cudaMemsetAsync(&ctl_of(c)->frag_eval, 0, 16, st));
     RenderArgs r = render_args(c, c->outs_fwd);
+    if (c->solid) {
+        r.kmask = nullptr;
+        if (ids) {
+            ENSURE(c->ids, 4 * (size_t)c->total_pix);
+            r.ids = P<int32_t>(c->ids);
+        }
+    }
     if (max_weight && n_pixels) {
         CK(cudaMemsetAsync(max_weight, 0, 4 * (size_t)c->n_items, st));
         CK(cudaMemsetAsync(n_pixels, 0, 4 * (size_t)c->n_items, st));
         r.stat_w = reinterpret_cast<uint32_t *>(max_weight);
         r.stat_n = reinterpret_cast<uint32_t *>(n_pixels);
     }
-    launch_render_fwd(r, c->sms, st);
+    launch_render_fwd(r, c->sms, st, c->solid);
     if ((s = launch_check(c, "render_fwd_kernel")) != TRI_OK) return s;
     for (int v = 0; v < c->nviews; ++v) {
         const ViewDev &V = c->views[v];
@@ -452,6 +468,8 @@ static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const
         if (n_contrib && n_contrib[v])
             CK(cudaMemcpyAsync(n_contrib[v], P<int32_t>(c->ncontrib) + V.pix_base, 4 * np, cudaMemcpyDeviceToDevice,
                                st));
+        if (r.ids && ids[v])
+            CK(cudaMemcpyAsync(ids[v], P<int32_t>(c->ids) + V.pix_base, 4 * np, cudaMemcpyDeviceToDevice, st));
     }
     c->stage = 3;
     return TRI_OK;
@@ -460,6 +478,14 @@ static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const
 tri_status tri_render_fwd(tri_ctx *c, float *const *images, float *const *T_final, int32_t *const *n_contrib,
                           void *stream) {
     return render_fwd_impl(c, images, T_final, n_contrib, nullptr, nullptr, stream);
+}
+
+tri_status tri_render_solid(tri_ctx *c, const tri_scene *scene, const tri_camera *cams, int nviews,
+                            float *const *images, int32_t *const *ids, int64_t *num_pairs_out, void *stream) {
+    tri_status s = preprocess_impl(c, scene, cams, nviews, true, stream);
+    if (s != TRI_OK) return s;
+    if ((s = tri_bin_sort(c, num_pairs_out, stream)) != TRI_OK) return s;
+    return render_fwd_impl(c, images, nullptr, nullptr, nullptr, nullptr, stream, ids);
 }
 
 tri_status tri_render_fwd_stats(tri_ctx *c, float *const *images, float *const *T_final,
@@ -471,6 +497,7 @@ tri_status tri_render_fwd_stats(tri_ctx *c, float *const *images, float *const *
 tri_status tri_render_bwd(tri_ctx *c, const float *const *dL, void *stream) {
     if (!c) return TRI_ERR_INVALID_ARG;
     if (c->stage < 3) return fail(c, TRI_ERR_STATE, "tri_render_bwd before tri_render_fwd");
+    if (c->solid) return fail(c, TRI_ERR_STATE, "tri_render_bwd after tri_render_solid (no backward)");
     if (!dL) return fail(c, TRI_ERR_INVALID_ARG, "dL_dimages is null");
     for (int v = 0; v < c->nviews; ++v)
         if (!dL[v]) return fail(c, TRI_ERR_INVALID_ARG, "dL_dimage pointer is null");

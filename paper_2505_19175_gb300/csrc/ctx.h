@@ -24,6 +24,7 @@ struct tri_ctx {
     int64_t total_pix = 0;
     int64_t pair_cap = 0;
     int stage = 0;  // 1 preprocessed, 2 sorted, 3 rendered, 4 backward rendered
+    bool solid = false;  // records of the opaque-triangle render (no backward)
     uint64_t realloc_gen = 0;   // bumped whenever a device buffer is reallocated
     // streams of the previous and the current call: a reallocation waits for both,
     // not for the whole device
@@ -32,10 +33,10 @@ struct tri_ctx {
     ts::ViewDev *h_views = nullptr;
     ts::ViewOut *h_outs_fwd = nullptr, *h_outs_bwd = nullptr;
     TsDevBuf views_d, outs_fwd, outs_bwd, ctl, recs, ntiles, rects, dkeys, tile_count, tile_cursor, big_tiles, kv,
-        kv_tmp, items, kmask, ranges, tile_max, Tfin, ncontrib, grad2d;
+        kv_tmp, items, kmask, ids, ranges, tile_max, Tfin, ncontrib, grad2d;
     std::vector<TsDevBuf *> all() {
         return {&views_d, &outs_fwd, &outs_bwd, &ctl, &recs, &ntiles, &rects, &dkeys, &tile_count, &tile_cursor,
-                &big_tiles, &kv, &kv_tmp, &items, &kmask, &ranges, &tile_max, &Tfin, &ncontrib, &grad2d};
+                &big_tiles, &kv, &kv_tmp, &items, &kmask, &ids, &ranges, &tile_max, &Tfin, &ncontrib, &grad2d};
     }
 };
 

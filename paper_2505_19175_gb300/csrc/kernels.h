@@ -18,6 +18,7 @@ struct PreArgs {
     Ctl *ctl;
     int depth_hist = 0;        // also accumulate the 4 digit histograms of the depth keys
     uint32_t *tile_count = nullptr;  // if set (zeroed): pairs per tile, for the binning
+    int solid = 0;                   // opaque-triangle records: full triangle, o = 1
 };
 
 struct PreBwdArgs {
@@ -110,13 +111,15 @@ struct RenderArgs {
     uint32_t *tile_max;             // [total tiles][8]: largest n_contrib of each warp
     uint32_t *stat_w;               // [items] largest T o as float bits (null: no statistics)
     uint32_t *stat_n;               // [items] pixels where the item was composited
+    int32_t *ids = nullptr;         // solid render: [total pixels] triangle id of the winner, -1
+    int64_t n_per_view = 0;         // triangles per view (item m = view * n_per_view + triangle)
     uint8_t *kmask;                 // [pairs]: bit w = warp w composited the pair (forward
                                     // writes it when set; the backward requires it)
     float *grad2d;                  // backward: [items][16]
     uint32_t n_items;               // bound of the item ids in `items`
     Ctl *ctl;
 };
-void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st);
+void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st, bool solid = false);
 void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st);
 
 void launch_loss_l1(const float *img, const float *tgt, int64_t n, float *grad, float *loss, cudaStream_t st);

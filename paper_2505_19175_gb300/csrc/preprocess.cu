@@ -92,7 +92,8 @@ preprocess_fwd_kernel(PreArgs a) {
     const float sig = alive ? __ldg(a.sigma + i) : 1.0f;
     const float *shp = s_sh + tid * odd_stride(nk * 3);
     // shrink factor of the tight rectangle (Supp. "Tile assignment")
-    const float fshrink = 1.0f - powf(ALPHA_MIN / o, 1.0f / sig);
+    // (solid records: the whole triangle, whatever its opacity)
+    const float fshrink = a.solid ? 1.0f : 1.0f - powf(ALPHA_MIN / o, 1.0f / sig);
     const float cen[3] = {(v[0] + v[3] + v[6]) * (1.0f / 3.0f), (v[1] + v[4] + v[7]) * (1.0f / 3.0f),
                           (v[2] + v[5] + v[8]) * (1.0f / 3.0f)};
 
@@ -152,7 +153,7 @@ preprocess_fwd_kernel(PreArgs a) {
             for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c], 0.0f);
             rec.a = make_float4(sx.hi, sy.hi, g.A[0], g.B[0]);
             rec.b = make_float4(C[0], g.A[1], g.B[1], C[1]);
-            rec.c = make_float4(g.A[2], g.B[2], C[2], o);
+            rec.c = make_float4(g.A[2], g.B[2], C[2], a.solid ? 1.0f : o);
             rec.d = make_float4(sig, col[0], col[1], col[2]);
             key = __float_as_uint(g.depth);
             ++nvis;

@@ -55,8 +55,9 @@ __device__ __forceinline__ bool line_reaches(float A, float B, float C, float sx
 // with origin (ox, oy): its pixel rectangle meets the block, and every edge line can
 // reach the record's cutoff ratio (1/255 / o)^(1/sigma), below which alpha < 1/255
 // (taken 0.1 % low, far beyond the error of the approximate lg2 / ex2).
-__device__ __forceinline__ uint32_t warp_mask(const Rec &r, const ushort4 bx, int ox, int oy) {
-    const float thr = 0.999f * ex2_approx(lg2_approx(ALPHA_MIN / r.c.w) * rcp_approx(r.d.x));
+// Solid records (opaque triangles) are tested against ratio 0, the triangle itself.
+__device__ __forceinline__ uint32_t warp_mask(const Rec &r, const ushort4 bx, int ox, int oy, bool solid = false) {
+    const float thr = solid ? 0.0f : 0.999f * ex2_approx(lg2_approx(ALPHA_MIN / r.c.w) * rcp_approx(r.d.x));
     uint32_t msk = 0;
 #pragma unroll
     for (int wb = 0; wb < REN_THREADS / 32; ++wb) {
@@ -87,6 +88,9 @@ __device__ __forceinline__ int warp_list(const uint8_t *s_mask, uint8_t *list, i
     return cnt;
 }
 
+// SOLID: opaque triangles (the sigma -> 0, o = 1 limit): each pixel takes the colour of
+// the first entry in depth order whose window ratio is positive.
+template <bool SOLID>
 __global__ void __launch_bounds__(REN_THREADS)
 render_fwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
@@ -135,7 +139,7 @@ render_fwd_kernel(RenderArgs a) {
                 }
                 const Rec r = a.recs[it];
                 s_rec[tid] = r;
-                s_mask[tid] = (uint8_t)warp_mask(r, a.rects[it], ox, oy);
+                s_mask[tid] = (uint8_t)warp_mask(r, a.rects[it], ox, oy, SOLID);
             } else {
                 s_mask[tid] = 0;
             }
@@ -155,6 +159,16 @@ render_fwd_kernel(RenderArgs a) {
                     const Frag f = eval_lines(ra, rb, rc, px, py);
                     if (f.ratio <= 0.0f) continue;
                     const float4 rd = s_rec[j].d;
+                    if (SOLID) {
+                        C0 = rd.y;
+                        C1 = rd.z;
+                        C2 = rd.w;
+                        T = 0.0f;
+                        last = b0 - start + (uint32_t)j + 1u;
+                        ++n_kept;
+                        done = true;
+                        break;
+                    }
                     const float I = window_pow(f.ratio, rd.x);
                     float al = __fmul_rn(rc.w, I);
                     if (al < ALPHA_MIN) continue;
@@ -208,6 +222,9 @@ render_fwd_kernel(RenderArgs a) {
             img[2 * HW + pix] = fmaf(T, V.bg[2], C2);
             a.T_final[V.pix_base + pix] = T;
             a.n_contrib[V.pix_base + pix] = (int32_t)last;
+            if (SOLID && a.ids)
+                a.ids[V.pix_base + pix] = last ? (int32_t)((int64_t)a.items[start + last - 1] - (int64_t)vw * a.n_per_view)
+                                               : -1;
         }
         const uint32_t wm = __reduce_max_sync(0xffffffffu, last);
         const uint32_t we = __reduce_add_sync(0xffffffffu, n_eval);
@@ -408,11 +425,13 @@ static int occupancy(const void *fn, int threads) {
     return occ;
 }
 
-void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st) {
-    static int occ = occupancy((const void *)render_fwd_kernel, REN_THREADS);
+void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st, bool solid) {
+    static int occ = occupancy((const void *)render_fwd_kernel<false>, REN_THREADS);
     int g = grid > 0 ? grid * occ : occ;
     if (g > a.total_tiles) g = a.total_tiles;
-    if (g > 0) render_fwd_kernel<<<g, REN_THREADS, 0, st>>>(a);
+    if (g <= 0) return;
+    if (solid) render_fwd_kernel<true><<<g, REN_THREADS, 0, st>>>(a);
+    else render_fwd_kernel<false><<<g, REN_THREADS, 0, st>>>(a);
 }
 
 void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st) {

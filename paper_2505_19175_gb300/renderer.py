@@ -117,6 +117,22 @@ class Context:
             self._ck(self._lib.tri_render_fwd_stats(self.h, ims, tf, nc, mw.data_ptr(), npx.data_ptr(),
                                                     _stream_handle(stream)))
 
+    def render_solid(self, scene: SceneTensors, cams, images, ids=None, sync_pairs: bool = True,
+                     stream=None) -> int:
+        """Opaque-triangle render of ``cams`` into ``images`` (and the winning triangle
+        index per pixel into ``ids``, int32 [H,W] tensors, -1 for background). Returns
+        the pair count when ``sync_pairs`` (growing the pair list if needed), else -1."""
+        self.cams = list(cams)
+        self._scene = scene
+        self._abi_scene = scene.as_abi()
+        self._abi_cams = N.camera_array(self.cams)
+        ims = N.ptr_array([x.data_ptr() for x in images])
+        idp = N.ptr_array([x.data_ptr() for x in ids]) if ids is not None else None
+        n = C.c_int64(-1)
+        self._ck(self._lib.tri_render_solid(self.h, C.byref(self._abi_scene), self._abi_cams, len(self.cams), ims,
+                                            idp, C.byref(n) if sync_pairs else None, _stream_handle(stream)))
+        return int(n.value)
+
     def render_bwd(self, dL_dimages, stream=None) -> None:
         self._dl = [x.contiguous() for x in dL_dimages]
         self._ck(self._lib.tri_render_bwd(self.h, N.ptr_array([x.data_ptr() for x in self._dl]),
