@@ -395,6 +395,8 @@ def run_ours(args, rank, world):
     if not args.no_multiview and world == 1:
         del g_step, g_fwd, g_fwd_stats
         line["multiview_3m_16views"] = run_multiview(max(3, min(args.steps, 10)), 3)
+    if not args.no_densify and world == 1:
+        line["densify_3m"] = run_densify(max(3, min(args.steps, 20)))
     if not args.no_solid and world == 1:
         line["solid_2m"] = run_solid(max(3, min(args.steps, 20)))
     if not args.no_serving:
@@ -517,6 +519,67 @@ def run_solid(steps: int, n_tris: int = 2_000_000):
 
 
 # ---------------------------------------------------------------------------------------
+# densification moves and the size regulariser on 3M triangles
+# ---------------------------------------------------------------------------------------
+def run_densify(steps: int, n: int = 3_000_000, frac: float = 0.1):
+    import torch
+    from paper_2505_19175_gb300 import native as N
+    from paper_2505_19175_gb300.renderer import Context
+    g = torch.Generator(device="cuda").manual_seed(1006)
+    k = int(n * frac)
+    cap = n + 3 * k
+    v0 = torch.randn((cap, 3, 3), device="cuda", generator=g) * 0.1
+    sh0 = torch.randn((cap, 16, 3), device="cuda", generator=g) * 0.2
+    o0 = torch.rand(cap, device="cuda", generator=g)
+    s0 = torch.rand(cap, device="cuda", generator=g) + 0.3
+    sel = torch.randperm(n, device="cuda", generator=g)[:k].to(torch.int32)
+    noise = torch.randn((k, 2), device="cuda", generator=g)
+    e1, e2 = v0[:n, 1] - v0[:n, 0], v0[:n, 2] - v0[:n, 0]
+    tau = float(0.5 * torch.linalg.cross(e1, e2).norm(dim=1).median())
+    ctx = Context()
+    n_out = torch.empty(1, dtype=torch.int64, device="cuda")
+    bufs = [x.clone() for x in (v0, sh0, o0, s0)]
+    st = torch.cuda.current_stream().cuda_stream
+    L = N.lib()
+
+    def once():
+        for b_, x in zip(bufs, (v0, sh0, o0, s0)):
+            b_[:n].copy_(x[:n])
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record()
+        N.check(L.tri_densify(ctx.h, bufs[0].data_ptr(), bufs[1].data_ptr(), bufs[2].data_ptr(), bufs[3].data_ptr(),
+                              3, n, cap, sel.data_ptr(), k, noise.data_ptr(), 0.01, tau, n_out.data_ptr(), st))
+        ev[1].record()
+        return ev
+
+    for _ in range(2):
+        once()
+    evs = [once() for _ in range(steps)]
+    torch.cuda.synchronize()
+    dms = float(np.median([a.elapsed_time(b) for a, b in evs]))
+    grad = torch.zeros_like(v0[:n])
+    loss = torch.empty((), device="cuda")
+    rev = []
+    for _ in range(steps + 2):
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record()
+        N.check(L.tri_size_reg(v0.data_ptr(), n, 1.0 / n, loss.data_ptr(), grad.data_ptr(), st))
+        ev[1].record()
+        rev.append(ev)
+    torch.cuda.synchronize()
+    rms = float(np.median([a.elapsed_time(b) for a, b in rev[2:]]))
+    added = int(n_out.item()) - n
+    # bytes: densify reads 236 B and writes 236 B per selected triangle plus 236 B per
+    # appended one; the regulariser reads 36 B and read-modify-writes 36 B of gradient
+    dens_bytes = k * 472 + added * 236
+    reg_bytes = n * 108
+    return {"workload": f"{n} tris SH3, {k} selected (tau_small = median area: about half split, half cloned)",
+            "densify_ms": round(dms, 4), "appended": added,
+            "densify_gbs": round(dens_bytes / (dms * 1e-3) / 1e9, 1),
+            "size_reg_ms": round(rms, 4), "size_reg_gbs": round(reg_bytes / (rms * 1e-3) / 1e9, 1)}
+
+
+# ---------------------------------------------------------------------------------------
 # serving: open-loop replay of a Poisson trace against one resident scene
 # ---------------------------------------------------------------------------------------
 def replay(srv, sid, trace, max_time_s=60.0):
@@ -586,6 +649,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-multiview", action="store_true")
     ap.add_argument("--no-solid", action="store_true")
+    ap.add_argument("--no-densify", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4096)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -217,6 +217,31 @@ tri_status tri_ctx_check(tri_ctx *ctx, tri_ctx_info *info, void *stream);
  *   8: per-item 2D gradients (float [n_items][16]) */
 tri_status tri_debug_copy(tri_ctx *ctx, int which, void *dst, size_t max_bytes, size_t *bytes);
 
+/* Densification moves (Sec. 3.3 "Densification"), in place on scene arrays with room
+ * for `capacity` triangles (device, same layouts as tri_scene; verts / sh 16-byte
+ * aligned not required). For each of the k distinct indices in sel (device int32):
+ *   - area >= tau_small: midpoint subdivision into four triangles that tile it: the
+ *     triangle becomes (v0, m01, m02) and (m01, v1, m12), (m02, m12, v2),
+ *     (m01, m12, m02) are appended (colour, opacity, sigma copied);
+ *   - area < tau_small: a clone translated by noise_scale (a e1 + b e2) is appended,
+ *     e1 the unit direction of v1 - v0, e2 = n x e1 (n the unit normal), (a, b) =
+ *     noise[2j], noise[2j + 1] (device, caller-drawn standard normals); the triangle
+ *     and its clone take opacity 1 - sqrt(1 - o) (the two composite to o).
+ * Appended triangles follow the order of sel, starting at index n. *n_out (device
+ * int64) receives the new count. The selection policy (the paper samples by opacity
+ * and 1 / sigma) is the caller's. Errors: TRI_ERR_CAPACITY when n + 3 k > capacity;
+ * out-of-range indices are skipped and reported by tri_ctx_check. Asynchronous. */
+tri_status tri_densify(tri_ctx *ctx, float *verts, float *sh, float *opacity, float *sigma, int sh_degree,
+                       int64_t n, int64_t capacity, const int32_t *sel, int64_t k, const float *noise,
+                       float noise_scale, float tau_small, int64_t *n_out, void *stream);
+
+/* Size regulariser of Sec. 3.4: loss = weight * sum_i 2 / |(v1 - v0) x (v2 - v0)|
+ * (weight = beta / n for the mean), written to the device scalar `loss` (nullable),
+ * and its gradient added to dverts [n][3][3] (nullable). Triangles with |cross| below
+ * 1e-12 contribute nothing. Uses the current device; asynchronous. */
+tri_status tri_size_reg(const float *verts, int64_t n, float weight, float *loss, float *dverts,
+                        void *stream);
+
 /* L1 photometric loss helper (Sec. 3.3 lists L1 among the loss terms): loss = mean
  * |image - target| over n values, written to the device scalar `loss` (may be null),
  * and dL/dimage = sign(image - target) / n into `dL_dimage`. */

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libtrisplat.so")
-SOURCES = ["api.cu", "preprocess.cu", "binning.cu", "sort.cu", "render.cu", "serve.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "binning.cu", "sort.cu", "render.cu", "serve.cu", "noalloc.cu", "densify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I" + INCLUDE,
                      "-I" + CSRC, "--expt-relaxed-constexpr"]

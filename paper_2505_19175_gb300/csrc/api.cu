@@ -488,6 +488,63 @@ tri_status tri_render_solid(tri_ctx *c, const tri_scene *scene, const tri_camera
     return render_fwd_impl(c, images, nullptr, nullptr, nullptr, nullptr, stream, ids);
 }
 
+tri_status tri_densify(tri_ctx *c, float *verts, float *sh, float *opacity, float *sigma, int sh_degree, int64_t n,
+                       int64_t capacity, const int32_t *sel, int64_t k, const float *noise, float noise_scale,
+                       float tau_small, int64_t *n_out, void *stream) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    if (!verts || !sh || !opacity || !sigma || !n_out || n < 0 || k < 0 || (k > 0 && (!sel || !noise)) ||
+        sh_degree < 0 || sh_degree > 3)
+        return fail(c, TRI_ERR_INVALID_ARG, "tri_densify: bad arguments");
+    if (k > n) return fail(c, TRI_ERR_INVALID_ARG, "tri_densify: more selections than triangles");
+    if (n + 3 * k > capacity) return fail(c, TRI_ERR_CAPACITY, "tri_densify: capacity below n + 3 k");
+    if (3 * k > (int64_t)LB_MASK) return fail(c, TRI_ERR_CAPACITY, "tri_densify: too many selections");
+    tri_status s = set_device(c);
+    if (s != TRI_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    begin_call(c, st);
+    ENSURE(c->ctl, sizeof(Ctl));
+    if (k == 0) {
+        CK(cudaMemcpyAsync(n_out, &n, sizeof n, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));   // the source is a host stack variable
+        return TRI_OK;
+    }
+    const size_t words = (size_t)((k + 255) / 256) + 1;
+    ENSURE(c->dens_status, 4 * words);
+    CK(cudaMemsetAsync(c->dens_status.p, 0, 4 * words, st));
+    CK(cudaMemsetAsync(&ctl_of(c)->cta_counter[2], 0, 4, st));
+    DensifyArgs a;
+    a.verts = verts;
+    a.sh = sh;
+    a.opacity = opacity;
+    a.sigma = sigma;
+    a.nk = (sh_degree + 1) * (sh_degree + 1);
+    a.n = n;
+    a.k = k;
+    a.sel = sel;
+    a.noise = noise;
+    a.noise_scale = noise_scale;
+    a.tau_small = tau_small;
+    a.n_out = n_out;
+    a.ticket = &ctl_of(c)->cta_counter[2];
+    a.lb_status = P<uint32_t>(c->dens_status);
+    a.err = &ctl_of(c)->error;
+    launch_densify(a, st);
+    return launch_check(c, "densify_kernel");
+}
+
+tri_status tri_size_reg(const float *verts, int64_t n, float weight, float *loss, float *dverts, void *stream) {
+    if (!verts || n < 0 || (!loss && !dverts)) return TRI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return TRI_ERR_CUDA;
+    }
+    if (loss && cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess) return TRI_ERR_CUDA;
+    launch_size_reg(verts, n, weight, loss, dverts, sms, st);
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+}
+
 tri_status tri_render_fwd_stats(tri_ctx *c, float *const *images, float *const *T_final,
                                 int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels, void *stream) {
     if (c && (!max_weight || !n_pixels)) return fail(c, TRI_ERR_INVALID_ARG, "statistics outputs are null");

@@ -96,6 +96,23 @@ void launch_bin_scan(const BinArgs &a, cudaStream_t st);
 void launch_bin_scatter(const BinArgs &a, int sms, cudaStream_t st);
 void launch_tile_sort(const BinArgs &a, int sms, cudaStream_t st);
 
+// ---- densification (densify.cu) ----
+struct DensifyArgs {
+    float *verts, *sh, *opacity, *sigma;   // capacity >= n + 3 k triangles
+    int nk;                                 // SH coefficients per channel
+    int64_t n, k;
+    const int32_t *sel;                     // [k] distinct triangle indices
+    const float *noise;                     // [k][2] standard normal draws
+    float noise_scale, tau_small;
+    int64_t *n_out;                         // device: triangle count afterwards
+    uint32_t *ticket;                       // zeroed CTA ticket
+    uint32_t *lb_status;                    // [ceil(k / 256)] zeroed look-back words
+    uint32_t *err;
+};
+void launch_densify(const DensifyArgs &a, cudaStream_t st);
+void launch_size_reg(const float *verts, int64_t n, float weight, float *loss, float *dverts, int sms,
+                     cudaStream_t st);
+
 // ---- rendering ----
 struct RenderArgs {
     const ViewDev *views;
