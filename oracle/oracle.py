@@ -32,7 +32,8 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
 DEFAULT_CONSTS = dict(alpha_max=0.99, alpha_min=1.0 / 255.0, t_eps=1e-4, z_near=0.2,
-                      r_min=1e-4, tile=16, rect_pad=2.0 ** -9)
+                      r_min=1e-4, tile=16, rect_pad=2.0 ** -9, window=0)
+WINDOW_POWER, WINDOW_SIGMOID = 0, 1       # Eq. indicator1 (the paper's), Eq. indicator2
 EXACT_CONSTS = dict(DEFAULT_CONSTS, alpha_max=1.0, alpha_min=0.0, t_eps=0.0)
 
 AMB_SKIP, AMB_STOP, AMB_ORDER, AMB_SENS, AMB_CULL = 1, 2, 4, 8, 16
@@ -69,6 +70,7 @@ def _load():
             lib.orc_tri_info.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P]
             lib.orc_tri2d.argtypes = [P, P]
             lib.orc_window.argtypes = [P, ctypes.c_double, ctypes.c_int, P, P, P]
+            lib.orc_window_sigmoid.argtypes = [P, ctypes.c_double, ctypes.c_int, P, P, P]
             lib.orc_sh_eval.argtypes = [ctypes.c_int, ctypes.c_int, P, P]
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -118,7 +120,7 @@ def _cam_array(cam):
 def _const_array(consts):
     c = consts or DEFAULT_CONSTS
     return np.array([c["alpha_max"], c["alpha_min"], c["t_eps"], c["z_near"], c["r_min"],
-                     c["tile"], c["rect_pad"]], dtype=np.float64)
+                     c["tile"], c["rect_pad"], c.get("window", 0)], dtype=np.float64)
 
 
 def render(scene, cam, consts=None, brute: bool = False, pix_mask=None, flags: bool = False):
@@ -248,6 +250,16 @@ def window(q, sigma, pts):
     ratio = np.zeros(len(pts)); I = np.zeros(len(pts))
     lib.orc_window(_ptr(q), float(sigma), len(pts), _ptr(pts), _ptr(ratio), _ptr(I))
     return ratio, I
+
+
+def window_sigmoid(q, sigma, pts):
+    """Eq. indicator2: signed distance phi(p) (pixels) and I = sigmoid(-phi / sigma)."""
+    lib = _load()
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(6)
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    phi = np.zeros(len(pts)); I = np.zeros(len(pts))
+    lib.orc_window_sigmoid(_ptr(q), float(sigma), len(pts), _ptr(pts), _ptr(phi), _ptr(I))
+    return phi, I
 
 
 def sh_eval(deg, dirs):

@@ -51,8 +51,13 @@
 /* ------------------------------------------------------------------ */
 /* constants and camera, passed as flat double arrays                  */
 /* ------------------------------------------------------------------ */
+/* window function: WIN_POWER is Eq. indicator1, I = ReLU(phi(p)/phi(s))^sigma;
+ * WIN_SIGMOID is Eq. indicator2, I = sigmoid(-phi(p)/sigma), sigma in pixels */
+enum { WIN_POWER = 0, WIN_SIGMOID = 1 };
+
 typedef struct {
     double alpha_max, alpha_min, t_eps, z_near, r_min, tile, rect_pad;
+    int window;
 } consts_t;
 
 typedef struct {
@@ -65,6 +70,7 @@ static consts_t load_consts(const double *c) {
     consts_t k;
     k.alpha_max = c[0]; k.alpha_min = c[1]; k.t_eps = c[2]; k.z_near = c[3];
     k.r_min = c[4]; k.tile = c[5]; k.rect_pad = c[6];
+    k.window = (int)c[7];
     return k;
 }
 
@@ -152,6 +158,13 @@ static dual ddiv(dual a, dual b) {
 static dual dsqrt(dual a) {
     dual r; r.v = sqrt(a.v);
     for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] / (2.0 * r.v);
+    return r;
+}
+/* 1 / (1 + exp(-a)) */
+static dual dsigmoid(dual a) {
+    dual r; r.v = 1.0 / (1.0 + exp(-a.v));
+    const double s = r.v * (1.0 - r.v);
+    for (int i = 0; i < ND; ++i) r.d[i] = s * a.d[i];
     return r;
 }
 /* a^b for a > 0, both dual */
@@ -264,6 +277,7 @@ typedef struct {
     double o, sigma;
     double dir[3], rgb_raw[3], rgb[3];
     double bbox[4];         /* vertex bbox (xmin, ymin, xmax, ymax) */
+    double ext[4];          /* pixel-candidate extent: bbox, or the rectangle when it is larger */
     /* tight rectangle */
     int rect_state;
     double f, rect[4];
@@ -330,6 +344,7 @@ static void tri_setup(int id, const double *verts, const double *sh, int sh_deg,
     T->bbox[2] = fmax(q[0][0], fmax(q[1][0], q[2][0]));
     T->bbox[3] = fmax(q[0][1], fmax(q[1][1], q[2][1]));
     T->tiles[2] = T->tiles[3] = -1;
+    memcpy(T->ext, T->bbox, sizeof T->ext);
     T->amb_cull = near_amb;
     tri2d_setup((const double (*)[2])q, &T->g);
     if (fabs(T->g.r - K->r_min) <= 0.01 * K->r_min) T->amb_cull = 1;
@@ -357,8 +372,14 @@ static void tri_setup(int id, const double *verts, const double *sh, int sh_deg,
         T->rgb[ch] = acc > 0 ? acc : 0.0;
     }
 
-    /* tight rectangle: triangle scaled about its incenter by f */
-    T->f = 1.0 - pow(K->alpha_min / T->o, 1.0 / T->sigma);
+    /* tight rectangle: triangle scaled about its incenter by f = 1 - c, c the window
+     * ratio below which o I < tau (Supp. "Tile assignment"); for the sigmoid window
+     * c = sigma ln(tau / (o - tau)) / r is negative when o > 2 tau: the support then
+     * exceeds the triangle */
+    if (K->window == WIN_SIGMOID)
+        T->f = T->o > K->alpha_min ? 1.0 - T->sigma * log(K->alpha_min / (T->o - K->alpha_min)) / T->g.r : 0.0;
+    else
+        T->f = 1.0 - pow(K->alpha_min / T->o, 1.0 / T->sigma);
     if (fabs(T->f) <= 1e-5) T->amb_rect = 1;
     if (!(T->f > 0)) {
         T->rect_state = RECT_LOW_OPACITY;
@@ -372,9 +393,14 @@ static void tri_setup(int id, const double *verts, const double *sh, int sh_deg,
     T->rect[1] = fmin(w[0][1], fmin(w[1][1], w[2][1]));
     T->rect[2] = fmax(w[0][0], fmax(w[1][0], w[2][0]));
     T->rect[3] = fmax(w[0][1], fmax(w[1][1], w[2][1]));
+    if (!(T->f < 1e6)) {   /* unbounded support (sigmoid window without a cutoff) */
+        T->rect[0] = T->rect[1] = -INFINITY;
+        T->rect[2] = T->rect[3] = INFINITY;
+    }
     int tile = (int)K->tile;
     rect_tiles(T->rect, K->rect_pad, C, tile, T->pix, T->tiles, &T->ntiles);
     T->rect_state = T->ntiles > 0 ? RECT_OK : RECT_EMPTY;
+    if (T->f > 1.0) memcpy(T->ext, T->rect, sizeof T->ext);
     /* a bound within the FP32 band of a boundary that changes the tile set */
     int pp[4], tt[4], nn;
     for (int sgn = -1; sgn <= 1; sgn += 2) {
@@ -455,7 +481,7 @@ static dual frag_alpha_dual(const tri_dual_t *D, double px, double py, const con
         if (L.v > phi.v) phi = L;
     }
     dual ratio = ddiv(dscale(phi, -1.0), D->r);
-    dual I = dpow(ratio, D->sigma);
+    dual I = K->window == WIN_SIGMOID ? dsigmoid(ddiv(dscale(phi, -1.0), D->sigma)) : dpow(ratio, D->sigma);
     dual a = dmul(D->o, I);
     if (a.v > K->alpha_max) a = dcst(K->alpha_max);
     return a;
@@ -486,6 +512,18 @@ static void vec_push(vec_t *v, ent_t x) {
         v->e = (ent_t *)realloc(v->e, v->cap * sizeof(ent_t));
     }
     v->e[v->n++] = x;
+}
+
+/* window value of triangle t at window ratio `ratio` (FP64) */
+static double window_I(const consts_t *K, const tri_t *t, double ratio) {
+    if (K->window == WIN_SIGMOID) return 1.0 / (1.0 + exp(-t->g.r * ratio / t->sigma));
+    return ratio > 0 ? pow(ratio, t->sigma) : 0.0;
+}
+
+/* relative error of the FP32 window evaluation (approximate lg2 / ex2 / rcp) */
+static double window_rel(const consts_t *K, const tri_t *t, double ratio) {
+    if (K->window == WIN_SIGMOID) return EPS_MUFU * (2.0 + fabs(t->g.r * ratio / t->sigma));
+    return EPS_MUFU * (1.0 + t->sigma * fabs(log2(fmax(ratio, 1e-300))));
 }
 
 static double ulp32(double x) {
@@ -555,9 +593,10 @@ static void shade_pixel(const job_t *J, const ent_t *e, size_t cnt, int x, int y
         const tri_t *t = &J->tris[f->id];
         if (f->kept < 0) { amb |= AMB_CULL; continue; }
         double band = ratio_band(&t->g, f->argmax, px, py);
-        double ahi = t->o * pow(f->ratio + band, t->sigma) * (1.0 + EPS_MUFU * (1.0 + t->sigma * fabs(log2(fmax(f->ratio, 1e-300)))));
+        double wrel = window_rel(K, t, f->ratio);
+        double ahi = t->o * window_I(K, t, f->ratio + band) * (1.0 + wrel);
         double rlo = f->ratio - band;
-        double alo = rlo > 0 ? t->o * pow(rlo, t->sigma) * (1.0 - EPS_MUFU * (1.0 + t->sigma * fabs(log2(fmax(f->ratio, 1e-300))))) : 0.0;
+        double alo = (rlo > 0 || K->window == WIN_SIGMOID) ? t->o * window_I(K, t, rlo) * (1.0 - wrel) : 0.0;
         if (!f->kept) {
             if (ahi >= K->alpha_min) amb |= AMB_SKIP;
             continue;
@@ -658,8 +697,8 @@ static void render_band(const job_t *J, int y0, int y1, const int *cand, int nca
         int xa, xb, ya, yb;
         if (J->brute) { xa = 0; xb = W - 1; ya = y0; yb = y1 - 1; }
         else {
-            pix_range(t->bbox[0] - 1.0, t->bbox[2] + 1.0, W, &xa, &xb);
-            pix_range(t->bbox[1] - 1.0, t->bbox[3] + 1.0, J->C.H, &ya, &yb);
+            pix_range(t->ext[0] - 1.0, t->ext[2] + 1.0, W, &xa, &xb);
+            pix_range(t->ext[1] - 1.0, t->ext[3] + 1.0, J->C.H, &ya, &yb);
             if (ya < y0) ya = y0;
             if (yb > y1 - 1) yb = y1 - 1;
         }
@@ -678,14 +717,16 @@ static void render_band(const job_t *J, int y0, int y1, const int *cand, int nca
                 }
                 int am;
                 double ratio = tri2d_ratio(&t->g, px, py, &am);
-                double araw = ratio > 0 ? t->o * pow(ratio, t->sigma) : 0.0;
-                /* a fragment needs a positive window (ratio > 0) and alpha >= ALPHA_MIN */
-                int kept = ratio > 0 && araw >= K->alpha_min;
+                const int sig = K->window == WIN_SIGMOID;
+                double araw = (ratio > 0 || sig) ? t->o * window_I(K, t, ratio) : 0.0;
+                /* a fragment needs alpha >= ALPHA_MIN (and, for the power window, a
+                 * positive window ratio) */
+                int kept = (ratio > 0 || sig) && araw >= K->alpha_min;
                 if (!kept) {
                     if (!want_flags) continue;
                     double band = ratio_band(&t->g, am, px, py);
-                    if (ratio + band <= 0) continue;
-                    double ahi = t->o * pow(ratio + band, t->sigma) * (1.0 + 4.0 * EPS_MUFU);
+                    if (!sig && ratio + band <= 0) continue;
+                    double ahi = t->o * window_I(K, t, ratio + band) * (1.0 + 4.0 * window_rel(K, t, ratio));
                     if (ahi < K->alpha_min) continue;
                 }
                 ent_t e;
@@ -724,7 +765,7 @@ static void run_job(job_t *J) {
             const tri_t *t = &J->tris[id];
             if (t->cull && !t->amb_cull) continue;
             int ya, yb;
-            pix_range(t->bbox[1] - 1.0, t->bbox[3] + 1.0, H, &ya, &yb);
+            pix_range(t->ext[1] - 1.0, t->ext[3] + 1.0, H, &ya, &yb);
             if (ya > yb) continue;
             for (int b = ya / BAND; b <= yb / BAND; ++b) cnt[b + 1]++;
         }
@@ -735,7 +776,7 @@ static void run_job(job_t *J) {
             const tri_t *t = &J->tris[id];
             if (t->cull && !t->amb_cull) continue;
             int ya, yb;
-            pix_range(t->bbox[1] - 1.0, t->bbox[3] + 1.0, H, &ya, &yb);
+            pix_range(t->ext[1] - 1.0, t->ext[3] + 1.0, H, &ya, &yb);
             if (ya > yb) continue;
             for (int b = ya / BAND; b <= yb / BAND; ++b) all[cnt[b] + fill[b]++] = id;
         }
@@ -987,6 +1028,24 @@ int orc_window(const double *q6, double sigma, int npts, const double *pts, doub
         double r = tri2d_ratio(&T, pts[2 * i], pts[2 * i + 1], NULL);
         if (ratio) ratio[i] = r;
         if (I) I[i] = r > 0 ? pow(r, sigma) : 0.0;
+    }
+    return 0;
+}
+
+/* Eq. indicator2: I = sigmoid(-phi(p) / sigma) with phi the signed distance field
+ * max_i L_i(p) (pixels); also returns phi. */
+int orc_window_sigmoid(const double *q6, double sigma, int npts, const double *pts, double *phi, double *I) {
+    double q[3][2] = {{q6[0], q6[1]}, {q6[2], q6[3]}, {q6[4], q6[5]}};
+    tri2d_t T;
+    tri2d_setup(q, &T);
+    for (int i = 0; i < npts; ++i) {
+        double ph = -INFINITY;
+        for (int k = 0; k < 3; ++k) {
+            double L = T.n[k][0] * pts[2 * i] + T.n[k][1] * pts[2 * i + 1] + T.d[k];
+            if (L > ph) ph = L;
+        }
+        if (phi) phi[i] = ph;
+        if (I) I[i] = 1.0 / (1.0 + exp(ph / sigma));
     }
     return 0;
 }
