@@ -340,6 +340,35 @@ def run_ours(args, rank, world):
         t = torch.tensor([e2e_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
+    # the same step with the sigmoid window (Eq. indicator2): supports beyond the triangles
+    ctx_s = Context(dev)
+    ctx_s.set_window(N.WINDOW_SIGMOID)
+    ctx_s.preprocess(st, [cam])
+    ctx_s.reserve(int(ctx_s.bin_sort(sync=True) * 1.25) + 1024)
+
+    def step_sigmoid():
+        ctx_s.preprocess(st, [cam])
+        ctx_s.bin_sort(sync=False)
+        ctx_s.render_fwd(imgs)
+        N.check(L.tri_loss_l1(imgs[0].data_ptr(), tgt.data_ptr(), imgs[0].numel(), grad.data_ptr(),
+                              loss.data_ptr(), int(torch.cuda.current_stream().cuda_stream)))
+        ctx_s.render_bwd([grad])
+        ctx_s.preprocess_bwd(dv, dsh, do, ds)
+
+    for _ in range(3):
+        step_sigmoid()
+    g_sig = capture(step_sigmoid)
+    for _ in range(3):
+        g_sig.replay()
+    ev_sig = timed(g_sig, args.steps)
+    torch.cuda.synchronize()
+    info_s = ctx_s.check()
+    sig_its = args.steps / (float(sum(a.elapsed_time(b) for a, b in ev_sig)) / 1000.0)
+    sigmoid_line = {"it_per_s": round(sig_its, 2), "pairs": int(info_s.n_pairs),
+                    "frag_composited": int(info_s.frag_composited),
+                    "workload": "the same fwd+bwd step with the sigmoid window of Eq. indicator2"}
+    del g_sig
+
     e2e = {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "it/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
@@ -381,6 +410,7 @@ def run_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single"},
         "fwd_fps": round(fps, 2),
         "fwd_fps_with_prune_stats": round(fps_stats, 2),
+        "sigmoid_window": sigmoid_line,
         "timing": "CUDA-graph replay of the whole step per timed iteration; stage_ms_median from eager "
                   "steps with events between the calls",
         "stage_ms_median": breakdown,

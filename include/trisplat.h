@@ -217,6 +217,18 @@ tri_status tri_ctx_check(tri_ctx *ctx, tri_ctx_info *info, void *stream);
  *   8: per-item 2D gradients (float [n_items][16]) */
 tri_status tri_debug_copy(tri_ctx *ctx, int which, void *dst, size_t max_bytes, size_t *bytes);
 
+/* Window function of the context's next tri_preprocess and of the renders that use its
+ * records. TRI_WINDOW_POWER (default) is the paper's Eq. indicator1, I =
+ * ReLU(phi(p)/phi(s))^sigma; TRI_WINDOW_SIGMOID is Eq. indicator2, the variant the
+ * paper compares against, I = sigmoid(-phi(p)/sigma) with phi the signed distance
+ * field in pixels: 1/2 on the triangle's edges and support beyond them (the tight
+ * rectangle is the triangle dilated about its incenter until o I falls below 1/255).
+ * The backward pass differentiates the chosen window. Resets the context's stage
+ * (the next call must be tri_preprocess). TRI_ERR_INVALID_ARG for another value. */
+#define TRI_WINDOW_POWER 0
+#define TRI_WINDOW_SIGMOID 1
+tri_status tri_set_window(tri_ctx *ctx, int window);
+
 /* Densification moves (Sec. 3.3 "Densification"), in place on scene arrays with room
  * for `capacity` triangles (device, same layouts as tri_scene; verts / sh 16-byte
  * aligned not required). For each of the k distinct indices in sel (device int32):

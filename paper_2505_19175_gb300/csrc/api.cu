@@ -350,11 +350,13 @@ static tri_status preprocess_impl(tri_ctx *c, const tri_scene *scene, const tri_
         a.ctl = ctl_of(c);
         a.tile_count = P<uint32_t>(c->tile_count);
         a.solid = solid ? 1 : 0;
+        a.window = c->window;
         launch_preprocess_fwd(a, st);
         if ((s = launch_check(c, "preprocess_fwd_kernel")) != TRI_OK) return s;
     }
     c->stage = 1;
     c->solid = solid;
+    c->rec_window = c->window;
     return TRI_OK;
 }
 
@@ -421,6 +423,7 @@ static RenderArgs render_args(tri_ctx *c, TsDevBuf &outs) {
     r.kmask = P<uint8_t>(c->kmask);
     r.stat_w = r.stat_n = nullptr;
     r.n_per_view = c->scene.n;
+    r.window = c->rec_window;
     r.n_items = (uint32_t)c->n_items;
     r.ctl = ctl_of(c);
     return r;
@@ -486,6 +489,15 @@ tri_status tri_render_solid(tri_ctx *c, const tri_scene *scene, const tri_camera
     if (s != TRI_OK) return s;
     if ((s = tri_bin_sort(c, num_pairs_out, stream)) != TRI_OK) return s;
     return render_fwd_impl(c, images, nullptr, nullptr, nullptr, nullptr, stream, ids);
+}
+
+tri_status tri_set_window(tri_ctx *c, int window) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    if (window != TRI_WINDOW_POWER && window != TRI_WINDOW_SIGMOID)
+        return fail(c, TRI_ERR_INVALID_ARG, "unknown window kind");
+    c->window = window;
+    c->stage = 0;   // records of the other kind are stale
+    return TRI_OK;
 }
 
 tri_status tri_densify(tri_ctx *c, float *verts, float *sh, float *opacity, float *sigma, int sh_degree, int64_t n,
@@ -585,6 +597,8 @@ tri_status tri_preprocess_bwd(tri_ctx *c, float *dverts, float *dsh, float *dopa
     PreBwdArgs a;
     a.verts = c->scene.verts;
     a.sh = c->scene.sh;
+    a.sigma = c->scene.sigma;
+    a.window = c->rec_window;
     a.n = c->scene.n;
     a.sh_degree = c->scene.sh_degree;
     a.views = P<ViewDev>(c->views_d);

@@ -171,6 +171,16 @@ __device__ __forceinline__ float window_pow(float ratio, float sigma) {
     return ex2_approx(__fmul_rn(sigma, lg2_approx(ratio)));
 }
 
+// Window kinds: WIN_POWER is the paper's Eq. indicator1, I = ratio^sigma (ratio > 0);
+// WIN_SIGMOID is Eq. indicator2, I = sigmoid(-phi / sigma) = sigmoid(kappa ratio) with
+// kappa = r / sigma (phi = -r ratio, r the inradius in pixels); the record stores
+// sigma or kappa in the same slot.
+enum { WIN_POWER = 0, WIN_SIGMOID = 1 };
+
+__device__ __forceinline__ float window_sigmoid(float ratio, float kappa) {
+    return rcp_approx(1.0f + ex2_approx(-1.4426950408889634f * __fmul_rn(kappa, ratio)));
+}
+
 // Exclusive scan across the CTA of one value per thread (blockDim.x <= 1024).
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_sums, uint32_t &total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;

@@ -25,6 +25,8 @@ struct tri_ctx {
     int64_t pair_cap = 0;
     int stage = 0;  // 1 preprocessed, 2 sorted, 3 rendered, 4 backward rendered
     bool solid = false;  // records of the opaque-triangle render (no backward)
+    int window = 0;      // window kind for the next tri_preprocess (tri_set_window)
+    int rec_window = 0;  // window kind of the current records
     uint64_t realloc_gen = 0;   // bumped whenever a device buffer is reallocated
     // streams of the previous and the current call: a reallocation waits for both,
     // not for the whole device

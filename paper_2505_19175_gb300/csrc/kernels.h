@@ -19,10 +19,12 @@ struct PreArgs {
     int depth_hist = 0;        // also accumulate the 4 digit histograms of the depth keys
     uint32_t *tile_count = nullptr;  // if set (zeroed): pairs per tile, for the binning
     int solid = 0;                   // opaque-triangle records: full triangle, o = 1
+    int window = WIN_POWER;          // window kind of the records
 };
 
 struct PreBwdArgs {
     const float *verts, *sh;
+    const float *sigma = nullptr;   // read by the sigmoid window's chain rule
     int64_t n;
     int sh_degree;
     const ViewDev *views;
@@ -31,6 +33,7 @@ struct PreBwdArgs {
     const float *grad2d;       // [items][16]
     float *dverts, *dsh, *dopacity, *dsigma;
     int accumulate;
+    int window = WIN_POWER;
 };
 
 void launch_preprocess_fwd(const PreArgs &a, cudaStream_t st);
@@ -130,6 +133,7 @@ struct RenderArgs {
     uint32_t *stat_n;               // [items] pixels where the item was composited
     int32_t *ids = nullptr;         // solid render: [total pixels] triangle id of the winner, -1
     int64_t n_per_view = 0;         // triangles per view (item m = view * n_per_view + triangle)
+    int window = WIN_POWER;         // window kind of the records
     uint8_t *kmask;                 // [pairs]: bit w = warp w composited the pair (forward
                                     // writes it when set; the backward requires it)
     float *grad2d;                  // backward: [items][16]

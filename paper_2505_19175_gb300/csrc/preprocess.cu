@@ -62,7 +62,7 @@ __device__ __forceinline__ int clamp_pix(float v, int n) {
     return (int)v;
 }
 
-template <int DEG>
+template <int DEG, int WIN>
 __global__ void __launch_bounds__(PRE_THREADS, 6)
 preprocess_fwd_kernel(PreArgs a) {
     __shared__ __align__(16) float s_v[PRE_THREADS * 9];
@@ -92,8 +92,11 @@ preprocess_fwd_kernel(PreArgs a) {
     const float sig = alive ? __ldg(a.sigma + i) : 1.0f;
     const float *shp = s_sh + tid * odd_stride(nk * 3);
     // shrink factor of the tight rectangle (Supp. "Tile assignment")
-    // (solid records: the whole triangle, whatever its opacity)
-    const float fshrink = a.solid ? 1.0f : 1.0f - powf(ALPHA_MIN / o, 1.0f / sig);
+    // (solid records: the whole triangle, whatever its opacity; for the sigmoid window
+    // the factor depends on the inradius and is set per view below)
+    const float fshrink_pow = a.solid ? 1.0f : (WIN == WIN_POWER ? 1.0f - powf(ALPHA_MIN / o, 1.0f / sig) : 0.0f);
+    // sigmoid window: o I >= tau where kappa ratio >= ln(tau / (o - tau))
+    const float lgt = (WIN == WIN_SIGMOID && o > ALPHA_MIN) ? logf(ALPHA_MIN / (o - ALPHA_MIN)) : 0.0f;
     const float cen[3] = {(v[0] + v[3] + v[6]) * (1.0f / 3.0f), (v[1] + v[4] + v[7]) * (1.0f / 3.0f),
                           (v[2] + v[5] + v[8]) * (1.0f / 3.0f)};
 
@@ -108,6 +111,9 @@ preprocess_fwd_kernel(PreArgs a) {
         ushort4 rect = make_ushort4(0, 0, 0, 0);
         Rec rec;
         rec.a = rec.b = rec.c = rec.d = make_float4(0.f, 0.f, 0.f, 0.f);
+        float fshrink = fshrink_pow;
+        if (WIN == WIN_SIGMOID && !a.solid && cull == CULL_NONE)
+            fshrink = o > ALPHA_MIN ? 1.0f - sig * lgt / g.r : 0.0f;   // > 1: support beyond the triangle
         if (cull == CULL_NONE && fshrink > 0.0f) {
             // shrunk triangle: S + f (Q_k - S), Q_0 = 0
             const float wx0 = g.S.x - fshrink * g.S.x, wy0 = g.S.y - fshrink * g.S.y;
@@ -154,7 +160,7 @@ preprocess_fwd_kernel(PreArgs a) {
             rec.a = make_float4(sx.hi, sy.hi, g.A[0], g.B[0]);
             rec.b = make_float4(C[0], g.A[1], g.B[1], C[1]);
             rec.c = make_float4(g.A[2], g.B[2], C[2], a.solid ? 1.0f : o);
-            rec.d = make_float4(sig, col[0], col[1], col[2]);
+            rec.d = make_float4(WIN == WIN_SIGMOID ? g.r / sig : sig, col[0], col[1], col[2]);
             key = __float_as_uint(g.depth);
             ++nvis;
         }
@@ -186,7 +192,7 @@ preprocess_fwd_kernel(PreArgs a) {
     if (tid == 0 && s_nvis) atomicAdd(&a.ctl->n_visible, s_nvis);
 }
 
-template <int DEG>
+template <int DEG, int WIN>
 __global__ void __launch_bounds__(PRE_BWD_THREADS, 8)
 preprocess_bwd_kernel(PreBwdArgs a) {
     __shared__ __align__(16) float s_v[PRE_BWD_THREADS * 9];
@@ -227,7 +233,10 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         Geom g;
         item_geometry<false>(v, V, g);
         go += G2.x;
-        gsig += G2.y;
+        // sigmoid window: field 9 holds dL/dkappa, kappa = r / sigma
+        const float sig_i = WIN == WIN_SIGMOID ? __ldg(a.sigma + i) : 0.0f;
+        if (WIN == WIN_SIGMOID) gsig -= G2.y * g.r / (sig_i * sig_i);
+        else gsig += G2.y;
         // s = q0 + S
         const float gsx = G0.x, gsy = G0.y;
         const float gA[3] = {G0.z, G1.x, G1.z}, gB[3] = {G0.w, G1.y, G1.w};
@@ -247,6 +256,12 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         const float Ey[3] = {g.Q2.y - g.Q1.y, -g.Q2.y, g.Q1.y};
         float gEx[3], gEy[3];
         const float ia2 = rcp_approx(g.area2);
+        if (WIN == WIN_SIGMOID) {
+            // r = |area2| / P
+            const float gr_in = G2.y / sig_i;
+            gA2 += gr_in * (g.area2 >= 0.0f ? iP : -iP);
+            gP -= gr_in * g.r * iP;
+        }
         float iell[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) iell[k] = rcp_approx(g.ell[k]);
@@ -356,11 +371,16 @@ void launch_preprocess_fwd(const PreArgs &a, cudaStream_t st) {
     const int grid = (int)((a.n + PRE_THREADS - 1) / PRE_THREADS);
     if (grid <= 0) return;
     const size_t smem = sizeof(ViewDev) * a.nviews;
+    const bool sg = a.window == WIN_SIGMOID;
     switch (a.sh_degree) {
-        case 0: preprocess_fwd_kernel<0><<<grid, PRE_THREADS, smem, st>>>(a); break;
-        case 1: preprocess_fwd_kernel<1><<<grid, PRE_THREADS, smem, st>>>(a); break;
-        case 2: preprocess_fwd_kernel<2><<<grid, PRE_THREADS, smem, st>>>(a); break;
-        default: preprocess_fwd_kernel<3><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        case 0: sg ? preprocess_fwd_kernel<0, 1><<<grid, PRE_THREADS, smem, st>>>(a)
+                   : preprocess_fwd_kernel<0, 0><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        case 1: sg ? preprocess_fwd_kernel<1, 1><<<grid, PRE_THREADS, smem, st>>>(a)
+                   : preprocess_fwd_kernel<1, 0><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        case 2: sg ? preprocess_fwd_kernel<2, 1><<<grid, PRE_THREADS, smem, st>>>(a)
+                   : preprocess_fwd_kernel<2, 0><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        default: sg ? preprocess_fwd_kernel<3, 1><<<grid, PRE_THREADS, smem, st>>>(a)
+                    : preprocess_fwd_kernel<3, 0><<<grid, PRE_THREADS, smem, st>>>(a); break;
     }
 }
 
@@ -368,11 +388,16 @@ void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st) {
     const int grid = (int)((a.n + PRE_BWD_THREADS - 1) / PRE_BWD_THREADS);
     if (grid <= 0) return;
     const size_t smem = sizeof(ViewDev) * a.nviews;
+    const bool sg = a.window == WIN_SIGMOID;
     switch (a.sh_degree) {
-        case 0: preprocess_bwd_kernel<0><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
-        case 1: preprocess_bwd_kernel<1><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
-        case 2: preprocess_bwd_kernel<2><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
-        default: preprocess_bwd_kernel<3><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+        case 0: sg ? preprocess_bwd_kernel<0, 1><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
+                   : preprocess_bwd_kernel<0, 0><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+        case 1: sg ? preprocess_bwd_kernel<1, 1><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
+                   : preprocess_bwd_kernel<1, 0><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+        case 2: sg ? preprocess_bwd_kernel<2, 1><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
+                   : preprocess_bwd_kernel<2, 0><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+        default: sg ? preprocess_bwd_kernel<3, 1><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
+                    : preprocess_bwd_kernel<3, 0><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
     }
 }
 

@@ -55,9 +55,15 @@ __device__ __forceinline__ bool line_reaches(float A, float B, float C, float sx
 // with origin (ox, oy): its pixel rectangle meets the block, and every edge line can
 // reach the record's cutoff ratio (1/255 / o)^(1/sigma), below which alpha < 1/255
 // (taken 0.1 % low, far beyond the error of the approximate lg2 / ex2).
-// Solid records (opaque triangles) are tested against ratio 0, the triangle itself.
+// Solid records (opaque triangles) are tested against ratio 0, the triangle itself;
+// sigmoid-window records against ln(tau / (o - tau)) / kappa (negative when o > 2 tau).
+template <int WIN>
 __device__ __forceinline__ uint32_t warp_mask(const Rec &r, const ushort4 bx, int ox, int oy, bool solid = false) {
-    const float thr = solid ? 0.0f : 0.999f * ex2_approx(lg2_approx(ALPHA_MIN / r.c.w) * rcp_approx(r.d.x));
+    float thr;
+    if (solid) thr = 0.0f;
+    else if (WIN == WIN_SIGMOID)
+        thr = 0.6931471805599453f * lg2_approx(ALPHA_MIN * rcp_approx(r.c.w - ALPHA_MIN)) * rcp_approx(r.d.x);
+    else thr = 0.999f * ex2_approx(lg2_approx(ALPHA_MIN / r.c.w) * rcp_approx(r.d.x));
     uint32_t msk = 0;
 #pragma unroll
     for (int wb = 0; wb < REN_THREADS / 32; ++wb) {
@@ -89,8 +95,8 @@ __device__ __forceinline__ int warp_list(const uint8_t *s_mask, uint8_t *list, i
 }
 
 // SOLID: opaque triangles (the sigma -> 0, o = 1 limit): each pixel takes the colour of
-// the first entry in depth order whose window ratio is positive.
-template <bool SOLID>
+// the first entry in depth order whose window ratio is positive. WIN: window kind.
+template <bool SOLID, int WIN>
 __global__ void __launch_bounds__(REN_THREADS)
 render_fwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
@@ -139,7 +145,7 @@ render_fwd_kernel(RenderArgs a) {
                 }
                 const Rec r = a.recs[it];
                 s_rec[tid] = r;
-                s_mask[tid] = (uint8_t)warp_mask(r, a.rects[it], ox, oy, SOLID);
+                s_mask[tid] = (uint8_t)warp_mask<WIN>(r, a.rects[it], ox, oy, SOLID);
             } else {
                 s_mask[tid] = 0;
             }
@@ -157,7 +163,7 @@ render_fwd_kernel(RenderArgs a) {
                     ++n_eval;
                     const float4 ra = s_rec[j].a, rb = s_rec[j].b, rc = s_rec[j].c;
                     const Frag f = eval_lines(ra, rb, rc, px, py);
-                    if (f.ratio <= 0.0f) continue;
+                    if ((SOLID || WIN == WIN_POWER) && f.ratio <= 0.0f) continue;
                     const float4 rd = s_rec[j].d;
                     if (SOLID) {
                         C0 = rd.y;
@@ -169,7 +175,7 @@ render_fwd_kernel(RenderArgs a) {
                         done = true;
                         break;
                     }
-                    const float I = window_pow(f.ratio, rd.x);
+                    const float I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, rd.x) : window_pow(f.ratio, rd.x);
                     float al = __fmul_rn(rc.w, I);
                     if (al < ALPHA_MIN) continue;
                     al = fminf(al, ALPHA_MAX);
@@ -267,6 +273,7 @@ __device__ __forceinline__ float warp_reduce16(float (&v)[16], int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+template <int WIN>
 __global__ void __launch_bounds__(REN_THREADS, 4)
 render_bwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
@@ -351,10 +358,11 @@ render_bwd_kernel(RenderArgs a) {
                 if ((uint32_t)(bstart + j) < last) {
                     const float4 ra = s_rec[j].a, rb = s_rec[j].b, rc = s_rec[j].c;
                     const Frag f = eval_lines(ra, rb, rc, px, py);
-                    if (f.ratio > 0.0f) {
+                    if (WIN == WIN_SIGMOID || f.ratio > 0.0f) {
                         const float4 rd = s_rec[j].d;
-                        const float lg = lg2_approx(f.ratio);
-                        const float I = ex2_approx(__fmul_rn(rd.x, lg));
+                        const float lg = WIN == WIN_SIGMOID ? 0.0f : lg2_approx(f.ratio);
+                        const float I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, rd.x)
+                                                           : ex2_approx(__fmul_rn(rd.x, lg));
                         const float araw = __fmul_rn(rc.w, I);
                         if (araw >= ALPHA_MIN) {
                             kept = true;
@@ -375,8 +383,16 @@ render_bwd_kernel(RenderArgs a) {
                             if (araw <= ALPHA_MAX) {
                                 const float gI = galpha * rc.w;
                                 gv[8] = galpha * I;                               // d/do
-                                gv[9] = gI * I * lg * 0.69314718055994531f;       // d/dsigma: I ln(ratio)
-                                const float gr = gI * rd.x * I * rcp_approx(f.ratio);  // d/dratio
+                                float gr;                                         // d/dratio
+                                if (WIN == WIN_SIGMOID) {
+                                    // I = sigmoid(kappa ratio): field 9 is d/dkappa
+                                    const float s1 = I * (1.0f - I);
+                                    gv[9] = gI * s1 * f.ratio;
+                                    gr = gI * rd.x * s1;
+                                } else {
+                                    gv[9] = gI * I * lg * 0.69314718055994531f;   // d/dsigma: I ln(ratio)
+                                    gr = gI * rd.x * I * rcp_approx(f.ratio);
+                                }
                                 // the active line: lowest index among the minima
                                 const int ia = (f.m0 <= f.m1 && f.m0 <= f.m2) ? 0 : (f.m1 <= f.m2 ? 1 : 2);
                                 const float Aa = ia == 0 ? ra.z : (ia == 1 ? rb.y : rc.x);
@@ -426,19 +442,22 @@ static int occupancy(const void *fn, int threads) {
 }
 
 void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st, bool solid) {
-    static int occ = occupancy((const void *)render_fwd_kernel<false>, REN_THREADS);
+    static int occ = occupancy((const void *)render_fwd_kernel<false, WIN_POWER>, REN_THREADS);
     int g = grid > 0 ? grid * occ : occ;
     if (g > a.total_tiles) g = a.total_tiles;
     if (g <= 0) return;
-    if (solid) render_fwd_kernel<true><<<g, REN_THREADS, 0, st>>>(a);
-    else render_fwd_kernel<false><<<g, REN_THREADS, 0, st>>>(a);
+    if (solid) render_fwd_kernel<true, WIN_POWER><<<g, REN_THREADS, 0, st>>>(a);
+    else if (a.window == WIN_SIGMOID) render_fwd_kernel<false, WIN_SIGMOID><<<g, REN_THREADS, 0, st>>>(a);
+    else render_fwd_kernel<false, WIN_POWER><<<g, REN_THREADS, 0, st>>>(a);
 }
 
 void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st) {
-    static int occ = occupancy((const void *)render_bwd_kernel, REN_THREADS);
+    static int occ = occupancy((const void *)render_bwd_kernel<WIN_POWER>, REN_THREADS);
     int g = grid > 0 ? grid * occ : occ;
     if (g > a.total_tiles) g = a.total_tiles;
-    if (g > 0) render_bwd_kernel<<<g, REN_THREADS, 0, st>>>(a);
+    if (g <= 0) return;
+    if (a.window == WIN_SIGMOID) render_bwd_kernel<WIN_SIGMOID><<<g, REN_THREADS, 0, st>>>(a);
+    else render_bwd_kernel<WIN_POWER><<<g, REN_THREADS, 0, st>>>(a);
 }
 
 // ---------------------------------------------------------------------------------

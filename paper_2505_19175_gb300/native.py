@@ -18,6 +18,9 @@ STATUS_NAMES = {0: "TRI_OK", 1: "TRI_ERR_INVALID_ARG", 2: "TRI_ERR_OOM", 3: "TRI
                 4: "TRI_ERR_CAPACITY", 5: "TRI_ERR_TIMEOUT", 6: "TRI_ERR_DEVICE_CHECK", 7: "TRI_ERR_STATE"}
 
 
+WINDOW_POWER, WINDOW_SIGMOID = 0, 1   # Eq. indicator1 (default), Eq. indicator2
+
+
 class TriError(RuntimeError):
     def __init__(self, status: int, msg: str = ""):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -89,6 +92,7 @@ def lib():
             _sig(L, "tri_densify", [vp, vp, vp, vp, vp, C.c_int, C.c_int64, C.c_int64, vp, C.c_int64, vp, C.c_float,
                                     C.c_float, vp, vp])
             _sig(L, "tri_size_reg", [vp, C.c_int64, C.c_float, vp, vp, vp])
+            _sig(L, "tri_set_window", [vp, C.c_int])
             _sig(L, "tri_render_solid", [vp, P(tri_scene), P(tri_camera), C.c_int, P(vp), P(vp),
                                          P(C.c_int64), vp])
             _sig(L, "tri_render_bwd", [vp, P(vp), vp])

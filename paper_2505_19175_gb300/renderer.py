@@ -117,6 +117,11 @@ class Context:
             self._ck(self._lib.tri_render_fwd_stats(self.h, ims, tf, nc, mw.data_ptr(), npx.data_ptr(),
                                                     _stream_handle(stream)))
 
+    def set_window(self, window: int) -> None:
+        """Window of the next preprocess: ``native.WINDOW_POWER`` (Eq. indicator1, the
+        default) or ``native.WINDOW_SIGMOID`` (Eq. indicator2)."""
+        self._ck(self._lib.tri_set_window(self.h, int(window)))
+
     def render_solid(self, scene: SceneTensors, cams, images, ids=None, sync_pairs: bool = True,
                      stream=None) -> int:
         """Opaque-triangle render of ``cams`` into ``images`` (and the winning triangle
