@@ -182,6 +182,42 @@ STAGES = ("preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preproc
 KERNELS_PER_STEP = 9
 
 
+def run_sigmoid_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds, capture, timed):
+    """The headline step with the sigmoid window of Eq. indicator2 (graph replay)."""
+    import torch
+    from paper_2505_19175_gb300 import native as N
+    from paper_2505_19175_gb300.renderer import Context
+    L = N.lib()
+    ctx_s = Context(dev)
+    ctx_s.set_window(N.WINDOW_SIGMOID)
+    ctx_s.preprocess(st, [cam])
+    ctx_s.reserve(int(ctx_s.bin_sort(sync=True) * 1.25) + 1024)
+
+    def step_sigmoid():
+        ctx_s.preprocess(st, [cam])
+        ctx_s.bin_sort(sync=False)
+        ctx_s.render_fwd(imgs)
+        N.check(L.tri_loss_l1(imgs[0].data_ptr(), tgt.data_ptr(), imgs[0].numel(), grad.data_ptr(),
+                              loss.data_ptr(), int(torch.cuda.current_stream().cuda_stream)))
+        ctx_s.render_bwd([grad])
+        ctx_s.preprocess_bwd(dv, dsh, do, ds)
+
+    for _ in range(3):
+        step_sigmoid()
+    g_sig = capture(step_sigmoid)
+    for _ in range(3):
+        g_sig.replay()
+    ev_sig = timed(g_sig, args.steps)
+    torch.cuda.synchronize()
+    info_s = ctx_s.check()
+    sig_its = args.steps / (float(sum(a.elapsed_time(b) for a, b in ev_sig)) / 1000.0)
+    sigmoid_line = {"it_per_s": round(sig_its, 2), "pairs": int(info_s.n_pairs),
+                    "frag_composited": int(info_s.frag_composited),
+                    "workload": "the same fwd+bwd step with the sigmoid window of Eq. indicator2"}
+    del g_sig
+    return sigmoid_line
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2505_19175_gb300 import native as N
@@ -341,36 +377,11 @@ def run_ours(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
     # the same step with the sigmoid window (Eq. indicator2): supports beyond the triangles
-    ctx_s = Context(dev)
-    ctx_s.set_window(N.WINDOW_SIGMOID)
-    ctx_s.preprocess(st, [cam])
-    ctx_s.reserve(int(ctx_s.bin_sort(sync=True) * 1.25) + 1024)
+    sigmoid_line = None
+    if not args.no_sigmoid:
+        sigmoid_line = run_sigmoid_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds, capture, timed)
 
-    def step_sigmoid():
-        ctx_s.preprocess(st, [cam])
-        ctx_s.bin_sort(sync=False)
-        ctx_s.render_fwd(imgs)
-        N.check(L.tri_loss_l1(imgs[0].data_ptr(), tgt.data_ptr(), imgs[0].numel(), grad.data_ptr(),
-                              loss.data_ptr(), int(torch.cuda.current_stream().cuda_stream)))
-        ctx_s.render_bwd([grad])
-        ctx_s.preprocess_bwd(dv, dsh, do, ds)
-
-    for _ in range(3):
-        step_sigmoid()
-    g_sig = capture(step_sigmoid)
-    for _ in range(3):
-        g_sig.replay()
-    ev_sig = timed(g_sig, args.steps)
-    torch.cuda.synchronize()
-    info_s = ctx_s.check()
-    sig_its = args.steps / (float(sum(a.elapsed_time(b) for a, b in ev_sig)) / 1000.0)
-    sigmoid_line = {"it_per_s": round(sig_its, 2), "pairs": int(info_s.n_pairs),
-                    "frag_composited": int(info_s.frag_composited),
-                    "workload": "the same fwd+bwd step with the sigmoid window of Eq. indicator2"}
-    del g_sig
-
-    e2e = {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "it/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h}
+    e2e = {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "it/s", "h2d_bytes_per_step": h2d,           "d2h_bytes_per_step": d2h}
 
     if rank != 0:
         return
@@ -680,6 +691,7 @@ def main():
     ap.add_argument("--no-multiview", action="store_true")
     ap.add_argument("--no-solid", action="store_true")
     ap.add_argument("--no-densify", action="store_true")
+    ap.add_argument("--no-sigmoid", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4096)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
