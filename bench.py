@@ -442,6 +442,8 @@ def run_ours(args, rank, world):
         line["solid_2m"] = run_solid(max(3, min(args.steps, 20)))
     if not args.no_serving:
         line["serving"] = run_serving(args.serve_requests, 2000.0, 1_000_000)
+    if not args.no_multiscene and world == 1:
+        line["multiscene_serving"] = run_multiscene(args.serve_requests)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(scene, cam, target, args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -679,6 +681,126 @@ def run_serving(n_req: int, rate_hz: float, n_tris: int):
     return out
 
 
+# ---------------------------------------------------------------------------------------
+# multi-scene serving under a memory budget with a concurrent training job
+# ---------------------------------------------------------------------------------------
+def run_multiscene(n_req: int, rate_hz: float = 2000.0, budget_gb: float = 60.0):
+    """8 resident scenes (N log-uniform in [200k, 2M]) served from one budget while a
+    fwd+bwd training job of 8 views at 1297x840 runs on scene 0 on its own stream."""
+    import threading
+    import torch
+    from paper_2505_19175_gb300 import native as N
+    from paper_2505_19175_gb300 import synth
+    from paper_2505_19175_gb300.renderer import Context, SceneTensors, new_images
+    from paper_2505_19175_gb300.serve import Server
+    sizes = synth.scene_sizes_multi()
+    scenes = [synth.scene_shells(n, seed=2000 + i) for i, n in enumerate(sizes)]
+    srv = Server(mem_budget_bytes=int(budget_gb * (1 << 30)), max_batch=16, slots=4, max_width=1920, max_height=1080)
+    sids = [srv.add_scene(sc) for sc in scenes]
+    trace = synth.serve_requests(n_req, seed=1007, rate_hz=rate_hz, n_scenes=len(scenes))
+    warm = synth.serve_requests(512, seed=998, rate_hz=rate_hz, n_scenes=len(scenes))
+
+    # training job on scene 0
+    st = SceneTensors.from_numpy(scenes[0])
+    cams = synth.ring_cameras(8, W=1297, H=840)
+    tstream = torch.cuda.Stream()
+    ctx = Context()
+    L = N.lib()
+    imgs = new_images(cams)
+    grads = [torch.empty_like(x) for x in imgs]
+    tgt = [torch.rand_like(x) for x in imgs]
+    loss = torch.empty((), device="cuda")
+    dv, dsh = torch.empty_like(st.verts), torch.empty_like(st.sh)
+    do, ds = torch.empty_like(st.opacity), torch.empty_like(st.sigma)
+    with torch.cuda.stream(tstream):
+        ctx.preprocess(st, cams, stream=tstream)
+        ctx.reserve(int(ctx.bin_sort(sync=True, stream=tstream) * 1.25) + 4096)
+
+    def train_step():
+        ctx.preprocess(st, cams, stream=tstream)
+        ctx.bin_sort(sync=False, stream=tstream)
+        ctx.render_fwd(imgs, stream=tstream)
+        for v in range(len(cams)):
+            N.check(L.tri_loss_l1(imgs[v].data_ptr(), tgt[v].data_ptr(), imgs[v].numel(), grads[v].data_ptr(),
+                                  loss.data_ptr(), int(tstream.cuda_stream)))
+        ctx.render_bwd(grads, stream=tstream)
+        ctx.preprocess_bwd(dv, dsh, do, ds, stream=tstream)
+
+    def train_for(seconds: float):
+        n, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < seconds:
+            train_step()
+            tstream.synchronize()
+            n += 1
+        return n / (time.perf_counter() - t0)
+
+    for _ in range(3):
+        train_step()
+    tstream.synchronize()
+    alone = train_for(1.0)
+
+    # serving with per-request latencies measured at poll (host clock)
+    def replay_lat(tr, max_time_s=60.0):
+        free, pending, lat = {}, {}, []
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(tr) or pending:
+            now = time.perf_counter() - t0
+            while i < len(tr) and tr[i][0] <= now:
+                _, sc, cam = tr[i]
+                key = (cam.H, cam.W)
+                buf = free.get(key, [])
+                out = buf.pop() if buf else torch.empty((3, cam.H, cam.W), device="cuda")
+                t, _ = srv.submit(sids[sc], cam, out)
+                pending[t] = (key, out, sc, time.perf_counter())
+                i += 1
+            for t, status in srv.poll():
+                key, out, sc, ts = pending.pop(t)
+                lat.append((sc, (time.perf_counter() - ts) * 1e3, status))
+                free.setdefault(key, []).append(out)
+            if now > max_time_s:
+                break
+            time.sleep(0.0001)
+        return lat, time.perf_counter() - t0
+
+    replay_lat(warm)
+    torch.cuda.synchronize()
+    stop = threading.Event()
+    steps = [0]
+
+    def trainer():
+        while not stop.is_set():
+            train_step()
+            tstream.synchronize()
+            steps[0] += 1
+
+    th = threading.Thread(target=trainer)
+    old_switch = sys.getswitchinterval()
+    sys.setswitchinterval(0.0002)      # the submit / poll loop and the trainer share the GIL
+    t_start = time.perf_counter()
+    th.start()
+    lat, wall = replay_lat(trace)
+    stop.set()
+    th.join()
+    sys.setswitchinterval(old_switch)
+    t_train = time.perf_counter() - t_start
+    stats = srv.stats()
+    srv.close()
+    per_scene = []
+    for k, n in enumerate(sizes):
+        ms = np.array([x[1] for x in lat if x[0] == k and x[2] == 0])
+        per_scene.append({"triangles": n, "completed": int(len(ms)),
+                          "p50_ms": round(float(np.percentile(ms, 50)), 3) if len(ms) else None,
+                          "p99_ms": round(float(np.percentile(ms, 99)), 3) if len(ms) else None})
+    return {"workload": f"{len(sizes)} shell scenes, {sum(sizes)} tris SH3 resident under a {budget_gb:.0f} GB budget; "
+                        f"{n_req} requests Poisson {rate_hz:.0f} req/s over the scenes, 640x360 : 1280x720 : 1920x1080 "
+                        "= 2:2:1; concurrently a fwd+bwd job of 8 views at 1297x840 on scene 0 on its own stream",
+            "per_scene": per_scene, "serving_fps": round(stats["fps"], 1), "rejected": int(stats["rejected"]),
+            "bytes_resident": int(stats["bytes_resident"]), "training_it_per_s": round(steps[0] / t_train, 2),
+            "training_it_per_s_alone": round(alone, 2), "wall_s": round(wall, 3),
+            "latency": "host clock from submit to poll (0.1 ms polling)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -692,6 +814,7 @@ def main():
     ap.add_argument("--no-solid", action="store_true")
     ap.add_argument("--no-densify", action="store_true")
     ap.add_argument("--no-sigmoid", action="store_true")
+    ap.add_argument("--no-multiscene", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4096)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

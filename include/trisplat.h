@@ -323,7 +323,8 @@ typedef struct {
     double queue_p99_ms;       /* p99 of submit -> launch of the completed requests */
 } tri_serve_stats_t;
 
-/* Create a server on `device`. Starts one dispatcher thread. */
+/* Create a server on `device`. Starts one dispatcher thread; the slots' streams take
+ * the device's highest stream priority. */
 tri_status tri_serve_create(tri_serve **out, const tri_serve_opts *opts, int device);
 
 /* Copy a scene into server-owned device memory (the scene's pointers may be host or

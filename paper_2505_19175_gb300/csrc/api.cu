@@ -39,27 +39,32 @@ void begin_call(tri_ctx *c, cudaStream_t st) {
     c->last_stream = st;
 }
 
-// Grow `b` to at least `bytes` (never shrinks). Before freeing the old allocation it
-// waits for the streams of this call and of the previous one, the only work of this
-// context that can still use it.
+// Grow `b` to at least `bytes` (never shrinks; a regrowth keeps 50 % headroom). Before
+// freeing the old allocation it waits for the streams of this call and of the previous
+// one, the only work of this context that can still use it. Allocation and release are
+// stream-ordered (the device's memory pool) on this call's stream, so a growth never
+// waits for other work on the device (cudaFree / cudaMalloc would synchronise it all);
+// the stream is then synchronised so that the new buffer is usable from any stream.
 tri_status ensure(tri_ctx *c, TsDevBuf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return TRI_OK;
+    cudaStream_t st = c->last_stream;
+    size_t want = b.p ? bytes + bytes / 2 : bytes + bytes / 8;
+    want = (want + 255) & ~(size_t)255;
     if (b.p) {
         CK(cudaStreamSynchronize(c->prev_stream));
         if (c->last_stream != c->prev_stream) CK(cudaStreamSynchronize(c->last_stream));
-        CK(cudaFree(b.p));
+        CK(cudaFreeAsync(b.p, st));
         b.p = nullptr;
         b.bytes = 0;
     }
-    size_t want = bytes + bytes / 8;
-    want = (want + 255) & ~(size_t)255;
-    cudaError_t e = cudaMalloc(&b.p, want);
+    cudaError_t e = cudaMallocAsync(&b.p, want, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
-        return cuda_fail(c, e, "cudaMalloc");
+        return cuda_fail(c, e, "cudaMallocAsync");
     }
+    CK(cudaStreamSynchronize(st));
     b.bytes = want;
     ++c->realloc_gen;
     return TRI_OK;
@@ -228,6 +233,16 @@ tri_status tri_ctx_create(tri_ctx **out, int device) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != device) cudaSetDevice(device);
+    {
+        // workspace growth releases memory to the device's default pool (cudaFreeAsync);
+        // keep it there for the next growth instead of returning it at every sync
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
     bool ok = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
               cudaMallocHost((void **)&c->h_views, sizeof(ViewDev) * MAX_VIEWS) == cudaSuccess &&
               cudaMallocHost((void **)&c->h_outs_fwd, sizeof(ViewOut) * MAX_VIEWS) == cudaSuccess &&
@@ -252,7 +267,8 @@ void tri_ctx_destroy(tri_ctx *c) {
     if (cur != c->device) cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     for (TsDevBuf *b : c->all())
-        if (b->p) cudaFree(b->p);
+        if (b->p) cudaFreeAsync(b->p, 0);   // pool allocations (see ensure)
+    cudaStreamSynchronize(0);
     if (c->h_views) cudaFreeHost(c->h_views);
     if (c->h_outs_fwd) cudaFreeHost(c->h_outs_fwd);
     if (c->h_outs_bwd) cudaFreeHost(c->h_outs_bwd);

@@ -422,9 +422,16 @@ tri_status tri_serve_create(tri_serve **out, const tri_serve_opts *opts, int dev
         S->opts.mem_budget_bytes = fr / 10 * 8;
     }
     S->slots.resize(opts->slots);
+    // serving streams take the device's highest priority: their blocks are scheduled
+    // ahead of pending blocks of other work (a training job) sharing the GPU
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+        cudaGetLastError();
+        prio_hi = 0;
+    }
     for (Slot &sl : S->slots) {
         if (tri_ctx_create(&sl.ctx, device) != TRI_OK ||
-            cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost((void **)&sl.h_ctl, sizeof(Ctl)) != cudaSuccess) {
             cudaGetLastError();
