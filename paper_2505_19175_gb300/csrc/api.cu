@@ -191,6 +191,8 @@ BinArgs bin_args(tri_ctx *c) {
     b.kv_tmp = P<unsigned long long>(c->kv_tmp);
     b.items = P<uint32_t>(c->items);
     b.big_tiles = P<uint32_t>(c->big_tiles);
+    b.scan_status = P<uint64_t>(c->scan_status);
+    b.scan_ticket = &ctl_of(c)->cta_counter[3];
     b.cap = (uint32_t)c->pair_cap;
     b.total_tiles = c->total_tiles;
     // a stride near 0.618 of the block count and coprime with it: a permutation
@@ -342,6 +344,7 @@ static tri_status preprocess_impl(tri_ctx *c, const tri_scene *scene, const tri_
     ENSURE(c->tile_count, 4 * (size_t)tiles);
     ENSURE(c->tile_cursor, 4 * (size_t)tiles);
     ENSURE(c->big_tiles, 4 * (size_t)tiles);
+    ENSURE(c->scan_status, 8 * bin_scan_status_words(tiles));
     ENSURE(c->ranges, sizeof(uint2) * (size_t)tiles);
     ENSURE(c->tile_max, 4 * 8 * (size_t)tiles);
     ENSURE(c->Tfin, 4 * (size_t)pix);
@@ -393,6 +396,8 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
     // counters owned by this step
     CK(cudaMemsetAsync(&ctl->n_pairs, 0, 3 * 4, st));  // n_pairs, n_pairs_used, overflow
     CK(cudaMemsetAsync(&ctl->work_counter[2], 0, 4 * 4, st));  // tile queue, (3), big_count, big_next
+    CK(cudaMemsetAsync(&ctl->cta_counter[3], 0, 4, st));
+    CK(cudaMemsetAsync(c->scan_status.p, 0, 8 * bin_scan_status_words(c->total_tiles), st));
     BinArgs b = bin_args(c);
     // 1. per-tile counts (from tri_preprocess), 2. ranges
     launch_bin_scan(b, st);
@@ -409,6 +414,8 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
             c->pair_cap = cap;
             if ((s = ensure_pairs(c)) != TRI_OK) return s;
             b = bin_args(c);
+            CK(cudaMemsetAsync(&ctl_of(c)->cta_counter[3], 0, 4, st));
+            CK(cudaMemsetAsync(c->scan_status.p, 0, 8 * bin_scan_status_words(c->total_tiles), st));
             launch_bin_scan(b, st);
             if ((s = launch_check(c, "bin_scan")) != TRI_OK) return s;
         }

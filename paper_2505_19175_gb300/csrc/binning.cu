@@ -6,7 +6,8 @@
 // bits) when the pairs are emitted in item order: within a tile, entries are ordered
 // by (depth key, item id). It is reached without a global sort:
 //   1. per-tile pair counts, accumulated by the preprocess kernel;
-//   2. bin_scan:    exclusive scan of the counts -> tile ranges and write cursors;
+//   2. bin_scan:    exclusive scan of the counts -> tile ranges and write cursors
+//                   (single pass, decoupled look-back);
 //   3. bin_scatter: each pair takes a slot in its tile's range (order within the
 //                   range is arbitrary at this point);
 //   4. tile_sort:   each tile's range is sorted by (depth key, item id) in shared
@@ -20,7 +21,6 @@
 namespace ts {
 
 constexpr int BIN_THREADS = 256;
-constexpr int SCAN_THREADS = 1024;
 constexpr int TSORT_THREADS = 256;
 constexpr int MERGE_PER_THREAD = 8;
 
@@ -104,19 +104,32 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_scatter_kernel(BinArgs a) {
     });
 }
 
-// One CTA: exclusive scan of the per-tile counts into ranges (clamped to the pair
-// capacity) and write cursors; totals into the control block.
+// Exclusive scan of the per-tile counts into ranges (clamped to the pair capacity) and
+// write cursors; totals into the control block. CTA b (ticket order) scans tiles
+// [1024 b, 1024 b + 1024) and takes its offset from a single-pass decoupled look-back
+// over 64-bit words.
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_PER = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER;
+
 __global__ void __launch_bounds__(SCAN_THREADS) bin_scan_kernel(BinArgs a) {
     __shared__ unsigned long long s_w[SCAN_THREADS / 32 + 1];
+    __shared__ uint32_t s_cta;
+    __shared__ unsigned long long s_base;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) s_cta = atomicAdd(a.scan_ticket, 1u);
+    __syncthreads();
+    const uint32_t cta = s_cta;
     const int T = a.total_tiles;
-    const int per = (T + SCAN_THREADS - 1) / SCAN_THREADS;
-    const int b = min(T, tid * per), e = min(T, b + per);
-    unsigned long long s = 0;
-#pragma unroll 8
-    for (int i = b; i < e; ++i) s += a.tile_count[i];
-    // block exclusive scan of s
-    unsigned long long x = s;
+    const int64_t t0 = (int64_t)cta * SCAN_TILE + tid * SCAN_PER;
+    uint32_t c[SCAN_PER];
+#pragma unroll
+    for (int q = 0; q < SCAN_PER; ++q) c[q] = t0 + q < T ? a.tile_count[t0 + q] : 0u;
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_PER; ++q) sum += c[q];
+    // block exclusive scan of the per-thread sums
+    unsigned long long x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -125,32 +138,38 @@ __global__ void __launch_bounds__(SCAN_THREADS) bin_scan_kernel(BinArgs a) {
     if (lane == 31) s_w[w] = x;
     __syncthreads();
     if (w == 0) {
-        const unsigned long long v = s_w[lane];
+        const unsigned long long v = lane < SCAN_THREADS / 32 ? s_w[lane] : 0ull;
         unsigned long long t = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
             if (lane >= o) t += y;
         }
-        s_w[lane] = t - v;
-        if (lane == 31) s_w[32] = t;
+        const unsigned long long total = __shfl_sync(0xffffffffu, t, SCAN_THREADS / 32 - 1);
+        if (lane < SCAN_THREADS / 32) s_w[lane] = t - v;
+        const unsigned long long b = warp_lookback_excl64(a.scan_status, cta, total, &a.ctl->error);
+        if (lane == 0) {
+            s_base = b;
+            if ((int64_t)(cta + 1) * SCAN_TILE >= T) {
+                const unsigned long long tot = b + total, cap = a.cap;
+                a.ctl->n_pairs = (uint32_t)(tot < 0xffffffffull ? tot : 0xffffffffull);
+                a.ctl->n_pairs_used = (uint32_t)(tot < cap ? tot : cap);
+                a.ctl->overflow = tot > cap ? 1u : 0u;
+            }
+        }
     }
     __syncthreads();
-    unsigned long long off = s_w[w] + x - s;
+    unsigned long long off = s_base + s_w[w] + x - sum;
     const unsigned long long cap = a.cap;
-    for (int i = b; i < e; ++i) {
-        const uint32_t c = a.tile_count[i];
-        const uint32_t lo = (uint32_t)(off < cap ? off : cap);
-        const uint32_t hi = (uint32_t)(off + c < cap ? off + c : cap);
-        a.ranges[i] = make_uint2(lo, hi);
-        a.tile_cursor[i] = lo;
-        off += c;
-    }
-    if (tid == 0) {
-        const unsigned long long tot = s_w[32];
-        a.ctl->n_pairs = (uint32_t)(tot < 0xffffffffull ? tot : 0xffffffffull);
-        a.ctl->n_pairs_used = (uint32_t)(tot < cap ? tot : cap);
-        a.ctl->overflow = tot > cap ? 1u : 0u;
+#pragma unroll
+    for (int q = 0; q < SCAN_PER; ++q) {
+        if (t0 + q < T) {
+            const uint32_t lo = (uint32_t)(off < cap ? off : cap);
+            const uint32_t hi = (uint32_t)(off + c[q] < cap ? off + c[q] : cap);
+            a.ranges[t0 + q] = make_uint2(lo, hi);
+            a.tile_cursor[t0 + q] = lo;
+        }
+        off += c[q];
     }
 }
 
@@ -370,8 +389,11 @@ __global__ void __launch_bounds__(TSORT_THREADS) tile_sort_big_kernel(BinArgs a)
 }
 
 void launch_bin_scan(const BinArgs &a, cudaStream_t st) {
-    if (a.total_tiles > 0) bin_scan_kernel<<<1, SCAN_THREADS, 0, st>>>(a);
+    const int g = (a.total_tiles + SCAN_TILE - 1) / SCAN_TILE;
+    if (g > 0) bin_scan_kernel<<<g, SCAN_THREADS, 0, st>>>(a);
 }
+
+size_t bin_scan_status_words(int total_tiles) { return (size_t)((total_tiles + SCAN_TILE - 1) / SCAN_TILE) + 1; }
 
 void launch_bin_scatter(const BinArgs &a, int sms, cudaStream_t st) {
     int64_t g = (a.n_items + BIN_THREADS - 1) / BIN_THREADS;

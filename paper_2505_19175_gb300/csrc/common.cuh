@@ -238,4 +238,66 @@ __device__ __forceinline__ uint32_t warp_lookback_excl(uint32_t *status, uint32_
     return excl;
 }
 
+// 64-bit look-back words: flag (LB64_AGG / LB64_PREFIX) in the top two bits, a 62-bit
+// count below; 0 = not yet published.
+constexpr uint64_t LB64_AGG = 1ull << 62;
+constexpr uint64_t LB64_PREFIX = 2ull << 62;
+constexpr uint64_t LB64_MASK = (1ull << 62) - 1;
+
+__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed64(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// As wait_status, for 64-bit words (bounded: 1 s, then ERR_SPIN and a zero prefix).
+__device__ __forceinline__ uint64_t wait_status64(const uint64_t *p, uint32_t *err) {
+    uint64_t s = ld_relaxed64(p);
+    if (s != 0) return s;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        s = ld_relaxed64(p);
+        if (s != 0) return s;
+        if ((it & 63) == 63) {
+            if (ld_relaxed(err) != 0 || global_ns() - t0 > 1000000000ull) {
+                atomicOr(err, ERR_SPIN);
+                return LB64_PREFIX;
+            }
+            __nanosleep(100);
+        }
+    }
+}
+
+// Warp-parallel decoupled look-back over 64-bit words (called by one full warp):
+// publishes `agg` for tile `idx` and returns the exclusive prefix.
+__device__ __forceinline__ uint64_t warp_lookback_excl64(uint64_t *status, uint32_t idx, uint64_t agg,
+                                                         uint32_t *err) {
+    const int lane = threadIdx.x & 31;
+    if (idx == 0) {
+        if (lane == 0) st_relaxed64(&status[0], LB64_PREFIX | agg);
+        return 0;
+    }
+    if (lane == 0) st_relaxed64(&status[idx], LB64_AGG | agg);
+    uint64_t excl = 0;
+    int base = (int)idx - 1;
+    while (true) {
+        const int k = base - lane;
+        const uint64_t s = k >= 0 ? wait_status64(&status[k], err) : LB64_PREFIX;
+        const unsigned pre = __ballot_sync(0xffffffffu, (s >> 62) == 2u);
+        const int stop = pre ? __ffs(pre) - 1 : 31;
+        uint64_t v = lane <= stop ? (s & LB64_MASK) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (pre) break;
+        base -= 32;
+    }
+    if (lane == 0) st_relaxed64(&status[idx], LB64_PREFIX | ((excl + agg) & LB64_MASK));
+    return excl;
+}
+
 }  // namespace ts

@@ -35,10 +35,10 @@ struct tri_ctx {
     ts::ViewDev *h_views = nullptr;
     ts::ViewOut *h_outs_fwd = nullptr, *h_outs_bwd = nullptr;
     TsDevBuf views_d, outs_fwd, outs_bwd, ctl, recs, ntiles, rects, dkeys, tile_count, tile_cursor, big_tiles, kv,
-        kv_tmp, items, kmask, ids, dens_status, ranges, tile_max, Tfin, ncontrib, grad2d;
+        kv_tmp, items, kmask, ids, dens_status, scan_status, ranges, tile_max, Tfin, ncontrib, grad2d;
     std::vector<TsDevBuf *> all() {
         return {&views_d, &outs_fwd, &outs_bwd, &ctl, &recs, &ntiles, &rects, &dkeys, &tile_count, &tile_cursor,
-                &big_tiles, &kv, &kv_tmp, &items, &kmask, &ids, &dens_status, &ranges, &tile_max, &Tfin, &ncontrib, &grad2d};
+                &big_tiles, &kv, &kv_tmp, &items, &kmask, &ids, &dens_status, &scan_status, &ranges, &tile_max, &Tfin, &ncontrib, &grad2d};
     }
 };
 

@@ -93,9 +93,12 @@ struct BinArgs {
     uint32_t cap;
     int total_tiles;
     uint64_t blk_stride;            // visiting order of the 256-item blocks: b * stride mod blocks
+    uint64_t *scan_status;          // [bin_scan_status_words] zeroed look-back words
+    uint32_t *scan_ticket;          // zeroed CTA ticket of the scan
     Ctl *ctl;                       // n_pairs / n_pairs_used / overflow, work_counter[2], big_*
 };
 void launch_bin_scan(const BinArgs &a, cudaStream_t st);
+size_t bin_scan_status_words(int total_tiles);
 void launch_bin_scatter(const BinArgs &a, int sms, cudaStream_t st);
 void launch_tile_sort(const BinArgs &a, int sms, cudaStream_t st);
 
