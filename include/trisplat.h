@@ -37,6 +37,10 @@
  *     message. Device-side checks (bounded spins, capacity) set a status word that
  *     tri_ctx_check reads back (that call synchronises the stream).
  *   Threads: a context is not thread-safe; use one per host thread.
+ *   Tracing: each pipeline call is an NVTX range (tri_preprocess, tri_bin_sort, ...).
+ *   Fault injection (tests, host side only): the environment variable TRI_FAULT read at
+ *     tri_ctx_create: "alloc:N" makes the context's N-th device allocation fail with
+ *     TRI_ERR_OOM; "slow:MS" delays every tri_bin_sort by MS milliseconds on the host.
  *   Streams: cudaStream_t values are passed as void* (0 = legacy default stream).
  *   CUDA graphs: tri_preprocess, tri_bin_sort (with num_pairs_out = NULL),
  *     tri_render_fwd, tri_render_bwd, tri_preprocess_bwd and tri_loss_l1 may be

@@ -1,10 +1,15 @@
 // C ABI of the triangle-splat renderer: contexts, workspace, pipeline sequencing.
 // Declarations and contracts: include/trisplat.h.
+#include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "kernels.h"
 #include "trisplat.h"
@@ -14,6 +19,12 @@ using namespace ts;
 #include "ctx.h"
 
 namespace {
+
+// NVTX range over one API call (host timeline of profilers; free without one attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 constexpr int64_t MAX_PAIRS = (int64_t)LB_MASK;  // pair slots and item ids stay below 2^30
 
@@ -58,6 +69,8 @@ tri_status ensure(tri_ctx *c, TsDevBuf &b, size_t bytes) {
         b.p = nullptr;
         b.bytes = 0;
     }
+    if (c->fault_alloc > 0 && ++c->n_allocs == c->fault_alloc)
+        return fail(c, TRI_ERR_OOM, "injected allocation failure (TRI_FAULT)");
     cudaError_t e = cudaMallocAsync(&b.p, want, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -232,6 +245,12 @@ tri_status tri_ctx_create(tri_ctx **out, int device) {
     }
     tri_ctx *c = new tri_ctx();
     c->device = device;
+    // host-side fault injection for tests: TRI_FAULT="alloc:N" fails the N-th device
+    // allocation of the context, "slow:MS" delays every tri_bin_sort by MS ms
+    if (const char *f = std::getenv("TRI_FAULT")) {
+        if (!strncmp(f, "alloc:", 6)) c->fault_alloc = atol(f + 6);
+        else if (!strncmp(f, "slow:", 5)) c->fault_slow_ms = atol(f + 5);
+    }
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != device) cudaSetDevice(device);
@@ -315,6 +334,7 @@ tri_status tri_reserve(tri_ctx *c, int64_t pair_capacity) {
 static tri_status preprocess_impl(tri_ctx *c, const tri_scene *scene, const tri_camera *cams, int nviews,
                                   bool solid, void *stream) {
     if (!c) return TRI_ERR_INVALID_ARG;
+    NvtxRange nv("tri_preprocess");
     tri_status s = validate_scene(c, scene);
     if (s != TRI_OK) return s;
     if ((s = set_device(c)) != TRI_OK) return s;
@@ -385,6 +405,8 @@ tri_status tri_preprocess(tri_ctx *c, const tri_scene *scene, const tri_camera *
 
 tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
     if (!c) return TRI_ERR_INVALID_ARG;
+    NvtxRange nv("tri_bin_sort");
+    if (c->fault_slow_ms > 0) std::this_thread::sleep_for(std::chrono::milliseconds(c->fault_slow_ms));
     if (c->stage < 1) return fail(c, TRI_ERR_STATE, "tri_bin_sort before tri_preprocess");
     tri_status s = set_device(c);
     if (s != TRI_OK) return s;
@@ -456,6 +478,7 @@ static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const
                                   int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels, void *stream,
                                   int32_t *const *ids = nullptr) {
     if (!c) return TRI_ERR_INVALID_ARG;
+    NvtxRange nv("tri_render_fwd");
     if (c->stage < 2) return fail(c, TRI_ERR_STATE, "tri_render_fwd before tri_bin_sort");
     if (!images) return fail(c, TRI_ERR_INVALID_ARG, "images is null");
     for (int v = 0; v < c->nviews; ++v)
@@ -588,6 +611,7 @@ tri_status tri_render_fwd_stats(tri_ctx *c, float *const *images, float *const *
 
 tri_status tri_render_bwd(tri_ctx *c, const float *const *dL, void *stream) {
     if (!c) return TRI_ERR_INVALID_ARG;
+    NvtxRange nv("tri_render_bwd");
     if (c->stage < 3) return fail(c, TRI_ERR_STATE, "tri_render_bwd before tri_render_fwd");
     if (c->solid) return fail(c, TRI_ERR_STATE, "tri_render_bwd after tri_render_solid (no backward)");
     if (!dL) return fail(c, TRI_ERR_INVALID_ARG, "dL_dimages is null");
@@ -613,6 +637,7 @@ tri_status tri_render_bwd(tri_ctx *c, const float *const *dL, void *stream) {
 tri_status tri_preprocess_bwd(tri_ctx *c, float *dverts, float *dsh, float *dopacity, float *dsigma, int accumulate,
                               void *stream) {
     if (!c) return TRI_ERR_INVALID_ARG;
+    NvtxRange nv("tri_preprocess_bwd");
     if (c->stage < 4) return fail(c, TRI_ERR_STATE, "tri_preprocess_bwd before tri_render_bwd");
     tri_status s = set_device(c);
     if (s != TRI_OK) return s;

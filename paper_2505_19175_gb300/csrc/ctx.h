@@ -27,6 +27,7 @@ struct tri_ctx {
     bool solid = false;  // records of the opaque-triangle render (no backward)
     int window = 0;      // window kind for the next tri_preprocess (tri_set_window)
     int rec_window = 0;  // window kind of the current records
+    long fault_alloc = 0, fault_slow_ms = 0, n_allocs = 0;   // TRI_FAULT injection (tests)
     uint64_t realloc_gen = 0;   // bumped whenever a device buffer is reallocated
     // streams of the previous and the current call: a reallocation waits for both,
     // not for the whole device
