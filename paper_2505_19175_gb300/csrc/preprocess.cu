@@ -192,8 +192,8 @@ preprocess_fwd_kernel(PreArgs a) {
     if (tid == 0 && s_nvis) atomicAdd(&a.ctl->n_visible, s_nvis);
 }
 
-template <int DEG, int WIN>
-__global__ void __launch_bounds__(PRE_BWD_THREADS, 8)
+template <int DEG, int WIN, bool MULTI>
+__global__ void __launch_bounds__(PRE_BWD_THREADS, MULTI ? 6 : 8)
 preprocess_bwd_kernel(PreBwdArgs a) {
     __shared__ __align__(16) float s_v[PRE_BWD_THREADS * 9];
     __shared__ __align__(16) float s_sh[PRE_BWD_THREADS * 49];
@@ -224,9 +224,25 @@ preprocess_bwd_kernel(PreBwdArgs a) {
     float *gsh = s_gsh + tid * sstride;
     for (int k = 0; k < nk * 3; ++k) gsh[k] = 0.f;
 
-    for (int vw = 0; vw < a.nviews && alive; ++vw) {
+    // views in which the triangle was binned: with several views the tile counts of all
+    // views are loaded back to back (one latency) into a bit mask, then only those views
+    // are visited
+    uint64_t vis = 0;
+    if (!MULTI) {
+        vis = alive && __ldg(a.ntiles + i) != 0u ? 1ull : 0ull;
+    } else if (alive) {
+        for (int v0 = 0; v0 < a.nviews; v0 += 8) {
+            uint32_t nt[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) nt[q] = v0 + q < a.nviews ? __ldg(a.ntiles + (int64_t)(v0 + q) * a.n + i) : 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) vis |= (uint64_t)(nt[q] != 0u) << (v0 + q);
+        }
+    }
+#pragma unroll 1
+    for (; vis; vis &= vis - 1) {
+        const int vw = __ffsll((long long)vis) - 1;
         const int64_t m = (int64_t)vw * a.n + i;
-        if (a.ntiles[m] == 0) continue;
         const float4 *gp = reinterpret_cast<const float4 *>(a.grad2d + m * GRAD_FIELDS);
         const float4 G0 = gp[0], G1 = gp[1], G2 = gp[2], G3 = gp[3];
         const ViewDev &V = s_view[vw];
@@ -384,21 +400,27 @@ void launch_preprocess_fwd(const PreArgs &a, cudaStream_t st) {
     }
 }
 
+template <bool MULTI>
+static void launch_bwd_views(const PreBwdArgs &a, int grid, size_t smem, cudaStream_t st) {
+    const bool sg = a.window == WIN_SIGMOID;
+    switch (a.sh_degree) {
+        case 0: sg ? preprocess_bwd_kernel<0, 1, MULTI><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
+                   : preprocess_bwd_kernel<0, 0, MULTI><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+        case 1: sg ? preprocess_bwd_kernel<1, 1, MULTI><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
+                   : preprocess_bwd_kernel<1, 0, MULTI><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+        case 2: sg ? preprocess_bwd_kernel<2, 1, MULTI><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
+                   : preprocess_bwd_kernel<2, 0, MULTI><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+        default: sg ? preprocess_bwd_kernel<3, 1, MULTI><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
+                    : preprocess_bwd_kernel<3, 0, MULTI><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
+    }
+}
+
 void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st) {
     const int grid = (int)((a.n + PRE_BWD_THREADS - 1) / PRE_BWD_THREADS);
     if (grid <= 0) return;
     const size_t smem = sizeof(ViewDev) * a.nviews;
-    const bool sg = a.window == WIN_SIGMOID;
-    switch (a.sh_degree) {
-        case 0: sg ? preprocess_bwd_kernel<0, 1><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
-                   : preprocess_bwd_kernel<0, 0><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
-        case 1: sg ? preprocess_bwd_kernel<1, 1><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
-                   : preprocess_bwd_kernel<1, 0><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
-        case 2: sg ? preprocess_bwd_kernel<2, 1><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
-                   : preprocess_bwd_kernel<2, 0><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
-        default: sg ? preprocess_bwd_kernel<3, 1><<<grid, PRE_BWD_THREADS, smem, st>>>(a)
-                    : preprocess_bwd_kernel<3, 0><<<grid, PRE_BWD_THREADS, smem, st>>>(a); break;
-    }
+    if (a.nviews > 1) launch_bwd_views<true>(a, grid, smem, st);
+    else launch_bwd_views<false>(a, grid, smem, st);
 }
 
 }  // namespace ts
