@@ -1,30 +1,35 @@
 // Tile rendering of the triangle-splat renderer, forward and backward.
 //
-// One CTA of 256 threads renders one 16x16 tile (one thread per pixel; each warp
-// covers an 8x4 block so that small triangles touch few warps). Tiles are taken from
-// a device work queue by a persistent grid, so a launch serves any mix of views and
-// resolutions. The tile's depth-sorted records are staged through shared memory 256
-// at a time (64 B each, one coalesced float4 x 4 gather per thread).
+// One CTA of 256 threads renders one 16x16 tile (one thread per pixel). Each warp
+// covers an 8x4 block and each half-warp a 4x4 half of it; every half-warp walks its
+// own list of the tile's records (those whose support meets its 4x4 block), so that a
+// small triangle costs only the half-warps it touches and the two halves of a warp
+// work on different records at the same time. Tiles are taken from a device work queue
+// by a persistent grid, so a launch serves any mix of views and resolutions. The
+// tile's depth-sorted records are staged through shared memory 256 at a time (64 B
+// each, one coalesced float4 x 4 gather per thread).
 //
 // Forward (Sec. 3.1, the rendering equation of prior splatting work): per pixel,
 // ratio = min_i m_i(p) (phi(p)/phi(s) of Eq. indicator1), I = ratio^sigma, alpha = o I,
 // skip below 1/255, clamp at 0.99, stop before T drops below 1e-4, C += rgb alpha T.
 // The CTA leaves a tile as soon as every pixel has stopped (__syncthreads_count).
 //
-// The forward pass also records, per pair, which warps composited it (one byte of
-// warp bits); the backward walks only those (warp, pair) combinations.
+// The forward pass also records, per pair, which half-warps composited it (16 bits);
+// the backward walks only those (half-warp, pair) combinations.
 //
 // Backward: per pixel, from its last composited entry back to the first,
 // T_k = T_{k+1} / (1 - alpha_k), dL/dalpha_k = sum_c g_c (rgb_c T_k - B_c / (1 - alpha_k))
 // with B the colour behind fragment k plus T_final bg; gradients of the record
-// fields are reduced across the warp with a transposed butterfly (16 shuffles for 16
-// fields), summed per record in shared memory, and added to the per-item gradient
-// record with four 16-byte vector atomics per (item, tile).
+// fields are reduced over each half-warp with a transposed butterfly (15 shuffles for
+// 16 fields, both halves' records at once), summed per record in shared memory, and
+// added to the per-item gradient record with four 16-byte vector atomics per (item,
+// tile).
 #include "kernels.h"
 
 namespace ts {
 
 constexpr int REN_THREADS = TILE_PIX;
+constexpr int HALVES = 2 * REN_THREADS / 32;   // 4x4 half-warp blocks per tile
 
 __device__ __forceinline__ int find_view(const ViewDev *vs, int nviews, int tile) {
     int v = 0;
@@ -33,10 +38,13 @@ __device__ __forceinline__ int find_view(const ViewDev *vs, int nviews, int tile
     return v;
 }
 
+// Pixel of thread tid: warp w covers the 8x4 block ((w & 1) 8, (w >> 1) 4) of the tile,
+// and each half-warp one 4x4 half of it (lanes 0-15 left, 16-31 right); within a half,
+// lane bits [1:0] are x and [3:2] are y.
 __device__ __forceinline__ void pixel_of(int tid, int &lx, int &ly) {
     const int w = tid >> 5, lane = tid & 31;
-    lx = ((w & 1) << 3) | (lane & 7);
-    ly = ((w >> 1) << 2) | (lane >> 3);
+    lx = ((w & 1) << 3) | ((lane >> 4) << 2) | (lane & 3);
+    ly = ((w >> 1) << 2) | ((lane >> 2) & 3);
 }
 
 // Can edge line (A, B, C) be positive at some pixel centre of the block
@@ -51,14 +59,24 @@ __device__ __forceinline__ bool line_reaches(float A, float B, float C, float sx
     return m >= thr - (1e-3f + 4e-7f * (fabsf(t1) + fabsf(t2) + fabsf(C)));
 }
 
-// Bit w set when the record may composite at a pixel of warp w's 8x4 block of the tile
-// with origin (ox, oy): its pixel rectangle meets the block, and every edge line can
-// reach the record's cutoff ratio (1/255 / o)^(1/sigma), below which alpha < 1/255
-// (taken 0.1 % low, far beyond the error of the approximate lg2 / ex2).
-// Solid records (opaque triangles) are tested against ratio 0, the triangle itself;
-// sigmoid-window records against ln(tau / (o - tau)) / kappa (negative when o > 2 tau).
+// May the record composite at a pixel centre of [x0, x1] x [y0, y1]? Its pixel
+// rectangle meets the block and every edge line can reach the cutoff ratio there (a
+// separating-axis test of the block against the record's support).
+__device__ __forceinline__ bool block_hit(const Rec &r, const ushort4 bx, int x0, int x1, int y0, int y1, float thr) {
+    if ((int)bx.x > x1 || (int)bx.z < x0 || (int)bx.y > y1 || (int)bx.w < y0) return false;
+    return line_reaches(r.a.z, r.a.w, r.b.x, r.a.x, r.a.y, x0, x1, y0, y1, thr) &&
+           line_reaches(r.b.y, r.b.z, r.b.w, r.a.x, r.a.y, x0, x1, y0, y1, thr) &&
+           line_reaches(r.c.x, r.c.y, r.c.z, r.a.x, r.a.y, x0, x1, y0, y1, thr);
+}
+
+// Bit 2w + h set when the record may composite at a pixel of half h of warp w's block
+// (tile origin (ox, oy)). The cutoff ratio below which alpha < 1/255 is
+// (1/255 / o)^(1/sigma) for the power window (taken 0.1 % low, far beyond the error of
+// the approximate lg2 / ex2), ln(tau / (o - tau)) / kappa for the sigmoid window
+// (negative when o > 2 tau), and 0 for solid records (the triangle itself). A half is
+// tested only when its warp's whole block passes.
 template <int WIN>
-__device__ __forceinline__ uint32_t warp_mask(const Rec &r, const ushort4 bx, int ox, int oy, bool solid = false) {
+__device__ __forceinline__ uint32_t half_mask(const Rec &r, const ushort4 bx, int ox, int oy, bool solid = false) {
     float thr;
     if (solid) thr = 0.0f;
     else if (WIN == WIN_SIGMOID)
@@ -68,46 +86,62 @@ __device__ __forceinline__ uint32_t warp_mask(const Rec &r, const ushort4 bx, in
 #pragma unroll
     for (int wb = 0; wb < REN_THREADS / 32; ++wb) {
         const int x0 = ox + ((wb & 1) << 3), y0 = oy + ((wb >> 1) << 2);
-        const int x1 = x0 + 7, y1 = y0 + 3;
-        if ((int)bx.x > x1 || (int)bx.z < x0 || (int)bx.y > y1 || (int)bx.w < y0) continue;
-        if (!line_reaches(r.a.z, r.a.w, r.b.x, r.a.x, r.a.y, x0, x1, y0, y1, thr)) continue;
-        if (!line_reaches(r.b.y, r.b.z, r.b.w, r.a.x, r.a.y, x0, x1, y0, y1, thr)) continue;
-        if (!line_reaches(r.c.x, r.c.y, r.c.z, r.a.x, r.a.y, x0, x1, y0, y1, thr)) continue;
-        msk |= 1u << wb;
+        if (!block_hit(r, bx, x0, x0 + 7, y0, y0 + 3, thr)) continue;
+        if (block_hit(r, bx, x0, x0 + 3, y0, y0 + 3, thr)) msk |= 1u << (2 * wb);
+        if (block_hit(r, bx, x0 + 4, x0 + 7, y0, y0 + 3, thr)) msk |= 2u << (2 * wb);
     }
     return msk;
 }
 
-// This warp's records of the staged batch, in batch order; returns the count.
-__device__ __forceinline__ int warp_list(const uint8_t *s_mask, uint8_t *list, int w, int lane) {
+// The two half-warps' records of the staged batch (bits 2w, 2w + 1 of s_mask), in batch
+// order, into list0 / list1; their counts into c0 / c1.
+__device__ __forceinline__ void half_lists(const uint16_t *s_mask, uint8_t *list0, uint8_t *list1, int w, int lane,
+                                           int &c0, int &c1) {
     const unsigned lt = lanemask_lt();
-    int cnt = 0;
+    int n0 = 0, n1 = 0;
 #pragma unroll
     for (int c = 0; c < REN_THREADS / 32; ++c) {
         const int j = c * 32 + lane;
-        const bool hit = (s_mask[j] >> w) & 1u;
-        const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        if (hit) list[cnt + __popc(bal & lt)] = (uint8_t)j;
-        cnt += __popc(bal);
+        const uint32_t m = s_mask[j] >> (2 * w);
+        const bool h0 = m & 1u, h1 = (m >> 1) & 1u;
+        const unsigned b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
+        if (h0) list0[n0 + __popc(b0 & lt)] = (uint8_t)j;
+        if (h1) list1[n1 + __popc(b1 & lt)] = (uint8_t)j;
+        n0 += __popc(b0);
+        n1 += __popc(b1);
     }
     __syncwarp();
-    return cnt;
+    c0 = n0;
+    c1 = n1;
+}
+
+// OR / max across the 16 lanes of a half-warp (full-warp shuffles that stay in the half).
+__device__ __forceinline__ uint32_t half_or(uint32_t v) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ uint32_t half_max(uint32_t v) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
 // SOLID: opaque triangles (the sigma -> 0, o = 1 limit): each pixel takes the colour of
 // the first entry in depth order whose window ratio is positive. WIN: window kind.
+// Each half-warp walks its own list; the warp runs as long as the longer of the two.
 template <bool SOLID, int WIN>
 __global__ void __launch_bounds__(REN_THREADS)
 render_fwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
-    __shared__ uint8_t s_mask[REN_THREADS];
-    __shared__ uint32_t s_km[REN_THREADS];   // warps that composited each staged record
+    __shared__ uint16_t s_mask[REN_THREADS];
+    __shared__ uint32_t s_km[REN_THREADS];   // half-warps that composited each staged record
     __shared__ uint32_t s_sw[REN_THREADS];   // pruning statistics of each staged record:
     __shared__ uint32_t s_sn[REN_THREADS];   // largest T o (float bits), composited pixels
-    __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
+    __shared__ uint8_t s_list[2 * REN_THREADS / 32][REN_THREADS];
     __shared__ ViewDev s_view[MAX_VIEWS];
     __shared__ uint32_t s_tile;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, h = lane >> 4, hl = lane & 15;
     for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += REN_THREADS)
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
     int lx, ly;
@@ -116,6 +150,7 @@ render_fwd_kernel(RenderArgs a) {
     s_sw[tid] = 0u;
     s_sn[tid] = 0u;
     const bool stats = a.stat_n != nullptr;
+    const uint8_t *L = s_list[2 * w + h];
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(&a.ctl->work_counter[0], 1u);
         __syncthreads();
@@ -145,21 +180,23 @@ render_fwd_kernel(RenderArgs a) {
                 }
                 const Rec r = a.recs[it];
                 s_rec[tid] = r;
-                s_mask[tid] = (uint8_t)warp_mask<WIN>(r, a.rects[it], ox, oy, SOLID);
+                s_mask[tid] = (uint16_t)half_mask<WIN>(r, a.rects[it], ox, oy, SOLID);
             } else {
                 s_mask[tid] = 0;
             }
             __syncthreads();
-            const int cnt = warp_list(s_mask, s_list[w], w, lane);
-            // chunks of 32 list entries; bit k of `kept` marks the entries this lane
-            // composited, and the warp's OR of them marks the pairs for the backward
-            for (int c = 0; c < cnt; c += 32) {
+            int c0, c1;
+            half_lists(s_mask, s_list[2 * w], s_list[2 * w + 1], w, lane, c0, c1);
+            const int cnt = h ? c1 : c0, cmax = max(c0, c1);
+            // chunks of 16 list entries; bit k of `kept` marks the entries this lane
+            // composited, and the half-warp's OR of them marks the pairs for the backward
+            for (int c = 0; c < cmax; c += 16) {
                 if (__all_sync(0xffffffffu, done)) break;
-                const int kend = min(cnt, c + 32);
+                const int kend = min(cnt, c + 16);
                 uint32_t kept = 0;
                 for (int k = c; k < kend; ++k) {
                     if (done) break;
-                    const int j = s_list[w][k];
+                    const int j = L[k];
                     ++n_eval;
                     const float4 ra = s_rec[j].a, rb = s_rec[j].b, rc = s_rec[j].c;
                     const Frag f = eval_lines(ra, rb, rc, px, py);
@@ -199,14 +236,14 @@ render_fwd_kernel(RenderArgs a) {
                     kept |= 1u << (k - c);
                 }
                 if (a.kmask) {
-                    const uint32_t wk = __reduce_or_sync(0xffffffffu, kept);
-                    if ((wk >> lane) & 1u) atomicOr(&s_km[s_list[w][c + lane]], 1u << w);
+                    const uint32_t hk = half_or(kept);
+                    if (c + hl < cnt && ((hk >> hl) & 1u)) atomicOr(&s_km[L[c + hl]], 1u << (2 * w + h));
                 }
             }
             if (a.kmask || stats) {
                 __syncthreads();
                 if (a.kmask) {
-                    if (idx < end) a.kmask[idx] = (uint8_t)s_km[tid];
+                    if (idx < end) a.kmask[idx] = (uint16_t)s_km[tid];
                     s_km[tid] = 0u;
                 }
                 if (stats) {
@@ -232,11 +269,11 @@ render_fwd_kernel(RenderArgs a) {
                 a.ids[V.pix_base + pix] = last ? (int32_t)((int64_t)a.items[start + last - 1] - (int64_t)vw * a.n_per_view)
                                                : -1;
         }
-        const uint32_t wm = __reduce_max_sync(0xffffffffu, last);
+        const uint32_t hm = half_max(last);
         const uint32_t we = __reduce_add_sync(0xffffffffu, n_eval);
         const uint32_t wk = __reduce_add_sync(0xffffffffu, n_kept);
+        if (hl == 0) a.tile_max[(size_t)tile * HALVES + 2 * w + h] = hm;
         if (lane == 0) {
-            a.tile_max[(size_t)tile * 8 + w] = wm;
             atomicAdd(&a.ctl->frag_eval, (unsigned long long)we);
             atomicAdd(&a.ctl->frag_kept, (unsigned long long)wk);
         }
@@ -244,51 +281,51 @@ render_fwd_kernel(RenderArgs a) {
     }
 }
 
-// Sum 16 per-lane values across the warp; lane l ends with field (l >> 1).
-__device__ __forceinline__ float warp_reduce16(float (&v)[16], int lane) {
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+// Sum 16 per-lane values over each half-warp: lane l ends with field (l & 15) of its
+// half's sum (transposed butterfly: 15 shuffles for 16 fields, both halves at once).
+__device__ __forceinline__ float half_reduce16(float (&v)[16], int lane) {
+    const bool b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const float send = b4 ? v[i] : v[i + 8];
-        const float keep = b4 ? v[i + 8] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float send = b3 ? v[i] : v[i + 4];
-        const float keep = b3 ? v[i + 4] : v[i];
+        const float send = b3 ? v[i] : v[i + 8];
+        const float keep = b3 ? v[i + 8] : v[i];
         v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float send = b2 ? v[i] : v[i + 2];
-        const float keep = b2 ? v[i + 2] : v[i];
+    for (int i = 0; i < 4; ++i) {
+        const float send = b2 ? v[i] : v[i + 4];
+        const float keep = b2 ? v[i + 4] : v[i];
         v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
     }
-    {
-        const float send = b1 ? v[0] : v[1];
-        const float keep = b1 ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b1 ? v[i] : v[i + 2];
+        const float keep = b1 ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    const float send = b0 ? v[0] : v[1];
+    const float keep = b0 ? v[1] : v[0];
+    return keep + __shfl_xor_sync(0xffffffffu, send, 1);
 }
 
 template <int WIN>
 __global__ void __launch_bounds__(REN_THREADS, 4)
 render_bwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
-    __shared__ uint8_t s_mask[REN_THREADS];
-    __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
+    __shared__ uint16_t s_mask[REN_THREADS];
+    __shared__ uint8_t s_list[2 * REN_THREADS / 32][REN_THREADS];
     __shared__ uint32_t s_item[REN_THREADS];
     __shared__ __align__(16) float s_acc[REN_THREADS][GRAD_FIELDS];
     __shared__ ViewDev s_view[MAX_VIEWS];
-    __shared__ uint32_t s_wmax[REN_THREADS / 32];
+    __shared__ uint32_t s_wmax[HALVES];
     __shared__ uint32_t s_tile;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, h = lane >> 4, hl = lane & 15;
     for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += REN_THREADS)
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
     int lx, ly;
     pixel_of(tid, lx, ly);
+    const uint8_t *L = s_list[2 * w + h];
+    const unsigned hmask = h ? 0xffff0000u : 0x0000ffffu;
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(&a.ctl->work_counter[1], 1u);
         __syncthreads();
@@ -302,12 +339,12 @@ render_bwd_kernel(RenderArgs a) {
         const bool inside = x < V.W && y < V.H;
         const float px = (float)x + 0.5f, py = (float)y + 0.5f;
         const uint32_t start = a.ranges[tile].x;
-        if (tid < REN_THREADS / 32) s_wmax[tid] = a.tile_max[(size_t)tile * 8 + tid];
+        if (tid < HALVES) s_wmax[tid] = a.tile_max[(size_t)tile * HALVES + tid];
         __syncthreads();
         uint32_t maxc = 0;
 #pragma unroll
-        for (int k = 0; k < REN_THREADS / 32; ++k) maxc = max(maxc, s_wmax[k]);
-        const int wmax = (int)s_wmax[w];
+        for (int k = 0; k < HALVES; ++k) maxc = max(maxc, s_wmax[k]);
+        const int hmax = (int)s_wmax[2 * w + h];
         float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
         uint32_t last = 0;
         if (inside) {
@@ -335,7 +372,7 @@ render_bwd_kernel(RenderArgs a) {
                 }
                 s_item[tid] = it;
                 s_rec[tid] = a.recs[it];
-                // the warps that composited this pair in the forward pass
+                // the half-warps that composited this pair in the forward pass
                 s_mask[tid] = a.kmask[start + bstart + tid];
             } else {
                 s_mask[tid] = 0;
@@ -346,16 +383,17 @@ render_bwd_kernel(RenderArgs a) {
                 for (int k = 0; k < 4; ++k) acc4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             __syncthreads();
-            const int jhi = min(nb, wmax - bstart);   // entries this warp composited
-            const int cnt = warp_list(s_mask, s_list[w], w, lane);
-            for (int k = cnt - 1; k >= 0; --k) {
-                const int j = s_list[w][k];
-                if (j >= jhi) continue;
+            const int jhi = min(nb, hmax - bstart);   // entries this half-warp composited
+            int c0, c1;
+            half_lists(s_mask, s_list[2 * w], s_list[2 * w + 1], w, lane, c0, c1);
+            const int cnt = h ? c1 : c0;
+            for (int k = max(c0, c1) - 1; k >= 0; --k) {
+                const int j = k < cnt ? (int)L[k] : REN_THREADS;
                 float gv[16];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) gv[k] = 0.f;
+                for (int q = 0; q < 16; ++q) gv[q] = 0.f;
                 bool kept = false;
-                if ((uint32_t)(bstart + j) < last) {
+                if (j < jhi && (uint32_t)(bstart + j) < last) {
                     const float4 ra = s_rec[j].a, rb = s_rec[j].b, rc = s_rec[j].c;
                     const Frag f = eval_lines(ra, rb, rc, px, py);
                     if (WIN == WIN_SIGMOID || f.ratio > 0.0f) {
@@ -410,9 +448,10 @@ render_bwd_kernel(RenderArgs a) {
                         }
                     }
                 }
-                if (__any_sync(0xffffffffu, kept)) {
-                    const float s = warp_reduce16(gv, lane);
-                    if (!(lane & 1)) atomicAdd(&s_acc[j][lane >> 1], s);
+                const unsigned bk = __ballot_sync(0xffffffffu, kept);
+                if (bk) {
+                    const float sum = half_reduce16(gv, lane);
+                    if ((bk & hmask) && hl < 13) atomicAdd(&s_acc[j][hl], sum);
                 }
             }
             __syncthreads();
