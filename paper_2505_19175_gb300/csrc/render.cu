@@ -69,14 +69,13 @@ __device__ __forceinline__ bool block_hit(const Rec &r, const ushort4 bx, int x0
            line_reaches(r.c.x, r.c.y, r.c.z, r.a.x, r.a.y, x0, x1, y0, y1, thr);
 }
 
-// Bit 2w + h set when the record may composite at a pixel of half h of warp w's block
-// (tile origin (ox, oy)). The cutoff ratio below which alpha < 1/255 is
+// Bit w set when the record may composite at a pixel of warp w's 8x4 block of the tile
+// with origin (ox, oy). The cutoff ratio below which alpha < 1/255 is
 // (1/255 / o)^(1/sigma) for the power window (taken 0.1 % low, far beyond the error of
 // the approximate lg2 / ex2), ln(tau / (o - tau)) / kappa for the sigmoid window
-// (negative when o > 2 tau), and 0 for solid records (the triangle itself). A half is
-// tested only when its warp's whole block passes.
+// (negative when o > 2 tau), and 0 for solid records (the triangle itself).
 template <int WIN>
-__device__ __forceinline__ uint32_t half_mask(const Rec &r, const ushort4 bx, int ox, int oy, bool solid = false) {
+__device__ __forceinline__ uint32_t warp_mask(const Rec &r, const ushort4 bx, int ox, int oy, bool solid = false) {
     float thr;
     if (solid) thr = 0.0f;
     else if (WIN == WIN_SIGMOID)
@@ -86,11 +85,25 @@ __device__ __forceinline__ uint32_t half_mask(const Rec &r, const ushort4 bx, in
 #pragma unroll
     for (int wb = 0; wb < REN_THREADS / 32; ++wb) {
         const int x0 = ox + ((wb & 1) << 3), y0 = oy + ((wb >> 1) << 2);
-        if (!block_hit(r, bx, x0, x0 + 7, y0, y0 + 3, thr)) continue;
-        if (block_hit(r, bx, x0, x0 + 3, y0, y0 + 3, thr)) msk |= 1u << (2 * wb);
-        if (block_hit(r, bx, x0 + 4, x0 + 7, y0, y0 + 3, thr)) msk |= 2u << (2 * wb);
+        if (block_hit(r, bx, x0, x0 + 7, y0, y0 + 3, thr)) msk |= 1u << wb;
     }
     return msk;
+}
+
+// This warp's records of the staged batch, in batch order; returns the count.
+__device__ __forceinline__ int warp_list(const uint16_t *s_mask, uint8_t *list, int w, int lane) {
+    const unsigned lt = lanemask_lt();
+    int cnt = 0;
+#pragma unroll
+    for (int c = 0; c < REN_THREADS / 32; ++c) {
+        const int j = c * 32 + lane;
+        const bool hit = (s_mask[j] >> w) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) list[cnt + __popc(bal & lt)] = (uint8_t)j;
+        cnt += __popc(bal);
+    }
+    __syncwarp();
+    return cnt;
 }
 
 // The two half-warps' records of the staged batch (bits 2w, 2w + 1 of s_mask), in batch
@@ -129,7 +142,9 @@ __device__ __forceinline__ uint32_t half_max(uint32_t v) {
 
 // SOLID: opaque triangles (the sigma -> 0, o = 1 limit): each pixel takes the colour of
 // the first entry in depth order whose window ratio is positive. WIN: window kind.
-// Each half-warp walks its own list; the warp runs as long as the longer of the two.
+// The forward walks one list per warp (measured faster than per-half lists here: the
+// early exit on transmittance keeps its lists short); it records per half-warp which
+// pairs were composited, for the backward's per-half lists.
 template <bool SOLID, int WIN>
 __global__ void __launch_bounds__(REN_THREADS)
 render_fwd_kernel(RenderArgs a) {
@@ -138,7 +153,7 @@ render_fwd_kernel(RenderArgs a) {
     __shared__ uint32_t s_km[REN_THREADS];   // half-warps that composited each staged record
     __shared__ uint32_t s_sw[REN_THREADS];   // pruning statistics of each staged record:
     __shared__ uint32_t s_sn[REN_THREADS];   // largest T o (float bits), composited pixels
-    __shared__ uint8_t s_list[2 * REN_THREADS / 32][REN_THREADS];
+    __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
     __shared__ ViewDev s_view[MAX_VIEWS];
     __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, h = lane >> 4, hl = lane & 15;
@@ -150,7 +165,7 @@ render_fwd_kernel(RenderArgs a) {
     s_sw[tid] = 0u;
     s_sn[tid] = 0u;
     const bool stats = a.stat_n != nullptr;
-    const uint8_t *L = s_list[2 * w + h];
+    const uint8_t *L = s_list[w];
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(&a.ctl->work_counter[0], 1u);
         __syncthreads();
@@ -180,19 +195,17 @@ render_fwd_kernel(RenderArgs a) {
                 }
                 const Rec r = a.recs[it];
                 s_rec[tid] = r;
-                s_mask[tid] = (uint16_t)half_mask<WIN>(r, a.rects[it], ox, oy, SOLID);
+                s_mask[tid] = (uint16_t)warp_mask<WIN>(r, a.rects[it], ox, oy, SOLID);
             } else {
                 s_mask[tid] = 0;
             }
             __syncthreads();
-            int c0, c1;
-            half_lists(s_mask, s_list[2 * w], s_list[2 * w + 1], w, lane, c0, c1);
-            const int cnt = h ? c1 : c0, cmax = max(c0, c1);
-            // chunks of 16 list entries; bit k of `kept` marks the entries this lane
-            // composited, and the half-warp's OR of them marks the pairs for the backward
-            for (int c = 0; c < cmax; c += 16) {
+            const int cnt = warp_list(s_mask, s_list[w], w, lane);
+            // chunks of 32 list entries; bit k of `kept` marks the entries this lane
+            // composited, and each half-warp's OR of them marks the pairs for the backward
+            for (int c = 0; c < cnt; c += 32) {
                 if (__all_sync(0xffffffffu, done)) break;
-                const int kend = min(cnt, c + 16);
+                const int kend = min(cnt, c + 32);
                 uint32_t kept = 0;
                 for (int k = c; k < kend; ++k) {
                     if (done) break;
@@ -237,7 +250,11 @@ render_fwd_kernel(RenderArgs a) {
                 }
                 if (a.kmask) {
                     const uint32_t hk = half_or(kept);
-                    if (c + hl < cnt && ((hk >> hl) & 1u)) atomicOr(&s_km[L[c + hl]], 1u << (2 * w + h));
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int b = 16 * q + hl;
+                        if (c + b < cnt && ((hk >> b) & 1u)) atomicOr(&s_km[L[c + b]], 1u << (2 * w + h));
+                    }
                 }
             }
             if (a.kmask || stats) {
