@@ -31,6 +31,18 @@ namespace ts {
 constexpr int REN_THREADS = TILE_PIX;
 constexpr int HALVES = 2 * REN_THREADS / 32;   // 4x4 half-warp blocks per tile
 
+// View of a tile from the views' first tile ids, by one warp (all lanes get it): the
+// last view whose first tile is <= tile.
+__device__ __forceinline__ int find_view_warp(const ViewDev *vs, int nviews, int tile, int lane) {
+    int v = 0;
+    for (int base = 0; base < nviews; base += 32) {
+        const int k = base + lane;
+        const unsigned b = __ballot_sync(0xffffffffu, k < nviews && vs[k].tile_base <= tile);
+        if (b) v = base + 31 - __clz((int)b);
+    }
+    return v;
+}
+
 __device__ __forceinline__ int find_view(const ViewDev *vs, int nviews, int tile) {
     int v = 0;
     for (int k = 1; k < nviews; ++k)
@@ -325,96 +337,137 @@ __device__ __forceinline__ float half_reduce16(float (&v)[16], int lane) {
     return keep + __shfl_xor_sync(0xffffffffu, send, 1);
 }
 
+constexpr int BWD_CHUNK = 256;   // pairs whose masks a warp scans per list build
+#ifndef BWD_CTAS
+#define BWD_CTAS 3               // resident backward CTAs per SM (80 registers a thread)
+#endif
+
+// Backward, one warp per work unit (tile, 8x4 block of it): the warp scans the masks of
+// the tile's pairs that its two half-warps composited in the forward pass, builds one
+// list per half (item ids), and walks both lists back to front with the record of the
+// next step already in flight; the warps of a CTA never wait for one another. Each
+// half's record gradient goes to the item's gradient record with one 13-lane global
+// reduction per step.
 template <int WIN>
-__global__ void __launch_bounds__(REN_THREADS, 4)
+__global__ void __launch_bounds__(REN_THREADS, BWD_CTAS)
 render_bwd_kernel(RenderArgs a) {
-    __shared__ Rec s_rec[REN_THREADS];
-    __shared__ uint16_t s_mask[REN_THREADS];
-    __shared__ uint8_t s_list[2 * REN_THREADS / 32][REN_THREADS];
-    __shared__ uint32_t s_item[REN_THREADS];
-    __shared__ __align__(16) float s_acc[REN_THREADS][GRAD_FIELDS];
-    __shared__ ViewDev s_view[MAX_VIEWS];
-    __shared__ uint32_t s_wmax[HALVES];
-    __shared__ uint32_t s_tile;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, h = lane >> 4, hl = lane & 15;
-    for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += REN_THREADS)
-        reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
-    int lx, ly;
-    pixel_of(tid, lx, ly);
-    const uint8_t *L = s_list[2 * w + h];
+    __shared__ uint32_t s_li[REN_THREADS / 32][2][BWD_CHUNK];   // per warp and half: item ids
+    __shared__ uint8_t s_lj[REN_THREADS / 32][2][BWD_CHUNK];    // and their pair index in the chunk
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, h = lane >> 4, hl = lane & 15;
     const unsigned hmask = h ? 0xffff0000u : 0x0000ffffu;
+    const unsigned lt_mask = lanemask_lt();
+    const uint32_t *LI = s_li[w][h];
+    const uint8_t *LJ = s_lj[w][h];
+    const uint32_t n_units = (uint32_t)a.total_tiles * (REN_THREADS / 32);
+    const Rec *__restrict__ recs = a.recs;
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(&a.ctl->work_counter[1], 1u);
-        __syncthreads();
-        const int tile = (int)s_tile;
-        if (tile >= a.total_tiles) break;
-        const int vw = find_view(s_view, a.nviews, tile);
-        const ViewDev &V = s_view[vw];
-        const int lt = tile - V.tile_base;
-        const int ox = (lt % V.tiles_x) * TILE, oy = (lt / V.tiles_x) * TILE;
-        const int x = ox + lx, y = oy + ly;
-        const bool inside = x < V.W && y < V.H;
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(&a.ctl->work_counter[1], 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= n_units) break;
+        const int tile = (int)(u / (REN_THREADS / 32)), blk = (int)(u % (REN_THREADS / 32));
+        const int vw = find_view_warp(a.views, a.nviews, tile, lane);
+        const ViewDev *V = a.views + vw;
+        const int tiles_x = V->tiles_x, W = V->W, H = V->H;
+        const int lt = tile - V->tile_base;
+        const int lx = ((blk & 1) << 3) | (h << 2) | (lane & 3), ly = ((blk >> 1) << 2) | ((lane >> 2) & 3);
+        const int x = (lt % tiles_x) * TILE + lx, y = (lt / tiles_x) * TILE + ly;
+        const bool inside = x < W && y < H;
         const float px = (float)x + 0.5f, py = (float)y + 0.5f;
         const uint32_t start = a.ranges[tile].x;
-        if (tid < HALVES) s_wmax[tid] = a.tile_max[(size_t)tile * HALVES + tid];
-        __syncthreads();
-        uint32_t maxc = 0;
-#pragma unroll
-        for (int k = 0; k < HALVES; ++k) maxc = max(maxc, s_wmax[k]);
-        const int hmax = (int)s_wmax[2 * w + h];
+        const uint32_t hmax = a.tile_max[(size_t)tile * HALVES + 2 * blk + h];
+        const int wmax = (int)max(hmax, __shfl_xor_sync(0xffffffffu, hmax, 16));
         float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
         uint32_t last = 0;
         if (inside) {
-            const int64_t HW = (int64_t)V.W * V.H;
-            const int64_t pix = (int64_t)y * V.W + x;
-            T = a.T_final[V.pix_base + pix];
-            last = (uint32_t)a.n_contrib[V.pix_base + pix];
+            const int64_t HW = (int64_t)W * H;
+            const int64_t pix = (int64_t)y * W + x;
+            const int64_t pb = V->pix_base;
+            T = a.T_final[pb + pix];
+            last = (uint32_t)a.n_contrib[pb + pix];
             const float *dL = a.outs[vw].dL;
             g0 = dL[pix];
             g1 = dL[HW + pix];
             g2 = dL[2 * HW + pix];
-            B0 = T * V.bg[0];
-            B1 = T * V.bg[1];
-            B2 = T * V.bg[2];
+            B0 = T * V->bg[0];
+            B1 = T * V->bg[1];
+            B2 = T * V->bg[2];
         }
-        for (int bend = (int)maxc; bend > 0; bend -= REN_THREADS) {
-            const int bstart = max(0, bend - REN_THREADS);
-            const int nb = bend - bstart;
-            __syncthreads();
-            if (tid < nb) {
-                uint32_t it = a.items[start + bstart + tid];
-                if (it >= a.n_items) {
+        const int sh0 = 2 * blk, sh1 = 2 * blk + 1;
+        for (int cend = wmax; cend > 0; cend -= BWD_CHUNK) {
+            const int cstart = max(0, cend - BWD_CHUNK);
+            const int nb = cend - cstart;
+            // the pairs of this chunk that each half composited, in tile order
+            uint32_t m[BWD_CHUNK / 32], itv[BWD_CHUNK / 32];
+#pragma unroll
+            for (int q = 0; q < BWD_CHUNK / 32; ++q) {
+                const int jj = 32 * q + lane;
+                m[q] = 0u;
+                itv[q] = 0u;
+                if (jj < nb) {
+                    m[q] = a.kmask[start + cstart + jj];
+                    itv[q] = a.items[start + cstart + jj];
+                }
+            }
+            __syncwarp();
+            int n0 = 0, n1 = 0;
+#pragma unroll
+            for (int q = 0; q < BWD_CHUNK / 32; ++q) {
+                const bool k0 = (m[q] >> sh0) & 1u, k1 = (m[q] >> sh1) & 1u;
+                uint32_t it = itv[q];
+                if ((k0 || k1) && it >= a.n_items) {
                     atomicOr(&a.ctl->error, ERR_INDEX);
                     it = 0;
                 }
-                s_item[tid] = it;
-                s_rec[tid] = a.recs[it];
-                // the half-warps that composited this pair in the forward pass
-                s_mask[tid] = a.kmask[start + bstart + tid];
-            } else {
-                s_mask[tid] = 0;
+                const unsigned b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
+                if (k0) {
+                    const int pos = n0 + __popc(b0 & lt_mask);
+                    s_li[w][0][pos] = it;
+                    s_lj[w][0][pos] = (uint8_t)(32 * q + lane);
+                }
+                if (k1) {
+                    const int pos = n1 + __popc(b1 & lt_mask);
+                    s_li[w][1][pos] = it;
+                    s_lj[w][1][pos] = (uint8_t)(32 * q + lane);
+                }
+                n0 += __popc(b0);
+                n1 += __popc(b1);
             }
-            {
-                float4 *acc4 = reinterpret_cast<float4 *>(&s_acc[tid][0]);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncwarp();
+            const int cnt = h ? n1 : n0;
+            // software pipeline: the record of step k - 1 loads while step k computes
+            uint32_t nit = 0;
+            int nj = 0;
+            float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb4 = na, nc = na, nd = na;
+            int k = max(n0, n1) - 1;
+            if (k >= 0 && k < cnt) {
+                nit = LI[k];
+                nj = LJ[k];
+                na = __ldg(&recs[nit].a);
+                nb4 = __ldg(&recs[nit].b);
+                nc = __ldg(&recs[nit].c);
+                nd = __ldg(&recs[nit].d);
             }
-            __syncthreads();
-            const int jhi = min(nb, hmax - bstart);   // entries this half-warp composited
-            int c0, c1;
-            half_lists(s_mask, s_list[2 * w], s_list[2 * w + 1], w, lane, c0, c1);
-            const int cnt = h ? c1 : c0;
-            for (int k = max(c0, c1) - 1; k >= 0; --k) {
-                const int j = k < cnt ? (int)L[k] : REN_THREADS;
+            for (; k >= 0; --k) {
+                const float4 ra = na, rb = nb4, rc = nc, rd = nd;
+                const uint32_t item = nit;
+                const int j = nj;
+                const bool has = k < cnt;
+                if (k >= 1 && k - 1 < cnt) {
+                    nit = LI[k - 1];
+                    nj = LJ[k - 1];
+                    na = __ldg(&recs[nit].a);
+                    nb4 = __ldg(&recs[nit].b);
+                    nc = __ldg(&recs[nit].c);
+                    nd = __ldg(&recs[nit].d);
+                }
                 float gv[16];
 #pragma unroll
                 for (int q = 0; q < 16; ++q) gv[q] = 0.f;
                 bool kept = false;
-                if (j < jhi && (uint32_t)(bstart + j) < last) {
-                    const float4 ra = s_rec[j].a, rb = s_rec[j].b, rc = s_rec[j].c;
+                if (has && (uint32_t)(cstart + j) < last) {
                     const Frag f = eval_lines(ra, rb, rc, px, py);
                     if (WIN == WIN_SIGMOID || f.ratio > 0.0f) {
-                        const float4 rd = s_rec[j].d;
                         const float lg = WIN == WIN_SIGMOID ? 0.0f : lg2_approx(f.ratio);
                         const float I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, rd.x)
                                                            : ex2_approx(__fmul_rn(rd.x, lg));
@@ -468,26 +521,11 @@ render_bwd_kernel(RenderArgs a) {
                 const unsigned bk = __ballot_sync(0xffffffffu, kept);
                 if (bk) {
                     const float sum = half_reduce16(gv, lane);
-                    if ((bk & hmask) && hl < 13) atomicAdd(&s_acc[j][hl], sum);
+                    if ((bk & hmask) && hl < 13) atomicAdd(a.grad2d + (size_t)item * GRAD_FIELDS + hl, sum);
                 }
             }
-            __syncthreads();
-            if (tid < nb) {
-                const float4 *acc4 = reinterpret_cast<const float4 *>(&s_acc[tid][0]);
-                const float4 q0 = acc4[0], q1 = acc4[1], q2 = acc4[2], q3 = acc4[3];
-                const bool nz = (q0.x != 0.f) | (q0.y != 0.f) | (q0.z != 0.f) | (q0.w != 0.f) | (q1.x != 0.f) |
-                                (q1.y != 0.f) | (q1.z != 0.f) | (q1.w != 0.f) | (q2.x != 0.f) | (q2.y != 0.f) |
-                                (q2.z != 0.f) | (q2.w != 0.f) | (q3.x != 0.f) | (q3.y != 0.f) | (q3.z != 0.f);
-                if (nz) {
-                    float *dst = a.grad2d + (size_t)s_item[tid] * GRAD_FIELDS;
-                    red_add_v4(dst, q0.x, q0.y, q0.z, q0.w);
-                    red_add_v4(dst + 4, q1.x, q1.y, q1.z, q1.w);
-                    red_add_v4(dst + 8, q2.x, q2.y, q2.z, q2.w);
-                    red_add_v4(dst + 12, q3.x, q3.y, q3.z, q3.w);
-                }
-            }
+            __syncwarp();
         }
-        __syncthreads();
     }
 }
 

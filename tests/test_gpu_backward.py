@@ -112,3 +112,33 @@ def test_fp32_directional_finite_difference():
         fd = (L(scale) - L(-scale)) / (2 * scale)
         an = float(np.sum(grads[key] * u))
         assert abs(fd - an) <= 2e-2 * (abs(an) + abs(fd)) + 1e-3, (key, fd, an)
+
+
+def _layered_tile_scene(seed, W=64, H=48):
+    """A tile (pixels 16..31) whose nearest 400 triangles all lie left of x = 21.5 and
+    whose next 400 cover the whole tile, at low opacity: lists longer than 256 entries,
+    where the blocks at x >= 24 composite nothing among the first 400."""
+    rng = np.random.default_rng(seed)
+    cam = synth.camera_identity(W, H)
+    groups = []
+    for n, z, xr, d in ((400, (2.0, 3.0), (18.0, 20.0), 1.5), (400, (4.0, 6.0), (17.0, 31.0), 2.5)):
+        zz = rng.uniform(*z, n)
+        u = rng.uniform(*xr, n)[:, None] + rng.uniform(-d, d, (n, 3))
+        v = rng.uniform(17.0, 31.0, n)[:, None] + rng.uniform(-d, d, (n, 3))
+        zv = zz[:, None] * (1.0 + 0.01 * rng.standard_normal((n, 3)))
+        groups.append(np.stack([(u - cam.cx) / cam.fx * zv, (v - cam.cy) / cam.fy * zv, zv], 2))
+    n = 800
+    scene = synth.Scene(np.concatenate(groups).astype(np.float32), (0.3 * rng.standard_normal((n, 1, 3))).astype(np.float32),
+                        rng.uniform(0.02, 0.08, n).astype(np.float32), rng.uniform(0.5, 2.0, n).astype(np.float32), 0)
+    return scene, cam
+
+
+def test_backward_long_tile_lists_with_empty_chunks():
+    scene, cam = _layered_tile_scene(7)
+    imgs, T, nc, ctx, st = gpu_forward(scene, [cam])
+    assert int(nc[0][16:32, 24:32].max()) > 400
+    ref = O.render(scene, cam, flags=True)
+    g = _masked_grad(ref, 8, (3, cam.H, cam.W))
+    got = gpu_backward(ctx, st, [g])
+    want = O.render_grad(scene, cam, g)
+    _check_grads(got, want)
