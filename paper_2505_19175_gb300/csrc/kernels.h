@@ -131,13 +131,13 @@ struct RenderArgs {
     const ushort4 *rects;           // per-item pixel rectangles
     float *T_final;                 // [total pixels]
     int32_t *n_contrib;             // [total pixels]
-    uint32_t *tile_max;             // [total tiles][16]: largest n_contrib of each half-warp
+    uint32_t *tile_max;             // [total tiles][32]: largest n_contrib of each 8-lane group
     uint32_t *stat_w;               // [items] largest T o as float bits (null: no statistics)
     uint32_t *stat_n;               // [items] pixels where the item was composited
     int32_t *ids = nullptr;         // solid render: [total pixels] triangle id of the winner, -1
     int64_t n_per_view = 0;         // triangles per view (item m = view * n_per_view + triangle)
     int window = WIN_POWER;         // window kind of the records
-    uint16_t *kmask;                // [pairs]: bit 2w + h = half h of warp w composited the pair (forward
+    uint32_t *kmask;                // [pairs]: bit 4w + g = group g of warp w composited the pair (forward
                                     // writes it when set; the backward requires it)
     float *grad2d;                  // backward: [items][16]
     uint32_t n_items;               // bound of the item ids in `items`

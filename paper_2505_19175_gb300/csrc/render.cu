@@ -1,35 +1,34 @@
 // Tile rendering of the triangle-splat renderer, forward and backward.
 //
-// One CTA of 256 threads renders one 16x16 tile (one thread per pixel). Each warp
-// covers an 8x4 block and each half-warp a 4x4 half of it; every half-warp walks its
-// own list of the tile's records (those whose support meets its 4x4 block), so that a
-// small triangle costs only the half-warps it touches and the two halves of a warp
-// work on different records at the same time. Tiles are taken from a device work queue
-// by a persistent grid, so a launch serves any mix of views and resolutions. The
-// tile's depth-sorted records are staged through shared memory 256 at a time (64 B
-// each, one coalesced float4 x 4 gather per thread).
+// A tile is 16x16 pixels, one thread per pixel, cut into eight 8x4 blocks (one warp
+// each) and each block into four 2x4 groups of 8 lanes. Tiles are taken from device
+// work queues by persistent grids, so a launch serves any mix of views and resolutions.
 //
-// Forward (Sec. 3.1, the rendering equation of prior splatting work): per pixel,
+// Forward (Sec. 3.1, the rendering equation of prior splatting work): one CTA of 256
+// threads per tile; the tile's depth-sorted records are staged through shared memory
+// 256 at a time (64 B each, one coalesced float4 x 4 gather per thread) and each warp
+// walks the list of records whose support meets its block. Per pixel,
 // ratio = min_i m_i(p) (phi(p)/phi(s) of Eq. indicator1), I = ratio^sigma, alpha = o I,
 // skip below 1/255, clamp at 0.99, stop before T drops below 1e-4, C += rgb alpha T.
-// The CTA leaves a tile as soon as every pixel has stopped (__syncthreads_count).
+// The CTA leaves a tile as soon as every pixel has stopped (__syncthreads_count). It
+// also records, per pair, which groups composited it (32 bits), and per group the
+// largest composited index.
 //
-// The forward pass also records, per pair, which half-warps composited it (16 bits);
-// the backward walks only those (half-warp, pair) combinations.
-//
-// Backward: per pixel, from its last composited entry back to the first,
+// Backward: one warp per (tile, block) work unit, with no CTA-wide barrier. Each group
+// walks only the pairs it composited, back to front: per pixel
 // T_k = T_{k+1} / (1 - alpha_k), dL/dalpha_k = sum_c g_c (rgb_c T_k - B_c / (1 - alpha_k))
-// with B the colour behind fragment k plus T_final bg; gradients of the record
-// fields are reduced over each half-warp with a transposed butterfly (15 shuffles for
-// 16 fields, both halves' records at once), summed per record in shared memory, and
-// added to the per-item gradient record with four 16-byte vector atomics per (item,
-// tile).
+// with B the colour behind fragment k plus T_final bg. The 13 record-field gradients
+// are summed over each group with a transposed butterfly (14 shuffles for 16 fields,
+// the four groups' records at once) and added to the per-item gradient record with
+// one 8-byte vector reduction per lane.
 #include "kernels.h"
 
 namespace ts {
 
 constexpr int REN_THREADS = TILE_PIX;
-constexpr int HALVES = 2 * REN_THREADS / 32;   // 4x4 half-warp blocks per tile
+constexpr int GROUP = 8;                          // lanes of a group: a 2x4 block of pixels
+constexpr int WGROUPS = 32 / GROUP;               // groups per warp
+constexpr int GROUPS = REN_THREADS / GROUP;       // groups per tile
 
 // View of a tile from the views' first tile ids, by one warp (all lanes get it): the
 // last view whose first tile is <= tile.
@@ -50,14 +49,14 @@ __device__ __forceinline__ int find_view(const ViewDev *vs, int nviews, int tile
     return v;
 }
 
-// Pixel of thread tid: warp w covers the 8x4 block ((w & 1) 8, (w >> 1) 4) of the tile,
-// and each half-warp one 4x4 half of it (lanes 0-15 left, 16-31 right); within a half,
-// lane bits [1:0] are x and [3:2] are y.
-__device__ __forceinline__ void pixel_of(int tid, int &lx, int &ly) {
-    const int w = tid >> 5, lane = tid & 31;
-    lx = ((w & 1) << 3) | ((lane >> 4) << 2) | (lane & 3);
-    ly = ((w >> 1) << 2) | ((lane >> 2) & 3);
+// Pixel of lane `lane` of the warp that covers 8x4 block w of the tile: block w sits at
+// ((w & 1) 8, (w >> 1) 4); each group of 8 lanes (g = lane / 8) covers its 2x4 column
+// pair at x 2g, with lane bit 0 as x and bits [2:1] as y.
+__device__ __forceinline__ void block_pixel(int w, int lane, int &lx, int &ly) {
+    lx = ((w & 1) << 3) | ((lane >> 3) << 1) | (lane & 1);
+    ly = ((w >> 1) << 2) | ((lane >> 1) & 3);
 }
+__device__ __forceinline__ void pixel_of(int tid, int &lx, int &ly) { block_pixel(tid >> 5, tid & 31, lx, ly); }
 
 // Can edge line (A, B, C) be positive at some pixel centre of the block
 // [x0, x1] x [y0, y1]? Its maximum over the block is at the corner its slope selects;
@@ -118,57 +117,35 @@ __device__ __forceinline__ int warp_list(const uint16_t *s_mask, uint8_t *list, 
     return cnt;
 }
 
-// The two half-warps' records of the staged batch (bits 2w, 2w + 1 of s_mask), in batch
-// order, into list0 / list1; their counts into c0 / c1.
-__device__ __forceinline__ void half_lists(const uint16_t *s_mask, uint8_t *list0, uint8_t *list1, int w, int lane,
-                                           int &c0, int &c1) {
-    const unsigned lt = lanemask_lt();
-    int n0 = 0, n1 = 0;
+// OR / max across the 8 lanes of a group (full-warp shuffles that stay in the group).
+__device__ __forceinline__ uint32_t group_or(uint32_t v) {
 #pragma unroll
-    for (int c = 0; c < REN_THREADS / 32; ++c) {
-        const int j = c * 32 + lane;
-        const uint32_t m = s_mask[j] >> (2 * w);
-        const bool h0 = m & 1u, h1 = (m >> 1) & 1u;
-        const unsigned b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
-        if (h0) list0[n0 + __popc(b0 & lt)] = (uint8_t)j;
-        if (h1) list1[n1 + __popc(b1 & lt)] = (uint8_t)j;
-        n0 += __popc(b0);
-        n1 += __popc(b1);
-    }
-    __syncwarp();
-    c0 = n0;
-    c1 = n1;
-}
-
-// OR / max across the 16 lanes of a half-warp (full-warp shuffles that stay in the half).
-__device__ __forceinline__ uint32_t half_or(uint32_t v) {
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = GROUP / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ uint32_t half_max(uint32_t v) {
+__device__ __forceinline__ uint32_t group_max(uint32_t v) {
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = GROUP / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
 // SOLID: opaque triangles (the sigma -> 0, o = 1 limit): each pixel takes the colour of
 // the first entry in depth order whose window ratio is positive. WIN: window kind.
 // The forward walks one list per warp (measured faster than per-half lists here: the
-// early exit on transmittance keeps its lists short); it records per half-warp which
-// pairs were composited, for the backward's per-half lists.
+// early exit on transmittance keeps its lists short); it records per group of 8 lanes
+// which pairs were composited, for the backward's per-group lists.
 template <bool SOLID, int WIN>
 __global__ void __launch_bounds__(REN_THREADS)
 render_fwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
     __shared__ uint16_t s_mask[REN_THREADS];
-    __shared__ uint32_t s_km[REN_THREADS];   // half-warps that composited each staged record
+    __shared__ uint32_t s_km[REN_THREADS];   // groups that composited each staged record
     __shared__ uint32_t s_sw[REN_THREADS];   // pruning statistics of each staged record:
     __shared__ uint32_t s_sn[REN_THREADS];   // largest T o (float bits), composited pixels
     __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
     __shared__ ViewDev s_view[MAX_VIEWS];
     __shared__ uint32_t s_tile;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, h = lane >> 4, hl = lane & 15;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = lane / GROUP, gl = lane % GROUP;
     for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += REN_THREADS)
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
     int lx, ly;
@@ -214,7 +191,7 @@ render_fwd_kernel(RenderArgs a) {
             __syncthreads();
             const int cnt = warp_list(s_mask, s_list[w], w, lane);
             // chunks of 32 list entries; bit k of `kept` marks the entries this lane
-            // composited, and each half-warp's OR of them marks the pairs for the backward
+            // composited, and each group's OR of them marks the pairs for the backward
             for (int c = 0; c < cnt; c += 32) {
                 if (__all_sync(0xffffffffu, done)) break;
                 const int kend = min(cnt, c + 32);
@@ -261,18 +238,18 @@ render_fwd_kernel(RenderArgs a) {
                     kept |= 1u << (k - c);
                 }
                 if (a.kmask) {
-                    const uint32_t hk = half_or(kept);
+                    const uint32_t gk = group_or(kept);
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int b = 16 * q + hl;
-                        if (c + b < cnt && ((hk >> b) & 1u)) atomicOr(&s_km[L[c + b]], 1u << (2 * w + h));
+                    for (int q = 0; q < 32 / GROUP; ++q) {
+                        const int b = GROUP * q + gl;
+                        if (c + b < cnt && ((gk >> b) & 1u)) atomicOr(&s_km[L[c + b]], 1u << (WGROUPS * w + g));
                     }
                 }
             }
             if (a.kmask || stats) {
                 __syncthreads();
                 if (a.kmask) {
-                    if (idx < end) a.kmask[idx] = (uint16_t)s_km[tid];
+                    if (idx < end) a.kmask[idx] = s_km[tid];
                     s_km[tid] = 0u;
                 }
                 if (stats) {
@@ -298,10 +275,10 @@ render_fwd_kernel(RenderArgs a) {
                 a.ids[V.pix_base + pix] = last ? (int32_t)((int64_t)a.items[start + last - 1] - (int64_t)vw * a.n_per_view)
                                                : -1;
         }
-        const uint32_t hm = half_max(last);
+        const uint32_t gm = group_max(last);
         const uint32_t we = __reduce_add_sync(0xffffffffu, n_eval);
         const uint32_t wk = __reduce_add_sync(0xffffffffu, n_kept);
-        if (hl == 0) a.tile_max[(size_t)tile * HALVES + 2 * w + h] = hm;
+        if (gl == 0) a.tile_max[(size_t)tile * GROUPS + WGROUPS * w + g] = gm;
         if (lane == 0) {
             atomicAdd(&a.ctl->frag_eval, (unsigned long long)we);
             atomicAdd(&a.ctl->frag_kept, (unsigned long long)wk);
@@ -310,73 +287,78 @@ render_fwd_kernel(RenderArgs a) {
     }
 }
 
-// Sum 16 per-lane values over each half-warp: lane l ends with field (l & 15) of its
-// half's sum (transposed butterfly: 15 shuffles for 16 fields, both halves at once).
-__device__ __forceinline__ float half_reduce16(float (&v)[16], int lane) {
-    const bool b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+// Sum 16 per-lane values over each group of 8 lanes: lane l ends with fields 2 (l & 7)
+// and 2 (l & 7) + 1 of its group's sum (transposed butterfly: 14 shuffles for 16
+// fields, the four groups' records at once).
+__device__ __forceinline__ float2 group_reduce16(float (&v)[16], int lane) {
+    const bool b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const float send = b3 ? v[i] : v[i + 8];
-        const float keep = b3 ? v[i + 8] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float send = b2 ? v[i] : v[i + 4];
-        const float keep = b2 ? v[i + 4] : v[i];
+        const float send = b2 ? v[i] : v[i + 8];
+        const float keep = b2 ? v[i + 8] : v[i];
         v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float send = b1 ? v[i] : v[i + 2];
-        const float keep = b1 ? v[i + 2] : v[i];
+    for (int i = 0; i < 4; ++i) {
+        const float send = b1 ? v[i] : v[i + 4];
+        const float keep = b1 ? v[i + 4] : v[i];
         v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
     }
-    const float send = b0 ? v[0] : v[1];
-    const float keep = b0 ? v[1] : v[0];
-    return keep + __shfl_xor_sync(0xffffffffu, send, 1);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b0 ? v[i] : v[i + 2];
+        const float keep = b0 ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+    }
+    return make_float2(v[0], v[1]);
 }
 
 constexpr int BWD_CHUNK = 256;   // pairs whose masks a warp scans per list build
+#ifndef BWD_THREADS
+#define BWD_THREADS 256          // threads of a backward CTA (its warps work independently)
+#endif
 #ifndef BWD_CTAS
 #define BWD_CTAS 3               // resident backward CTAs per SM (80 registers a thread)
 #endif
+constexpr int BWD_WARPS = BWD_THREADS / 32;
+constexpr int TILE_BLOCKS = TILE_PIX / 32;   // 8x4 blocks of a tile
 
 // Backward, one warp per work unit (tile, 8x4 block of it): the warp scans the masks of
-// the tile's pairs that its two half-warps composited in the forward pass, builds one
-// list per half (item ids), and walks both lists back to front with the record of the
-// next step already in flight; the warps of a CTA never wait for one another. Each
-// half's record gradient goes to the item's gradient record with one 13-lane global
-// reduction per step.
+// the tile's pairs that its four groups of 8 lanes composited in the forward pass,
+// builds one list per group (item ids), and walks the lists back to front with the
+// record of the next step already in flight; the warps of a CTA never wait for one
+// another. Each group's record gradient goes to the item's gradient record with one
+// 7-lane global vector reduction per step.
 template <int WIN>
-__global__ void __launch_bounds__(REN_THREADS, BWD_CTAS)
+__global__ void __launch_bounds__(BWD_THREADS, BWD_CTAS)
 render_bwd_kernel(RenderArgs a) {
-    __shared__ uint32_t s_li[REN_THREADS / 32][2][BWD_CHUNK];   // per warp and half: item ids
-    __shared__ uint8_t s_lj[REN_THREADS / 32][2][BWD_CHUNK];    // and their pair index in the chunk
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, h = lane >> 4, hl = lane & 15;
-    const unsigned hmask = h ? 0xffff0000u : 0x0000ffffu;
+    __shared__ uint32_t s_li[BWD_WARPS][WGROUPS][BWD_CHUNK];   // per warp and group: item ids
+    __shared__ uint8_t s_lj[BWD_WARPS][WGROUPS][BWD_CHUNK];    // and their pair index in the chunk
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane / GROUP, gl = lane % GROUP;
+    const unsigned gmask = 0xffu << (GROUP * g);
     const unsigned lt_mask = lanemask_lt();
-    const uint32_t *LI = s_li[w][h];
-    const uint8_t *LJ = s_lj[w][h];
-    const uint32_t n_units = (uint32_t)a.total_tiles * (REN_THREADS / 32);
+    const uint32_t *LI = s_li[w][g];
+    const uint8_t *LJ = s_lj[w][g];
+    const uint32_t n_units = (uint32_t)a.total_tiles * TILE_BLOCKS;
     const Rec *__restrict__ recs = a.recs;
     for (;;) {
         uint32_t u = 0;
         if (lane == 0) u = atomicAdd(&a.ctl->work_counter[1], 1u);
         u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= n_units) break;
-        const int tile = (int)(u / (REN_THREADS / 32)), blk = (int)(u % (REN_THREADS / 32));
+        const int tile = (int)(u / TILE_BLOCKS), blk = (int)(u % TILE_BLOCKS);
         const int vw = find_view_warp(a.views, a.nviews, tile, lane);
         const ViewDev *V = a.views + vw;
         const int tiles_x = V->tiles_x, W = V->W, H = V->H;
         const int lt = tile - V->tile_base;
-        const int lx = ((blk & 1) << 3) | (h << 2) | (lane & 3), ly = ((blk >> 1) << 2) | ((lane >> 2) & 3);
+        int lx, ly;
+        block_pixel(blk, lane, lx, ly);
         const int x = (lt % tiles_x) * TILE + lx, y = (lt / tiles_x) * TILE + ly;
         const bool inside = x < W && y < H;
         const float px = (float)x + 0.5f, py = (float)y + 0.5f;
         const uint32_t start = a.ranges[tile].x;
-        const uint32_t hmax = a.tile_max[(size_t)tile * HALVES + 2 * blk + h];
-        const int wmax = (int)max(hmax, __shfl_xor_sync(0xffffffffu, hmax, 16));
+        const uint32_t gmax = a.tile_max[(size_t)tile * GROUPS + WGROUPS * blk + g];
+        const int wmax = (int)__reduce_max_sync(0xffffffffu, gmax);
         float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
         uint32_t last = 0;
         if (inside) {
@@ -393,11 +375,10 @@ render_bwd_kernel(RenderArgs a) {
             B1 = T * V->bg[1];
             B2 = T * V->bg[2];
         }
-        const int sh0 = 2 * blk, sh1 = 2 * blk + 1;
         for (int cend = wmax; cend > 0; cend -= BWD_CHUNK) {
             const int cstart = max(0, cend - BWD_CHUNK);
             const int nb = cend - cstart;
-            // the pairs of this chunk that each half composited, in tile order
+            // the pairs of this chunk that each group composited, in tile order
             uint32_t m[BWD_CHUNK / 32], itv[BWD_CHUNK / 32];
 #pragma unroll
             for (int q = 0; q < BWD_CHUNK / 32; ++q) {
@@ -410,36 +391,34 @@ render_bwd_kernel(RenderArgs a) {
                 }
             }
             __syncwarp();
-            int n0 = 0, n1 = 0;
+            int n[WGROUPS] = {0, 0, 0, 0};
 #pragma unroll
             for (int q = 0; q < BWD_CHUNK / 32; ++q) {
-                const bool k0 = (m[q] >> sh0) & 1u, k1 = (m[q] >> sh1) & 1u;
+                const uint32_t mq = (m[q] >> (WGROUPS * blk)) & 0xfu;
                 uint32_t it = itv[q];
-                if ((k0 || k1) && it >= a.n_items) {
+                if (mq && it >= a.n_items) {
                     atomicOr(&a.ctl->error, ERR_INDEX);
                     it = 0;
                 }
-                const unsigned b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
-                if (k0) {
-                    const int pos = n0 + __popc(b0 & lt_mask);
-                    s_li[w][0][pos] = it;
-                    s_lj[w][0][pos] = (uint8_t)(32 * q + lane);
+#pragma unroll
+                for (int e = 0; e < WGROUPS; ++e) {
+                    const bool ke = (mq >> e) & 1u;
+                    const unsigned be = __ballot_sync(0xffffffffu, ke);
+                    if (ke) {
+                        const int pos = n[e] + __popc(be & lt_mask);
+                        s_li[w][e][pos] = it;
+                        s_lj[w][e][pos] = (uint8_t)(32 * q + lane);
+                    }
+                    n[e] += __popc(be);
                 }
-                if (k1) {
-                    const int pos = n1 + __popc(b1 & lt_mask);
-                    s_li[w][1][pos] = it;
-                    s_lj[w][1][pos] = (uint8_t)(32 * q + lane);
-                }
-                n0 += __popc(b0);
-                n1 += __popc(b1);
             }
             __syncwarp();
-            const int cnt = h ? n1 : n0;
+            const int cnt = g == 0 ? n[0] : (g == 1 ? n[1] : (g == 2 ? n[2] : n[3]));
             // software pipeline: the record of step k - 1 loads while step k computes
             uint32_t nit = 0;
             int nj = 0;
             float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb4 = na, nc = na, nd = na;
-            int k = max(n0, n1) - 1;
+            int k = max(max(n[0], n[1]), max(n[2], n[3])) - 1;
             if (k >= 0 && k < cnt) {
                 nit = LI[k];
                 nj = LJ[k];
@@ -520,8 +499,9 @@ render_bwd_kernel(RenderArgs a) {
                 }
                 const unsigned bk = __ballot_sync(0xffffffffu, kept);
                 if (bk) {
-                    const float sum = half_reduce16(gv, lane);
-                    if ((bk & hmask) && hl < 13) atomicAdd(a.grad2d + (size_t)item * GRAD_FIELDS + hl, sum);
+                    const float2 sum = group_reduce16(gv, lane);
+                    // fields 2 gl, 2 gl + 1 (field 13 is padding and receives 0)
+                    if ((bk & gmask) && gl < 7) red_add_v2(a.grad2d + (size_t)item * GRAD_FIELDS + 2 * gl, sum.x, sum.y);
                 }
             }
             __syncwarp();
@@ -546,12 +526,13 @@ void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st, bool soli
 }
 
 void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st) {
-    static int occ = occupancy((const void *)render_bwd_kernel<WIN_POWER>, REN_THREADS);
-    int g = grid > 0 ? grid * occ : occ;
-    if (g > a.total_tiles) g = a.total_tiles;
+    static int occ = occupancy((const void *)render_bwd_kernel<WIN_POWER>, BWD_THREADS);
+    int64_t g = grid > 0 ? (int64_t)grid * occ : occ;
+    const int64_t need = ((int64_t)a.total_tiles * TILE_BLOCKS + BWD_WARPS - 1) / BWD_WARPS;
+    if (g > need) g = need;
     if (g <= 0) return;
-    if (a.window == WIN_SIGMOID) render_bwd_kernel<WIN_SIGMOID><<<g, REN_THREADS, 0, st>>>(a);
-    else render_bwd_kernel<WIN_POWER><<<g, REN_THREADS, 0, st>>>(a);
+    if (a.window == WIN_SIGMOID) render_bwd_kernel<WIN_SIGMOID><<<(unsigned)g, BWD_THREADS, 0, st>>>(a);
+    else render_bwd_kernel<WIN_POWER><<<(unsigned)g, BWD_THREADS, 0, st>>>(a);
 }
 
 // ---------------------------------------------------------------------------------
