@@ -184,7 +184,7 @@ tri_status ensure_pairs(tri_ctx *c) {
     ENSURE(c->kv, 8 * (size_t)c->pair_cap);
     ENSURE(c->kv_tmp, 8 * (size_t)c->pair_cap);
     ENSURE(c->items, 4 * (size_t)c->pair_cap);
-    ENSURE(c->kmask, 4 * (size_t)c->pair_cap);
+    ENSURE(c->kmask, sizeof(kmask_t) * (size_t)c->pair_cap);
     return TRI_OK;
 }
 
@@ -366,7 +366,7 @@ static tri_status preprocess_impl(tri_ctx *c, const tri_scene *scene, const tri_
     ENSURE(c->big_tiles, 4 * (size_t)tiles);
     ENSURE(c->scan_status, 8 * bin_scan_status_words(tiles));
     ENSURE(c->ranges, sizeof(uint2) * (size_t)tiles);
-    ENSURE(c->tile_max, 4 * 32 * (size_t)tiles);
+    ENSURE(c->tile_max, 4 * GROUPS_PER_TILE * (size_t)tiles);
     ENSURE(c->Tfin, 4 * (size_t)pix);
     ENSURE(c->ncontrib, 4 * (size_t)pix);
     if ((s = upload(c, c->views_d.p, views.data(), sizeof(ViewDev) * nviews, c->h_views, st)) != TRI_OK) return s;
@@ -465,7 +465,7 @@ static RenderArgs render_args(tri_ctx *c, TsDevBuf &outs) {
     r.n_contrib = P<int32_t>(c->ncontrib);
     r.tile_max = P<uint32_t>(c->tile_max);
     r.grad2d = P<float>(c->grad2d);
-    r.kmask = P<uint32_t>(c->kmask);
+    r.kmask = P<kmask_t>(c->kmask);
     r.stat_w = r.stat_n = nullptr;
     r.n_per_view = c->scene.n;
     r.window = c->rec_window;

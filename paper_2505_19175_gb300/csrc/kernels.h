@@ -120,6 +120,19 @@ void launch_size_reg(const float *verts, int64_t n, float weight, float *loss, f
                      cudaStream_t st);
 
 // ---- rendering ----
+// Render groups: lanes of a warp that walk one backward list together (a 2x4 block of
+// pixels for 8, 2x2 for 4); the forward marks per pair which groups composited it.
+#ifndef KM_GROUP
+#define KM_GROUP 4
+#endif
+constexpr int GROUP = KM_GROUP;
+constexpr int GROUPS_PER_TILE = TILE_PIX / GROUP;
+#if KM_GROUP == 8
+typedef uint32_t kmask_t;            // one bit per group of the tile
+#else
+typedef unsigned long long kmask_t;
+#endif
+
 struct RenderArgs {
     const ViewDev *views;
     const ViewOut *outs;
@@ -131,13 +144,13 @@ struct RenderArgs {
     const ushort4 *rects;           // per-item pixel rectangles
     float *T_final;                 // [total pixels]
     int32_t *n_contrib;             // [total pixels]
-    uint32_t *tile_max;             // [total tiles][32]: largest n_contrib of each 8-lane group
+    uint32_t *tile_max;             // [total tiles][GROUPS_PER_TILE]: largest n_contrib of each group
     uint32_t *stat_w;               // [items] largest T o as float bits (null: no statistics)
     uint32_t *stat_n;               // [items] pixels where the item was composited
     int32_t *ids = nullptr;         // solid render: [total pixels] triangle id of the winner, -1
     int64_t n_per_view = 0;         // triangles per view (item m = view * n_per_view + triangle)
     int window = WIN_POWER;         // window kind of the records
-    uint32_t *kmask;                // [pairs]: bit 4w + g = group g of warp w composited the pair (forward
+    kmask_t *kmask;                 // [pairs]: bit (32 / GROUP) w + g = group g of warp w composited the pair (forward
                                     // writes it when set; the backward requires it)
     float *grad2d;                  // backward: [items][16]
     uint32_t n_items;               // bound of the item ids in `items`

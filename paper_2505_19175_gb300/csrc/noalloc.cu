@@ -52,7 +52,7 @@ constexpr size_t OFF_PV0 = OFF_PK1 + align256(4 * NA_PAIRS);
 constexpr size_t OFF_PV1 = OFF_PV0 + align256(4 * NA_PAIRS);
 constexpr size_t OFF_RANGES = OFF_PV1 + align256(4 * NA_PAIRS);
 constexpr size_t OFF_TMAX = OFF_RANGES + align256(8 * NA_TILES);
-constexpr size_t OFF_TFIN = OFF_TMAX + align256(128 * NA_TILES);
+constexpr size_t OFF_TFIN = OFF_TMAX + align256(4 * GROUPS_PER_TILE * NA_TILES);
 constexpr size_t OFF_NCON = OFF_TFIN + align256(4 * NA_PIXELS);
 constexpr size_t DEPTH_WORDS = (NA_TRIS + NA_DEPTH_TILE - 1) / NA_DEPTH_TILE * 256;
 constexpr size_t PAIR_WORDS = (NA_PAIRS + NA_DEPTH_TILE - 1) / NA_DEPTH_TILE * 256;

@@ -1,7 +1,8 @@
 // Tile rendering of the triangle-splat renderer, forward and backward.
 //
 // A tile is 16x16 pixels, one thread per pixel, cut into eight 8x4 blocks (one warp
-// each) and each block into four 2x4 groups of 8 lanes. Tiles are taken from device
+// each) and each block into groups of GROUP lanes (eight 2x2 groups of 4 lanes by
+// default; four 2x4 groups of 8 with KM_GROUP=8). Tiles are taken from device
 // work queues by persistent grids, so a launch serves any mix of views and resolutions.
 //
 // Forward (Sec. 3.1, the rendering equation of prior splatting work): one CTA of 256
@@ -11,24 +12,27 @@
 // ratio = min_i m_i(p) (phi(p)/phi(s) of Eq. indicator1), I = ratio^sigma, alpha = o I,
 // skip below 1/255, clamp at 0.99, stop before T drops below 1e-4, C += rgb alpha T.
 // The CTA leaves a tile as soon as every pixel has stopped (__syncthreads_count). It
-// also records, per pair, which groups composited it (32 bits), and per group the
+// also records, per pair, which groups composited it (one bit per group), and per group the
 // largest composited index.
 //
 // Backward: one warp per (tile, block) work unit, with no CTA-wide barrier. Each group
 // walks only the pairs it composited, back to front: per pixel
 // T_k = T_{k+1} / (1 - alpha_k), dL/dalpha_k = sum_c g_c (rgb_c T_k - B_c / (1 - alpha_k))
 // with B the colour behind fragment k plus T_final bg. The 13 record-field gradients
-// are summed over each group with a transposed butterfly (14 shuffles for 16 fields,
-// the four groups' records at once) and added to the per-item gradient record with
-// one 8-byte vector reduction per lane.
+// are summed over each group with a transposed butterfly (all the warp's groups'
+// records at once) and added to the per-item gradient record with one vector
+// reduction per lane.
 #include "kernels.h"
 
 namespace ts {
 
 constexpr int REN_THREADS = TILE_PIX;
-constexpr int GROUP = 8;                          // lanes of a group: a 2x4 block of pixels
 constexpr int WGROUPS = 32 / GROUP;               // groups per warp
-constexpr int GROUPS = REN_THREADS / GROUP;       // groups per tile
+constexpr int GROUPS = GROUPS_PER_TILE;           // groups per tile
+constexpr int KM_WORDS = (int)sizeof(kmask_t) / 4;   // 32-bit words of a pair's group mask
+// word and bit offset of warp w's groups in the pair's group mask
+#define KM_WORD(w) ((w) / (32 / WGROUPS))
+#define KM_SHIFT(w) (WGROUPS * ((w) % (32 / WGROUPS)))
 
 // View of a tile from the views' first tile ids, by one warp (all lanes get it): the
 // last view whose first tile is <= tile.
@@ -50,11 +54,18 @@ __device__ __forceinline__ int find_view(const ViewDev *vs, int nviews, int tile
 }
 
 // Pixel of lane `lane` of the warp that covers 8x4 block w of the tile: block w sits at
-// ((w & 1) 8, (w >> 1) 4); each group of 8 lanes (g = lane / 8) covers its 2x4 column
-// pair at x 2g, with lane bit 0 as x and bits [2:1] as y.
+// ((w & 1) 8, (w >> 1) 4). A group of 8 lanes (g = lane / 8) covers the 2x4 column pair
+// at x 2g, lane bit 0 as x and bits [2:1] as y; a group of 4 (g = lane / 4) the 2x2
+// square at (2 (g & 3), 2 (g >> 2)), lane bit 0 as x and bit 1 as y.
 __device__ __forceinline__ void block_pixel(int w, int lane, int &lx, int &ly) {
-    lx = ((w & 1) << 3) | ((lane >> 3) << 1) | (lane & 1);
-    ly = ((w >> 1) << 2) | ((lane >> 1) & 3);
+    if (GROUP == 8) {
+        lx = ((w & 1) << 3) | ((lane >> 3) << 1) | (lane & 1);
+        ly = ((w >> 1) << 2) | ((lane >> 1) & 3);
+    } else {
+        const int g = lane >> 2;
+        lx = ((w & 1) << 3) | ((g & 3) << 1) | (lane & 1);
+        ly = ((w >> 1) << 2) | ((g >> 2) << 1) | ((lane >> 1) & 1);
+    }
 }
 __device__ __forceinline__ void pixel_of(int tid, int &lx, int &ly) { block_pixel(tid >> 5, tid & 31, lx, ly); }
 
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(REN_THREADS)
 render_fwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
     __shared__ uint16_t s_mask[REN_THREADS];
-    __shared__ uint32_t s_km[REN_THREADS];   // groups that composited each staged record
+    __shared__ uint32_t s_km[KM_WORDS][REN_THREADS];   // groups that composited each staged record
     __shared__ uint32_t s_sw[REN_THREADS];   // pruning statistics of each staged record:
     __shared__ uint32_t s_sn[REN_THREADS];   // largest T o (float bits), composited pixels
     __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
@@ -150,7 +161,8 @@ render_fwd_kernel(RenderArgs a) {
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
     int lx, ly;
     pixel_of(tid, lx, ly);
-    s_km[tid] = 0u;
+#pragma unroll
+    for (int q = 0; q < KM_WORDS; ++q) s_km[q][tid] = 0u;
     s_sw[tid] = 0u;
     s_sn[tid] = 0u;
     const bool stats = a.stat_n != nullptr;
@@ -238,19 +250,25 @@ render_fwd_kernel(RenderArgs a) {
                     kept |= 1u << (k - c);
                 }
                 if (a.kmask) {
+                    // lane b gathers which groups of the warp composited entry c + b
                     const uint32_t gk = group_or(kept);
+                    uint32_t mb = 0;
 #pragma unroll
-                    for (int q = 0; q < 32 / GROUP; ++q) {
-                        const int b = GROUP * q + gl;
-                        if (c + b < cnt && ((gk >> b) & 1u)) atomicOr(&s_km[L[c + b]], 1u << (WGROUPS * w + g));
-                    }
+                    for (int e = 0; e < WGROUPS; ++e) mb |= ((__shfl_sync(0xffffffffu, gk, e * GROUP) >> lane) & 1u) << e;
+                    if (mb && c + lane < cnt) atomicOr(&s_km[KM_WORD(w)][L[c + lane]], mb << KM_SHIFT(w));
                 }
             }
             if (a.kmask || stats) {
                 __syncthreads();
                 if (a.kmask) {
-                    if (idx < end) a.kmask[idx] = s_km[tid];
-                    s_km[tid] = 0u;
+                    if (idx < end) {
+                        kmask_t km = 0;
+#pragma unroll
+                        for (int q = 0; q < KM_WORDS; ++q) km |= (kmask_t)s_km[q][tid] << (32 * q);
+                        a.kmask[idx] = km;
+                    }
+#pragma unroll
+                    for (int q = 0; q < KM_WORDS; ++q) s_km[q][tid] = 0u;
                 }
                 if (stats) {
                     if (s_sn[tid]) {
@@ -287,33 +305,23 @@ render_fwd_kernel(RenderArgs a) {
     }
 }
 
-// Sum 16 per-lane values over each group of 8 lanes: lane l ends with fields 2 (l & 7)
-// and 2 (l & 7) + 1 of its group's sum (transposed butterfly: 14 shuffles for 16
-// fields, the four groups' records at once).
-__device__ __forceinline__ float2 group_reduce16(float (&v)[16], int lane) {
-    const bool b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+// Sum 16 per-lane values over each group (transposed butterfly, all groups' records at
+// once): lane l ends with fields (16 / GROUP) (l % GROUP) + i, i < 16 / GROUP, of its
+// group's sum in v[i] (14 shuffles for groups of 8, 12 for groups of 4).
+__device__ __forceinline__ void group_reduce16(float (&v)[16], int lane) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const float send = b2 ? v[i] : v[i + 8];
-        const float keep = b2 ? v[i + 8] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
+    for (int o = GROUP / 2, nf = 8; o > 0; o >>= 1, nf >>= 1) {
+        const bool up = lane & o;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float send = b1 ? v[i] : v[i + 4];
-        const float keep = b1 ? v[i + 4] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        for (int i = 0; i < nf; ++i) {
+            const float send = up ? v[i] : v[i + nf];
+            const float keep = up ? v[i + nf] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
     }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float send = b0 ? v[i] : v[i + 2];
-        const float keep = b0 ? v[i + 2] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
-    }
-    return make_float2(v[0], v[1]);
 }
 
-constexpr int BWD_CHUNK = 256;   // pairs whose masks a warp scans per list build
+constexpr int BWD_CHUNK = GROUP == 8 ? 256 : 128;   // pairs whose masks a warp scans per list build
 #ifndef BWD_THREADS
 #define BWD_THREADS 256          // threads of a backward CTA (its warps work independently)
 #endif
@@ -324,7 +332,7 @@ constexpr int BWD_WARPS = BWD_THREADS / 32;
 constexpr int TILE_BLOCKS = TILE_PIX / 32;   // 8x4 blocks of a tile
 
 // Backward, one warp per work unit (tile, 8x4 block of it): the warp scans the masks of
-// the tile's pairs that its four groups of 8 lanes composited in the forward pass,
+// the tile's pairs that each of its groups composited in the forward pass,
 // builds one list per group (item ids), and walks the lists back to front with the
 // record of the next step already in flight; the warps of a CTA never wait for one
 // another. Each group's record gradient goes to the item's gradient record with one
@@ -335,7 +343,7 @@ render_bwd_kernel(RenderArgs a) {
     __shared__ uint32_t s_li[BWD_WARPS][WGROUPS][BWD_CHUNK];   // per warp and group: item ids
     __shared__ uint8_t s_lj[BWD_WARPS][WGROUPS][BWD_CHUNK];    // and their pair index in the chunk
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane / GROUP, gl = lane % GROUP;
-    const unsigned gmask = 0xffu << (GROUP * g);
+    const unsigned gmask = ((1u << GROUP) - 1u) << (GROUP * g);
     const unsigned lt_mask = lanemask_lt();
     const uint32_t *LI = s_li[w][g];
     const uint8_t *LJ = s_lj[w][g];
@@ -379,7 +387,8 @@ render_bwd_kernel(RenderArgs a) {
             const int cstart = max(0, cend - BWD_CHUNK);
             const int nb = cend - cstart;
             // the pairs of this chunk that each group composited, in tile order
-            uint32_t m[BWD_CHUNK / 32], itv[BWD_CHUNK / 32];
+            kmask_t m[BWD_CHUNK / 32];
+            uint32_t itv[BWD_CHUNK / 32];
 #pragma unroll
             for (int q = 0; q < BWD_CHUNK / 32; ++q) {
                 const int jj = 32 * q + lane;
@@ -391,10 +400,12 @@ render_bwd_kernel(RenderArgs a) {
                 }
             }
             __syncwarp();
-            int n[WGROUPS] = {0, 0, 0, 0};
+            int n[WGROUPS];
+#pragma unroll
+            for (int e = 0; e < WGROUPS; ++e) n[e] = 0;
 #pragma unroll
             for (int q = 0; q < BWD_CHUNK / 32; ++q) {
-                const uint32_t mq = (m[q] >> (WGROUPS * blk)) & 0xfu;
+                const uint32_t mq = (uint32_t)(m[q] >> (WGROUPS * blk)) & ((1u << WGROUPS) - 1u);
                 uint32_t it = itv[q];
                 if (mq && it >= a.n_items) {
                     atomicOr(&a.ctl->error, ERR_INDEX);
@@ -413,12 +424,17 @@ render_bwd_kernel(RenderArgs a) {
                 }
             }
             __syncwarp();
-            const int cnt = g == 0 ? n[0] : (g == 1 ? n[1] : (g == 2 ? n[2] : n[3]));
+            int cnt = 0, nmax = 0;
+#pragma unroll
+            for (int e = 0; e < WGROUPS; ++e) {
+                cnt = e == g ? n[e] : cnt;
+                nmax = max(nmax, n[e]);
+            }
             // software pipeline: the record of step k - 1 loads while step k computes
             uint32_t nit = 0;
             int nj = 0;
             float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb4 = na, nc = na, nd = na;
-            int k = max(max(n[0], n[1]), max(n[2], n[3])) - 1;
+            int k = nmax - 1;
             if (k >= 0 && k < cnt) {
                 nit = LI[k];
                 nj = LJ[k];
@@ -499,9 +515,14 @@ render_bwd_kernel(RenderArgs a) {
                 }
                 const unsigned bk = __ballot_sync(0xffffffffu, kept);
                 if (bk) {
-                    const float2 sum = group_reduce16(gv, lane);
-                    // fields 2 gl, 2 gl + 1 (field 13 is padding and receives 0)
-                    if ((bk & gmask) && gl < 7) red_add_v2(a.grad2d + (size_t)item * GRAD_FIELDS + 2 * gl, sum.x, sum.y);
+                    group_reduce16(gv, lane);
+                    // fields 13..15 are padding and receive 0
+                    float *dst = a.grad2d + (size_t)item * GRAD_FIELDS + (16 / GROUP) * gl;
+                    if (GROUP == 8) {
+                        if ((bk & gmask) && gl < 7) red_add_v2(dst, gv[0], gv[1]);
+                    } else {
+                        if (bk & gmask) red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
+                    }
                 }
             }
             __syncwarp();
