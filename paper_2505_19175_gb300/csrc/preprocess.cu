@@ -19,41 +19,76 @@ namespace ts {
 constexpr int PRE_THREADS = 128;
 constexpr int PRE_BWD_THREADS = 64;
 
+// Asynchronous global -> shared copies (cp.async): every copy of a CTA's staging is in
+// flight at once, with no register round trip.
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Stage `count` floats starting at `src` (16-byte aligned) into shared memory.
+template <int T>
 __device__ __forceinline__ void stage_floats(float *dst, const float *src, int count) {
     const int n4 = count >> 2;
-    const float4 *s4 = reinterpret_cast<const float4 *>(src);
-    float4 *d4 = reinterpret_cast<float4 *>(dst);
-    for (int k = threadIdx.x; k < n4; k += blockDim.x) d4[k] = __ldg(s4 + k);
-    for (int k = (n4 << 2) + threadIdx.x; k < count; k += blockDim.x) dst[k] = __ldg(src + k);
+    for (int k = threadIdx.x; k < n4; k += T) cp_async16(dst + 4 * k, src + 4 * k);
+    for (int k = (n4 << 2) + threadIdx.x; k < count; k += T) cp_async4(dst + k, src + k);
 }
 
-// Per-thread stride in shared memory for records of `len` floats: odd, so that the 32
-// lanes reading element k of their own record hit 32 different banks.
-__host__ __device__ constexpr int odd_stride(int len) { return len | 1; }
-
-// Stage records of `len` floats (count of them, contiguous in global memory) into
-// shared memory at stride odd_stride(len), with coalesced float4 global loads. `len` is
-// a compile-time constant, so the divisions below are multiplications.
+// Shared-memory layout of per-thread records of `len` floats. With len a multiple of 4
+// the records are read as float4 at a stride of an odd number of float4 (conflict-free
+// per quarter-warp) and staged with 16-byte copies; otherwise they are read as floats
+// at an odd stride (conflict-free per warp) and staged with 4-byte copies.
 template <int len>
+struct RecLayout {
+    static constexpr bool V4 = len % 4 == 0;
+    static constexpr int stride = V4 ? ((len / 4) % 2 ? len : len + 4) : (len | 1);
+};
+
+// Stage records of `len` floats (count of them, contiguous in global memory, 16-byte
+// aligned when len is a multiple of 4) into shared memory in RecLayout<len>. `len` is
+// a compile-time constant, so the divisions below are multiplications.
+template <int len, int T>
 __device__ __forceinline__ void stage_records(float *dst, const float *src, int count) {
-    constexpr int stride = odd_stride(len);
-    const int total = count * len;
-    const int n4 = total >> 2;
-    const float4 *s4 = reinterpret_cast<const float4 *>(src);
-    for (int k = threadIdx.x; k < n4; k += blockDim.x) {
-        const float4 v = __ldg(s4 + k);
-        const float e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int f = 4 * k + q;
+    constexpr int stride = RecLayout<len>::stride;
+    if constexpr (RecLayout<len>::V4) {
+        constexpr int q4 = len / 4;
+        const int n4 = count * q4;
+        for (int q = threadIdx.x; q < n4; q += T) {
+            const int r = q / q4;
+            cp_async16(dst + r * stride + 4 * (q - r * q4), src + 4 * q);
+        }
+    } else {
+        const int total = count * len;
+        for (int f = threadIdx.x; f < total; f += T) {
             const int r = f / len;
-            dst[r * stride + (f - r * len)] = e[q];
+            cp_async4(dst + r * stride + (f - r * len), src + f);
         }
     }
-    for (int f = (n4 << 2) + threadIdx.x; f < total; f += blockDim.x) {
-        const int r = f / len;
-        dst[r * stride + (f - r * len)] = __ldg(src + f);
+}
+
+// col[c] += sum_k Y[k] sh[3 k + c] over the nk coefficients of a record staged in
+// RecLayout<3 nk>.
+template <int nk>
+__device__ __forceinline__ void sh_accumulate(const float *shp, const float *Y, float *col) {
+    constexpr int len = 3 * nk;
+    if constexpr (RecLayout<len>::V4) {
+#pragma unroll
+        for (int q = 0; q < len / 4; ++q) {
+            const float4 x = *reinterpret_cast<const float4 *>(shp + 4 * q);
+            const float e[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) col[(4 * q + t) % 3] = fmaf(Y[(4 * q + t) / 3], e[t], col[(4 * q + t) % 3]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < nk; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) col[c] = fmaf(Y[k], shp[k * 3 + c], col[c]);
     }
 }
 
@@ -66,7 +101,7 @@ template <int DEG, int WIN>
 __global__ void __launch_bounds__(PRE_THREADS, 6)
 preprocess_fwd_kernel(PreArgs a) {
     __shared__ __align__(16) float s_v[PRE_THREADS * 9];
-    __shared__ __align__(16) float s_sh[PRE_THREADS * 49];
+    __shared__ __align__(16) float s_sh[PRE_THREADS * 52];
     __shared__ uint32_t s_hist[4][256];
     __shared__ uint32_t s_nvis;
     extern __shared__ ViewDev s_view[];   // nviews entries
@@ -79,18 +114,19 @@ preprocess_fwd_kernel(PreArgs a) {
     const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
     const int cnt = (int)(a.n - i0 < PRE_THREADS ? a.n - i0 : PRE_THREADS);
     constexpr int nk = (DEG + 1) * (DEG + 1);
-    stage_floats(s_v, a.verts + i0 * 9, cnt * 9);
-    stage_records<nk * 3>(s_sh, a.sh + i0 * nk * 3, cnt);
-    __syncthreads();
-
+    stage_floats<PRE_THREADS>(s_v, a.verts + i0 * 9, cnt * 9);
+    stage_records<nk * 3, PRE_THREADS>(s_sh, a.sh + i0 * nk * 3, cnt);
     const int64_t i = i0 + tid;
     const bool alive = tid < cnt;
+    const float o = alive ? __ldg(a.opacity + i) : 1.0f;
+    const float sig = alive ? __ldg(a.sigma + i) : 1.0f;
+    cp_async_wait_all();
+    __syncthreads();
+
     float v[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) v[k] = s_v[tid * 9 + k];
-    const float o = alive ? __ldg(a.opacity + i) : 1.0f;
-    const float sig = alive ? __ldg(a.sigma + i) : 1.0f;
-    const float *shp = s_sh + tid * odd_stride(nk * 3);
+    const float *shp = s_sh + tid * RecLayout<nk * 3>::stride;
     // shrink factor of the tight rectangle (Supp. "Tile assignment")
     // (solid records: the whole triangle, whatever its opacity; for the sigmoid window
     // the factor depends on the inradius and is set per view below)
@@ -148,13 +184,7 @@ preprocess_fwd_kernel(PreArgs a) {
             float Y[16];
             sh_basis(DEG, w0 * inv, w1 * inv, w2 * inv, Y);
             float col[3] = {0.5f, 0.5f, 0.5f};
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                if (k < nk) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) col[c] = fmaf(Y[k], shp[k * 3 + c], col[c]);
-                }
-            }
+            sh_accumulate<nk>(shp, Y, col);
 #pragma unroll
             for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c], 0.0f);
             rec.a = make_float4(sx.hi, sy.hi, g.A[0], g.B[0]);
@@ -196,8 +226,8 @@ template <int DEG, int WIN, bool MULTI>
 __global__ void __launch_bounds__(PRE_BWD_THREADS, MULTI ? 6 : 8)
 preprocess_bwd_kernel(PreBwdArgs a) {
     __shared__ __align__(16) float s_v[PRE_BWD_THREADS * 9];
-    __shared__ __align__(16) float s_sh[PRE_BWD_THREADS * 49];
-    __shared__ __align__(16) float s_gsh[PRE_BWD_THREADS * 49];
+    __shared__ __align__(16) float s_sh[PRE_BWD_THREADS * 52];
+    __shared__ __align__(16) float s_gsh[PRE_BWD_THREADS * 52];
     extern __shared__ ViewDev s_view[];   // nviews entries
     const int tid = threadIdx.x;
     for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += PRE_BWD_THREADS)
@@ -205,15 +235,16 @@ preprocess_bwd_kernel(PreBwdArgs a) {
     const int64_t i0 = (int64_t)blockIdx.x * PRE_BWD_THREADS;
     const int cnt = (int)(a.n - i0 < PRE_BWD_THREADS ? a.n - i0 : PRE_BWD_THREADS);
     constexpr int nk = (DEG + 1) * (DEG + 1);
-    stage_floats(s_v, a.verts + i0 * 9, cnt * 9);
-    stage_records<nk * 3>(s_sh, a.sh + i0 * nk * 3, cnt);
+    stage_floats<PRE_BWD_THREADS>(s_v, a.verts + i0 * 9, cnt * 9);
+    stage_records<nk * 3, PRE_BWD_THREADS>(s_sh, a.sh + i0 * nk * 3, cnt);
+    cp_async_wait_all();
     __syncthreads();
     const int64_t i = i0 + tid;
     const bool alive = tid < cnt;
     float v[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) v[k] = s_v[tid * 9 + k];
-    constexpr int sstride = odd_stride(nk * 3);
+    constexpr int sstride = RecLayout<nk * 3>::stride;
     float *shp = s_sh + tid * sstride;
     const float cen[3] = {(v[0] + v[3] + v[6]) * (1.0f / 3.0f), (v[1] + v[4] + v[7]) * (1.0f / 3.0f),
                           (v[2] + v[5] + v[8]) * (1.0f / 3.0f)};
@@ -222,7 +253,12 @@ preprocess_bwd_kernel(PreBwdArgs a) {
     for (int k = 0; k < 9; ++k) gv[k] = 0.f;
     float go = 0.f, gsig = 0.f;
     float *gsh = s_gsh + tid * sstride;
-    for (int k = 0; k < nk * 3; ++k) gsh[k] = 0.f;
+    if constexpr (RecLayout<nk * 3>::V4) {
+#pragma unroll
+        for (int q = 0; q < nk * 3 / 4; ++q) reinterpret_cast<float4 *>(gsh)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        for (int k = 0; k < nk * 3; ++k) gsh[k] = 0.f;
+    }
 
     // views in which the triangle was binned: with several views the tile counts of all
     // views are loaded back to back (one latency) into a bit mask, then only those views
@@ -251,7 +287,7 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         go += G2.x;
         // sigmoid window: field 9 holds dL/dkappa, kappa = r / sigma
         const float sig_i = WIN == WIN_SIGMOID ? __ldg(a.sigma + i) : 0.0f;
-        if (WIN == WIN_SIGMOID) gsig -= G2.y * g.r / (sig_i * sig_i);
+        if constexpr (WIN == WIN_SIGMOID) gsig -= G2.y * g.r / (sig_i * sig_i);
         else gsig += G2.y;
         // s = q0 + S
         const float gsx = G0.x, gsy = G0.y;
@@ -272,7 +308,7 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         const float Ey[3] = {g.Q2.y - g.Q1.y, -g.Q2.y, g.Q1.y};
         float gEx[3], gEy[3];
         const float ia2 = rcp_approx(g.area2);
-        if (WIN == WIN_SIGMOID) {
+        if constexpr (WIN == WIN_SIGMOID) {
             // r = |area2| / P
             const float gr_in = G2.y / sig_i;
             gA2 += gr_in * (g.area2 >= 0.0f ? iP : -iP);
@@ -325,26 +361,36 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         sh_basis(DEG, dx, dy, dz, Y);
         const float grgb[3] = {G2.z, G2.w, G3.x};
         float raw[3] = {0.5f, 0.5f, 0.5f};
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            if (k < nk) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) raw[c] = fmaf(Y[k], shp[k * 3 + c], raw[c]);
-            }
-        }
+        sh_accumulate<nk>(shp, Y, raw);
         float graw[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) graw[c] = raw[c] > 0.0f ? grgb[c] : 0.0f;
         float gY[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            if (k < nk) {
+        for (int k = 0; k < 16; ++k) gY[k] = 0.f;
+        if constexpr (RecLayout<nk * 3>::V4) {
+#pragma unroll
+            for (int q = 0; q < nk * 3 / 4; ++q) {
+                const float4 x = reinterpret_cast<const float4 *>(shp)[q];
+                float4 &gq = reinterpret_cast<float4 *>(gsh)[q];
+                float4 gg = gq;
+                const float e[4] = {x.x, x.y, x.z, x.w};
+                float ge[4] = {gg.x, gg.y, gg.z, gg.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int k = (4 * q + t) / 3, c = (4 * q + t) % 3;
+                    ge[t] = fmaf(graw[c], Y[k], ge[t]);
+                    gY[k] = fmaf(graw[c], e[t], gY[k]);
+                }
+                gq = make_float4(ge[0], ge[1], ge[2], ge[3]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < nk; ++k) {
                 gsh[k * 3 + 0] += graw[0] * Y[k];
                 gsh[k * 3 + 1] += graw[1] * Y[k];
                 gsh[k * 3 + 2] += graw[2] * Y[k];
                 gY[k] = graw[0] * shp[k * 3] + graw[1] * shp[k * 3 + 1] + graw[2] * shp[k * 3 + 2];
-            } else {
-                gY[k] = 0.f;
             }
         }
         if (DEG > 0) {
