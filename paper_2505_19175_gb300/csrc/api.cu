@@ -437,6 +437,7 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
             if ((s = ensure_pairs(c)) != TRI_OK) return s;
             b = bin_args(c);
             CK(cudaMemsetAsync(&ctl_of(c)->cta_counter[3], 0, 4, st));
+            CK(cudaMemsetAsync(&ctl_of(c)->big_count, 0, 4, st));
             CK(cudaMemsetAsync(c->scan_status.p, 0, 8 * bin_scan_status_words(c->total_tiles), st));
             launch_bin_scan(b, st);
             if ((s = launch_check(c, "bin_scan")) != TRI_OK) return s;

@@ -22,6 +22,7 @@ namespace ts {
 
 constexpr int BIN_THREADS = 256;
 constexpr int TSORT_THREADS = 256;
+constexpr int WS_MAX = 512;               // words one warp sorts; longer ranges take a CTA
 constexpr int MERGE_PER_THREAD = 8;
 
 // Per-item expansion of a CTA's 256 items into their (item, tile) pairs. Calls
@@ -168,6 +169,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) bin_scan_kernel(BinArgs a) {
             const uint32_t hi = (uint32_t)(off + c[q] < cap ? off + c[q] : cap);
             a.ranges[t0 + q] = make_uint2(lo, hi);
             a.tile_cursor[t0 + q] = lo;
+            if (hi - lo > (uint32_t)WS_MAX) {
+                // queued for a CTA-wide sort
+                const uint32_t k = atomicAdd(&a.ctl->big_count, 1u);
+                if (k < (uint32_t)T) a.big_tiles[k] = (uint32_t)(t0 + q);
+                else atomicOr(&a.ctl->error, ERR_INDEX);
+            }
         }
         off += c[q];
     }
@@ -175,15 +182,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) bin_scan_kernel(BinArgs a) {
 
 // ---- per-tile order ----
 // Each tile's range of (depth key << 32 | item) words is sorted ascending, which is
-// the (depth key, item id) order. Ranges of at most WS_MAX words are sorted by one
-// warp in registers (tile_sort_small_kernel, bitonic network: lane l holds words
-// [l E, l E + E), strides below E are exchanges between registers and larger ones
-// warp shuffles); longer ranges are queued for tile_sort_big_kernel, where the CTA's
-// warps sort 256-word chunks the same way and merge them in shared memory (merge
-// path). Ranges beyond BS_MAX words are sorted in BS_MAX chunks that are then merged
-// pairwise in global memory.
-constexpr int WS_WARPS = 4;               // warps of tile_sort_small_kernel
-constexpr int WS_MAX = 512;               // words one warp sorts
+// the (depth key, item id) order, by one kernel (tile_sort_kernel). Ranges of at most
+// WS_MAX words are sorted by one warp in registers (bitonic network: lane l holds
+// words [l E, l E + E), strides below E are exchanges between registers and larger
+// ones warp shuffles); longer ranges, queued by the scan, take a whole CTA, whose warps
+// sort 256-word chunks the same way and merge them in shared memory (merge path).
+// Ranges beyond BS_MAX words are sorted in BS_MAX chunks that are then merged pairwise
+// in global memory.
 constexpr int BS_MAX = 2048;              // words one CTA sorts in shared memory
 
 __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int m) {
@@ -247,37 +252,6 @@ __device__ __forceinline__ void warp_sort_range(const BinArgs &a, uint32_t start
         if (base + e < n) a.items[start + base + e] = (uint32_t)x[e];
 }
 
-__global__ void __launch_bounds__(WS_WARPS * 32, 6) tile_sort_small_kernel(BinArgs a) {
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        uint32_t t = 0;
-        if (lane == 0) t = atomicAdd(&a.ctl->work_counter[2], 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= (uint32_t)a.total_tiles) break;
-        const uint2 r = a.ranges[t];
-        const int n = (int)(r.y - r.x);
-        if (n <= 1) {
-            if (n == 1 && lane == 0) a.items[r.x] = (uint32_t)a.kv[r.x];
-        } else if (n > WS_MAX) {
-            if (lane == 0) {
-                const uint32_t q = atomicAdd(&a.ctl->big_count, 1u);
-                if (q < (uint32_t)a.total_tiles) a.big_tiles[q] = t;
-                else atomicOr(&a.ctl->error, ERR_INDEX);
-            }
-        } else if (n <= 32) {
-            warp_sort_range<1>(a, r.x, n);
-        } else if (n <= 64) {
-            warp_sort_range<2>(a, r.x, n);
-        } else if (n <= 128) {
-            warp_sort_range<4>(a, r.x, n);
-        } else if (n <= 256) {
-            warp_sort_range<8>(a, r.x, n);
-        } else {
-            warp_sort_range<16>(a, r.x, n);
-        }
-    }
-}
-
 // The CTA sorts src[0, n) (1 <= n <= BS_MAX) into shared memory: warps sort 256-word
 // chunks in registers, then merge levels 256 -> 512 -> ... between A and B. Returns
 // the buffer with the result (padded with the largest word to a power of two).
@@ -323,20 +297,24 @@ __device__ unsigned long long *block_sort(const unsigned long long *src, int n, 
     return A;
 }
 
-__global__ void __launch_bounds__(TSORT_THREADS) tile_sort_big_kernel(BinArgs a) {
+// One launch sorts every range: each CTA first takes the ranges longer than WS_MAX that
+// the scan queued (one CTA each), then its warps take the others from the tile queue
+// (one warp each, ranges longer than WS_MAX skipped), so the long ranges overlap with
+// the many short ones.
+__global__ void __launch_bounds__(TSORT_THREADS, 3) tile_sort_kernel(BinArgs a) {
     __shared__ unsigned long long s_a[BS_MAX], s_b[BS_MAX];
     __shared__ uint32_t s_q;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t nbig = min(a.ctl->big_count, (uint32_t)a.total_tiles);
     for (;;) {
         if (tid == 0) s_q = atomicAdd(&a.ctl->big_next, 1u);
         __syncthreads();
         const uint32_t q = s_q;
+        __syncthreads();
         if (q >= nbig) break;
         const uint32_t t = a.big_tiles[q];
         if (t >= (uint32_t)a.total_tiles) {
             if (tid == 0) atomicOr(&a.ctl->error, ERR_INDEX);
-            __syncthreads();
             continue;
         }
         const uint2 r = a.ranges[t];
@@ -386,6 +364,29 @@ __global__ void __launch_bounds__(TSORT_THREADS) tile_sort_big_kernel(BinArgs a)
         }
         __syncthreads();
     }
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(&a.ctl->work_counter[2], 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (uint32_t)a.total_tiles) break;
+        const uint2 r = a.ranges[t];
+        const int n = (int)(r.y - r.x);
+        if (n <= 1) {
+            if (n == 1 && lane == 0) a.items[r.x] = (uint32_t)a.kv[r.x];
+        } else if (n > WS_MAX) {
+            // sorted above
+        } else if (n <= 32) {
+            warp_sort_range<1>(a, r.x, n);
+        } else if (n <= 64) {
+            warp_sort_range<2>(a, r.x, n);
+        } else if (n <= 128) {
+            warp_sort_range<4>(a, r.x, n);
+        } else if (n <= 256) {
+            warp_sort_range<8>(a, r.x, n);
+        } else {
+            warp_sort_range<16>(a, r.x, n);
+        }
+    }
 }
 
 void launch_bin_scan(const BinArgs &a, cudaStream_t st) {
@@ -408,17 +409,12 @@ static int occupancy_of(const void *fn, int threads) {
 }
 
 void launch_tile_sort(const BinArgs &a, int sms, cudaStream_t st) {
-    static const int occ_small = occupancy_of((const void *)tile_sort_small_kernel, WS_WARPS * 32);
-    static const int occ_big = occupancy_of((const void *)tile_sort_big_kernel, TSORT_THREADS);
+    static const int occ = occupancy_of((const void *)tile_sort_kernel, TSORT_THREADS);
     if (a.total_tiles <= 0) return;
-    // one warp per tile: enough CTAs for every tile's warp, at most a full machine
-    int64_t g = ((int64_t)a.total_tiles + WS_WARPS - 1) / WS_WARPS;
-    if (g > (int64_t)sms * occ_small) g = (int64_t)sms * occ_small;
-    tile_sort_small_kernel<<<(unsigned)g, WS_WARPS * 32, 0, st>>>(a);
-    // the long ranges the first kernel queued; CTAs with nothing queued return at once
-    int64_t gb = (int64_t)sms * occ_big;
-    if (gb > a.total_tiles) gb = a.total_tiles;
-    tile_sort_big_kernel<<<(unsigned)gb, TSORT_THREADS, 0, st>>>(a);
+    // one warp per short range: enough CTAs for every tile's warp, at most a full machine
+    int64_t g = ((int64_t)a.total_tiles + TSORT_THREADS / 32 - 1) / (TSORT_THREADS / 32);
+    if (g > (int64_t)sms * occ) g = (int64_t)sms * occ;
+    tile_sort_kernel<<<(unsigned)g, TSORT_THREADS, 0, st>>>(a);
 }
 
 }  // namespace ts
