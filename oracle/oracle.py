@@ -32,8 +32,11 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
 DEFAULT_CONSTS = dict(alpha_max=0.99, alpha_min=1.0 / 255.0, t_eps=1e-4, z_near=0.2,
-                      r_min=1e-4, tile=16, rect_pad=2.0 ** -9, window=0)
+                      r_min=1e-4, tile=16, rect_pad=2.0 ** -9, window=0, sort=0)
 WINDOW_POWER, WINDOW_SIGMOID = 0, 1       # Eq. indicator1 (the paper's), Eq. indicator2
+# compositing order: per tile by centroid depth (the paper's), or per pixel by the depth
+# of the triangle's plane along the pixel's ray (the per-pixel sort of its future work)
+SORT_TILE, SORT_PIXEL = 0, 1
 EXACT_CONSTS = dict(DEFAULT_CONSTS, alpha_max=1.0, alpha_min=0.0, t_eps=0.0)
 
 AMB_SKIP, AMB_STOP, AMB_ORDER, AMB_SENS, AMB_CULL = 1, 2, 4, 8, 16
@@ -120,7 +123,7 @@ def _cam_array(cam):
 def _const_array(consts):
     c = consts or DEFAULT_CONSTS
     return np.array([c["alpha_max"], c["alpha_min"], c["t_eps"], c["z_near"], c["r_min"],
-                     c["tile"], c["rect_pad"], c.get("window", 0)], dtype=np.float64)
+                     c["tile"], c["rect_pad"], c.get("window", 0), c.get("sort", 0)], dtype=np.float64)
 
 
 def render(scene, cam, consts=None, brute: bool = False, pix_mask=None, flags: bool = False):

@@ -19,7 +19,9 @@
  *     back in order of camera-space centroid depth (ties: triangle id), stopping
  *     before a fragment that would drop transmittance below T_EPS (Sec. 3.1: the
  *     rendering equation of prior splatting work; depth sort by triangle centre,
- *     Supp. "Depth sorting");
+ *     Supp. "Depth sorting"); with the sort constant set to SORT_PIXEL, the order is
+ *     instead each pixel's own: the depth of the triangle's plane along the pixel's
+ *     ray (the per-pixel sort the paper leaves to future work);
  *   - view-dependent colour from real spherical harmonics up to degree 3
  *     (Sec. 4: 48 colour floats per triangle), rgb = max(0, sum Y_lm c_lm + 0.5);
  *   - the tight screen rectangle of Supp. "Tile assignment": edges moved inward by
@@ -55,9 +57,15 @@
  * WIN_SIGMOID is Eq. indicator2, I = sigmoid(-phi(p)/sigma), sigma in pixels */
 enum { WIN_POWER = 0, WIN_SIGMOID = 1 };
 
+/* compositing order: SORT_TILE is the paper's (each tile's entries by the camera depth
+ * of the triangle's centroid, Supp. "Tile assignment"); SORT_PIXEL, the per-pixel
+ * sort the paper leaves to future work, orders each pixel's fragments by the depth of
+ * the triangle's plane along the pixel's ray. Ties go to the lower triangle id. */
+enum { SORT_TILE = 0, SORT_PIXEL = 1 };
+
 typedef struct {
     double alpha_max, alpha_min, t_eps, z_near, r_min, tile, rect_pad;
-    int window;
+    int window, sort;
 } consts_t;
 
 typedef struct {
@@ -71,6 +79,7 @@ static consts_t load_consts(const double *c) {
     k.alpha_max = c[0]; k.alpha_min = c[1]; k.t_eps = c[2]; k.z_near = c[3];
     k.r_min = c[4]; k.tile = c[5]; k.rect_pad = c[6];
     k.window = (int)c[7];
+    k.sort = (int)c[8];
     return k;
 }
 
@@ -273,6 +282,7 @@ typedef struct {
     int cull;               /* CULL_* : removes the triangle from the image */
     int amb_cull;           /* a cull decision within the FP32 band */
     double z[3], depth;
+    double xc[3][3];        /* camera-space vertices */
     tri2d_t g;
     double o, sigma;
     double dir[3], rgb_raw[3], rgb[3];
@@ -327,6 +337,7 @@ static void tri_setup(int id, const double *verts, const double *sh, int sh_deg,
         double yc = C->R[3] * X + C->R[4] * Y + C->R[5] * Z + C->t[1];
         double zc = C->R[6] * X + C->R[7] * Y + C->R[8] * Z + C->t[2];
         T->z[i] = zc;
+        T->xc[i][0] = xc; T->xc[i][1] = yc; T->xc[i][2] = zc;
         if (zc < K->z_near) near = 1;
         if (fabs(zc - K->z_near) <= 1e-5 * (1.0 + fabs(K->z_near))) near_amb = 1;
         if (zc > 0) {
@@ -514,6 +525,16 @@ static void vec_push(vec_t *v, ent_t x) {
     v->e[v->n++] = x;
 }
 
+/* camera depth of the plane of triangle t along the ray through pixel point (px, py):
+ * z = (n . x0) / (n . d), n = (x1 - x0) x (x2 - x0), d = ((px - cx) / fx, (py - cy) / fy, 1) */
+static double pixel_depth(const tri_t *t, const cam_t *C, double px, double py) {
+    const double *a = t->xc[0], *b = t->xc[1], *c = t->xc[2];
+    double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double d[3] = {(px - C->cx) / C->fx, (py - C->cy) / C->fy, 1.0};
+    return (n[0] * a[0] + n[1] * a[1] + n[2] * a[2]) / (n[0] * d[0] + n[1] * d[1] + n[2] * d[2]);
+}
+
 /* window value of triangle t at window ratio `ratio` (FP64) */
 static double window_I(const consts_t *K, const tri_t *t, double ratio) {
     if (K->window == WIN_SIGMOID) return 1.0 / (1.0 + exp(-t->g.r * ratio / t->sigma));
@@ -606,7 +627,10 @@ static void shade_pixel(const job_t *J, const ent_t *e, size_t cnt, int x, int y
         double da;
         if (alo >= K->alpha_max) da = 0.0;
         else da = fmax(fmin(ahi, K->alpha_max) - a, a - alo);
-        if (!isnan(prev_depth) && fabs(f->depth - prev_depth) <= 4.0 * ulp32(f->depth)) amb |= AMB_ORDER;
+        /* FP32 depth keys that may swap: the centroid depth (a few roundings), or the
+         * per-pixel plane depth (a plane evaluation and a reciprocal) */
+        const double dband = (K->sort == SORT_PIXEL ? 64.0 : 4.0) * ulp32(f->depth);
+        if (!isnan(prev_depth) && fabs(f->depth - prev_depth) <= dband) amb |= AMB_ORDER;
         prev_depth = f->depth;
         double test = T * (1.0 - a);
         if (K->t_eps > 0) {
@@ -730,7 +754,8 @@ static void render_band(const job_t *J, int y0, int y1, const int *cand, int nca
                     if (ahi < K->alpha_min) continue;
                 }
                 ent_t e;
-                e.pix = (int)pix; e.id = id; e.depth = t->depth;
+                e.pix = (int)pix; e.id = id;
+                e.depth = K->sort == SORT_PIXEL ? pixel_depth(t, &J->C, px, py) : t->depth;
                 e.alpha = araw < K->alpha_max ? araw : K->alpha_max;
                 e.ratio = ratio; e.kept = kept; e.argmax = am;
                 vec_push(&v, e);
