@@ -233,6 +233,23 @@ tri_status tri_debug_copy(tri_ctx *ctx, int which, void *dst, size_t max_bytes, 
 #define TRI_WINDOW_SIGMOID 1
 tri_status tri_set_window(tri_ctx *ctx, int window);
 
+/* Compositing order of the context's next tri_preprocess and of the renders that use
+ * its records. TRI_SORT_TILE (default) is the paper's: each tile's entries by the
+ * camera depth of the triangle's centroid (Supp. "Tile assignment", "depth sorting").
+ * TRI_SORT_PIXEL is the per-pixel sort the paper leaves to future work: each pixel's
+ * fragments (alpha >= 1/255) by the depth of the triangle's plane along the pixel's
+ * ray, ties to the lower triangle id, so intersecting triangles composite correctly.
+ * Under TRI_SORT_PIXEL tri_preprocess also writes each item's inverse-depth plane (16 B
+ * per item); tri_render_fwd counts every pixel's candidates, reads their total back
+ * (a stream synchronisation; under stream capture the buffer sized by an earlier
+ * uncaptured forward must suffice, else tri_ctx_check reports an index error), and
+ * keeps each pixel's sorted candidates (8 B each) for tri_render_bwd. Not with
+ * tri_render_fwd_stats (TRI_ERR_INVALID_ARG) or tri_render_solid (which always uses
+ * the tile order). Resets the context's stage. TRI_ERR_INVALID_ARG for another value. */
+#define TRI_SORT_TILE 0
+#define TRI_SORT_PIXEL 1
+tri_status tri_set_sort(tri_ctx *ctx, int sort);
+
 /* Densification moves (Sec. 3.3 "Densification"), in place on scene arrays with room
  * for `capacity` triangles (device, same layouts as tri_scene; verts / sh 16-byte
  * aligned not required). For each of the k distinct indices in sel (device int32):

@@ -390,12 +390,17 @@ static tri_status preprocess_impl(tri_ctx *c, const tri_scene *scene, const tri_
         a.tile_count = P<uint32_t>(c->tile_count);
         a.solid = solid ? 1 : 0;
         a.window = c->window;
+        if (!solid && c->sort == TRI_SORT_PIXEL) {
+            ENSURE(c->zplane, sizeof(float4) * (size_t)M);
+            a.zplane = P<float4>(c->zplane);
+        }
         launch_preprocess_fwd(a, st);
         if ((s = launch_check(c, "preprocess_fwd_kernel")) != TRI_OK) return s;
     }
     c->stage = 1;
     c->solid = solid;
     c->rec_window = c->window;
+    c->rec_sort = solid ? TRI_SORT_TILE : c->sort;
     return TRI_OK;
 }
 
@@ -475,6 +480,44 @@ static RenderArgs render_args(tri_ctx *c, TsDevBuf &outs) {
     return r;
 }
 
+// Forward of the per-pixel sort: candidate counts, their scan, then (outside stream
+// capture) the total read back to size the candidate buffer; under capture the buffer
+// must already hold them (overflow is reported by tri_ctx_check as an index error).
+static tri_status render_fwd_pps(tri_ctx *c, RenderArgs &r, cudaStream_t st) {
+    Ctl *ctl = ctl_of(c);
+    const int64_t pix = c->total_pix;
+    ENSURE(c->pcount, 4 * (size_t)pix);
+    ENSURE(c->poff, 8 * (size_t)pix);
+    ENSURE(c->pscan_status, 8 * pps_scan_status_words(pix));
+    CK(cudaMemsetAsync(&ctl->work_counter[3], 0, 4, st));
+    CK(cudaMemsetAsync(&ctl->cta_counter[4], 0, 4, st));
+    CK(cudaMemsetAsync(c->pscan_status.p, 0, 8 * pps_scan_status_words(pix), st));
+    r.zplane = P<float4>(c->zplane);
+    r.pcount = P<uint32_t>(c->pcount);
+    r.poff = P<unsigned long long>(c->poff);
+    r.pscan_status = P<unsigned long long>(c->pscan_status);
+    r.total_pix = pix;
+    launch_pps_count(r, c->sms, st);
+    launch_pps_scan(r, st);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+        unsigned long long total = 0;
+        CK(cudaMemcpyAsync(&total, &ctl->pps_total, 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (total > c->cand_cap) {
+            c->cand_cap = total + total / 4 + 1024;
+            ENSURE(c->cand, 8 * (size_t)c->cand_cap);
+        }
+    } else if (c->cand_cap == 0) {
+        return fail(c, TRI_ERR_STATE, "per-pixel sort captured before an uncaptured forward sized its buffer");
+    }
+    r.cand = P<unsigned long long>(c->cand);
+    r.cand_cap = c->cand_cap;
+    launch_pps_fwd(r, c->sms, st);
+    return TRI_OK;
+}
+
 static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const *T_final,
                                   int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels, void *stream,
                                   int32_t *const *ids = nullptr) {
@@ -508,7 +551,12 @@ static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const
         r.stat_w = reinterpret_cast<uint32_t *>(max_weight);
         r.stat_n = reinterpret_cast<uint32_t *>(n_pixels);
     }
-    launch_render_fwd(r, c->sms, st, c->solid);
+    if (c->rec_sort == TRI_SORT_PIXEL) {
+        if (r.stat_w) return fail(c, TRI_ERR_INVALID_ARG, "pruning statistics need the tile sort");
+        if ((s = render_fwd_pps(c, r, st)) != TRI_OK) return s;
+    } else {
+        launch_render_fwd(r, c->sms, st, c->solid);
+    }
     if ((s = launch_check(c, "render_fwd_kernel")) != TRI_OK) return s;
     for (int v = 0; v < c->nviews; ++v) {
         const ViewDev &V = c->views[v];
@@ -543,6 +591,14 @@ tri_status tri_set_window(tri_ctx *c, int window) {
     if (window != TRI_WINDOW_POWER && window != TRI_WINDOW_SIGMOID)
         return fail(c, TRI_ERR_INVALID_ARG, "unknown window kind");
     c->window = window;
+    c->stage = 0;   // records of the other kind are stale
+    return TRI_OK;
+}
+
+tri_status tri_set_sort(tri_ctx *c, int sort) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    if (sort != TRI_SORT_TILE && sort != TRI_SORT_PIXEL) return fail(c, TRI_ERR_INVALID_ARG, "unknown sort kind");
+    c->sort = sort;
     c->stage = 0;   // records of the other kind are stale
     return TRI_OK;
 }
@@ -629,7 +685,16 @@ tri_status tri_render_bwd(tri_ctx *c, const float *const *dL, void *stream) {
         return s;
     CK(cudaMemsetAsync(c->grad2d.p, 0, sizeof(float) * GRAD_FIELDS * (size_t)c->n_items, st));
     CK(cudaMemsetAsync(&ctl_of(c)->work_counter[1], 0, 4, st));
-    launch_render_bwd(render_args(c, c->outs_bwd), c->sms, st);
+    RenderArgs r = render_args(c, c->outs_bwd);
+    if (c->rec_sort == TRI_SORT_PIXEL) {
+        r.poff = P<unsigned long long>(c->poff);
+        r.cand = P<unsigned long long>(c->cand);
+        r.cand_cap = c->cand_cap;
+        r.total_pix = c->total_pix;
+        launch_pps_bwd(r, st);
+    } else {
+        launch_render_bwd(r, c->sms, st);
+    }
     if ((s = launch_check(c, "render_bwd_kernel")) != TRI_OK) return s;
     c->stage = 4;
     return TRI_OK;

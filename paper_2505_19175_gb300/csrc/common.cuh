@@ -62,6 +62,7 @@ struct Ctl {
     uint32_t big_next;         // next queued tile to sort
     unsigned long long frag_eval;   // forward: (pixel, entry) evaluations
     unsigned long long frag_kept;   // forward: composited fragments
+    unsigned long long pps_total;   // per-pixel sort: candidates of all pixels
     uint32_t depth_hist[4][256];
     uint32_t tile_hist[4][256];
 };

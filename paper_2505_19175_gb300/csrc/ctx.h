@@ -27,6 +27,9 @@ struct tri_ctx {
     bool solid = false;  // records of the opaque-triangle render (no backward)
     int window = 0;      // window kind for the next tri_preprocess (tri_set_window)
     int rec_window = 0;  // window kind of the current records
+    int sort = 0;        // compositing order for the next tri_preprocess (tri_set_sort)
+    int rec_sort = 0;    // compositing order of the current records
+    uint64_t cand_cap = 0;   // per-pixel sort: candidate capacity
     long fault_alloc = 0, fault_slow_ms = 0, n_allocs = 0;   // TRI_FAULT injection (tests)
     uint64_t realloc_gen = 0;   // bumped whenever a device buffer is reallocated
     // streams of the previous and the current call: a reallocation waits for both,
@@ -36,10 +39,12 @@ struct tri_ctx {
     ts::ViewDev *h_views = nullptr;
     ts::ViewOut *h_outs_fwd = nullptr, *h_outs_bwd = nullptr;
     TsDevBuf views_d, outs_fwd, outs_bwd, ctl, recs, ntiles, rects, dkeys, tile_count, tile_cursor, big_tiles, kv,
-        kv_tmp, items, kmask, ids, dens_status, scan_status, ranges, tile_max, Tfin, ncontrib, grad2d;
+        kv_tmp, items, kmask, ids, dens_status, scan_status, ranges, tile_max, Tfin, ncontrib, grad2d, zplane, pcount,
+        poff, cand, pscan_status;
     std::vector<TsDevBuf *> all() {
         return {&views_d, &outs_fwd, &outs_bwd, &ctl, &recs, &ntiles, &rects, &dkeys, &tile_count, &tile_cursor,
-                &big_tiles, &kv, &kv_tmp, &items, &kmask, &ids, &dens_status, &scan_status, &ranges, &tile_max, &Tfin, &ncontrib, &grad2d};
+                &big_tiles, &kv, &kv_tmp, &items, &kmask, &ids, &dens_status, &scan_status, &ranges, &tile_max, &Tfin, &ncontrib, &grad2d,
+                &zplane, &pcount, &poff, &cand, &pscan_status};
     }
 };
 

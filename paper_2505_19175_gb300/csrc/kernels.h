@@ -20,6 +20,7 @@ struct PreArgs {
     uint32_t *tile_count = nullptr;  // if set (zeroed): pairs per tile, for the binning
     int solid = 0;                   // opaque-triangle records: full triangle, o = 1
     int window = WIN_POWER;          // window kind of the records
+    float4 *zplane = nullptr;        // if set: [items] (a, b, c, 0), 1/z(p) = a (p.x - cx) + b (p.y - cy) + c
 };
 
 struct PreBwdArgs {
@@ -155,9 +156,25 @@ struct RenderArgs {
     float *grad2d;                  // backward: [items][16]
     uint32_t n_items;               // bound of the item ids in `items`
     Ctl *ctl;
+    // per-pixel sort: the items' inverse-depth planes, per-pixel candidate counts and
+    // offsets, and the candidates (depth bits << 32 | item), sorted per pixel
+    const float4 *zplane = nullptr;
+    uint32_t *pcount = nullptr;
+    unsigned long long *poff = nullptr;
+    unsigned long long *cand = nullptr;
+    unsigned long long cand_cap = 0;
+    unsigned long long *pscan_status = nullptr;
+    int64_t total_pix = 0;
 };
 void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st, bool solid = false);
 void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st);
+// per-pixel sort: count the candidates (alpha >= 1/255) of every pixel; scan the counts
+// into offsets (total into ctl->pps_total); fill, sort per pixel and composite; backward.
+void launch_pps_count(const RenderArgs &a, int grid, cudaStream_t st);
+void launch_pps_scan(const RenderArgs &a, cudaStream_t st);
+size_t pps_scan_status_words(int64_t total_pix);
+void launch_pps_fwd(const RenderArgs &a, int grid, cudaStream_t st);
+void launch_pps_bwd(const RenderArgs &a, cudaStream_t st);
 
 void launch_loss_l1(const float *img, const float *tgt, int64_t n, float *grad, float *loss, cudaStream_t st);
 

@@ -97,7 +97,8 @@ __device__ __forceinline__ int clamp_pix(float v, int n) {
     return (int)v;
 }
 
-template <int DEG, int WIN>
+// ZP: also write the items' inverse-depth planes (per-pixel sort).
+template <int DEG, int WIN, bool ZP>
 __global__ void __launch_bounds__(PRE_THREADS, 6)
 preprocess_fwd_kernel(PreArgs a) {
     __shared__ __align__(16) float s_v[PRE_THREADS * 9];
@@ -193,6 +194,23 @@ preprocess_fwd_kernel(PreArgs a) {
             rec.d = make_float4(WIN == WIN_SIGMOID ? g.r / sig : sig, col[0], col[1], col[2]);
             key = __float_as_uint(g.depth);
             ++nvis;
+            if (ZP) {
+                // inverse depth along the ray through p: (n . d) / (n . x0), n the plane
+                // normal (x1 - x0) x (x2 - x0), d = ((p.x - cx) / fx, (p.y - cy) / fy, 1)
+                float e[2][3];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float dx = v[3 * q + 3] - v[0], dy = v[3 * q + 4] - v[1], dz = v[3 * q + 5] - v[2];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) e[q][r] = fmaf(V.R[3 * r], dx, fmaf(V.R[3 * r + 1], dy, V.R[3 * r + 2] * dz));
+                }
+                const float nx = e[0][1] * e[1][2] - e[0][2] * e[1][1];
+                const float ny = e[0][2] * e[1][0] - e[0][0] * e[1][2];
+                const float nz = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+                const float D = fmaf(nx, g.xc[0].x, fmaf(ny, g.xc[0].y, nz * g.xc[0].z));
+                a.zplane[m] = D != 0.0f ? make_float4(nx / (V.fx * D), ny / (V.fy * D), nz / D, 0.0f)
+                                        : make_float4(0.0f, 0.0f, 1.0f / g.depth, 0.0f);
+            }
         }
         a.recs[m] = rec;
         a.ntiles[m] = nt;
@@ -429,21 +447,27 @@ preprocess_bwd_kernel(PreBwdArgs a) {
     }
 }
 
+template <bool ZP>
+static void launch_fwd_zp(const PreArgs &a, int grid, size_t smem, cudaStream_t st) {
+    const bool sg = a.window == WIN_SIGMOID;
+    switch (a.sh_degree) {
+        case 0: sg ? preprocess_fwd_kernel<0, 1, ZP><<<grid, PRE_THREADS, smem, st>>>(a)
+                   : preprocess_fwd_kernel<0, 0, ZP><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        case 1: sg ? preprocess_fwd_kernel<1, 1, ZP><<<grid, PRE_THREADS, smem, st>>>(a)
+                   : preprocess_fwd_kernel<1, 0, ZP><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        case 2: sg ? preprocess_fwd_kernel<2, 1, ZP><<<grid, PRE_THREADS, smem, st>>>(a)
+                   : preprocess_fwd_kernel<2, 0, ZP><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        default: sg ? preprocess_fwd_kernel<3, 1, ZP><<<grid, PRE_THREADS, smem, st>>>(a)
+                    : preprocess_fwd_kernel<3, 0, ZP><<<grid, PRE_THREADS, smem, st>>>(a); break;
+    }
+}
+
 void launch_preprocess_fwd(const PreArgs &a, cudaStream_t st) {
     const int grid = (int)((a.n + PRE_THREADS - 1) / PRE_THREADS);
     if (grid <= 0) return;
     const size_t smem = sizeof(ViewDev) * a.nviews;
-    const bool sg = a.window == WIN_SIGMOID;
-    switch (a.sh_degree) {
-        case 0: sg ? preprocess_fwd_kernel<0, 1><<<grid, PRE_THREADS, smem, st>>>(a)
-                   : preprocess_fwd_kernel<0, 0><<<grid, PRE_THREADS, smem, st>>>(a); break;
-        case 1: sg ? preprocess_fwd_kernel<1, 1><<<grid, PRE_THREADS, smem, st>>>(a)
-                   : preprocess_fwd_kernel<1, 0><<<grid, PRE_THREADS, smem, st>>>(a); break;
-        case 2: sg ? preprocess_fwd_kernel<2, 1><<<grid, PRE_THREADS, smem, st>>>(a)
-                   : preprocess_fwd_kernel<2, 0><<<grid, PRE_THREADS, smem, st>>>(a); break;
-        default: sg ? preprocess_fwd_kernel<3, 1><<<grid, PRE_THREADS, smem, st>>>(a)
-                    : preprocess_fwd_kernel<3, 0><<<grid, PRE_THREADS, smem, st>>>(a); break;
-    }
+    if (a.zplane) launch_fwd_zp<true>(a, grid, smem, st);
+    else launch_fwd_zp<false>(a, grid, smem, st);
 }
 
 template <bool MULTI>

@@ -560,6 +560,345 @@ void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------------
+// Per-pixel sort (the ordering the paper leaves to future work after its per-tile
+// centroid sort): each pixel's fragments composite in the order of the depth of their
+// triangle's plane along the pixel's ray, z(p) = 1 / (a (p.x - cx) + b (p.y - cy) + c)
+// from the item's inverse-depth plane, ties to the lower item id. Three passes over
+// each tile's list: count the pixel's candidates (alpha >= 1/255), scan the counts
+// into offsets, then write the candidates as (z bits << 32 | item), sort each pixel's
+// run on its own thread (insertion sort, heapsort beyond 24 entries) and composite.
+// The backward walks each pixel's sorted run back to front, one thread per pixel,
+// adding each fragment's 13 gradient fields to its item with four vector reductions.
+// ---------------------------------------------------------------------------------
+
+__device__ __forceinline__ float pps_depth(const float4 zp, const ViewDev &V, float px, float py) {
+    return 1.0f / fmaf(zp.x, px - V.cx, fmaf(zp.y, py - V.cy, zp.z));
+}
+
+// Fragment alpha o I of record r at (px, py) before the clamp (0 below 1/255), as the
+// tile-sorted forward; the window value into I.
+template <int WIN>
+__device__ __forceinline__ float pps_alpha(const Rec &r, float px, float py, Frag &f, float &I) {
+    f = eval_lines(r.a, r.b, r.c, px, py);
+    I = 0.0f;
+    if (WIN == WIN_POWER && f.ratio <= 0.0f) return 0.0f;
+    I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, r.d.x) : window_pow(f.ratio, r.d.x);
+    const float al = __fmul_rn(r.c.w, I);
+    return al < ALPHA_MIN ? 0.0f : al;
+}
+
+__device__ void pps_sort_run(unsigned long long *v, int n) {
+    if (n <= 24) {
+        for (int i = 1; i < n; ++i) {
+            const unsigned long long x = v[i];
+            int j = i - 1;
+            while (j >= 0 && v[j] > x) {
+                v[j + 1] = v[j];
+                --j;
+            }
+            v[j + 1] = x;
+        }
+        return;
+    }
+    // heapsort (max-heap, in place)
+    auto sift = [&](int root, int end) {
+        const unsigned long long x = v[root];
+        int i = root;
+        while (true) {
+            int c = 2 * i + 1;
+            if (c >= end) break;
+            if (c + 1 < end && v[c + 1] > v[c]) ++c;
+            if (v[c] <= x) break;
+            v[i] = v[c];
+            i = c;
+        }
+        v[i] = x;
+    };
+    for (int i = n / 2 - 1; i >= 0; --i) sift(i, n);
+    for (int e = n - 1; e > 0; --e) {
+        const unsigned long long t = v[0];
+        v[0] = v[e];
+        v[e] = t;
+        sift(0, e);
+    }
+}
+
+// PASS 0: candidate counts; PASS 1: candidates, per-pixel sort, compositing.
+template <int PASS, int WIN>
+__global__ void __launch_bounds__(REN_THREADS) pps_tile_kernel(RenderArgs a) {
+    __shared__ Rec s_rec[REN_THREADS];
+    __shared__ float4 s_zp[REN_THREADS];
+    __shared__ uint32_t s_item[REN_THREADS];
+    __shared__ uint16_t s_mask[REN_THREADS];
+    __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
+    __shared__ ViewDev s_view[MAX_VIEWS];
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += REN_THREADS)
+        reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
+    int lx, ly;
+    pixel_of(tid, lx, ly);
+    const uint8_t *L = s_list[w];
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&a.ctl->work_counter[PASS == 0 ? 0 : 3], 1u);
+        __syncthreads();
+        const int tile = (int)s_tile;
+        if (tile >= a.total_tiles) break;
+        const int vw = find_view(s_view, a.nviews, tile);
+        const ViewDev &V = s_view[vw];
+        const int lt = tile - V.tile_base;
+        const int ox = (lt % V.tiles_x) * TILE, oy = (lt / V.tiles_x) * TILE;
+        const int x = ox + lx, y = oy + ly;
+        const bool inside = x < V.W && y < V.H;
+        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+        const int64_t pg = inside ? V.pix_base + (int64_t)y * V.W + x : 0;
+        const uint2 rg = a.ranges[tile];
+        const uint32_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
+        uint32_t cnt = 0, want = 0;
+        unsigned long long off = 0;
+        if (PASS == 1 && inside) {
+            off = a.poff[pg];
+            want = a.pcount[pg];
+        }
+        for (uint32_t b0 = start; b0 < end; b0 += REN_THREADS) {
+            __syncthreads();
+            const uint32_t idx = b0 + tid;
+            if (idx < end) {
+                uint32_t it = a.items[idx];
+                if (it >= a.n_items) {
+                    atomicOr(&a.ctl->error, ERR_INDEX);
+                    it = 0;
+                }
+                const Rec r = a.recs[it];
+                s_rec[tid] = r;
+                s_item[tid] = it;
+                if (PASS == 1) s_zp[tid] = a.zplane[it];
+                s_mask[tid] = (uint16_t)warp_mask(r, a.rects[it], ox, oy, cutoff_ratio<WIN>(r, false));
+            } else {
+                s_mask[tid] = 0;
+            }
+            __syncthreads();
+            const int n = warp_list(s_mask, s_list[w], w, lane);
+            if (!inside) continue;
+            for (int k = 0; k < n; ++k) {
+                const int j = L[k];
+                Frag f;
+                float I;
+                if (pps_alpha<WIN>(s_rec[j], px, py, f, I) <= 0.0f) continue;
+                if (PASS == 1) {
+                    if (cnt < want && off + cnt < a.cand_cap) {
+                        const float z = pps_depth(s_zp[j], V, px, py);
+                        a.cand[off + cnt] = ((unsigned long long)__float_as_uint(z) << 32) | s_item[j];
+                    } else {
+                        atomicOr(&a.ctl->error, ERR_INDEX);
+                    }
+                }
+                ++cnt;
+            }
+        }
+        if (PASS == 0) {
+            if (inside) a.pcount[pg] = cnt;
+        } else if (inside) {
+            const int m = (int)min(cnt, want);
+            const bool fits = off + (unsigned long long)m <= a.cand_cap;
+            unsigned long long *run = a.cand + off;
+            if (fits) pps_sort_run(run, m);
+            float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+            uint32_t last = 0;
+            for (int i = 0; fits && i < m; ++i) {
+                const uint32_t it = (uint32_t)run[i];
+                const Rec r = a.recs[it];
+                Frag f;
+                float I;
+                float al = pps_alpha<WIN>(r, px, py, f, I);
+                if (al <= 0.0f) continue;
+                al = fminf(al, ALPHA_MAX);
+                const float tT = __fmul_rn(T, __fsub_rn(1.0f, al));
+                if (tT < T_EPS) break;
+                const float wgt = __fmul_rn(al, T);
+                C0 = fmaf(r.d.y, wgt, C0);
+                C1 = fmaf(r.d.z, wgt, C1);
+                C2 = fmaf(r.d.w, wgt, C2);
+                T = tT;
+                last = (uint32_t)i + 1u;
+            }
+            const int64_t HW = (int64_t)V.W * V.H;
+            const int64_t pix = (int64_t)y * V.W + x;
+            float *img = a.outs[vw].image;
+            img[pix] = fmaf(T, V.bg[0], C0);
+            img[HW + pix] = fmaf(T, V.bg[1], C1);
+            img[2 * HW + pix] = fmaf(T, V.bg[2], C2);
+            a.T_final[pg] = T;
+            a.n_contrib[pg] = (int32_t)last;
+        }
+        __syncthreads();   // every thread has read s_tile before it changes
+    }
+}
+
+// Exclusive scan of the per-pixel counts into 64-bit offsets (single pass, decoupled
+// look-back over 1024-count blocks, CTA order by ticket); the total into ctl->pps_total.
+__global__ void __launch_bounds__(256) pps_scan_kernel(RenderArgs a) {
+    __shared__ unsigned long long s_w[9];
+    __shared__ uint32_t s_cta;
+    __shared__ unsigned long long s_base;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) s_cta = atomicAdd(&a.ctl->cta_counter[4], 1u);
+    __syncthreads();
+    const uint32_t cta = s_cta;
+    const int64_t p0 = (int64_t)cta * 1024 + tid * 4;
+    uint32_t c[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[q] = p0 + q < a.total_pix ? a.pcount[p0 + q] : 0u;
+    const unsigned long long sum = (unsigned long long)c[0] + c[1] + c[2] + c[3];
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const unsigned long long v = lane < 8 ? s_w[lane] : 0ull;
+        unsigned long long t = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        const unsigned long long total = __shfl_sync(0xffffffffu, t, 7);
+        if (lane < 8) s_w[lane] = t - v;
+        const unsigned long long b =
+            warp_lookback_excl64(reinterpret_cast<uint64_t *>(a.pscan_status), cta, total, &a.ctl->error);
+        if (lane == 0) {
+            s_base = b;
+            if ((int64_t)(cta + 1) * 1024 >= a.total_pix) a.ctl->pps_total = b + total;
+        }
+    }
+    __syncthreads();
+    unsigned long long off = s_base + s_w[w] + x - sum;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (p0 + q < a.total_pix) a.poff[p0 + q] = off;
+        off += c[q];
+    }
+}
+
+size_t pps_scan_status_words(int64_t total_pix) { return (size_t)((total_pix + 1023) / 1024) + 1; }
+
+// Backward of the per-pixel sort: one thread per pixel, its sorted run from the last
+// composited fragment back to the first.
+template <int WIN>
+__global__ void __launch_bounds__(256) pps_bwd_kernel(RenderArgs a) {
+    for (int64_t pg = (int64_t)blockIdx.x * 256 + threadIdx.x; pg < a.total_pix;
+         pg += (int64_t)gridDim.x * 256) {
+        int vw = 0;
+        for (int k = 1; k < a.nviews; ++k)
+            if (a.views[k].pix_base <= pg) vw = k;
+        const ViewDev &V = a.views[vw];
+        const int64_t pix = pg - V.pix_base;
+        const int x = (int)(pix % V.W), y = (int)(pix / V.W);
+        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+        const int64_t HW = (int64_t)V.W * V.H;
+        const float *dL = a.outs[vw].dL;
+        const float g0 = dL[pix], g1 = dL[HW + pix], g2 = dL[2 * HW + pix];
+        float T = a.T_final[pg];
+        float B0 = T * V.bg[0], B1 = T * V.bg[1], B2 = T * V.bg[2];
+        const int last = a.n_contrib[pg];
+        const unsigned long long *run = a.cand + a.poff[pg];
+        for (int k = last - 1; k >= 0; --k) {
+            const uint32_t it = (uint32_t)run[k];
+            if (it >= a.n_items) {
+                atomicOr(&a.ctl->error, ERR_INDEX);
+                continue;
+            }
+            const Rec r = a.recs[it];
+            Frag f;
+            float I;
+            const float araw = pps_alpha<WIN>(r, px, py, f, I);
+            if (araw <= 0.0f) continue;
+            float gv[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) gv[q] = 0.f;
+            const float al = fminf(araw, ALPHA_MAX);
+            const float iom = rcp_approx(__fsub_rn(1.0f, al));
+            T = T * iom;
+            const float wgt = al * T;
+            gv[10] = g0 * wgt;
+            gv[11] = g1 * wgt;
+            gv[12] = g2 * wgt;
+            const float gc = fmaf(g0, r.d.y, fmaf(g1, r.d.z, g2 * r.d.w));
+            const float gb = fmaf(g0, B0, fmaf(g1, B1, g2 * B2));
+            const float galpha = T * gc - iom * gb;
+            B0 = fmaf(r.d.y, wgt, B0);
+            B1 = fmaf(r.d.z, wgt, B1);
+            B2 = fmaf(r.d.w, wgt, B2);
+            if (araw <= ALPHA_MAX) {
+                const float gI = galpha * r.c.w;
+                gv[8] = galpha * I;
+                float gr;
+                if (WIN == WIN_SIGMOID) {
+                    const float s1 = I * (1.0f - I);
+                    gv[9] = gI * s1 * f.ratio;
+                    gr = gI * r.d.x * s1;
+                } else {
+                    gv[9] = gI * I * lg2_approx(f.ratio) * 0.69314718055994531f;
+                    gr = gI * r.d.x * I * rcp_approx(f.ratio);
+                }
+                const int ia = (f.m0 <= f.m1 && f.m0 <= f.m2) ? 0 : (f.m1 <= f.m2 ? 1 : 2);
+                const float Aa = ia == 0 ? r.a.z : (ia == 1 ? r.b.y : r.c.x);
+                const float Ba = ia == 0 ? r.a.w : (ia == 1 ? r.b.z : r.c.y);
+                gv[0] = -gr * Aa;
+                gv[1] = -gr * Ba;
+                const float gA = gr * f.dx, gB = gr * f.dy;
+                gv[2] = ia == 0 ? gA : 0.f;
+                gv[3] = ia == 0 ? gB : 0.f;
+                gv[4] = ia == 1 ? gA : 0.f;
+                gv[5] = ia == 1 ? gB : 0.f;
+                gv[6] = ia == 2 ? gA : 0.f;
+                gv[7] = ia == 2 ? gB : 0.f;
+            }
+            float *dst = a.grad2d + (size_t)it * GRAD_FIELDS;
+            red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
+            red_add_v4(dst + 4, gv[4], gv[5], gv[6], gv[7]);
+            red_add_v4(dst + 8, gv[8], gv[9], gv[10], gv[11]);
+            red_add_v4(dst + 12, gv[12], 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+void launch_pps_count(const RenderArgs &a, int grid, cudaStream_t st) {
+    static int occ = occupancy((const void *)pps_tile_kernel<0, WIN_POWER>, REN_THREADS);
+    int g = grid > 0 ? grid * occ : occ;
+    if (g > a.total_tiles) g = a.total_tiles;
+    if (g <= 0) return;
+    if (a.window == WIN_SIGMOID) pps_tile_kernel<0, WIN_SIGMOID><<<g, REN_THREADS, 0, st>>>(a);
+    else pps_tile_kernel<0, WIN_POWER><<<g, REN_THREADS, 0, st>>>(a);
+}
+
+void launch_pps_scan(const RenderArgs &a, cudaStream_t st) {
+    const int64_t g = (a.total_pix + 1023) / 1024;
+    if (g > 0) pps_scan_kernel<<<(unsigned)g, 256, 0, st>>>(a);
+}
+
+void launch_pps_fwd(const RenderArgs &a, int grid, cudaStream_t st) {
+    static int occ = occupancy((const void *)pps_tile_kernel<1, WIN_POWER>, REN_THREADS);
+    int g = grid > 0 ? grid * occ : occ;
+    if (g > a.total_tiles) g = a.total_tiles;
+    if (g <= 0) return;
+    if (a.window == WIN_SIGMOID) pps_tile_kernel<1, WIN_SIGMOID><<<g, REN_THREADS, 0, st>>>(a);
+    else pps_tile_kernel<1, WIN_POWER><<<g, REN_THREADS, 0, st>>>(a);
+}
+
+void launch_pps_bwd(const RenderArgs &a, cudaStream_t st) {
+    int64_t g = (a.total_pix + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g <= 0) return;
+    if (a.window == WIN_SIGMOID) pps_bwd_kernel<WIN_SIGMOID><<<(unsigned)g, 256, 0, st>>>(a);
+    else pps_bwd_kernel<WIN_POWER><<<(unsigned)g, 256, 0, st>>>(a);
+}
+
+// ---------------------------------------------------------------------------------
 // L1 loss: mean |image - target| and its gradient sign(image - target) / n
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ float l1_sign(float d, float inv) { return d > 0.f ? inv : (d < 0.f ? -inv : 0.f); }

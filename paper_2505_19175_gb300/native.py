@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "TRI_OK", 1: "TRI_ERR_INVALID_ARG", 2: "TRI_ERR_OOM", 3: "TRI
 
 
 WINDOW_POWER, WINDOW_SIGMOID = 0, 1   # Eq. indicator1 (default), Eq. indicator2
+SORT_TILE, SORT_PIXEL = 0, 1       # per tile by centroid depth (default), per pixel by plane depth
 
 
 class TriError(RuntimeError):
@@ -93,6 +94,7 @@ def lib():
                                     C.c_float, vp, vp])
             _sig(L, "tri_size_reg", [vp, C.c_int64, C.c_float, vp, vp, vp])
             _sig(L, "tri_set_window", [vp, C.c_int])
+            _sig(L, "tri_set_sort", [vp, C.c_int])
             _sig(L, "tri_render_solid", [vp, P(tri_scene), P(tri_camera), C.c_int, P(vp), P(vp),
                                          P(C.c_int64), vp])
             _sig(L, "tri_render_bwd", [vp, P(vp), vp])

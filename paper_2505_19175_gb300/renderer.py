@@ -122,6 +122,12 @@ class Context:
         default) or ``native.WINDOW_SIGMOID`` (Eq. indicator2)."""
         self._ck(self._lib.tri_set_window(self.h, int(window)))
 
+    def set_sort(self, sort: int) -> None:
+        """Compositing order of the next preprocess: ``native.SORT_TILE`` (per tile by
+        centroid depth, the default) or ``native.SORT_PIXEL`` (per pixel by the depth of
+        the triangle's plane along the pixel's ray)."""
+        self._ck(self._lib.tri_set_sort(self.h, int(sort)))
+
     def render_solid(self, scene: SceneTensors, cams, images, ids=None, sync_pairs: bool = True,
                      stream=None) -> int:
         """Opaque-triangle render of ``cams`` into ``images`` (and the winning triangle
