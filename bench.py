@@ -224,6 +224,50 @@ def run_sigmoid_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds,
     return sigmoid_line
 
 
+def run_pixel_sort_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds, capture, timed):
+    """The headline step with the per-pixel sort (graph replay; the uncaptured warm-up
+    sizes the candidate buffer), and its forward alone."""
+    import torch
+    from paper_2505_19175_gb300 import native as N
+    from paper_2505_19175_gb300.renderer import Context
+    L = N.lib()
+    ctx_p = Context(dev)
+    ctx_p.set_sort(N.SORT_PIXEL)
+    ctx_p.preprocess(st, [cam])
+    ctx_p.reserve(int(ctx_p.bin_sort(sync=True) * 1.25) + 1024)
+
+    def fwd_pixel():
+        ctx_p.preprocess(st, [cam])
+        ctx_p.bin_sort(sync=False)
+        ctx_p.render_fwd(imgs)
+
+    def step_pixel():
+        fwd_pixel()
+        N.check(L.tri_loss_l1(imgs[0].data_ptr(), tgt.data_ptr(), imgs[0].numel(), grad.data_ptr(),
+                              loss.data_ptr(), int(torch.cuda.current_stream().cuda_stream)))
+        ctx_p.render_bwd([grad])
+        ctx_p.preprocess_bwd(dv, dsh, do, ds)
+
+    for _ in range(3):
+        step_pixel()
+    torch.cuda.synchronize()
+    g_step, g_fwd = capture(step_pixel), capture(fwd_pixel)
+    for _ in range(3):
+        g_step.replay()
+        g_fwd.replay()
+    ev_step = timed(g_step, args.steps)
+    ev_fwd = timed(g_fwd, args.steps)
+    torch.cuda.synchronize()
+    info_p = ctx_p.check()
+    its = args.steps / (float(sum(a.elapsed_time(b) for a, b in ev_step)) / 1000.0)
+    fps = args.steps / (float(sum(a.elapsed_time(b) for a, b in ev_fwd)) / 1000.0)
+    line = {"it_per_s": round(its, 2), "fwd_fps": round(fps, 2), "pairs": int(info_p.n_pairs),
+            "workload": "the same fwd+bwd step with the per-pixel sort (fragments ordered by the depth of "
+                        "their triangle's plane along each pixel's ray)"}
+    del g_step, g_fwd
+    return line
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2505_19175_gb300 import native as N
@@ -393,6 +437,10 @@ def run_ours(args, rank, world):
     sigmoid_line = None
     if not args.no_sigmoid:
         sigmoid_line = run_sigmoid_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds, capture, timed)
+    pixel_sort_line = None
+    if not args.no_pixel_sort:
+        pixel_sort_line = run_pixel_sort_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds, capture,
+                                              timed)
 
     e2e = {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "it/s", "h2d_bytes_per_step": h2d,           "d2h_bytes_per_step": d2h}
 
@@ -448,6 +496,7 @@ def run_ours(args, rank, world):
         "fwd_fps": round(fps, 2),
         "fwd_fps_with_prune_stats": round(fps_stats, 2),
         "sigmoid_window": sigmoid_line,
+        "per_pixel_sort": pixel_sort_line,
         "timing": "CUDA-graph replay of the whole step per timed iteration; stage_ms_median from eager "
                   "steps with events between the calls",
         "stage_ms_median": breakdown,
@@ -841,6 +890,7 @@ def main():
     ap.add_argument("--no-solid", action="store_true")
     ap.add_argument("--no-densify", action="store_true")
     ap.add_argument("--no-sigmoid", action="store_true")
+    ap.add_argument("--no-pixel-sort", action="store_true")
     ap.add_argument("--no-multiscene", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4096)
     args = ap.parse_args()

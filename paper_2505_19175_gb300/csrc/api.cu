@@ -688,6 +688,7 @@ tri_status tri_render_bwd(tri_ctx *c, const float *const *dL, void *stream) {
     RenderArgs r = render_args(c, c->outs_bwd);
     if (c->rec_sort == TRI_SORT_PIXEL) {
         r.poff = P<unsigned long long>(c->poff);
+        r.pcount = P<uint32_t>(c->pcount);
         r.cand = P<unsigned long long>(c->cand);
         r.cand_cap = c->cand_cap;
         r.total_pix = c->total_pix;

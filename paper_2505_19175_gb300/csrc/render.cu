@@ -566,8 +566,11 @@ void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st) {
 // from the item's inverse-depth plane, ties to the lower item id. Three passes over
 // each tile's list: count the pixel's candidates (alpha >= 1/255), scan the counts
 // into offsets, then write the candidates as (z bits << 32 | item), sort each pixel's
-// run on its own thread (insertion sort, heapsort beyond 24 entries) and composite.
-// The backward walks each pixel's sorted run back to front, one thread per pixel,
+// run on its own thread and composite: the run becomes a min-heap and fragments are
+// taken nearest first until transmittance stops the pixel (O(n + k log n) for k
+// composited of n candidates), each taken one moving to the run's free tail, so the
+// k composited fragments end at positions [n - k, n), the farthest first.
+// The backward walks those positions in order (back to front), one thread per pixel,
 // adding each fragment's 13 gradient fields to its item with four vector reductions.
 // ---------------------------------------------------------------------------------
 
@@ -587,40 +590,18 @@ __device__ __forceinline__ float pps_alpha(const Rec &r, float px, float py, Fra
     return al < ALPHA_MIN ? 0.0f : al;
 }
 
-__device__ void pps_sort_run(unsigned long long *v, int n) {
-    if (n <= 24) {
-        for (int i = 1; i < n; ++i) {
-            const unsigned long long x = v[i];
-            int j = i - 1;
-            while (j >= 0 && v[j] > x) {
-                v[j + 1] = v[j];
-                --j;
-            }
-            v[j + 1] = x;
-        }
-        return;
+// Min-heap of a pixel's run: v[i] <= v[2 i + 1], v[2 i + 2].
+__device__ __forceinline__ void heap_sift_down(unsigned long long *v, int i, int end) {
+    const unsigned long long x = v[i];
+    while (true) {
+        int c = 2 * i + 1;
+        if (c >= end) break;
+        if (c + 1 < end && v[c + 1] < v[c]) ++c;
+        if (v[c] >= x) break;
+        v[i] = v[c];
+        i = c;
     }
-    // heapsort (max-heap, in place)
-    auto sift = [&](int root, int end) {
-        const unsigned long long x = v[root];
-        int i = root;
-        while (true) {
-            int c = 2 * i + 1;
-            if (c >= end) break;
-            if (c + 1 < end && v[c + 1] > v[c]) ++c;
-            if (v[c] <= x) break;
-            v[i] = v[c];
-            i = c;
-        }
-        v[i] = x;
-    };
-    for (int i = n / 2 - 1; i >= 0; --i) sift(i, n);
-    for (int e = n - 1; e > 0; --e) {
-        const unsigned long long t = v[0];
-        v[0] = v[e];
-        v[e] = t;
-        sift(0, e);
-    }
+    v[i] = x;
 }
 
 // PASS 0: candidate counts; PASS 1: candidates, per-pixel sort, compositing.
@@ -700,27 +681,32 @@ __global__ void __launch_bounds__(REN_THREADS) pps_tile_kernel(RenderArgs a) {
             if (inside) a.pcount[pg] = cnt;
         } else if (inside) {
             const int m = (int)min(cnt, want);
-            const bool fits = off + (unsigned long long)m <= a.cand_cap;
+            const bool fits = cnt == want && off + (unsigned long long)m <= a.cand_cap;
             unsigned long long *run = a.cand + off;
-            if (fits) pps_sort_run(run, m);
             float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-            uint32_t last = 0;
-            for (int i = 0; fits && i < m; ++i) {
-                const uint32_t it = (uint32_t)run[i];
-                const Rec r = a.recs[it];
-                Frag f;
-                float I;
-                float al = pps_alpha<WIN>(r, px, py, f, I);
-                if (al <= 0.0f) continue;
-                al = fminf(al, ALPHA_MAX);
-                const float tT = __fmul_rn(T, __fsub_rn(1.0f, al));
-                if (tT < T_EPS) break;
-                const float wgt = __fmul_rn(al, T);
-                C0 = fmaf(r.d.y, wgt, C0);
-                C1 = fmaf(r.d.z, wgt, C1);
-                C2 = fmaf(r.d.w, wgt, C2);
-                T = tT;
-                last = (uint32_t)i + 1u;
+            uint32_t last = 0;   // fragments composited
+            if (fits) {
+                for (int i = m / 2 - 1; i >= 0; --i) heap_sift_down(run, i, m);
+                for (int end = m; end > 0;) {
+                    const unsigned long long top = run[0];
+                    --end;
+                    run[0] = run[end];
+                    heap_sift_down(run, 0, end);
+                    run[end] = top;
+                    const uint32_t it = (uint32_t)top;
+                    const Rec r = a.recs[it];
+                    Frag f;
+                    float I;
+                    float al = fminf(pps_alpha<WIN>(r, px, py, f, I), ALPHA_MAX);
+                    const float tT = __fmul_rn(T, __fsub_rn(1.0f, al));
+                    if (tT < T_EPS) break;
+                    const float wgt = __fmul_rn(al, T);
+                    C0 = fmaf(r.d.y, wgt, C0);
+                    C1 = fmaf(r.d.z, wgt, C1);
+                    C2 = fmaf(r.d.w, wgt, C2);
+                    T = tT;
+                    ++last;
+                }
             }
             const int64_t HW = (int64_t)V.W * V.H;
             const int64_t pix = (int64_t)y * V.W + x;
@@ -805,8 +791,9 @@ __global__ void __launch_bounds__(256) pps_bwd_kernel(RenderArgs a) {
         float T = a.T_final[pg];
         float B0 = T * V.bg[0], B1 = T * V.bg[1], B2 = T * V.bg[2];
         const int last = a.n_contrib[pg];
-        const unsigned long long *run = a.cand + a.poff[pg];
-        for (int k = last - 1; k >= 0; --k) {
+        // the composited fragments at [n - last, n), the farthest first
+        const unsigned long long *run = a.cand + a.poff[pg] + a.pcount[pg] - last;
+        for (int k = 0; k < last; ++k) {
             const uint32_t it = (uint32_t)run[k];
             if (it >= a.n_items) {
                 atomicOr(&a.ctl->error, ERR_INDEX);
