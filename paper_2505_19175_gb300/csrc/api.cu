@@ -89,6 +89,17 @@ tri_status ensure(tri_ctx *c, TsDevBuf &b, size_t bytes) {
         if (s_ != TRI_OK) return s_;            \
     } while (0)
 
+// ensure() for buffers that must hold zeros when a kernel first sees them (look-back
+// status words, which the kernels clear again after use): zeroed when (re)allocated.
+static tri_status ensure_zeroed(tri_ctx *c, TsDevBuf &b, size_t bytes, cudaStream_t st) {
+    void *old = b.p;
+    const size_t old_bytes = b.bytes;
+    const tri_status s = ensure(c, b, bytes);
+    if (s != TRI_OK) return s;
+    if (b.p != old || b.bytes != old_bytes) CK(cudaMemsetAsync(b.p, 0, b.bytes, st));
+    return TRI_OK;
+}
+
 template <class T>
 T *P(TsDevBuf &b) {
     return reinterpret_cast<T *>(b.p);
@@ -364,7 +375,7 @@ static tri_status preprocess_impl(tri_ctx *c, const tri_scene *scene, const tri_
     ENSURE(c->tile_count, 4 * (size_t)tiles);
     ENSURE(c->tile_cursor, 4 * (size_t)tiles);
     ENSURE(c->big_tiles, 4 * (size_t)tiles);
-    ENSURE(c->scan_status, 8 * bin_scan_status_words(tiles));
+    if ((s = ensure_zeroed(c, c->scan_status, 8 * bin_scan_status_words(tiles), st)) != TRI_OK) return s;
     ENSURE(c->ranges, sizeof(uint2) * (size_t)tiles);
     ENSURE(c->tile_max, 4 * GROUPS_PER_TILE * (size_t)tiles);
     ENSURE(c->Tfin, 4 * (size_t)pix);
@@ -420,11 +431,8 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
     Ctl *ctl = ctl_of(c);
     if (c->pair_cap <= 0) c->pair_cap = default_pair_cap(c->n_items);
     if ((s = ensure_pairs(c)) != TRI_OK) return s;
-    // counters owned by this step
-    CK(cudaMemsetAsync(&ctl->n_pairs, 0, 3 * 4, st));  // n_pairs, n_pairs_used, overflow
-    CK(cudaMemsetAsync(&ctl->work_counter[2], 0, 4 * 4, st));  // tile queue, (3), big_count, big_next
-    CK(cudaMemsetAsync(&ctl->cta_counter[3], 0, 4, st));
-    CK(cudaMemsetAsync(c->scan_status.p, 0, 8 * bin_scan_status_words(c->total_tiles), st));
+    // the scan and the sort leave their tickets, queues and look-back words at zero
+    // (last_cta_done), and the scan assigns the pair totals
     BinArgs b = bin_args(c);
     // 1. per-tile counts (from tri_preprocess), 2. ranges
     launch_bin_scan(b, st);
@@ -441,9 +449,7 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
             c->pair_cap = cap;
             if ((s = ensure_pairs(c)) != TRI_OK) return s;
             b = bin_args(c);
-            CK(cudaMemsetAsync(&ctl_of(c)->cta_counter[3], 0, 4, st));
-            CK(cudaMemsetAsync(&ctl_of(c)->big_count, 0, 4, st));
-            CK(cudaMemsetAsync(c->scan_status.p, 0, 8 * bin_scan_status_words(c->total_tiles), st));
+            CK(cudaMemsetAsync(&ctl_of(c)->big_count, 0, 4, st));   // queued by the first scan
             launch_bin_scan(b, st);
             if ((s = launch_check(c, "bin_scan")) != TRI_OK) return s;
         }
@@ -488,10 +494,8 @@ static tri_status render_fwd_pps(tri_ctx *c, RenderArgs &r, cudaStream_t st) {
     const int64_t pix = c->total_pix;
     ENSURE(c->pcount, 4 * (size_t)pix);
     ENSURE(c->poff, 8 * (size_t)pix);
-    ENSURE(c->pscan_status, 8 * pps_scan_status_words(pix));
-    CK(cudaMemsetAsync(&ctl->work_counter[3], 0, 4, st));
-    CK(cudaMemsetAsync(&ctl->cta_counter[4], 0, 4, st));
-    CK(cudaMemsetAsync(c->pscan_status.p, 0, 8 * pps_scan_status_words(pix), st));
+    tri_status s;
+    if ((s = ensure_zeroed(c, c->pscan_status, 8 * pps_scan_status_words(pix), st)) != TRI_OK) return s;
     r.zplane = P<float4>(c->zplane);
     r.pcount = P<uint32_t>(c->pcount);
     r.poff = P<unsigned long long>(c->poff);
@@ -535,7 +539,6 @@ static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const
     for (int v = 0; v < c->nviews; ++v) outs[v] = ViewOut{images[v], nullptr};
     if ((s = upload(c, c->outs_fwd.p, outs.data(), sizeof(ViewOut) * c->nviews, c->h_outs_fwd, st)) != TRI_OK)
         return s;
-    CK(cudaMemsetAsync(&ctl_of(c)->work_counter[0], 0, 4, st));
     CK(cudaMemsetAsync(&ctl_of(c)->frag_eval, 0, 16, st));
     RenderArgs r = render_args(c, c->outs_fwd);
     if (c->solid) {
@@ -684,7 +687,6 @@ tri_status tri_render_bwd(tri_ctx *c, const float *const *dL, void *stream) {
     if ((s = upload(c, c->outs_bwd.p, outs.data(), sizeof(ViewOut) * c->nviews, c->h_outs_bwd, st)) != TRI_OK)
         return s;
     CK(cudaMemsetAsync(c->grad2d.p, 0, sizeof(float) * GRAD_FIELDS * (size_t)c->n_items, st));
-    CK(cudaMemsetAsync(&ctl_of(c)->work_counter[1], 0, 4, st));
     RenderArgs r = render_args(c, c->outs_bwd);
     if (c->rec_sort == TRI_SORT_PIXEL) {
         r.poff = P<unsigned long long>(c->poff);

@@ -178,6 +178,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) bin_scan_kernel(BinArgs a) {
         }
         off += c[q];
     }
+    if (last_cta_done(&a.ctl->done[3])) {
+        // every CTA's look-back is over: clear the status words and the ticket
+        const int words = (T + SCAN_TILE - 1) / SCAN_TILE + 1;
+        for (int k = tid; k < words; k += SCAN_THREADS) a.scan_status[k] = 0ull;
+        if (tid == 0) *a.scan_ticket = 0u;
+    }
 }
 
 // ---- per-tile order ----
@@ -386,6 +392,11 @@ __global__ void __launch_bounds__(TSORT_THREADS, 3) tile_sort_kernel(BinArgs a) 
         } else {
             warp_sort_range<16>(a, r.x, n);
         }
+    }
+    if (last_cta_done(&a.ctl->done[2]) && tid == 0) {
+        a.ctl->work_counter[2] = 0u;
+        a.ctl->big_count = 0u;
+        a.ctl->big_next = 0u;
     }
 }
 

@@ -60,6 +60,7 @@ struct Ctl {
     uint32_t work_counter[4];  // render work queues
     uint32_t big_count;        // tiles queued for the CTA-wide sort
     uint32_t big_next;         // next queued tile to sort
+    uint32_t done[8];          // CTAs finished, per self-cleaning kernel (see last_cta_done)
     unsigned long long frag_eval;   // forward: (pixel, entry) evaluations
     unsigned long long frag_kept;   // forward: composited fragments
     unsigned long long pps_total;   // per-pixel sort: candidates of all pixels
@@ -303,6 +304,23 @@ __device__ __forceinline__ uint64_t warp_lookback_excl64(uint64_t *status, uint3
     }
     if (lane == 0) st_relaxed64(&status[idx], LB64_PREFIX | ((excl + agg) & LB64_MASK));
     return excl;
+}
+
+// Called by every thread of every CTA as a kernel's last step: true in the CTA that
+// finishes last (every other CTA has passed this point), which then resets the
+// kernel's queue counters for the next launch; the done counter resets itself. The
+// kernels that use it leave their counters at zero, so no memset precedes them.
+__device__ __forceinline__ bool last_cta_done(uint32_t *done) {
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t d = atomicAdd(done, 1u);
+        s_last = d == gridDim.x - 1;
+        if (s_last) *done = 0u;
+    }
+    __syncthreads();
+    return s_last;
 }
 
 }  // namespace ts

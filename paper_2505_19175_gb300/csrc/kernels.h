@@ -172,7 +172,7 @@ void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st);
 // into offsets (total into ctl->pps_total); fill, sort per pixel and composite; backward.
 void launch_pps_count(const RenderArgs &a, int grid, cudaStream_t st);
 void launch_pps_scan(const RenderArgs &a, cudaStream_t st);
-size_t pps_scan_status_words(int64_t total_pix);
+__host__ __device__ size_t pps_scan_status_words(int64_t total_pix);
 void launch_pps_fwd(const RenderArgs &a, int grid, cudaStream_t st);
 void launch_pps_bwd(const RenderArgs &a, cudaStream_t st);
 

@@ -306,6 +306,7 @@ render_fwd_kernel(RenderArgs a) {
         }
         __syncthreads();
     }
+    if (last_cta_done(&a.ctl->done[0]) && tid == 0) a.ctl->work_counter[0] = 0u;
 }
 
 // Sum 16 per-lane values over each group (transposed butterfly, all groups' records at
@@ -339,7 +340,7 @@ constexpr int TILE_BLOCKS = TILE_PIX / 32;   // 8x4 blocks of a tile
 // builds one list per group (item ids), and walks the lists back to front with the
 // record of the next step already in flight; the warps of a CTA never wait for one
 // another. Each group's record gradient goes to the item's gradient record with one
-// 7-lane global vector reduction per step.
+// vector reduction per lane per step.
 template <int WIN>
 __global__ void __launch_bounds__(BWD_THREADS, BWD_CTAS)
 render_bwd_kernel(RenderArgs a) {
@@ -531,6 +532,7 @@ render_bwd_kernel(RenderArgs a) {
             __syncwarp();
         }
     }
+    if (last_cta_done(&a.ctl->done[1]) && threadIdx.x == 0) a.ctl->work_counter[1] = 0u;
 }
 
 static int occupancy(const void *fn, int threads) {
@@ -719,7 +721,10 @@ __global__ void __launch_bounds__(REN_THREADS) pps_tile_kernel(RenderArgs a) {
         }
         __syncthreads();   // every thread has read s_tile before it changes
     }
+    if (last_cta_done(&a.ctl->done[PASS == 0 ? 4 : 5]) && tid == 0) a.ctl->work_counter[PASS == 0 ? 0 : 3] = 0u;
 }
+
+__host__ __device__ size_t pps_scan_status_words(int64_t total_pix) { return (size_t)((total_pix + 1023) / 1024) + 1; }
 
 // Exclusive scan of the per-pixel counts into 64-bit offsets (single pass, decoupled
 // look-back over 1024-count blocks, CTA order by ticket); the total into ctl->pps_total.
@@ -768,9 +773,14 @@ __global__ void __launch_bounds__(256) pps_scan_kernel(RenderArgs a) {
         if (p0 + q < a.total_pix) a.poff[p0 + q] = off;
         off += c[q];
     }
+    if (last_cta_done(&a.ctl->done[6])) {
+        // every CTA's look-back is over: clear the status words and the ticket
+        const int64_t words = (int64_t)pps_scan_status_words(a.total_pix);
+        for (int64_t k = tid; k < words; k += 256) a.pscan_status[k] = 0ull;
+        if (tid == 0) a.ctl->cta_counter[4] = 0u;
+    }
 }
 
-size_t pps_scan_status_words(int64_t total_pix) { return (size_t)((total_pix + 1023) / 1024) + 1; }
 
 // Backward of the per-pixel sort: one thread per pixel, its sorted run from the last
 // composited fragment back to the first.
