@@ -102,8 +102,8 @@ typedef struct {
     int32_t overflow;      /* 1 when n_pairs > pair_capacity (pairs were dropped) */
     int32_t device_error;  /* bit 0: a bounded spin gave up; bit 1: index check failed */
     int32_t n_views, total_tiles;
-    int64_t frag_evaluated;   /* last forward: (pixel, list entry) window evaluations */
-    int64_t frag_composited;  /* last forward: fragments composited */
+    int64_t frag_evaluated;   /* forwards since the last tri_preprocess: (pixel, list entry) window evaluations */
+    int64_t frag_composited;  /* forwards since the last tri_preprocess: fragments composited */
 } tri_ctx_info;
 
 /* Create a context on CUDA device `device`. Allocates nothing until first use.

@@ -539,7 +539,6 @@ static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const
     for (int v = 0; v < c->nviews; ++v) outs[v] = ViewOut{images[v], nullptr};
     if ((s = upload(c, c->outs_fwd.p, outs.data(), sizeof(ViewOut) * c->nviews, c->h_outs_fwd, st)) != TRI_OK)
         return s;
-    CK(cudaMemsetAsync(&ctl_of(c)->frag_eval, 0, 16, st));
     RenderArgs r = render_args(c, c->outs_fwd);
     if (c->solid) {
         r.kmask = nullptr;
