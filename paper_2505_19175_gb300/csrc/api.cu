@@ -177,14 +177,25 @@ namespace {
 // stages the pageable source, so the caller may reuse it at once. Under capture the
 // copy node must read memory that outlives the call: the context's pinned buffer,
 // which a replay re-reads (the tables of the most recent captured call of this kind).
-tri_status upload(tri_ctx *c, void *dst, const void *src, size_t bytes, void *pinned, cudaStream_t st) {
+// The per-view output pointers of a render call: by value in the launch for a few views
+// (no copy), through the page-locked host copy while the stream is captured (a replay
+// reads what was written there before it), else copied to the device table.
+static tri_status set_outs(tri_ctx *c, RenderArgs &r, const std::vector<ViewOut> &outs, TsDevBuf &dev, ViewOut *pinned,
+                           cudaStream_t st) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(st, &cs));
+    const int n = (int)outs.size();
     if (cs == cudaStreamCaptureStatusActive) {
-        memcpy(pinned, src, bytes);
-        CK(cudaMemcpyAsync(dst, pinned, bytes, cudaMemcpyHostToDevice, st));
+        memcpy(pinned, outs.data(), sizeof(ViewOut) * n);
+        r.outs = pinned;
+        r.outs_by_value = 0;
+    } else if (n <= OUTS_INLINE) {
+        for (int v = 0; v < n; ++v) r.outs_inline[v] = outs[v];
+        r.outs_by_value = 1;
     } else {
-        CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dev.p, outs.data(), sizeof(ViewOut) * n, cudaMemcpyHostToDevice, st));
+        r.outs = P<ViewOut>(dev);
+        r.outs_by_value = 0;
     }
     return TRI_OK;
 }
@@ -380,9 +391,20 @@ static tri_status preprocess_impl(tri_ctx *c, const tri_scene *scene, const tri_
     ENSURE(c->tile_max, 4 * GROUPS_PER_TILE * (size_t)tiles);
     ENSURE(c->Tfin, 4 * (size_t)pix);
     ENSURE(c->ncontrib, 4 * (size_t)pix);
-    if ((s = upload(c, c->views_d.p, views.data(), sizeof(ViewDev) * nviews, c->h_views, st)) != TRI_OK) return s;
-    CK(cudaMemsetAsync(c->ctl.p, 0, sizeof(Ctl), st));
-    CK(cudaMemsetAsync(c->tile_count.p, 0, 4 * (size_t)tiles, st));
+    {
+        // the view table: by value, or, while the stream is captured, through the pinned
+        // copy that a replay reads at run time
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(st, &cs));
+        const ViewDev *pinned = nullptr;
+        if (cs == cudaStreamCaptureStatusActive) {
+            memcpy(c->h_views, views.data(), sizeof(ViewDev) * nviews);
+            pinned = c->h_views;
+        }
+        launch_step_init(views.data(), pinned, nviews, P<ViewDev>(c->views_d), ctl_of(c), P<uint32_t>(c->tile_count),
+                         tiles, st);
+        if ((s = launch_check(c, "step_init_kernel")) != TRI_OK) return s;
+    }
     if (M > 0) {
         PreArgs a;
         a.verts = scene->verts;
@@ -537,9 +559,8 @@ static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const
     begin_call(c, st);
     std::vector<ViewOut> outs(c->nviews);
     for (int v = 0; v < c->nviews; ++v) outs[v] = ViewOut{images[v], nullptr};
-    if ((s = upload(c, c->outs_fwd.p, outs.data(), sizeof(ViewOut) * c->nviews, c->h_outs_fwd, st)) != TRI_OK)
-        return s;
     RenderArgs r = render_args(c, c->outs_fwd);
+    if ((s = set_outs(c, r, outs, c->outs_fwd, c->h_outs_fwd, st)) != TRI_OK) return s;
     if (c->solid) {
         r.kmask = nullptr;
         if (ids) {
@@ -683,10 +704,9 @@ tri_status tri_render_bwd(tri_ctx *c, const float *const *dL, void *stream) {
     std::vector<ViewOut> outs(c->nviews);
     for (int v = 0; v < c->nviews; ++v) outs[v] = ViewOut{nullptr, dL[v]};
     ENSURE(c->grad2d, sizeof(float) * GRAD_FIELDS * (size_t)c->n_items);
-    if ((s = upload(c, c->outs_bwd.p, outs.data(), sizeof(ViewOut) * c->nviews, c->h_outs_bwd, st)) != TRI_OK)
-        return s;
     CK(cudaMemsetAsync(c->grad2d.p, 0, sizeof(float) * GRAD_FIELDS * (size_t)c->n_items, st));
     RenderArgs r = render_args(c, c->outs_bwd);
+    if ((s = set_outs(c, r, outs, c->outs_bwd, c->h_outs_bwd, st)) != TRI_OK) return s;
     if (c->rec_sort == TRI_SORT_PIXEL) {
         r.poff = P<unsigned long long>(c->poff);
         r.pcount = P<uint32_t>(c->pcount);

@@ -37,6 +37,12 @@ struct PreBwdArgs {
     int window = WIN_POWER;
 };
 
+// Start of a pipeline run in one kernel: the view table into views_d, the control
+// block and the per-tile counts to zero. The table is passed by value, or, with
+// `pinned`, read at run time from that page-locked host copy (what a captured graph
+// does, so that its replays pick up the cameras written there before each launch).
+void launch_step_init(const ViewDev *views, const ViewDev *pinned, int nviews, ViewDev *views_d, Ctl *ctl,
+                      uint32_t *tile_count, int tiles, cudaStream_t st);
 void launch_preprocess_fwd(const PreArgs &a, cudaStream_t st);
 void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st);
 
@@ -134,9 +140,13 @@ typedef uint32_t kmask_t;            // one bit per group of the tile
 typedef unsigned long long kmask_t;
 #endif
 
+constexpr int OUTS_INLINE = 4;   // views whose output pointers a launch can carry by value
+
 struct RenderArgs {
     const ViewDev *views;
-    const ViewOut *outs;
+    const ViewOut *outs;            // device table, or a page-locked host copy (captured graphs)
+    ViewOut outs_inline[OUTS_INLINE];   // used instead of `outs` when outs_by_value
+    int outs_by_value = 0;
     int nviews;
     int total_tiles;
     const uint2 *ranges;
@@ -166,6 +176,9 @@ struct RenderArgs {
     unsigned long long *pscan_status = nullptr;
     int64_t total_pix = 0;
 };
+__device__ __forceinline__ ViewOut view_out(const RenderArgs &a, int vw) {
+    return a.outs_by_value ? a.outs_inline[vw] : a.outs[vw];
+}
 void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st, bool solid = false);
 void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st);
 // per-pixel sort: count the candidates (alpha >= 1/255) of every pixel; scan the counts

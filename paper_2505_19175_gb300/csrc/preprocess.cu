@@ -447,6 +447,52 @@ preprocess_bwd_kernel(PreBwdArgs a) {
     }
 }
 
+template <int NV>
+struct InitArgs {
+    ViewDev views[NV];
+    const ViewDev *pinned;   // if set: the table is read from here instead
+    int nviews, tiles;
+    ViewDev *views_d;
+    uint32_t *ctl;
+    uint32_t *tile_count;
+};
+
+template <int NV>
+__global__ void __launch_bounds__(256) step_init_kernel(const __grid_constant__ InitArgs<NV> a) {
+    constexpr int vw = (int)(sizeof(ViewDev) / 4), cw = (int)(sizeof(Ctl) / 4);
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(a.pinned ? a.pinned : a.views);
+    const int n = max(max(a.nviews * vw, cw), a.tiles);
+    for (int k = blockIdx.x * 256 + threadIdx.x; k < n; k += gridDim.x * 256) {
+        if (k < a.nviews * vw) reinterpret_cast<uint32_t *>(a.views_d)[k] = src[k];
+        if (k < cw) a.ctl[k] = 0u;
+        if (k < a.tiles) a.tile_count[k] = 0u;
+    }
+}
+
+template <int NV>
+static void step_init(const ViewDev *views, const ViewDev *pinned, int nviews, ViewDev *views_d, Ctl *ctl,
+                      uint32_t *tile_count, int tiles, cudaStream_t st) {
+    InitArgs<NV> a;
+    if (!pinned)
+        for (int v = 0; v < nviews; ++v) a.views[v] = views[v];
+    a.pinned = pinned;
+    a.nviews = nviews;
+    a.tiles = tiles;
+    a.views_d = views_d;
+    a.ctl = reinterpret_cast<uint32_t *>(ctl);
+    a.tile_count = tile_count;
+    const int words = max(max(nviews * (int)(sizeof(ViewDev) / 4), (int)(sizeof(Ctl) / 4)), tiles);
+    int g = (words + 255) / 256;
+    if (g > 304) g = 304;
+    step_init_kernel<NV><<<g, 256, 0, st>>>(a);
+}
+
+void launch_step_init(const ViewDev *views, const ViewDev *pinned, int nviews, ViewDev *views_d, Ctl *ctl,
+                      uint32_t *tile_count, int tiles, cudaStream_t st) {
+    if (pinned || nviews <= 4) step_init<4>(views, pinned, nviews, views_d, ctl, tile_count, tiles, st);
+    else step_init<MAX_VIEWS>(views, pinned, nviews, views_d, ctl, tile_count, tiles, st);
+}
+
 template <bool ZP>
 static void launch_fwd_zp(const PreArgs &a, int grid, size_t smem, cudaStream_t st) {
     const bool sg = a.window == WIN_SIGMOID;

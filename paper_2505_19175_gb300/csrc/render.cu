@@ -286,7 +286,7 @@ render_fwd_kernel(RenderArgs a) {
         if (inside) {
             const int64_t HW = (int64_t)V.W * V.H;
             const int64_t pix = (int64_t)y * V.W + x;
-            float *img = a.outs[vw].image;
+            float *img = view_out(a, vw).image;
             img[pix] = fmaf(T, V.bg[0], C0);
             img[HW + pix] = fmaf(T, V.bg[1], C1);
             img[2 * HW + pix] = fmaf(T, V.bg[2], C2);
@@ -379,7 +379,7 @@ render_bwd_kernel(RenderArgs a) {
             const int64_t pb = V->pix_base;
             T = a.T_final[pb + pix];
             last = (uint32_t)a.n_contrib[pb + pix];
-            const float *dL = a.outs[vw].dL;
+            const float *dL = view_out(a, vw).dL;
             g0 = dL[pix];
             g1 = dL[HW + pix];
             g2 = dL[2 * HW + pix];
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(REN_THREADS) pps_tile_kernel(RenderArgs a) {
             }
             const int64_t HW = (int64_t)V.W * V.H;
             const int64_t pix = (int64_t)y * V.W + x;
-            float *img = a.outs[vw].image;
+            float *img = view_out(a, vw).image;
             img[pix] = fmaf(T, V.bg[0], C0);
             img[HW + pix] = fmaf(T, V.bg[1], C1);
             img[2 * HW + pix] = fmaf(T, V.bg[2], C2);
@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(256) pps_bwd_kernel(RenderArgs a) {
         const int x = (int)(pix % V.W), y = (int)(pix / V.W);
         const float px = (float)x + 0.5f, py = (float)y + 0.5f;
         const int64_t HW = (int64_t)V.W * V.H;
-        const float *dL = a.outs[vw].dL;
+        const float *dL = view_out(a, vw).dL;
         const float g0 = dL[pix], g1 = dL[HW + pix], g2 = dL[2 * HW + pix];
         float T = a.T_final[pg];
         float B0 = T * V.bg[0], B1 = T * V.bg[1], B2 = T * V.bg[2];
