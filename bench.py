@@ -184,8 +184,8 @@ def run_reference(args, rank, world):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 STAGES = ("preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd")
-# preprocess, bin_scan, bin_scatter, tile_sort, render_fwd, loss, render_bwd, preprocess_bwd
-KERNELS_PER_STEP = 8
+# step_init, preprocess, bin_scan, bin_scatter, tile_sort, render_fwd, loss, render_bwd, preprocess_bwd
+KERNELS_PER_STEP = 9
 
 
 def run_sigmoid_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds, capture, timed):
