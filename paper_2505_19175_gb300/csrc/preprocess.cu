@@ -255,10 +255,21 @@ preprocess_bwd_kernel(PreBwdArgs a) {
     constexpr int nk = (DEG + 1) * (DEG + 1);
     stage_floats<PRE_BWD_THREADS>(s_v, a.verts + i0 * 9, cnt * 9);
     stage_records<nk * 3, PRE_BWD_THREADS>(s_sh, a.sh + i0 * nk * 3, cnt);
-    cp_async_wait_all();
-    __syncthreads();
     const int64_t i = i0 + tid;
     const bool alive = tid < cnt;
+    // one view: its tile count and gradient record load while the staging completes
+    uint32_t nt1 = 0;
+    float4 R0 = make_float4(0.f, 0.f, 0.f, 0.f), R1 = R0, R2 = R0, R3 = R0;
+    if (!MULTI && alive) {
+        nt1 = __ldg(a.ntiles + i);
+        const float4 *gp = reinterpret_cast<const float4 *>(a.grad2d + i * GRAD_FIELDS);
+        R0 = __ldg(gp);
+        R1 = __ldg(gp + 1);
+        R2 = __ldg(gp + 2);
+        R3 = __ldg(gp + 3);
+    }
+    cp_async_wait_all();
+    __syncthreads();
     float v[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) v[k] = s_v[tid * 9 + k];
@@ -283,7 +294,7 @@ preprocess_bwd_kernel(PreBwdArgs a) {
     // are visited
     uint64_t vis = 0;
     if (!MULTI) {
-        vis = alive && __ldg(a.ntiles + i) != 0u ? 1ull : 0ull;
+        vis = nt1 != 0u ? 1ull : 0ull;
     } else if (alive) {
         for (int v0 = 0; v0 < a.nviews; v0 += 8) {
             uint32_t nt[8];
@@ -298,7 +309,8 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         const int vw = __ffsll((long long)vis) - 1;
         const int64_t m = (int64_t)vw * a.n + i;
         const float4 *gp = reinterpret_cast<const float4 *>(a.grad2d + m * GRAD_FIELDS);
-        const float4 G0 = gp[0], G1 = gp[1], G2 = gp[2], G3 = gp[3];
+        const float4 G0 = MULTI ? gp[0] : R0, G1 = MULTI ? gp[1] : R1, G2 = MULTI ? gp[2] : R2,
+                     G3 = MULTI ? gp[3] : R3;
         const ViewDev &V = s_view[vw];
         Geom g;
         item_geometry<false>(v, V, g);
