@@ -206,7 +206,7 @@ tri_status ensure_pairs(tri_ctx *c) {
     ENSURE(c->kv, 8 * (size_t)c->pair_cap);
     ENSURE(c->kv_tmp, 8 * (size_t)c->pair_cap);
     ENSURE(c->items, 4 * (size_t)c->pair_cap);
-    ENSURE(c->kmask, sizeof(kmask_t) * (size_t)c->pair_cap);
+    ENSURE(c->kmask, 4 * KM_WORDS * (size_t)c->pair_cap);
     return TRI_OK;
 }
 
@@ -499,7 +499,7 @@ static RenderArgs render_args(tri_ctx *c, TsDevBuf &outs) {
     r.n_contrib = P<int32_t>(c->ncontrib);
     r.tile_max = P<uint32_t>(c->tile_max);
     r.grad2d = P<float>(c->grad2d);
-    r.kmask = P<kmask_t>(c->kmask);
+    r.kmask = P<uint32_t>(c->kmask);
     r.stat_w = r.stat_n = nullptr;
     r.n_per_view = c->scene.n;
     r.window = c->rec_window;

@@ -127,18 +127,15 @@ void launch_size_reg(const float *verts, int64_t n, float weight, float *loss, f
                      cudaStream_t st);
 
 // ---- rendering ----
-// Render groups: lanes of a warp that walk one backward list together (a 2x4 block of
-// pixels for 8, 2x2 for 4); the forward marks per pair which groups composited it.
+// Render groups: the lanes of a warp that walk one backward list together (2x1 pixels
+// for 2, 2x2 for 4, 2x4 for 8); the forward marks per pair which groups composited it,
+// as KM_WORDS 32-bit words per pair (bit (32 / GROUP) b + g: group g of 8x4 block b).
 #ifndef KM_GROUP
 #define KM_GROUP 4
 #endif
 constexpr int GROUP = KM_GROUP;
 constexpr int GROUPS_PER_TILE = TILE_PIX / GROUP;
-#if KM_GROUP == 8
-typedef uint32_t kmask_t;            // one bit per group of the tile
-#else
-typedef unsigned long long kmask_t;
-#endif
+constexpr int KM_WORDS = GROUPS_PER_TILE / 32;
 
 constexpr int OUTS_INLINE = 4;   // views whose output pointers a launch can carry by value
 
@@ -161,7 +158,7 @@ struct RenderArgs {
     int32_t *ids = nullptr;         // solid render: [total pixels] triangle id of the winner, -1
     int64_t n_per_view = 0;         // triangles per view (item m = view * n_per_view + triangle)
     int window = WIN_POWER;         // window kind of the records
-    kmask_t *kmask;                 // [pairs]: bit (32 / GROUP) w + g = group g of warp w composited the pair (forward
+    uint32_t *kmask;                // [pairs][KM_WORDS]: bit (32 / GROUP) w + g = group g of warp w composited the pair (forward
                                     // writes it when set; the backward requires it)
     float *grad2d;                  // backward: [items][16]
     uint32_t n_items;               // bound of the item ids in `items`

@@ -2,7 +2,8 @@
 //
 // A tile is 16x16 pixels, one thread per pixel, cut into eight 8x4 blocks (one warp
 // each) and each block into groups of GROUP lanes (eight 2x2 groups of 4 lanes by
-// default; four 2x4 groups of 8 with KM_GROUP=8). Tiles are taken from device
+// default; 2x4 groups of 8 or 2x1 groups of 2 with KM_GROUP=8 or 2, both measured
+// slower on the patches workload). Tiles are taken from device
 // work queues by persistent grids, so a launch serves any mix of views and resolutions.
 //
 // Forward (Sec. 3.1, the rendering equation of prior splatting work): one CTA of 256
@@ -29,7 +30,6 @@ namespace ts {
 constexpr int REN_THREADS = TILE_PIX;
 constexpr int WGROUPS = 32 / GROUP;               // groups per warp
 constexpr int GROUPS = GROUPS_PER_TILE;           // groups per tile
-constexpr int KM_WORDS = (int)sizeof(kmask_t) / 4;   // 32-bit words of a pair's group mask
 // word and bit offset of warp w's groups in the pair's group mask
 #define KM_WORD(w) ((w) / (32 / WGROUPS))
 #define KM_SHIFT(w) (WGROUPS * ((w) % (32 / WGROUPS)))
@@ -61,6 +61,10 @@ __device__ __forceinline__ void block_pixel(int w, int lane, int &lx, int &ly) {
     if (GROUP == 8) {
         lx = ((w & 1) << 3) | ((lane >> 3) << 1) | (lane & 1);
         ly = ((w >> 1) << 2) | ((lane >> 1) & 3);
+    } else if (GROUP == 2) {
+        const int g = lane >> 1;
+        lx = ((w & 1) << 3) | ((g & 3) << 1) | (lane & 1);
+        ly = ((w >> 1) << 2) | (g >> 2);
     } else {
         const int g = lane >> 2;
         lx = ((w & 1) << 3) | ((g & 3) << 1) | (lane & 1);
@@ -265,10 +269,8 @@ render_fwd_kernel(RenderArgs a) {
                 __syncthreads();
                 if (a.kmask) {
                     if (idx < end) {
-                        kmask_t km = 0;
 #pragma unroll
-                        for (int q = 0; q < KM_WORDS; ++q) km |= (kmask_t)s_km[q][tid] << (32 * q);
-                        a.kmask[idx] = km;
+                        for (int q = 0; q < KM_WORDS; ++q) a.kmask[(size_t)idx * KM_WORDS + q] = s_km[q][tid];
                     }
 #pragma unroll
                     for (int q = 0; q < KM_WORDS; ++q) s_km[q][tid] = 0u;
@@ -325,7 +327,7 @@ __device__ __forceinline__ void group_reduce16(float (&v)[16], int lane) {
     }
 }
 
-constexpr int BWD_CHUNK = GROUP == 8 ? 256 : 128;   // pairs whose masks a warp scans per list build
+constexpr int BWD_CHUNK = GROUP == 8 ? 256 : (GROUP == 4 ? 128 : 64);   // pairs whose masks a warp scans per list build
 #ifndef BWD_THREADS
 #define BWD_THREADS 256          // threads of a backward CTA (its warps work independently)
 #endif
@@ -391,7 +393,7 @@ render_bwd_kernel(RenderArgs a) {
             const int cstart = max(0, cend - BWD_CHUNK);
             const int nb = cend - cstart;
             // the pairs of this chunk that each group composited, in tile order
-            kmask_t m[BWD_CHUNK / 32];
+            uint32_t m[BWD_CHUNK / 32];
             uint32_t itv[BWD_CHUNK / 32];
 #pragma unroll
             for (int q = 0; q < BWD_CHUNK / 32; ++q) {
@@ -399,7 +401,8 @@ render_bwd_kernel(RenderArgs a) {
                 m[q] = 0u;
                 itv[q] = 0u;
                 if (jj < nb) {
-                    m[q] = a.kmask[start + cstart + jj];
+                    // the word of this block's groups
+                    m[q] = a.kmask[(size_t)(start + cstart + jj) * KM_WORDS + KM_WORD(blk)];
                     itv[q] = a.items[start + cstart + jj];
                 }
             }
@@ -409,7 +412,7 @@ render_bwd_kernel(RenderArgs a) {
             for (int e = 0; e < WGROUPS; ++e) n[e] = 0;
 #pragma unroll
             for (int q = 0; q < BWD_CHUNK / 32; ++q) {
-                const uint32_t mq = (uint32_t)(m[q] >> (WGROUPS * blk)) & ((1u << WGROUPS) - 1u);
+                const uint32_t mq = (m[q] >> KM_SHIFT(blk)) & (WGROUPS == 32 ? 0xffffffffu : ((1u << WGROUPS) - 1u));
                 uint32_t it = itv[q];
                 if (mq && it >= a.n_items) {
                     atomicOr(&a.ctl->error, ERR_INDEX);
@@ -524,8 +527,11 @@ render_bwd_kernel(RenderArgs a) {
                     float *dst = a.grad2d + (size_t)item * GRAD_FIELDS + (16 / GROUP) * gl;
                     if (GROUP == 8) {
                         if ((bk & gmask) && gl < 7) red_add_v2(dst, gv[0], gv[1]);
-                    } else {
+                    } else if (GROUP == 4) {
                         if (bk & gmask) red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
+                    } else if (bk & gmask) {
+                        red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
+                        red_add_v4(dst + 4, gv[4], gv[5], gv[6], gv[7]);
                     }
                 }
             }
