@@ -1,0 +1,83 @@
+"""Pipeline calls repeated without their predecessors give the same results: the scan,
+sort and render kernels leave their queues and look-back words at zero for the next
+launch, so a second tri_bin_sort, tri_render_fwd or tri_render_bwd after one
+tri_preprocess must match the first one bit for bit (the backward up to the order of
+its atomic additions)."""
+import numpy as np
+import pytest
+
+from paper_2505_19175_gb300 import synth
+from gpu_util import gpu_backward, gpu_forward
+
+pytestmark = pytest.mark.gpu
+
+
+def _grads(ctx, st, g):
+    return gpu_backward(ctx, st, [g])
+
+
+def test_repeated_stages_match():
+    import torch
+    from paper_2505_19175_gb300.renderer import new_images
+    scene = synth.random_scene(800, seed=91, deg=2, size=(0.05, 0.6))
+    cam = synth.camera_identity(96, 80)
+    imgs, T, nc, ctx, st = gpu_forward(scene, [cam])
+    items = ctx.debug("pair_items").copy()
+    # sort again: same lists
+    ctx.bin_sort(sync=True)
+    np.testing.assert_array_equal(ctx.debug("pair_items"), items)
+    # render twice: same images
+    for _ in range(2):
+        out = new_images([cam])
+        ctx.render_fwd(out)
+        ctx.check()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out[0].cpu().numpy().astype(np.float64), imgs[0])
+    # backward twice: the second sees freshly cleared gradient records
+    g = np.random.default_rng(5).standard_normal((3, cam.H, cam.W))
+    a = _grads(ctx, st, g)
+    b = _grads(ctx, st, g)
+    for k in a:
+        np.testing.assert_allclose(a[k], b[k], rtol=1e-5, atol=1e-6 * (np.abs(a[k]).max() + 1e-30))
+
+
+def test_captured_step_replays_match_eager():
+    """A CUDA graph of the whole step replayed several times gives the eager results."""
+    import torch
+    from paper_2505_19175_gb300 import native as N
+    from paper_2505_19175_gb300.renderer import Context, SceneTensors, new_images, loss_l1
+    scene = synth.random_scene(600, seed=92, deg=1, size=(0.05, 0.5))
+    cam = synth.camera_identity(80, 64)
+    st = SceneTensors.from_numpy(scene)
+    tgt = torch.as_tensor(synth.target_image(cam.H, cam.W, seed=3)).cuda()
+    ctx = Context()
+    ctx.preprocess(st, [cam])
+    ctx.reserve(int(ctx.bin_sort(sync=True) * 1.5) + 1024)
+    imgs = new_images([cam])
+    dv, dsh = torch.empty_like(st.verts), torch.empty_like(st.sh)
+    do, ds = torch.empty_like(st.opacity), torch.empty_like(st.sigma)
+    state = {}
+
+    def step():
+        ctx.preprocess(st, [cam])
+        ctx.bin_sort(sync=False)
+        ctx.render_fwd(imgs)
+        loss, grad = loss_l1(imgs[0], tgt)
+        state["grad"] = grad
+        ctx.render_bwd([grad])
+        ctx.preprocess_bwd(dv, dsh, do, ds)
+
+    step()
+    torch.cuda.synchronize()
+    want = [x.clone() for x in (imgs[0], dv, dsh, do, ds)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for _ in range(3):
+        g.replay()
+        torch.cuda.synchronize()
+        ctx.check()
+        got = (imgs[0], dv, dsh, do, ds)
+        torch.testing.assert_close(got[0], want[0], rtol=0, atol=0)
+        for x, y in zip(got[1:], want[1:]):
+            torch.testing.assert_close(x, y, rtol=1e-5, atol=1e-6 * float(y.abs().max()) + 1e-30)
