@@ -208,6 +208,10 @@ def run_sigmoid_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds,
         ctx_s.render_bwd([grad])
         ctx_s.preprocess_bwd(dv, dsh, do, ds)
 
+    ctx_s.set_fragment_counting(True)
+    step_sigmoid()
+    info_s = ctx_s.check()
+    ctx_s.set_fragment_counting(False)
     for _ in range(3):
         step_sigmoid()
     g_sig = capture(step_sigmoid)
@@ -215,9 +219,9 @@ def run_sigmoid_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds,
         g_sig.replay()
     ev_sig = timed(g_sig, args.steps)
     torch.cuda.synchronize()
-    info_s = ctx_s.check()
+    n_pairs_s = int(ctx_s.check().n_pairs)
     sig_its = args.steps / (float(sum(a.elapsed_time(b) for a, b in ev_sig)) / 1000.0)
-    sigmoid_line = {"it_per_s": round(sig_its, 2), "pairs": int(info_s.n_pairs),
+    sigmoid_line = {"it_per_s": round(sig_its, 2), "pairs": n_pairs_s,
                     "frag_composited": int(info_s.frag_composited),
                     "workload": "the same fwd+bwd step with the sigmoid window of Eq. indicator2"}
     del g_sig
@@ -316,13 +320,17 @@ def run_ours(args, rank, world):
     for _ in range(args.warmup):
         step()
     info = ctx.check()
-    # fragments of the workload: per pixel, its last composited list entry + 1
+    # fragments of the workload: per pixel, its last composited list entry + 1; and the
+    # forward's own counts of evaluated and composited entries (one counted forward)
     t_fin = [torch.empty((cam.H, cam.W), device="cuda")]
     n_con = [torch.empty((cam.H, cam.W), device="cuda", dtype=torch.int32)]
+    ctx.set_fragment_counting(True)
     ctx.preprocess(st, [cam])
     ctx.bin_sort(sync=False)
     ctx.render_fwd(imgs, t_fin, n_con)
     frags = int(n_con[0].sum(dtype=torch.int64).item())
+    info_counted = ctx.check()
+    ctx.set_fragment_counting(False)
     torch.cuda.synchronize()
 
     # the whole step as one CUDA graph (buffers are sized by the warm-up; capture allocates nothing)
@@ -457,7 +465,7 @@ def run_ours(args, rank, world):
     # stage time, against that pipe's peak at the measured maximum clock; the binding
     # pipe is the one with the largest fraction
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    F_eval, F_kept = int(info.frag_evaluated), int(info.frag_composited)
+    F_eval, F_kept = int(info_counted.frag_evaluated), int(info_counted.frag_composited)
 
     def pipe_roofline(kernel):
         t = med[STAGES.index(kernel)] / 1e3
@@ -582,6 +590,9 @@ def run_multiview(steps: int, warmup: int, n_tris: int = 3_000_000, n_views: int
     info = ctx.check()
     ms_fwd = timed(warmup + steps, True)
     info_f = ctx.check()
+    ctx.set_fragment_counting(True)
+    step(warmup + 2 * steps)
+    info = ctx.check()
     return {"workload": f"{n_tris} tris SH3 on 16 shells, {n_views} ring views {W}x{H} per step, ring offset "
                         "re-drawn every step, fwd+bwd with L1 loss; params 708 MB > L2",
             "it_per_s": round(1000.0 * steps / float(ms.sum()), 3), "ms_per_step_median": round(float(np.median(ms)), 3),

@@ -503,6 +503,7 @@ static RenderArgs render_args(tri_ctx *c, TsDevBuf &outs) {
     r.stat_w = r.stat_n = nullptr;
     r.n_per_view = c->scene.n;
     r.window = c->rec_window;
+    r.count_frags = c->count_frags;
     r.n_items = (uint32_t)c->n_items;
     r.ctl = ctl_of(c);
     return r;
@@ -615,6 +616,12 @@ tri_status tri_set_window(tri_ctx *c, int window) {
         return fail(c, TRI_ERR_INVALID_ARG, "unknown window kind");
     c->window = window;
     c->stage = 0;   // records of the other kind are stale
+    return TRI_OK;
+}
+
+tri_status tri_set_fragment_counting(tri_ctx *c, int on) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    c->count_frags = on ? 1 : 0;
     return TRI_OK;
 }
 

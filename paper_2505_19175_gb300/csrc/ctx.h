@@ -28,6 +28,7 @@ struct tri_ctx {
     int window = 0;      // window kind for the next tri_preprocess (tri_set_window)
     int rec_window = 0;  // window kind of the current records
     int sort = 0;        // compositing order for the next tri_preprocess (tri_set_sort)
+    int count_frags = 0; // forwards count their fragments (tri_set_fragment_counting)
     int rec_sort = 0;    // compositing order of the current records
     uint64_t cand_cap = 0;   // per-pixel sort: candidate capacity
     long fault_alloc = 0, fault_slow_ms = 0, n_allocs = 0;   // TRI_FAULT injection (tests)

@@ -158,6 +158,7 @@ struct RenderArgs {
     int32_t *ids = nullptr;         // solid render: [total pixels] triangle id of the winner, -1
     int64_t n_per_view = 0;         // triangles per view (item m = view * n_per_view + triangle)
     int window = WIN_POWER;         // window kind of the records
+    int count_frags = 0;            // forward: count evaluated / composited fragments into the control block
     uint32_t *kmask;                // [pairs][KM_WORDS]: bit (32 / GROUP) w + g = group g of warp w composited the pair (forward
                                     // writes it when set; the backward requires it)
     float *grad2d;                  // backward: [items][16]

@@ -152,7 +152,8 @@ __device__ __forceinline__ uint32_t group_max(uint32_t v) {
 // The forward walks one list per warp (measured faster than per-half lists here: the
 // early exit on transmittance keeps its lists short); it records per group of 8 lanes
 // which pairs were composited, for the backward's per-group lists.
-template <bool SOLID, int WIN>
+// COUNT: also count evaluated and composited fragments (tri_ctx_info).
+template <bool SOLID, int WIN, bool COUNT>
 __global__ void __launch_bounds__(REN_THREADS)
 render_fwd_kernel(RenderArgs a) {
     __shared__ Rec s_rec[REN_THREADS];
@@ -218,7 +219,7 @@ render_fwd_kernel(RenderArgs a) {
                 for (int k = c; k < kend; ++k) {
                     if (done) break;
                     const int j = L[k];
-                    ++n_eval;
+                    if (COUNT) ++n_eval;
                     const float4 ra = s_rec[j].a, rb = s_rec[j].b, rc = s_rec[j].c;
                     const Frag f = eval_lines(ra, rb, rc, px, py);
                     if ((SOLID || WIN == WIN_POWER) && f.ratio <= 0.0f) continue;
@@ -229,7 +230,7 @@ render_fwd_kernel(RenderArgs a) {
                         C2 = rd.w;
                         T = 0.0f;
                         last = b0 - start + (uint32_t)j + 1u;
-                        ++n_kept;
+                        if (COUNT) ++n_kept;
                         done = true;
                         break;
                     }
@@ -253,7 +254,7 @@ render_fwd_kernel(RenderArgs a) {
                     C2 = fmaf(rd.w, wgt, C2);
                     T = tT;
                     last = b0 - start + (uint32_t)j + 1u;
-                    ++n_kept;
+                    if (COUNT) ++n_kept;
                     kept |= 1u << (k - c);
                 }
                 if (a.kmask) {
@@ -299,8 +300,8 @@ render_fwd_kernel(RenderArgs a) {
                                                : -1;
         }
         const uint32_t gm = group_max(last);
-        const uint32_t we = __reduce_add_sync(0xffffffffu, n_eval);
-        const uint32_t wk = __reduce_add_sync(0xffffffffu, n_kept);
+        const uint32_t we = COUNT ? __reduce_add_sync(0xffffffffu, n_eval) : 0u;
+        const uint32_t wk = COUNT ? __reduce_add_sync(0xffffffffu, n_kept) : 0u;
         if (gl == 0) a.tile_max[(size_t)tile * GROUPS + WGROUPS * w + g] = gm;
         if (lane == 0) {
             atomicAdd(&a.ctl->frag_eval, (unsigned long long)we);
@@ -547,14 +548,20 @@ static int occupancy(const void *fn, int threads) {
     return occ;
 }
 
+template <bool COUNT>
+static void launch_fwd_count(const RenderArgs &a, int g, cudaStream_t st, bool solid) {
+    if (solid) render_fwd_kernel<true, WIN_POWER, COUNT><<<g, REN_THREADS, 0, st>>>(a);
+    else if (a.window == WIN_SIGMOID) render_fwd_kernel<false, WIN_SIGMOID, COUNT><<<g, REN_THREADS, 0, st>>>(a);
+    else render_fwd_kernel<false, WIN_POWER, COUNT><<<g, REN_THREADS, 0, st>>>(a);
+}
+
 void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st, bool solid) {
-    static int occ = occupancy((const void *)render_fwd_kernel<false, WIN_POWER>, REN_THREADS);
+    static int occ = occupancy((const void *)render_fwd_kernel<false, WIN_POWER, false>, REN_THREADS);
     int g = grid > 0 ? grid * occ : occ;
     if (g > a.total_tiles) g = a.total_tiles;
     if (g <= 0) return;
-    if (solid) render_fwd_kernel<true, WIN_POWER><<<g, REN_THREADS, 0, st>>>(a);
-    else if (a.window == WIN_SIGMOID) render_fwd_kernel<false, WIN_SIGMOID><<<g, REN_THREADS, 0, st>>>(a);
-    else render_fwd_kernel<false, WIN_POWER><<<g, REN_THREADS, 0, st>>>(a);
+    if (a.count_frags) launch_fwd_count<true>(a, g, st, solid);
+    else launch_fwd_count<false>(a, g, st, solid);
 }
 
 void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st) {

@@ -95,6 +95,7 @@ def lib():
             _sig(L, "tri_size_reg", [vp, C.c_int64, C.c_float, vp, vp, vp])
             _sig(L, "tri_set_window", [vp, C.c_int])
             _sig(L, "tri_set_sort", [vp, C.c_int])
+            _sig(L, "tri_set_fragment_counting", [vp, C.c_int])
             _sig(L, "tri_render_solid", [vp, P(tri_scene), P(tri_camera), C.c_int, P(vp), P(vp),
                                          P(C.c_int64), vp])
             _sig(L, "tri_render_bwd", [vp, P(vp), vp])

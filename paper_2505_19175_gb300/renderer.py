@@ -122,6 +122,11 @@ class Context:
         default) or ``native.WINDOW_SIGMOID`` (Eq. indicator2)."""
         self._ck(self._lib.tri_set_window(self.h, int(window)))
 
+    def set_fragment_counting(self, on: bool) -> None:
+        """Count the forward's evaluated and composited fragments into ``info()``
+        (off by default)."""
+        self._ck(self._lib.tri_set_fragment_counting(self.h, int(bool(on))))
+
     def set_sort(self, sort: int) -> None:
         """Compositing order of the next preprocess: ``native.SORT_TILE`` (per tile by
         centroid depth, the default) or ``native.SORT_PIXEL`` (per pixel by the depth of
