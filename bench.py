@@ -405,8 +405,10 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     stage_ms = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(6)] for k in range(args.steps)])
 
-    # end to end through the C ABI with host buffers: H2D of the scene and target from
-    # pinned memory, the step, D2H of the loss and the parameter gradients
+    # end to end through the C ABI with host buffers: every step copies its scene and
+    # target in from pinned host memory and its loss and parameter gradients back out.
+    # Two device buffer sets (one captured step graph each) let step k + 1's copy-in and
+    # step k's copy-out (separate copy streams, one per direction) overlap the compute.
     host = {k: v.cpu().pin_memory() for k, v in (("verts", st.verts), ("sh", st.sh), ("opacity", st.opacity),
                                                   ("sigma", st.sigma), ("target", tgt))}
     hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in
@@ -414,29 +416,70 @@ def run_ours(args, rank, world):
     h2d = sum(v.numel() * 4 for v in host.values())
     d2h = sum(v.numel() * 4 for v in hout.values())
 
-    def e2e_step():
-        st.verts.copy_(host["verts"], non_blocking=True)
-        st.sh.copy_(host["sh"], non_blocking=True)
-        st.opacity.copy_(host["opacity"], non_blocking=True)
-        st.sigma.copy_(host["sigma"], non_blocking=True)
-        tgt.copy_(host["target"], non_blocking=True)
-        g_step.replay()
-        hout["dv"].copy_(dv, non_blocking=True)
-        hout["dsh"].copy_(dsh, non_blocking=True)
-        hout["do"].copy_(do, non_blocking=True)
-        hout["ds"].copy_(ds, non_blocking=True)
-        hout["loss"].copy_(loss, non_blocking=True)
+    def buffer_set():
+        b = {"st": SceneTensors(torch.empty_like(st.verts), torch.empty_like(st.sh), torch.empty_like(st.opacity),
+                                torch.empty_like(st.sigma), st.sh_degree),
+             "tgt": torch.empty_like(tgt), "loss": torch.empty((), device="cuda"),
+             "g": [torch.empty_like(x) for x in (dv, dsh, do, ds)]}
+        for k in ("verts", "sh", "opacity", "sigma"):
+            getattr(b["st"], k).copy_(getattr(st, k))
+        b["tgt"].copy_(tgt)
 
-    for _ in range(2):
-        e2e_step()
+        def fn():
+            ctx.preprocess(b["st"], [cam])
+            ctx.bin_sort(sync=False)
+            ctx.render_fwd(imgs)
+            N.check(L.tri_loss_l1(imgs[0].data_ptr(), b["tgt"].data_ptr(), imgs[0].numel(), grad.data_ptr(),
+                                  b["loss"].data_ptr(), int(torch.cuda.current_stream().cuda_stream)))
+            ctx.render_bwd([grad])
+            ctx.preprocess_bwd(*b["g"])
+        fn()
+        torch.cuda.synchronize()
+        b["graph"] = capture(fn)
+        return b
+
+    sets = [buffer_set(), buffer_set()]
+    cs, up, down = torch.cuda.current_stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    inputs_free = [ev(), ev()]     # the step that read a set's inputs has finished
+    outputs_free = [ev(), ev()]    # a set's gradients have been copied out
+    for e in inputs_free + outputs_free:
+        e.record(cs)
+
+    def e2e_step(k):
+        b = sets[k % 2]
+        with torch.cuda.stream(up):
+            up.wait_event(inputs_free[k % 2])
+            for key in ("verts", "sh", "opacity", "sigma"):
+                getattr(b["st"], key).copy_(host[key], non_blocking=True)
+            b["tgt"].copy_(host["target"], non_blocking=True)
+            copied_in = torch.cuda.Event()
+            copied_in.record(up)
+        cs.wait_event(copied_in)
+        cs.wait_event(outputs_free[k % 2])
+        b["graph"].replay()
+        inputs_free[k % 2].record(cs)
+        with torch.cuda.stream(down):
+            down.wait_event(inputs_free[k % 2])
+            for key, x in zip(("dv", "dsh", "do", "ds"), b["g"]):
+                hout[key].copy_(x, non_blocking=True)
+            hout["loss"].copy_(b["loss"], non_blocking=True)
+            outputs_free[k % 2].record(down)
+
+    for k in range(4):
+        e2e_step(k)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record()
+    e0.record(cs)
+    up.wait_event(e0)
+    down.wait_event(e0)
+    for k in range(args.steps):
+        e2e_step(k)
+    cs.wait_event(outputs_free[(args.steps - 1) % 2])
+    e1.record(cs)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
+    del sets
     if world > 1:
         t = torch.tensor([e2e_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
