@@ -45,9 +45,11 @@
  *   CUDA graphs: tri_preprocess, tri_bin_sort (with num_pairs_out = NULL),
  *     tri_render_fwd, tri_render_bwd, tri_preprocess_bwd and tri_loss_l1 may be
  *     captured once the context's buffers are sized by an eager run of the same
- *     workload (a capture allocates nothing). A replay re-reads the context's pinned
- *     copies of its camera and output-pointer tables, written by its most recent
- *     captured call of each kind (eager calls do not touch them).
+ *     workload (a capture allocates nothing). A replay's kernels read the context's
+ *     page-locked copies of its camera and output-pointer tables at run time, as written
+ *     by its most recent captured call of each kind (eager calls pass the tables by
+ *     value, or copy them to the device, and do not touch these copies). A step makes no
+ *     other host copies; its queues and look-back words are reset by the kernels.
  */
 #ifndef TRISPLAT_H
 #define TRISPLAT_H
