@@ -3,8 +3,8 @@
 // A tile is 16x16 pixels, one thread per pixel, cut into eight 8x4 blocks (one warp
 // each) and each block into groups of GROUP lanes (eight 2x2 groups of 4 lanes by
 // default; 2x4 groups of 8 or 2x1 groups of 2 with KM_GROUP=8 or 2, both measured
-// slower on the patches workload). Tiles are taken from device
-// work queues by persistent grids, so a launch serves any mix of views and resolutions.
+// slower on the patches workload). Tiles are taken from device work queues by
+// persistent grids, so a launch serves any mix of views and resolutions.
 //
 // Forward (Sec. 3.1, the rendering equation of prior splatting work): one CTA of 256
 // threads per tile; the tile's depth-sorted records are staged through shared memory
@@ -13,8 +13,8 @@
 // ratio = min_i m_i(p) (phi(p)/phi(s) of Eq. indicator1), I = ratio^sigma, alpha = o I,
 // skip below 1/255, clamp at 0.99, stop before T drops below 1e-4, C += rgb alpha T.
 // The CTA leaves a tile as soon as every pixel has stopped (__syncthreads_count). It
-// also records, per pair, which groups composited it (one bit per group), and per group the
-// largest composited index.
+// also records, per pair, which groups composited it (one bit per group, KM_WORDS
+// 32-bit words per pair), and per group the largest composited index.
 //
 // Backward: one warp per (tile, block) work unit, with no CTA-wide barrier. Each group
 // walks only the pairs it composited, back to front: per pixel
@@ -150,8 +150,8 @@ __device__ __forceinline__ uint32_t group_max(uint32_t v) {
 // SOLID: opaque triangles (the sigma -> 0, o = 1 limit): each pixel takes the colour of
 // the first entry in depth order whose window ratio is positive. WIN: window kind.
 // The forward walks one list per warp (measured faster than per-half lists here: the
-// early exit on transmittance keeps its lists short); it records per group of 8 lanes
-// which pairs were composited, for the backward's per-group lists.
+// early exit on transmittance keeps its lists short); it records per group which pairs
+// were composited, for the backward's per-group lists.
 // COUNT: also count evaluated and composited fragments (tri_ctx_info).
 template <bool SOLID, int WIN, bool COUNT>
 __global__ void __launch_bounds__(REN_THREADS)
