@@ -81,3 +81,24 @@ def test_captured_step_replays_match_eager():
         torch.testing.assert_close(got[0], want[0], rtol=0, atol=0)
         for x, y in zip(got[1:], want[1:]):
             torch.testing.assert_close(x, y, rtol=1e-5, atol=1e-6 * float(y.abs().max()) + 1e-30)
+
+
+def test_fragment_counting_is_opt_in():
+    import torch
+    from paper_2505_19175_gb300.renderer import Context, SceneTensors, new_images
+    scene = synth.random_scene(500, seed=93, deg=0, size=(0.05, 0.5))
+    cam = synth.camera_identity(64, 48)
+    st = SceneTensors.from_numpy(scene)
+    ctx = Context()
+    counts = []
+    for on in (False, True):
+        ctx.set_fragment_counting(on)
+        ctx.preprocess(st, [cam])
+        ctx.bin_sort(sync=True)
+        img = new_images([cam])
+        ctx.render_fwd(img)
+        info = ctx.check()
+        torch.cuda.synchronize()
+        counts.append((info.frag_evaluated, info.frag_composited))
+    assert counts[0] == (0, 0)
+    assert counts[1][0] >= counts[1][1] > 0
