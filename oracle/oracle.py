@@ -45,8 +45,14 @@ _lock = threading.Lock()
 _lib = None
 
 
+_CHECK_SRC = os.path.join(_HERE, "sanitize_check.c")
+_CHECK_EXE = os.path.join(_BUILD, "sanitize_check")
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (OpenMP, no fast-math, no FMA contraction)."""
+    """Compile the oracle with gcc (OpenMP, no fast-math, no FMA contraction), and the C
+    driver of its sanitizer test (built here without the sanitizers, which the test
+    adds when it runs it)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
@@ -54,6 +60,12 @@ def build(force: bool = False) -> str:
                "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_CHECK_SRC))
+    if force or not os.path.exists(_CHECK_EXE) or os.path.getmtime(_CHECK_EXE) < newest:
+        tmp = _CHECK_EXE + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-o", tmp, _CHECK_SRC, _SRC, "-lm"],
+                       check=True)
+        os.replace(tmp, _CHECK_EXE)
     return _LIB
 
 
