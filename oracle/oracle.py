@@ -80,7 +80,7 @@ def _load():
                                        P, P, P, P, P, P]
             lib.orc_render_grad.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P,
                                             P, P, P, P, P, P, P]
-            lib.orc_render_solid.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P, P]
+            lib.orc_render_solid.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P, P, P]
             lib.orc_render_stats.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P, P]
             lib.orc_tri_info.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P]
             lib.orc_tri2d.argtypes = [P, P]
@@ -178,17 +178,19 @@ def render_stats(scene, cam, consts=None):
     return dict(max_weight=mw, n_pix=npix, amb=amb)
 
 
-def render_solid(scene, cam, consts=None):
+def render_solid(scene, cam, consts=None, pix_mask=None):
     """Solid-triangle image [3,H,W], winning triangle id [H,W] (-1: background) and the
-    per-pixel FP32-band flags: the sigma -> 0, o = 1 limit of the splat render."""
+    per-pixel FP32-band flags: the sigma -> 0, o = 1 limit of the splat render. With
+    pix_mask [H,W] only the pixels where it is non-zero are evaluated."""
     lib = _load()
     n, verts, sh, opac, sig, deg = _scene_arrays(scene)
     W, H = int(_get(cam, "W")), int(_get(cam, "H"))
     img = np.zeros((3, H, W), dtype=np.float64)
     ids = np.zeros((H, W), dtype=np.int32)
     fl = np.zeros((H, W), dtype=np.uint8)
+    pm = None if pix_mask is None else np.ascontiguousarray(pix_mask, dtype=np.uint8).reshape(H, W)
     rc = lib.orc_render_solid(n, _ptr(verts), _ptr(sh), deg, _ptr(opac), _ptr(sig), _ptr(_cam_array(cam)),
-                              _ptr(_const_array(consts)), _ptr(img), _ptr(ids), _ptr(fl))
+                              _ptr(_const_array(consts)), _ptr(pm), _ptr(img), _ptr(ids), _ptr(fl))
     if rc != 0:
         raise ValueError(f"orc_render_solid failed ({rc})")
     return dict(image=img, id=ids, flags=fl)

@@ -21,8 +21,8 @@ int orc_render_stats(int n, const double *verts, const double *sh, int sh_deg, c
                      const double *sigma, const double *cam, const double *consts, double *max_weight,
                      int32_t *n_pix, uint8_t *amb);
 int orc_render_solid(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
-                     const double *sigma, const double *cam, const double *consts, double *image, int32_t *ids,
-                     uint8_t *flags);
+                     const double *sigma, const double *cam, const double *consts, const uint8_t *pix_mask,
+                     double *image, int32_t *ids, uint8_t *flags);
 
 static uint64_t state = 88172645463325252ull;
 static double rnd(void) {   /* xorshift64, uniform [0, 1) */
@@ -63,7 +63,7 @@ int main(void) {
                                   dsigma);
             if (window == 0 && sort == 0) {
                 rc |= orc_render_stats(N, verts, sh, DEG, opac, sigma, cam, consts, mw, n_pix, amb);
-                rc |= orc_render_solid(N, verts, sh, DEG, opac, sigma, cam, consts, image, ids, flags);
+                rc |= orc_render_solid(N, verts, sh, DEG, opac, sigma, cam, consts, NULL, image, ids, flags);
             }
         }
     printf("sanitize check rc=%d\n", rc);

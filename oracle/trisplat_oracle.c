@@ -908,12 +908,14 @@ int orc_render_stats(int n, const double *verts, const double *sh, int sh_deg, c
  * takes the colour of the nearest triangle, by (centroid depth, id), whose window
  * ratio at the pixel centre is positive, else the background. Opacity and sigma are
  * ignored and only near-plane and degenerate triangles are culled. image [3,H,W],
- * id [H,W] (-1: background). flags (nullable) marks pixels whose winner is within
+ * id [H,W] (-1: background). pix_mask (nullable) limits the work to the pixels where
+ * it is non-zero; the others get the background and id -1. flags (nullable) marks
+ * pixels whose winner is within
  * the FP32 band: a ratio within EPS_LINE of zero for the winner or a nearer
  * triangle, or a depth within 4 FP32 ulps of the winner's. */
 int orc_render_solid(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
-                     const double *sigma, const double *cam, const double *consts, double *image,
-                     int32_t *id_out, uint8_t *flags) {
+                     const double *sigma, const double *cam, const double *consts, const uint8_t *pix_mask,
+                     double *image, int32_t *id_out, uint8_t *flags) {
     if (n < 0 || sh_deg < 0 || sh_deg > 3 || !image || !id_out) return 1;
     cam_t C = load_cam(cam);
     consts_t K = load_consts(consts);
@@ -928,6 +930,13 @@ int orc_render_solid(int n, const double *verts, const double *sh, int sh_deg, c
             const double px = x + 0.5;
             int best = -1;
             double bd = 0.0;
+            const size_t pix = (size_t)y * W + x;
+            if (pix_mask && !pix_mask[pix]) {          /* not sampled: background, id -1 */
+                id_out[pix] = -1;
+                for (int c = 0; c < 3; ++c) image[(size_t)c * W * H + pix] = C.bg[c];
+                if (flags) flags[pix] = 0;
+                continue;
+            }
             for (int id = 0; id < n; ++id) {
                 const tri_t *t = &tris[id];
                 if (t->cull) continue;
@@ -936,7 +945,6 @@ int orc_render_solid(int n, const double *verts, const double *sh, int sh_deg, c
                 if (tri2d_ratio(&t->g, px, py, NULL) <= 0.0) continue;
                 if (best < 0 || t->depth < bd || (t->depth == bd && id < best)) { best = id; bd = t->depth; }
             }
-            const size_t pix = (size_t)y * W + x;
             id_out[pix] = best;
             for (int c = 0; c < 3; ++c)
                 image[(size_t)c * W * H + pix] = best >= 0 ? tris[best].rgb[c] : C.bg[c];
@@ -945,7 +953,11 @@ int orc_render_solid(int n, const double *verts, const double *sh, int sh_deg, c
             for (int id = 0; id < n; ++id) {
                 const tri_t *t = &tris[id];
                 if (t->cull) {
-                    if (t->amb_cull) amb |= AMB_CULL;
+                    /* a cull within the FP32 band can only change the pixels the
+                     * triangle covers: those of its bounding box, when it projects */
+                    if (t->amb_cull && t->z[0] > 0 && t->z[1] > 0 && t->z[2] > 0 && px >= t->bbox[0] - 1.0 &&
+                        px <= t->bbox[2] + 1.0 && py >= t->bbox[1] - 1.0 && py <= t->bbox[3] + 1.0)
+                        amb |= AMB_CULL;
                     continue;
                 }
                 if (px < t->bbox[0] - 1.0 || px > t->bbox[2] + 1.0 || py < t->bbox[1] - 1.0 || py > t->bbox[3] + 1.0)

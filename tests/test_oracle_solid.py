@@ -56,3 +56,38 @@ def test_equals_the_exact_mode_limit_of_the_splat_render():
     assert ok.mean() > 0.9
     np.testing.assert_allclose(splat["image"][:, ok], solid["image"][:, ok], atol=1e-6)
     np.testing.assert_array_equal(splat["n_kept"][ok] > 0, solid["id"][ok] >= 0)
+
+
+def test_pixel_mask_evaluates_only_the_sampled_pixels():
+    scene = synth.random_scene(300, seed=56, deg=1, size=(0.05, 0.6))
+    cam = synth.camera_identity(72, 56)
+    full = O.render_solid(scene, cam)
+    mask = (np.random.default_rng(4).uniform(size=(cam.H, cam.W)) < 0.2).astype(np.uint8)
+    part = O.render_solid(scene, cam, pix_mask=mask)
+    sel = mask.astype(bool)
+    np.testing.assert_array_equal(part["id"][sel], full["id"][sel])
+    np.testing.assert_array_equal(part["image"][:, sel], full["image"][:, sel])
+    np.testing.assert_array_equal(part["flags"][sel], full["flags"][sel])
+    assert (part["id"][~sel] == -1).all() and (part["flags"][~sel] == 0).all()
+
+
+def test_ambiguous_cull_flags_only_the_triangles_own_pixels():
+    """A triangle culled by a near-plane test within the FP32 band (one vertex a hair in
+    front of the plane) marks the pixels of its bounding box, and no pixel far from it."""
+    cam = synth.camera_identity(64, 48, fx=50.0)
+    uv_c = np.array([[6.0, 6.0], [24.0, 8.0], [10.0, 22.0]])
+    z_near = O.DEFAULT_CONSTS["z_near"]
+    culled = one_tri_scene(cam, uv_c, np.array([z_near * (1 - 1e-7), 3.0, 3.0]))
+    uv_o = np.array([[40.0, 26.0], [60.0, 30.0], [46.0, 44.0]])
+    other = one_tri_scene(cam, uv_o, np.full(3, 3.0))
+    ref = O.render_solid(stack(culled, other), cam)
+    assert (ref["id"] != 0).all()                       # the first triangle is culled
+    X, Y = np.meshgrid(np.arange(cam.W) + 0.5, np.arange(cam.H) + 0.5)
+
+    def box(uv, pad):
+        lo, hi = uv.min(0) - pad, uv.max(0) + pad
+        return (X >= lo[0]) & (X <= hi[0]) & (Y >= lo[1]) & (Y <= hi[1])
+    assert (ref["flags"][box(uv_c, 1)] != 0).all()
+    # away from both triangles (the other one's edges carry band flags of their own)
+    far = ~box(uv_c, 2) & ~box(uv_o, 2)
+    assert far.sum() > 500 and (ref["flags"][far] == 0).all()
