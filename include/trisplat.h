@@ -221,7 +221,9 @@ tri_status tri_ctx_check(tri_ctx *ctx, tri_ctx_info *info, void *stream);
  *      within a tile in scatter order, except tiles of more than 2048 pairs, whose
  *      ranges hold the sort's intermediate runs
  *   7: per-item render records (float [n_items][16])
- *   8: per-item 2D gradients (float [n_items][16]) */
+ *   8: per-item 2D gradients (float [n_items][16])
+ *   9: the forward's tile visiting order (uint32 [total_tiles]): a permutation of the
+ *      tiles by descending half-octave bucket of their pair count */
 tri_status tri_debug_copy(tri_ctx *ctx, int which, void *dst, size_t max_bytes, size_t *bytes);
 
 /* Window function of the context's next tri_preprocess and of the renders that use its

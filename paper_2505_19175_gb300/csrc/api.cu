@@ -226,6 +226,7 @@ BinArgs bin_args(tri_ctx *c) {
     b.kv_tmp = P<unsigned long long>(c->kv_tmp);
     b.items = P<uint32_t>(c->items);
     b.big_tiles = P<uint32_t>(c->big_tiles);
+    b.tile_order = P<uint32_t>(c->tile_order);
     b.scan_status = P<uint64_t>(c->scan_status);
     b.scan_ticket = &ctl_of(c)->cta_counter[3];
     b.cap = (uint32_t)c->pair_cap;
@@ -336,7 +337,7 @@ tri_status tri_workspace_query(const tri_scene *scene, const tri_camera *cams, i
     size_t b = 0;
     b += (size_t)M * (sizeof(Rec) + 4 + 8 + 4 + GRAD_FIELDS * 4);    // records, counts, rects, keys, grads
     b += (size_t)cap * (8 + 8 + 4 + 2);                               // binned pairs, merge buffer, items, masks
-    b += (size_t)tiles * (4 + 4 + 4 + 8 + 64) + (size_t)pix * 8;      // counts, cursors, queue, ranges, maxima
+    b += (size_t)tiles * (4 + 4 + 4 + 4 + 8 + 64) + (size_t)pix * 8;  // counts, cursors, queue, order, ranges, maxima
     b += sizeof(Ctl) + nviews * (sizeof(ViewDev) + 2 * sizeof(ViewOut));
     b += 256 * 18;                                                    // allocation rounding
     *bytes = b;
@@ -386,6 +387,7 @@ static tri_status preprocess_impl(tri_ctx *c, const tri_scene *scene, const tri_
     ENSURE(c->tile_count, 4 * (size_t)tiles);
     ENSURE(c->tile_cursor, 4 * (size_t)tiles);
     ENSURE(c->big_tiles, 4 * (size_t)tiles);
+    ENSURE(c->tile_order, 4 * (size_t)tiles);
     if ((s = ensure_zeroed(c, c->scan_status, 8 * bin_scan_status_words(tiles), st)) != TRI_OK) return s;
     ENSURE(c->ranges, sizeof(uint2) * (size_t)tiles);
     ENSURE(c->tile_max, 4 * GROUPS_PER_TILE * (size_t)tiles);
@@ -471,7 +473,8 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
             c->pair_cap = cap;
             if ((s = ensure_pairs(c)) != TRI_OK) return s;
             b = bin_args(c);
-            CK(cudaMemsetAsync(&ctl_of(c)->big_count, 0, 4, st));   // queued by the first scan
+            CK(cudaMemsetAsync(&ctl_of(c)->big_count, 0, 4, st));   // queued and counted by the first scan
+            CK(cudaMemsetAsync(ctl_of(c)->ord_hist, 0, sizeof(ctl_of(c)->ord_hist), st));
             launch_bin_scan(b, st);
             if ((s = launch_check(c, "bin_scan")) != TRI_OK) return s;
         }
@@ -492,6 +495,7 @@ static RenderArgs render_args(tri_ctx *c, TsDevBuf &outs) {
     r.nviews = c->nviews;
     r.total_tiles = c->total_tiles;
     r.ranges = P<uint2>(c->ranges);
+    r.tile_order = P<uint32_t>(c->tile_order);
     r.items = P<uint32_t>(c->items);
     r.recs = P<Rec>(c->recs);
     r.rects = P<ushort4>(c->rects);
@@ -816,6 +820,7 @@ tri_status tri_debug_copy(tri_ctx *c, int which, void *dst, size_t max_bytes, si
         case 6: src = c->kv.p; n = 8 * np; break;
         case 7: src = c->recs.p; n = sizeof(Rec) * M; break;
         case 8: src = c->grad2d.p; n = sizeof(float) * GRAD_FIELDS * M; break;
+        case 9: src = c->tile_order.p; n = 4 * (size_t)c->total_tiles; break;
         default: return fail(c, TRI_ERR_INVALID_ARG, "unknown buffer");
     }
     if (n > max_bytes) return fail(c, TRI_ERR_CAPACITY, "destination too small");

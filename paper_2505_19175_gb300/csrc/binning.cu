@@ -117,7 +117,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) bin_scan_kernel(BinArgs a) {
     __shared__ unsigned long long s_w[SCAN_THREADS / 32 + 1];
     __shared__ uint32_t s_cta;
     __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_oh[ORD_BUCKETS];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid < ORD_BUCKETS) s_oh[tid] = 0u;
     if (tid == 0) s_cta = atomicAdd(a.scan_ticket, 1u);
     __syncthreads();
     const uint32_t cta = s_cta;
@@ -175,8 +177,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) bin_scan_kernel(BinArgs a) {
                 if (k < (uint32_t)T) a.big_tiles[k] = (uint32_t)(t0 + q);
                 else atomicOr(&a.ctl->error, ERR_INDEX);
             }
+            if (a.tile_order) atomicAdd(&s_oh[tile_order_key(hi - lo)], 1u);
         }
         off += c[q];
+    }
+    if (a.tile_order) {
+        // tiles per order key, for tile_sort's placement
+        __syncthreads();
+        if (tid < ORD_BUCKETS && s_oh[tid]) atomicAdd(&a.ctl->ord_hist[tid], s_oh[tid]);
     }
     if (last_cta_done(&a.ctl->done[3])) {
         // every CTA's look-back is over: clear the status words and the ticket
@@ -310,8 +318,34 @@ __device__ unsigned long long *block_sort(const unsigned long long *src, int n, 
 __global__ void __launch_bounds__(TSORT_THREADS, 3) tile_sort_kernel(BinArgs a) {
     __shared__ unsigned long long s_a[BS_MAX], s_b[BS_MAX];
     __shared__ uint32_t s_q;
+    __shared__ uint32_t s_ob[ORD_BUCKETS];
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t nbig = min(a.ctl->big_count, (uint32_t)a.total_tiles);
+    if (a.tile_order && (tid >> 5) == 1) {
+        // first slot of each order key (the tiles of larger keys come first), by warp 1
+        // while thread 0 takes the first queued tile: lane l holds keys 3l .. 3l + 2
+        uint32_t h[3], tot = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int k = 3 * lane + j;
+            h[j] = k < ORD_BUCKETS ? a.ctl->ord_hist[k] : 0u;
+            tot += h[j];
+        }
+        uint32_t suf = tot;      // inclusive sum over lanes >= this one
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_down_sync(0xffffffffu, suf, o);
+            if (lane + o < 32) suf += y;
+        }
+        uint32_t acc = suf - tot;
+#pragma unroll
+        for (int j = 2; j >= 0; --j) {
+            const int k = 3 * lane + j;
+            if (k < ORD_BUCKETS) s_ob[k] = acc;
+            acc += h[j];
+        }
+    }
+    // (s_ob is read after the barriers of the first loop)
     for (;;) {
         if (tid == 0) s_q = atomicAdd(&a.ctl->big_next, 1u);
         __syncthreads();
@@ -377,6 +411,14 @@ __global__ void __launch_bounds__(TSORT_THREADS, 3) tile_sort_kernel(BinArgs a) 
         if (t >= (uint32_t)a.total_tiles) break;
         const uint2 r = a.ranges[t];
         const int n = (int)(r.y - r.x);
+        // this tile's place in the render order: the rank is taken now and stored after
+        // the sort, which hides the atomic's round trip
+        uint32_t obase = 0, orank = 0;
+        if (a.tile_order && lane == 0) {
+            const int key = tile_order_key((uint32_t)n);
+            obase = s_ob[key];
+            orank = atomicAdd(&a.ctl->ord_next[key], 1u);
+        }
         if (n <= 1) {
             if (n == 1 && lane == 0) a.items[r.x] = (uint32_t)a.kv[r.x];
         } else if (n > WS_MAX) {
@@ -392,11 +434,20 @@ __global__ void __launch_bounds__(TSORT_THREADS, 3) tile_sort_kernel(BinArgs a) 
         } else {
             warp_sort_range<16>(a, r.x, n);
         }
+        if (a.tile_order && lane == 0) {
+            const uint32_t slot = obase + orank;
+            if (slot < (uint32_t)a.total_tiles) a.tile_order[slot] = t;
+            else atomicOr(&a.ctl->error, ERR_INDEX);
+        }
     }
     if (last_cta_done(&a.ctl->done[2]) && tid == 0) {
         a.ctl->work_counter[2] = 0u;
         a.ctl->big_count = 0u;
         a.ctl->big_next = 0u;
+        for (int k = 0; k < ORD_BUCKETS; ++k) {
+            a.ctl->ord_hist[k] = 0u;
+            a.ctl->ord_next[k] = 0u;
+        }
     }
 }
 

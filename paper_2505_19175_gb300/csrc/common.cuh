@@ -49,6 +49,22 @@ struct ViewOut {
 };
 
 // Device control block: counters, histograms and work queues of one pipeline run.
+// Tiles are rendered in descending order of their pair count (longest first, so that
+// no long tile starts last and leaves the machine idle at the end): counts fall into
+// half-octave buckets, key 0 for an empty tile and 1 + 2 floor(log2 n) + (the bit
+// below the leading one) otherwise, 1..64.
+constexpr int ORD_BUCKETS = 65;
+__host__ __device__ __forceinline__ int tile_order_key(uint32_t n) {
+    if (n == 0) return 0;
+#ifdef __CUDA_ARCH__
+    const int lg = 31 - __clz(n);
+#else
+    int lg = 0;
+    while ((n >> lg) > 1u) ++lg;
+#endif
+    return 1 + 2 * lg + (lg > 0 ? (int)((n >> (lg - 1)) & 1u) : 0);
+}
+
 struct Ctl {
     uint32_t n_visible;        // visible items after preprocess
     uint32_t n_pairs;          // pairs emitted (may exceed capacity)
@@ -64,6 +80,8 @@ struct Ctl {
     unsigned long long frag_eval;   // forward: (pixel, entry) evaluations
     unsigned long long frag_kept;   // forward: composited fragments
     unsigned long long pps_total;   // per-pixel sort: candidates of all pixels
+    uint32_t ord_hist[ORD_BUCKETS];  // tiles per order key (bin_scan)
+    uint32_t ord_next[ORD_BUCKETS];  // tiles placed per order key (tile_sort)
     uint32_t depth_hist[4][256];
     uint32_t tile_hist[4][256];
 };

@@ -97,6 +97,7 @@ struct BinArgs {
     unsigned long long *kv_tmp;     // [cap] merge buffer for ranges longer than one chunk
     uint32_t *items;                // [cap] sorted item ids
     uint32_t *big_tiles;            // [total_tiles] tiles whose range one warp cannot sort
+    uint32_t *tile_order = nullptr; // [total_tiles] if set: tiles by descending pair count
     uint32_t cap;
     int total_tiles;
     uint64_t blk_stride;            // visiting order of the 256-item blocks: b * stride mod blocks
@@ -147,6 +148,7 @@ struct RenderArgs {
     int nviews;
     int total_tiles;
     const uint2 *ranges;
+    const uint32_t *tile_order = nullptr;   // if set: the forward's tile visiting order
     const uint32_t *items;          // sorted pair item ids
     const Rec *recs;
     const ushort4 *rects;           // per-item pixel rectangles

@@ -176,7 +176,15 @@ render_fwd_kernel(RenderArgs a) {
     const bool stats = a.stat_n != nullptr;
     const uint8_t *L = s_list[w];
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(&a.ctl->work_counter[0], 1u);
+        if (tid == 0) {
+            uint32_t q = atomicAdd(&a.ctl->work_counter[0], 1u);
+            if (a.tile_order && q < (uint32_t)a.total_tiles) {
+                const uint32_t t = a.tile_order[q];
+                if (t < (uint32_t)a.total_tiles) q = t;
+                else atomicOr(&a.ctl->error, ERR_INDEX);
+            }
+            s_tile = q;
+        }
         __syncthreads();
         const int tile = (int)s_tile;
         if (tile >= a.total_tiles) break;

@@ -173,7 +173,8 @@ class Context:
 
     _DEBUG = {"pair_tiles": (0, np.uint32, 1), "pair_items": (1, np.uint32, 1), "ranges": (2, np.uint32, 2),
               "depth_keys": (3, np.uint32, 1), "rects": (4, np.uint16, 4), "ntiles": (5, np.uint32, 1),
-              "binned": (6, np.uint64, 1), "records": (7, np.float32, 16), "grad2d": (8, np.float32, 16)}
+              "binned": (6, np.uint64, 1), "records": (7, np.float32, 16), "grad2d": (8, np.float32, 16),
+              "tile_order": (9, np.uint32, 1)}
 
     def debug(self, name: str) -> np.ndarray:
         which, dt, width = self._DEBUG[name]

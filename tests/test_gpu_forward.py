@@ -193,6 +193,8 @@ def test_pair_overflow_is_reported_and_recovered():
     ctx.render_fwd(img)
     ctx.check()
     assert n > 64
+    # the re-run scan counted the tiles once: the visiting order is a permutation
+    np.testing.assert_array_equal(np.sort(ctx.debug("tile_order")), np.arange(len(ctx.debug("ranges"))))
     ref = O.render(scene, cam, flags=True)
     ok = ref["flags"] == 0
     assert np.abs(img[0].cpu().numpy() - ref["image"])[:, ok].max() <= TOL
@@ -217,3 +219,29 @@ def test_full_size_patch_workload_sampled_pixels():
     err = np.abs(imgs[0] - ref["image"])[:, ok]
     assert err.max() <= TOL, err.max()
     assert np.abs(T[0] - ref["T_final"])[ok].max() <= TOL
+
+
+def _order_key(n):
+    """Half-octave bucket of a pair count: 0 when empty, else 1 + 2 floor(log2 n) + the
+    bit below the leading one."""
+    n = np.asarray(n, np.int64)
+    lg = np.where(n > 0, np.floor(np.log2(np.maximum(n, 1))).astype(np.int64), 0)
+    half = np.where(lg > 0, (n >> np.maximum(lg - 1, 0)) & 1, 0)
+    return np.where(n > 0, 1 + 2 * lg + half, 0)
+
+
+def test_tiles_are_visited_longest_first():
+    """The forward's tile order is a permutation of the tiles, by descending bucket of
+    their pair count, and stays one over repeated sorts and a capacity regrowth."""
+    scene = synth.random_scene(3000, seed=17, deg=1, size=(0.02, 0.9))
+    cams = [synth.camera_identity(200, 150), synth.camera_identity(77, 45)]
+    imgs, T, nc, ctx, _ = gpu_forward(scene, cams)
+    for _ in range(2):
+        order = ctx.debug("tile_order").astype(np.int64)
+        rg = ctx.debug("ranges").astype(np.int64)
+        assert len(order) == len(rg)
+        np.testing.assert_array_equal(np.sort(order), np.arange(len(rg)))
+        keys = _order_key(rg[order, 1] - rg[order, 0])
+        assert (np.diff(keys) <= 0).all() and keys[0] > keys[-1]
+        ctx.bin_sort(sync=True)
+    ctx.check()
