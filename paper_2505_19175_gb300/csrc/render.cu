@@ -369,7 +369,14 @@ render_bwd_kernel(RenderArgs a) {
         if (lane == 0) u = atomicAdd(&a.ctl->work_counter[1], 1u);
         u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= n_units) break;
-        const int tile = (int)(u / TILE_BLOCKS), blk = (int)(u % TILE_BLOCKS);
+        // the tiles in the forward's order (longest first), each as its 8 units
+        uint32_t tq = u / TILE_BLOCKS;
+        if (a.tile_order) {
+            const uint32_t t = a.tile_order[tq];
+            if (t < (uint32_t)a.total_tiles) tq = t;
+            else if (lane == 0) atomicOr(&a.ctl->error, ERR_INDEX);
+        }
+        const int tile = (int)tq, blk = (int)(u % TILE_BLOCKS);
         const int vw = find_view_warp(a.views, a.nviews, tile, lane);
         const ViewDev *V = a.views + vw;
         const int tiles_x = V->tiles_x, W = V->W, H = V->H;
