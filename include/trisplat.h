@@ -215,7 +215,8 @@ tri_status tri_ctx_check(tri_ctx *ctx, tri_ctx_info *info, void *stream);
  * `dst` (at most `max_bytes`), synchronously; `*bytes` receives the byte count used.
  *   0: sorted pair tile keys (uint32 [n_pairs])   1: sorted pair item ids (uint32)
  *   2: tile ranges (uint32 [total_tiles][2])       3: item depth keys (uint32 [n_items])
- *   4: item pixel rectangles (uint16 [n_items][4]: x0, y0, x1, y1 inclusive)
+ *   4: item pixel rectangles (uint16 [n_items][4]: x0, y0, x1, y1 inclusive; written
+ *      only for items with a non-zero tile count, as are the records of 7)
  *   5: item tile counts (uint32 [n_items])
  *   6: binned pairs (uint64 [n_pairs]: depth key << 32 | item id), grouped by tile;
  *      within a tile in scatter order, except tiles of more than 2048 pairs, whose

@@ -18,6 +18,7 @@ constexpr float T_EPS = 1e-4f;           // stop before transmittance drops belo
 constexpr float Z_NEAR = 0.2f;           // cull a triangle with a vertex nearer than this
 constexpr float R_MIN = 1e-4f;           // cull a triangle whose inradius (px) is below this
 constexpr float RECT_PAD = 1.0f / 512.0f;  // px added around the tight rectangle (FP32 slack)
+constexpr float FRUSTUM_PAD = 2.0f;        // px beyond the image edges of the preprocess's view test
 constexpr int MAX_VIEWS = 64;            // views per preprocess call
 
 // Status words of the decoupled look-back scans: 2 flag bits over a 30-bit count.

@@ -137,9 +137,60 @@ preprocess_fwd_kernel(PreArgs a) {
     const float cen[3] = {(v[0] + v[3] + v[6]) * (1.0f / 3.0f), (v[1] + v[4] + v[7]) * (1.0f / 3.0f),
                           (v[2] + v[5] + v[8]) * (1.0f / 3.0f)};
 
+    // views the triangle may touch: its bounding sphere (centroid, largest vertex
+    // distance) against the near plane and the four side planes of each view's frustum
+    // widened by FRUSTUM_PAD pixels. A sphere wholly outside a side plane means that
+    // either a vertex is nearer than Z_NEAR (the exact test culls the item) or every
+    // vertex projects beyond the image by more than FP32 error (no tile); wholly in
+    // front of the near plane means all vertices are. Either way the exact path would
+    // emit nothing, so only the views left are visited, which most triangles of a
+    // many-view batch are not in. (Not for the sigmoid window, whose support reaches
+    // beyond the triangle.)
+    uint64_t vis = 0;
+    if (alive) {
+        float rad2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float dx = v[3 * k] - cen[0], dy = v[3 * k + 1] - cen[1], dz = v[3 * k + 2] - cen[2];
+            rad2 = fmaxf(rad2, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        }
+        const float rad = fmaf(sqrtf(rad2), 1.0001f, 1e-6f);
+        const bool test = (WIN == WIN_POWER || a.solid) && rad < 1e30f;
+        for (int vw = 0; vw < a.nviews; ++vw) {
+            const ViewDev &V = s_view[vw];
+            bool out = false;
+            if (test && V.fx > 0.0f && V.fy > 0.0f) {
+                const float xc = fmaf(V.R[0], cen[0], fmaf(V.R[1], cen[1], fmaf(V.R[2], cen[2], V.t[0])));
+                const float yc = fmaf(V.R[3], cen[0], fmaf(V.R[4], cen[1], fmaf(V.R[5], cen[2], V.t[1])));
+                const float zc = fmaf(V.R[6], cen[0], fmaf(V.R[7], cen[1], fmaf(V.R[8], cen[2], V.t[2])));
+                const float ul = V.cx + FRUSTUM_PAD, ur = (float)V.W + FRUSTUM_PAD - V.cx;
+                const float vt = V.cy + FRUSTUM_PAD, vb = (float)V.H + FRUSTUM_PAD - V.cy;
+                // (the near test keeps half the plane distance as slack for the FP32
+                // vertex depths of the exact test)
+                out = zc + rad < 0.5f * Z_NEAR ||
+                      fmaf(V.fx, xc, ul * zc) * rsqrtf(fmaf(V.fx, V.fx, ul * ul)) < -rad ||
+                      fmaf(-V.fx, xc, ur * zc) * rsqrtf(fmaf(V.fx, V.fx, ur * ur)) < -rad ||
+                      fmaf(V.fy, yc, vt * zc) * rsqrtf(fmaf(V.fy, V.fy, vt * vt)) < -rad ||
+                      fmaf(-V.fy, yc, vb * zc) * rsqrtf(fmaf(V.fy, V.fy, vb * vb)) < -rad;
+            }
+            if (!out) {
+                vis |= 1ull << vw;
+                continue;
+            }
+            const int64_t m = (int64_t)vw * a.n + i;
+            a.ntiles[m] = 0u;
+            a.dkeys[m] = 0xffffffffu;
+            if (a.depth_hist) {
+#pragma unroll
+                for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][255], 1u);
+            }
+        }
+    }
+
     uint32_t nvis = 0;
-    for (int vw = 0; vw < a.nviews; ++vw) {
-        if (!alive) break;
+#pragma unroll 1
+    for (; vis; vis &= vis - 1) {
+        const int vw = __ffsll((long long)vis) - 1;
         const ViewDev &V = s_view[vw];
         const int64_t m = (int64_t)vw * a.n + i;
         Geom g;
@@ -147,7 +198,6 @@ preprocess_fwd_kernel(PreArgs a) {
         uint32_t nt = 0;
         ushort4 rect = make_ushort4(0, 0, 0, 0);
         Rec rec;
-        rec.a = rec.b = rec.c = rec.d = make_float4(0.f, 0.f, 0.f, 0.f);
         float fshrink = fshrink_pow;
         if (WIN == WIN_SIGMOID && !a.solid && cull == CULL_NONE)
             fshrink = o > ALPHA_MIN ? 1.0f - sig * lgt / g.r : 0.0f;   // > 1: support beyond the triangle
@@ -212,9 +262,13 @@ preprocess_fwd_kernel(PreArgs a) {
                                         : make_float4(0.0f, 0.0f, 1.0f / g.depth, 0.0f);
             }
         }
-        a.recs[m] = rec;
+        // records and rectangles are read only through the tile lists: an item that
+        // touches no tile skips them (most items of a many-view batch are off screen)
+        if (nt > 0) {
+            a.recs[m] = rec;
+            a.rects[m] = rect;
+        }
         a.ntiles[m] = nt;
-        a.rects[m] = rect;
         a.dkeys[m] = key;
         if (a.tile_count && nt) {
             // per-tile pair counts of the binning (fire-and-forget reductions)

@@ -245,3 +245,28 @@ def test_tiles_are_visited_longest_first():
         assert (np.diff(keys) <= 0).all() and keys[0] > keys[-1]
         ctx.bin_sort(sync=True)
     ctx.check()
+
+
+def test_views_around_the_triangles_match_oracle_rectangles():
+    """Cameras inside nested shells of small triangles: most triangles lie beside or
+    behind each camera or straddle its frustum and near plane. Per view, the (tile,
+    triangle) pairs equal the oracle's FP64 rectangles (ambiguous triangles aside), so
+    the preprocess's view culling drops nothing that touches a tile."""
+    scene = synth.scene_shells(40_000, seed=71, n_shell=5, r_lo=0.5, r_hi=3.0)
+    cams = synth.ring_cameras(6, radius=1.2, W=160, H=112, offset=0.3)
+    _, _, _, ctx, _ = gpu_forward(scene, cams)
+    tiles = ctx.debug("pair_tiles").astype(np.int64)
+    items = ctx.debug("pair_items").astype(np.int64)
+    n = scene.n
+    base = 0
+    for v, cam in enumerate(cams):
+        nt = ((cam.W + 15) // 16) * ((cam.H + 15) // 16)
+        sel = (items // n) == v
+        info = O.tri_info(scene, cam)
+        ot, oi = O.tile_pairs(scene, cam, info=info)
+        amb = info["amb"] != 0
+        gset = {(t - base, i % n) for t, i in zip(tiles[sel], items[sel]) if not amb[i % n]}
+        oset = {(t, i) for t, i in zip(ot, oi) if not amb[i]}
+        assert len(oset) > 1000 and gset == oset, (v, len(gset ^ oset))
+        assert amb.mean() < 0.01
+        base += nt
