@@ -9,7 +9,7 @@
 // tri_densify is one kernel: each CTA takes 256 selected triangles in order (ticket),
 // counts the triangles each appends (3 or 1), and finds its output offset with a
 // single-pass scan (decoupled look-back), so the appended triangles follow the order
-// of the selection list.
+// of the selection list. Geometry is written per thread, SH records per warp.
 #include "kernels.h"
 
 namespace ts {
@@ -67,41 +67,53 @@ __global__ void __launch_bounds__(DENS_THREADS) densify_kernel(DensifyArgs a) {
     __syncthreads();
     const int64_t base = a.n + s_base;
     if (tid == 0 && (int64_t)(cta + 1) * DENS_THREADS >= a.k) *a.n_out = base + total;
-    if (i < 0) return;
     const int64_t pos = base + local;
-    const int nsh = a.nk * 3;
-    auto copy_attr = [&](int64_t dst) {
-        const float *s = a.sh + i * nsh;
-        float *d = a.sh + dst * nsh;
-        for (int q = 0; q < nsh; ++q) d[q] = s[q];
-        a.opacity[dst] = a.opacity[i];
-        a.sigma[dst] = a.sigma[i];
-    };
-    if (!small) {
-        const float3 m01 = mul3(add3(v0, v1), 0.5f), m12 = mul3(add3(v1, v2), 0.5f), m02 = mul3(add3(v0, v2), 0.5f);
-        float *vp = a.verts + i * 9;
-        put3(vp + 3, m01);
-        put3(vp + 6, m02);
-        float *d = a.verts + pos * 9;
-        put3(d, m01), put3(d + 3, v1), put3(d + 6, m12);
-        put3(d + 9, m02), put3(d + 12, m12), put3(d + 15, v2);
-        put3(d + 18, m01), put3(d + 21, m12), put3(d + 24, m02);
-        for (int q = 0; q < 3; ++q) copy_attr(pos + q);
-    } else {
-        const float nc = fmaxf(norm3(c), DENS_EPS);
-        const float3 nrm = mul3(c, 1.0f / nc);
-        const float3 e = sub3(v1, v0);
-        const float3 e1 = mul3(e, 1.0f / fmaxf(norm3(e), DENS_EPS));
-        const float3 e2 = cross3(nrm, e1);
-        const float na = a.noise[2 * j], nb = a.noise[2 * j + 1];
-        const float3 t = mul3(add3(mul3(e1, na), mul3(e2, nb)), a.noise_scale);
-        // both copies take 1 - sqrt(1 - o) = o / (1 + sqrt(1 - o)) (no cancellation):
-        // together they composite to o
-        const float oi = a.opacity[i];
-        a.opacity[i] = oi / (1.0f + sqrtf(fmaxf(1.0f - oi, 0.0f)));
-        float *d = a.verts + pos * 9;
-        put3(d, add3(v0, t)), put3(d + 3, add3(v1, t)), put3(d + 6, add3(v2, t));
-        copy_attr(pos);
+    if (i >= 0) {
+        auto copy_scalars = [&](int64_t dst) {
+            a.opacity[dst] = a.opacity[i];
+            a.sigma[dst] = a.sigma[i];
+        };
+        if (!small) {
+            const float3 m01 = mul3(add3(v0, v1), 0.5f), m12 = mul3(add3(v1, v2), 0.5f), m02 = mul3(add3(v0, v2), 0.5f);
+            float *vp = a.verts + i * 9;
+            put3(vp + 3, m01);
+            put3(vp + 6, m02);
+            float *d = a.verts + pos * 9;
+            put3(d, m01), put3(d + 3, v1), put3(d + 6, m12);
+            put3(d + 9, m02), put3(d + 12, m12), put3(d + 15, v2);
+            put3(d + 18, m01), put3(d + 21, m12), put3(d + 24, m02);
+            for (int q = 0; q < 3; ++q) copy_scalars(pos + q);
+        } else {
+            const float nc = fmaxf(norm3(c), DENS_EPS);
+            const float3 nrm = mul3(c, 1.0f / nc);
+            const float3 e = sub3(v1, v0);
+            const float3 e1 = mul3(e, 1.0f / fmaxf(norm3(e), DENS_EPS));
+            const float3 e2 = cross3(nrm, e1);
+            const float na = a.noise[2 * j], nb = a.noise[2 * j + 1];
+            const float3 t = mul3(add3(mul3(e1, na), mul3(e2, nb)), a.noise_scale);
+            // both copies take 1 - sqrt(1 - o) = o / (1 + sqrt(1 - o)) (no cancellation):
+            // together they composite to o
+            const float oi = a.opacity[i];
+            a.opacity[i] = oi / (1.0f + sqrtf(fmaxf(1.0f - oi, 0.0f)));
+            float *d = a.verts + pos * 9;
+            put3(d, add3(v0, t)), put3(d + 3, add3(v1, t)), put3(d + 6, add3(v2, t));
+            copy_scalars(pos);
+        }
+    }
+    // SH records of the appended triangles, copied by the whole warp one selected
+    // triangle at a time (32 consecutive floats per access instead of one record per
+    // thread at a 4-byte stride)
+    const int nsh = a.nk * 3, lane = tid & 31;
+    for (int l = 0; l < 32; ++l) {
+        const long long si = __shfl_sync(0xffffffffu, (long long)i, l);
+        if (si < 0) continue;
+        const long long dp = __shfl_sync(0xffffffffu, (long long)pos, l);
+        const int ncp = __shfl_sync(0xffffffffu, (int)cnt, l);
+        const float *src = a.sh + si * nsh;
+        for (int q = lane; q < nsh; q += 32) {
+            const float x = src[q];
+            for (int k = 0; k < ncp; ++k) a.sh[(dp + k) * nsh + q] = x;
+        }
     }
 }
 
