@@ -118,33 +118,51 @@ __global__ void __launch_bounds__(DENS_THREADS) densify_kernel(DensifyArgs a) {
 }
 
 // L_s = weight * sum_i 2 / |c_i|, c_i = (v1 - v0) x (v2 - v0); dverts += dL_s/dverts.
+// Blocks of 256 triangles pass through shared memory, so that global accesses are
+// consecutive floats rather than 9-float records at a stride.
 __global__ void __launch_bounds__(DENS_THREADS) size_reg_kernel(const float *__restrict__ verts, int64_t n, float weight,
                                                               float *loss, float *dverts) {
     __shared__ float s_part[DENS_THREADS / 32];
+    __shared__ float s_v[DENS_THREADS * 9];
+    __shared__ float s_d[DENS_THREADS * 9];
+    const int tid = threadIdx.x;
     float acc = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * DENS_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * DENS_THREADS) {
-        const float *vp = verts + i * 9;
-        const float3 v0 = f3(vp), e1 = sub3(f3(vp + 3), v0), e2 = sub3(f3(vp + 6), v0);
-        const float3 c = cross3(e1, e2);
-        const float nc = norm3(c);
-        if (!(nc >= 1e-12f)) continue;
-        const float inv = 1.0f / nc;
-        acc += 2.0f * inv;
-        if (dverts) {
-            const float3 g = mul3(c, -2.0f * weight * inv * inv * inv);   // dL/dc
-            const float3 d1 = cross3(e2, g), d2 = cross3(g, e1);
-            float *dp = dverts + i * 9;
-            dp[0] -= d1.x + d2.x, dp[1] -= d1.y + d2.y, dp[2] -= d1.z + d2.z;
-            dp[3] += d1.x, dp[4] += d1.y, dp[5] += d1.z;
-            dp[6] += d2.x, dp[7] += d2.y, dp[8] += d2.z;
+    for (int64_t b0 = (int64_t)blockIdx.x * DENS_THREADS; b0 < n; b0 += (int64_t)gridDim.x * DENS_THREADS) {
+        const int cnt = (int)(n - b0 < DENS_THREADS ? n - b0 : DENS_THREADS);
+        for (int k = tid; k < cnt * 9; k += DENS_THREADS) {
+            s_v[k] = verts[b0 * 9 + k];
+            if (dverts) s_d[k] = dverts[b0 * 9 + k];
         }
+        __syncthreads();
+        if (tid < cnt) {
+            const float *vp = s_v + tid * 9;
+            const float3 v0 = f3(vp), e1 = sub3(f3(vp + 3), v0), e2 = sub3(f3(vp + 6), v0);
+            const float3 c = cross3(e1, e2);
+            const float nc = norm3(c);
+            if (nc >= 1e-12f) {
+                const float inv = 1.0f / nc;
+                acc += 2.0f * inv;
+                if (dverts) {
+                    const float3 g = mul3(c, -2.0f * weight * inv * inv * inv);   // dL/dc
+                    const float3 d1 = cross3(e2, g), d2 = cross3(g, e1);
+                    float *dp = s_d + tid * 9;
+                    dp[0] -= d1.x + d2.x, dp[1] -= d1.y + d2.y, dp[2] -= d1.z + d2.z;
+                    dp[3] += d1.x, dp[4] += d1.y, dp[5] += d1.z;
+                    dp[6] += d2.x, dp[7] += d2.y, dp[8] += d2.z;
+                }
+            }
+        }
+        __syncthreads();
+        if (dverts)
+            for (int k = tid; k < cnt * 9; k += DENS_THREADS) dverts[b0 * 9 + k] = s_d[k];
+        __syncthreads();
     }
     if (loss) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+        if ((tid & 31) == 0) s_part[tid >> 5] = acc;
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             float t = 0.f;
             for (int k = 0; k < DENS_THREADS / 32; ++k) t += s_part[k];
             atomicAdd(loss, weight * t);
