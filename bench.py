@@ -162,6 +162,16 @@ def cpu_baseline(scene, cam, target, budget_s: float = 20.0):
                       f"runs of {dt:.2f} s"}
 
 
+def max_over_ranks(x: float, device: str) -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's); `device`
+    is where the process group's backend keeps tensors (cuda for NCCL, cpu for gloo)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -394,9 +404,7 @@ def run_ours(args, rank, world):
     step_ms = np.array([a.elapsed_time(b) for a, b in ev_step])
     total_ms = float(step_ms.sum())
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, "cuda")
     value = world * args.steps / (total_ms / 1000.0)
     fwd_ms = float(sum(a.elapsed_time(b) for a, b in ev_fwd))
     fps = args.steps / (fwd_ms / 1000.0)
@@ -486,9 +494,7 @@ def run_ours(args, rank, world):
     e2e_ms = e0.elapsed_time(e1)
     del sets
     if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms, "cuda")
     # the same step with the sigmoid window (Eq. indicator2): supports beyond the triangles
     sigmoid_line = None
     if not args.no_sigmoid:
