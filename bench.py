@@ -198,9 +198,9 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------
-STAGES = ("preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd")
+STAGES = ("preprocess", "bin_sort", "render_fwd", "render_bwd", "preprocess_bwd")   # render_fwd: with the L1 loss
 # step_init, preprocess, bin_scan, bin_scatter, tile_sort, render_fwd, loss, render_bwd, preprocess_bwd
-KERNELS_PER_STEP = 9
+KERNELS_PER_STEP = 8
 
 
 def run_sigmoid_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds, capture, timed):
@@ -208,7 +208,6 @@ def run_sigmoid_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds,
     import torch
     from paper_2505_19175_gb300 import native as N
     from paper_2505_19175_gb300.renderer import Context
-    L = N.lib()
     ctx_s = Context(dev)
     ctx_s.set_window(N.WINDOW_SIGMOID)
     ctx_s.preprocess(st, [cam])
@@ -217,9 +216,7 @@ def run_sigmoid_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds,
     def step_sigmoid():
         ctx_s.preprocess(st, [cam])
         ctx_s.bin_sort(sync=False)
-        ctx_s.render_fwd(imgs)
-        N.check(L.tri_loss_l1(imgs[0].data_ptr(), tgt.data_ptr(), imgs[0].numel(), grad.data_ptr(),
-                              loss.data_ptr(), int(torch.cuda.current_stream().cuda_stream)))
+        ctx_s.render_fwd_l1(imgs, [tgt], [grad], loss)
         ctx_s.render_bwd([grad])
         ctx_s.preprocess_bwd(dv, dsh, do, ds)
 
@@ -289,7 +286,6 @@ def run_pixel_sort_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, 
 
 def run_ours(args, rank, world):
     import torch
-    from paper_2505_19175_gb300 import native as N
     from paper_2505_19175_gb300.renderer import Context, SceneTensors, new_images
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
@@ -306,7 +302,6 @@ def run_ours(args, rank, world):
     loss = torch.empty((), device="cuda")
     dv, dsh = torch.empty_like(st.verts), torch.empty_like(st.sh)
     do, ds = torch.empty_like(st.opacity), torch.empty_like(st.sigma)
-    L = N.lib()
 
     def step(ev=None):
         if ev:
@@ -317,19 +312,15 @@ def run_ours(args, rank, world):
         ctx.bin_sort(sync=False)
         if ev:
             ev[2].record()
-        ctx.render_fwd(imgs)
+        ctx.render_fwd_l1(imgs, [tgt], [grad], loss)     # the forward with the L1 loss fused
         if ev:
             ev[3].record()
-        N.check(L.tri_loss_l1(imgs[0].data_ptr(), tgt.data_ptr(), imgs[0].numel(), grad.data_ptr(),
-                              loss.data_ptr(), int(torch.cuda.current_stream().cuda_stream)))
-        if ev:
-            ev[4].record()
         ctx.render_bwd([grad])
         if ev:
-            ev[5].record()
+            ev[4].record()
         ctx.preprocess_bwd(dv, dsh, do, ds)
         if ev:
-            ev[6].record()
+            ev[5].record()
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MB > 129 MB L2
     for _ in range(args.warmup):
@@ -411,12 +402,13 @@ def run_ours(args, rank, world):
     fps_stats = args.steps / (float(sum(a.elapsed_time(b) for a, b in ev_fwd_stats)) / 1000.0)
 
     # per-stage breakdown: eager steps with events between the calls (same stream)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(args.steps)]
     for k in range(args.steps):
         flush.zero_()
         step(evs[k])
     torch.cuda.synchronize()
-    stage_ms = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(6)] for k in range(args.steps)])
+    stage_ms = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(len(STAGES))]
+                         for k in range(args.steps)])
 
     # end to end through the C ABI with host buffers: every step copies its scene and
     # target in from pinned host memory and its loss and parameter gradients back out.
@@ -441,9 +433,7 @@ def run_ours(args, rank, world):
         def fn():
             ctx.preprocess(b["st"], [cam])
             ctx.bin_sort(sync=False)
-            ctx.render_fwd(imgs)
-            N.check(L.tri_loss_l1(imgs[0].data_ptr(), b["tgt"].data_ptr(), imgs[0].numel(), grad.data_ptr(),
-                                  b["loss"].data_ptr(), int(torch.cuda.current_stream().cuda_stream)))
+            ctx.render_fwd_l1(imgs, [b["tgt"]], [grad], b["loss"])
             ctx.render_bwd([grad])
             ctx.preprocess_bwd(*b["g"])
         fn()
@@ -594,7 +584,6 @@ def run_multiview(steps: int, warmup: int, n_tris: int = 3_000_000, n_views: int
     """fwd+bwd over all views per step, cameras re-drawn every step (seeded ring offset);
     eager calls, since the cameras change between steps. Returns a dict for the JSON line."""
     import torch
-    from paper_2505_19175_gb300 import native as N
     from paper_2505_19175_gb300 import synth
     from paper_2505_19175_gb300.renderer import Context, SceneTensors
     st = SceneTensors.from_numpy(synth.scene_shells(n_tris, seed=1003))
@@ -611,19 +600,18 @@ def run_multiview(steps: int, warmup: int, n_tris: int = 3_000_000, n_views: int
     ctx = Context()
     ctx.preprocess(st, cams0)
     ctx.reserve(int(ctx.bin_sort(sync=True) * 1.5) + 4096)
-    L = N.lib()
     views = [imgs[v] for v in range(n_views)]
     grads = [grad[v] for v in range(n_views)]
+    tgts = [tgt[v] for v in range(n_views)]
 
     def step(k, fwd_only=False):
         cams = synth.ring_cameras(n_views, W=W, H=H, offset=float(offsets[k]))
         ctx.preprocess(st, cams)
         ctx.bin_sort(sync=False)
-        ctx.render_fwd(views)
         if fwd_only:
+            ctx.render_fwd(views)
             return
-        N.check(L.tri_loss_l1(imgs.data_ptr(), tgt.data_ptr(), imgs.numel(), grad.data_ptr(), loss.data_ptr(),
-                              int(torch.cuda.current_stream().cuda_stream)))
+        ctx.render_fwd_l1(views, tgts, grads, loss)
         ctx.render_bwd(grads)
         ctx.preprocess_bwd(dv, dsh, do, ds)
 
@@ -830,7 +818,6 @@ def run_multiscene(n_req: int, rate_hz: float = 2000.0, budget_gb: float = 60.0)
     fwd+bwd training job of 8 views at 1297x840 runs on scene 0 on its own stream."""
     import threading
     import torch
-    from paper_2505_19175_gb300 import native as N
     from paper_2505_19175_gb300 import synth
     from paper_2505_19175_gb300.renderer import Context, SceneTensors, new_images
     from paper_2505_19175_gb300.serve import Server
@@ -846,7 +833,6 @@ def run_multiscene(n_req: int, rate_hz: float = 2000.0, budget_gb: float = 60.0)
     cams = synth.ring_cameras(8, W=1297, H=840)
     tstream = torch.cuda.Stream()
     ctx = Context()
-    L = N.lib()
     imgs = new_images(cams)
     grads = [torch.empty_like(x) for x in imgs]
     tgt = [torch.rand_like(x) for x in imgs]
@@ -860,10 +846,7 @@ def run_multiscene(n_req: int, rate_hz: float = 2000.0, budget_gb: float = 60.0)
     def train_step():
         ctx.preprocess(st, cams, stream=tstream)
         ctx.bin_sort(sync=False, stream=tstream)
-        ctx.render_fwd(imgs, stream=tstream)
-        for v in range(len(cams)):
-            N.check(L.tri_loss_l1(imgs[v].data_ptr(), tgt[v].data_ptr(), imgs[v].numel(), grads[v].data_ptr(),
-                                  loss.data_ptr(), int(tstream.cuda_stream)))
+        ctx.render_fwd_l1(imgs, [tgt[v] for v in range(len(cams))], grads, loss, stream=tstream)
         ctx.render_bwd(grads, stream=tstream)
         ctx.preprocess_bwd(dv, dsh, do, ds, stream=tstream)
 

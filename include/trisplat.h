@@ -165,6 +165,18 @@ tri_status tri_bin_sort(tri_ctx *ctx, int64_t *num_pairs_out, void *stream);
 tri_status tri_render_fwd(tri_ctx *ctx, float *const *images, float *const *T_final,
                           int32_t *const *n_contrib, void *stream);
 
+/* Step 3 fused with the L1 photometric loss (Sec. 3.3 lists L1 among the loss terms):
+ * as tri_render_fwd (images only), and in the same kernel, per view v,
+ * dL_dimages[v] = sign(image - targets[v]) / n and, when `loss` is not null,
+ * *loss = sum over views of |image - target| / n, with n = sum_v 3 W_v H_v: the values
+ * tri_loss_l1 gives over the views' images as one array (the gradient bit for bit, the
+ * loss up to summation order), without a second pass over the images. targets and
+ * dL_dimages: nviews device pointers [3][H_v][W_v] (caller-owned); loss: a device
+ * float. TRI_ERR_INVALID_ARG for null pointers or with TRI_SORT_PIXEL (use
+ * tri_loss_l1 there); TRI_ERR_STATE after tri_render_solid. Graph-capturable. */
+tri_status tri_render_fwd_l1(tri_ctx *ctx, float *const *images, const float *const *targets,
+                             float *const *dL_dimages, float *loss, void *stream);
+
 /* Step 3 with the pruning statistics of Sec. 3.3 ("Pruning"): as tri_render_fwd, and
  * for every (view, triangle) item m = v n + i, max_weight[m] = the largest blending
  * weight T o over the pixels where the item was composited (T = transmittance in

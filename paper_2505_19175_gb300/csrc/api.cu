@@ -551,7 +551,8 @@ static tri_status render_fwd_pps(tri_ctx *c, RenderArgs &r, cudaStream_t st) {
 
 static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const *T_final,
                                   int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels, void *stream,
-                                  int32_t *const *ids = nullptr) {
+                                  int32_t *const *ids = nullptr, const float *const *targets = nullptr,
+                                  float *const *grads = nullptr, float *loss = nullptr) {
     if (!c) return TRI_ERR_INVALID_ARG;
     NvtxRange nv("tri_render_fwd");
     if (c->stage < 2) return fail(c, TRI_ERR_STATE, "tri_render_fwd before tri_bin_sort");
@@ -563,9 +564,22 @@ static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const
     cudaStream_t st = (cudaStream_t)stream;
     begin_call(c, st);
     std::vector<ViewOut> outs(c->nviews);
-    for (int v = 0; v < c->nviews; ++v) outs[v] = ViewOut{images[v], nullptr};
+    int64_t n_loss = 0;
+    for (int v = 0; v < c->nviews; ++v) {
+        outs[v] = ViewOut{images[v], nullptr};
+        if (targets) {
+            outs[v].target = targets[v];
+            outs[v].grad = grads[v];
+            n_loss += 3 * (int64_t)c->views[v].W * c->views[v].H;
+        }
+    }
     RenderArgs r = render_args(c, c->outs_fwd);
     if ((s = set_outs(c, r, outs, c->outs_fwd, c->h_outs_fwd, st)) != TRI_OK) return s;
+    if (targets) {
+        r.loss = loss;
+        r.loss_scale = 1.0f / (float)n_loss;
+        if (loss) CK(cudaMemsetAsync(loss, 0, sizeof(float), st));
+    }
     if (c->solid) {
         r.kmask = nullptr;
         if (ids) {
@@ -604,6 +618,18 @@ static tri_status render_fwd_impl(tri_ctx *c, float *const *images, float *const
 tri_status tri_render_fwd(tri_ctx *c, float *const *images, float *const *T_final, int32_t *const *n_contrib,
                           void *stream) {
     return render_fwd_impl(c, images, T_final, n_contrib, nullptr, nullptr, stream);
+}
+
+tri_status tri_render_fwd_l1(tri_ctx *c, float *const *images, const float *const *targets, float *const *dL_dimages,
+                             float *loss, void *stream) {
+    if (!c) return TRI_ERR_INVALID_ARG;
+    if (!targets || !dL_dimages) return fail(c, TRI_ERR_INVALID_ARG, "targets or dL_dimages is null");
+    for (int v = 0; v < c->nviews; ++v)
+        if (!targets[v] || !dL_dimages[v]) return fail(c, TRI_ERR_INVALID_ARG, "target or dL_dimage pointer is null");
+    if (c->solid) return fail(c, TRI_ERR_STATE, "the L1 forward after tri_render_solid");
+    if (c->rec_sort == TRI_SORT_PIXEL)
+        return fail(c, TRI_ERR_INVALID_ARG, "the fused L1 loss needs the tile sort (use tri_loss_l1)");
+    return render_fwd_impl(c, images, nullptr, nullptr, nullptr, nullptr, stream, nullptr, targets, dL_dimages, loss);
 }
 
 tri_status tri_render_solid(tri_ctx *c, const tri_scene *scene, const tri_camera *cams, int nviews,

@@ -47,6 +47,8 @@ struct ViewDev {
 struct ViewOut {
     float *image;          // [3][H][W]
     const float *dL;       // [3][H][W] (backward)
+    const float *target = nullptr;   // [3][H][W] forward with the L1 loss: target image
+    float *grad = nullptr;           // [3][H][W] and its dL/dimage output
 };
 
 // Device control block: counters, histograms and work queues of one pipeline run.

@@ -175,6 +175,9 @@ struct RenderArgs {
     unsigned long long cand_cap = 0;
     unsigned long long *pscan_status = nullptr;
     int64_t total_pix = 0;
+    // forward with the L1 loss (views with a target): *loss += loss_scale sum |image - target|
+    float *loss = nullptr;
+    float loss_scale = 0.0f;
 };
 __device__ __forceinline__ ViewOut view_out(const RenderArgs &a, int vw) {
     return a.outs_by_value ? a.outs_inline[vw] : a.outs[vw];

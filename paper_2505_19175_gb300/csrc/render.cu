@@ -107,6 +107,9 @@ __device__ __forceinline__ float cutoff_ratio(const Rec &r, bool solid) {
     return 0.999f * ex2_approx(lg2_approx(ALPHA_MIN / r.c.w) * rcp_approx(r.d.x));
 }
 
+// dL/dd of inv |d| (0 at d = 0): the L1 loss gradient of one value.
+__device__ __forceinline__ float l1_sign(float d, float inv) { return d > 0.f ? inv : (d < 0.f ? -inv : 0.f); }
+
 // Bit w set when the record (cutoff ratio thr) may composite at a pixel of warp w's
 // 8x4 block of the tile with origin (ox, oy).
 __device__ __forceinline__ uint32_t warp_mask(const Rec &r, const ushort4 bx, int ox, int oy, float thr) {
@@ -164,11 +167,13 @@ render_fwd_kernel(RenderArgs a) {
     __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
     __shared__ ViewDev s_view[MAX_VIEWS];
     __shared__ uint32_t s_tile;
+    __shared__ float s_l1[REN_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = lane / GROUP, gl = lane % GROUP;
     for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += REN_THREADS)
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
     int lx, ly;
     pixel_of(tid, lx, ly);
+    float l1_acc = 0.f;               // this thread's share of the L1 loss
 #pragma unroll
     for (int q = 0; q < KM_WORDS; ++q) s_km[q][tid] = 0u;
     s_sw[tid] = 0u;
@@ -297,10 +302,19 @@ render_fwd_kernel(RenderArgs a) {
         if (inside) {
             const int64_t HW = (int64_t)V.W * V.H;
             const int64_t pix = (int64_t)y * V.W + x;
-            float *img = view_out(a, vw).image;
-            img[pix] = fmaf(T, V.bg[0], C0);
-            img[HW + pix] = fmaf(T, V.bg[1], C1);
-            img[2 * HW + pix] = fmaf(T, V.bg[2], C2);
+            const ViewOut vo = view_out(a, vw);
+            const float c[3] = {fmaf(T, V.bg[0], C0), fmaf(T, V.bg[1], C1), fmaf(T, V.bg[2], C2)};
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) vo.image[ch * HW + pix] = c[ch];
+            if (vo.target) {
+                // the L1 loss of the pixel and its gradient, while the colour is in registers
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float d = c[ch] - vo.target[ch * HW + pix];
+                    l1_acc += fabsf(d);
+                    vo.grad[ch * HW + pix] = l1_sign(d, a.loss_scale);
+                }
+            }
             a.T_final[V.pix_base + pix] = T;
             a.n_contrib[V.pix_base + pix] = (int32_t)last;
             if (SOLID && a.ids)
@@ -316,6 +330,20 @@ render_fwd_kernel(RenderArgs a) {
             atomicAdd(&a.ctl->frag_kept, (unsigned long long)wk);
         }
         __syncthreads();
+    }
+    if (a.loss) {
+        // one reduction per CTA
+        float v = l1_acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_l1[w] = v;
+        __syncthreads();
+        if (tid == 0) {
+            float t = 0.f;
+#pragma unroll
+            for (int k = 0; k < REN_THREADS / 32; ++k) t += s_l1[k];
+            atomicAdd(a.loss, t * a.loss_scale);
+        }
     }
     if (last_cta_done(&a.ctl->done[0]) && tid == 0) a.ctl->work_counter[0] = 0u;
 }
@@ -926,7 +954,6 @@ void launch_pps_bwd(const RenderArgs &a, cudaStream_t st) {
 // ---------------------------------------------------------------------------------
 // L1 loss: mean |image - target| and its gradient sign(image - target) / n
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ float l1_sign(float d, float inv) { return d > 0.f ? inv : (d < 0.f ? -inv : 0.f); }
 
 // VEC: img, tgt and grad are 16-byte aligned; float4 accesses, 4 in flight per thread.
 template <bool VEC>

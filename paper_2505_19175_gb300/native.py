@@ -90,6 +90,7 @@ def lib():
             _sig(L, "tri_bin_sort", [vp, P(i64), vp])
             _sig(L, "tri_render_fwd", [vp, P(vp), P(vp), P(vp), vp])
             _sig(L, "tri_render_fwd_stats", [vp, P(vp), P(vp), P(vp), vp, vp, vp])
+            _sig(L, "tri_render_fwd_l1", [vp, P(vp), P(vp), P(vp), vp, vp])
             _sig(L, "tri_densify", [vp, vp, vp, vp, vp, C.c_int, C.c_int64, C.c_int64, vp, C.c_int64, vp, C.c_float,
                                     C.c_float, vp, vp])
             _sig(L, "tri_size_reg", [vp, C.c_int64, C.c_float, vp, vp, vp])

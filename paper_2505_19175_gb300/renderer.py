@@ -117,6 +117,16 @@ class Context:
             self._ck(self._lib.tri_render_fwd_stats(self.h, ims, tf, nc, mw.data_ptr(), npx.data_ptr(),
                                                     _stream_handle(stream)))
 
+    def render_fwd_l1(self, images, targets, grads, loss=None, stream=None) -> None:
+        """Composite the views into ``images`` and, in the same kernel, write the L1
+        loss gradient sign(image - target) / n into ``grads`` and (if given) the mean
+        absolute difference into the device scalar ``loss`` (n = all views' values)."""
+        ims = N.ptr_array([x.data_ptr() for x in images])
+        tg = N.ptr_array([x.data_ptr() for x in targets])
+        gr = N.ptr_array([x.data_ptr() for x in grads])
+        self._ck(self._lib.tri_render_fwd_l1(self.h, ims, tg, gr, loss.data_ptr() if loss is not None else None,
+                                             _stream_handle(stream)))
+
     def set_window(self, window: int) -> None:
         """Window of the next preprocess: ``native.WINDOW_POWER`` (Eq. indicator1, the
         default) or ``native.WINDOW_SIGMOID`` (Eq. indicator2)."""
