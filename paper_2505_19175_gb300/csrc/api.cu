@@ -232,7 +232,9 @@ BinArgs bin_args(tri_ctx *c) {
     b.cap = (uint32_t)c->pair_cap;
     b.total_tiles = c->total_tiles;
     // a stride near 0.618 of the block count and coprime with it: a permutation
-    const uint64_t nblk = (uint64_t)(c->n_items + 255) / 256;
+    b.bin_per = bin_per_for(c->n_items, c->sms);
+    const uint64_t chunk = 256ull * (uint64_t)b.bin_per;
+    const uint64_t nblk = (uint64_t)(c->n_items + chunk - 1) / chunk;
     uint64_t stride = nblk > 2 ? (uint64_t)((double)nblk * 0.6180339887) | 1u : 1u;
     auto gcd = [](uint64_t x, uint64_t y) {
         while (y) {

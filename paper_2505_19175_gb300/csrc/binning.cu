@@ -25,9 +25,11 @@ constexpr int TSORT_THREADS = 256;
 constexpr int WS_MAX = 512;               // words one warp sorts; longer ranges take a CTA
 constexpr int MERGE_PER_THREAD = 8;
 
-// Per-item expansion of a CTA's 256 items into their (item, tile) pairs. Calls
-// f(valid, item, tile) for every pair, in rounds of BIN_THREADS pairs in which all
-// threads of the block take part (so that f may use warp collectives).
+// Per-item expansion into (item, tile) pairs. A CTA takes chunks of bin_per x 256
+// items, compacts the items with a non-zero tile count into shared memory, and expands
+// them 256 at a time: f(valid, item, tile) is called for every pair, in rounds of
+// BIN_THREADS pairs in which all threads of the block take part (so that f may use warp
+// collectives).
 template <class F>
 __device__ __forceinline__ void for_each_pair(const BinArgs &a, F &&f) {
     __shared__ uint32_t s_off[BIN_THREADS];
@@ -36,60 +38,80 @@ __device__ __forceinline__ void for_each_pair(const BinArgs &a, F &&f) {
     __shared__ uint32_t s_wx[BIN_THREADS];          // (rect width in tiles << 16) | view tiles_x
     __shared__ float s_iw[BIN_THREADS];             // 1 / rect width
     __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t s_vis[BIN_THREADS * BIN_PER_MAX];   // the chunk's items that touch a tile
     __shared__ int2 s_vt[MAX_VIEWS];                // (tiles_x, tile_base)
     const int tid = threadIdx.x;
     for (int k = tid; k < a.nviews; k += BIN_THREADS) s_vt[k] = make_int2(a.views[k].tiles_x, a.views[k].tile_base);
     __syncthreads();
-    const uint64_t nblk = (uint64_t)(a.n_items + BIN_THREADS - 1) / BIN_THREADS;
-    for (uint64_t bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
-        // item blocks in a strided order: neighbouring items (often neighbours on screen)
-        // go to CTAs far apart in time, which spreads the atomics over many tiles
-        const int64_t m0 = (int64_t)((bi * a.blk_stride) % nblk) * BIN_THREADS;
-        const int64_t m = m0 + tid;
-        const bool valid = m < a.n_items;
-        const uint32_t nt = valid ? a.ntiles[m] : 0u;
-        uint32_t total;
-        const uint32_t local = block_excl_scan(nt, s_tmp, total);
-        s_off[tid] = local;
-        s_item[tid] = (uint32_t)m;
-        if (nt) {
-            const ushort4 pr = a.rects[m];
-            const uint32_t tx0 = pr.x / TILE, ty0 = pr.y / TILE, wdt = pr.z / TILE - tx0 + 1;
-            const int2 vt = s_vt[a.nviews > 1 ? (int)(m / a.n) : 0];
-            s_base_tile[tid] = (uint32_t)vt.y + ty0 * (uint32_t)vt.x + tx0;
-            s_wx[tid] = (wdt << 16) | (uint32_t)vt.x;
-            s_iw[tid] = 1.0f / (float)wdt;
-        }
-        __syncthreads();
-        for (uint32_t r0 = 0; r0 < total; r0 += BIN_THREADS) {
-            const uint32_t o = r0 + tid;
-            const bool ok = o < total;
-            uint32_t item = 0, tile = 0xffffffffu;
-            if (ok) {
-                // owner: the last thread whose offset is <= o (threads with no tile
-                // share their successor's offset and lose the search)
-                int lo = 0, hi = BIN_THREADS - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_off[mid] <= o) lo = mid;
-                    else hi = mid - 1;
-                }
-                const uint32_t k = o - s_off[lo];
-                const uint32_t wx = s_wx[lo], wdt = wx >> 16, tiles_x = wx & 0xffffu;
-                uint32_t row = (uint32_t)(((float)k + 0.5f) * s_iw[lo]);
-                if (row * wdt > k) --row;                 // guard the FP32 quotient
-                else if ((row + 1) * wdt <= k) ++row;
-                const uint32_t col = k - row * wdt;
-                item = s_item[lo];
-                tile = s_base_tile[lo] + row * tiles_x + col;
-                if (tile >= (uint32_t)a.total_tiles) {
-                    atomicOr(&a.ctl->error, ERR_INDEX);
-                    tile = 0xffffffffu;
-                }
+    const int per = a.bin_per < 1 ? 1 : (a.bin_per > BIN_PER_MAX ? BIN_PER_MAX : a.bin_per);
+    const int64_t chunk = (int64_t)BIN_THREADS * per;
+    const uint64_t nchunk = (uint64_t)((a.n_items + chunk - 1) / chunk);
+    for (uint64_t ci = blockIdx.x; ci < nchunk; ci += gridDim.x) {
+        // chunks in a strided order: neighbouring items (often neighbours on screen) go
+        // to CTAs far apart in time, which spreads the atomics over many tiles
+        const int64_t c0 = (int64_t)((ci * a.blk_stride) % nchunk) * chunk;
+        uint32_t nvis;
+        if (per == 1) {
+            // one round over the chunk itself (items without tiles expand to nothing)
+            nvis = (uint32_t)(a.n_items - c0 < BIN_THREADS ? a.n_items - c0 : BIN_THREADS);
+        } else {
+            uint32_t flags = 0;
+            for (int k = 0; k < per; ++k) {
+                const int64_t m = c0 + (int64_t)k * BIN_THREADS + tid;
+                if (m < a.n_items && a.ntiles[m]) flags |= 1u << k;
             }
-            f(ok && tile != 0xffffffffu, item, tile);
+            uint32_t p = block_excl_scan((uint32_t)__popc(flags), s_tmp, nvis);
+            for (int k = 0; k < per; ++k)
+                if ((flags >> k) & 1u) s_vis[p++] = (uint32_t)(c0 + (int64_t)k * BIN_THREADS + tid);
+            __syncthreads();
         }
-        __syncthreads();
+        for (uint32_t v0 = 0; v0 < nvis; v0 += BIN_THREADS) {
+            const bool valid = v0 + tid < nvis;
+            const uint32_t m = !valid ? 0u : (per == 1 ? (uint32_t)(c0 + tid) : s_vis[v0 + tid]);
+            const uint32_t nt = valid ? a.ntiles[m] : 0u;
+            uint32_t total;
+            const uint32_t local = block_excl_scan(nt, s_tmp, total);
+            s_off[tid] = local;
+            s_item[tid] = m;
+            if (nt) {
+                const ushort4 pr = a.rects[m];
+                const uint32_t tx0 = pr.x / TILE, ty0 = pr.y / TILE, wdt = pr.z / TILE - tx0 + 1;
+                const int2 vt = s_vt[a.nviews > 1 ? (int)((int64_t)m / a.n) : 0];
+                s_base_tile[tid] = (uint32_t)vt.y + ty0 * (uint32_t)vt.x + tx0;
+                s_wx[tid] = (wdt << 16) | (uint32_t)vt.x;
+                s_iw[tid] = 1.0f / (float)wdt;
+            }
+            __syncthreads();
+            for (uint32_t r0 = 0; r0 < total; r0 += BIN_THREADS) {
+                const uint32_t o = r0 + tid;
+                const bool ok = o < total;
+                uint32_t item = 0, tile = 0xffffffffu;
+                if (ok) {
+                    // owner: the last thread whose offset is <= o (threads with no tile
+                    // share their successor's offset and lose the search)
+                    int lo = 0, hi = BIN_THREADS - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_off[mid] <= o) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const uint32_t k = o - s_off[lo];
+                    const uint32_t wx = s_wx[lo], wdt = wx >> 16, tiles_x = wx & 0xffffu;
+                    uint32_t row = (uint32_t)(((float)k + 0.5f) * s_iw[lo]);
+                    if (row * wdt > k) --row;                 // guard the FP32 quotient
+                    else if ((row + 1) * wdt <= k) ++row;
+                    const uint32_t col = k - row * wdt;
+                    item = s_item[lo];
+                    tile = s_base_tile[lo] + row * tiles_x + col;
+                    if (tile >= (uint32_t)a.total_tiles) {
+                        atomicOr(&a.ctl->error, ERR_INDEX);
+                        tile = 0xffffffffu;
+                    }
+                }
+                f(ok && tile != 0xffffffffu, item, tile);
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -459,7 +481,8 @@ void launch_bin_scan(const BinArgs &a, cudaStream_t st) {
 size_t bin_scan_status_words(int total_tiles) { return (size_t)((total_tiles + SCAN_TILE - 1) / SCAN_TILE) + 1; }
 
 void launch_bin_scatter(const BinArgs &a, int sms, cudaStream_t st) {
-    int64_t g = (a.n_items + BIN_THREADS - 1) / BIN_THREADS;
+    const int64_t chunk = (int64_t)BIN_THREADS * (a.bin_per < 1 ? 1 : a.bin_per);
+    int64_t g = (a.n_items + chunk - 1) / chunk;
     if (g > (int64_t)sms * 16) g = (int64_t)sms * 16;
     if (g > 0) bin_scatter_kernel<<<(unsigned)g, BIN_THREADS, 0, st>>>(a);
 }

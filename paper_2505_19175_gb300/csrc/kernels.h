@@ -100,7 +100,8 @@ struct BinArgs {
     uint32_t *tile_order = nullptr; // [total_tiles] if set: tiles by descending pair count
     uint32_t cap;
     int total_tiles;
-    uint64_t blk_stride;            // visiting order of the 256-item blocks: b * stride mod blocks
+    uint64_t blk_stride;            // visiting order of the item chunks: c * stride mod chunks
+    int bin_per = 1;                // chunk = bin_per x 256 items (1..BIN_PER_MAX)
     uint64_t *scan_status;          // [bin_scan_status_words] zeroed look-back words
     uint32_t *scan_ticket;          // zeroed CTA ticket of the scan
     Ctl *ctl;                       // n_pairs / n_pairs_used / overflow, work_counter[2], big_*
@@ -108,6 +109,14 @@ struct BinArgs {
 void launch_bin_scan(const BinArgs &a, cudaStream_t st);
 size_t bin_scan_status_words(int total_tiles);
 void launch_bin_scatter(const BinArgs &a, int sms, cudaStream_t st);
+constexpr int BIN_PER_MAX = 8;
+// Items per thread of a scatter chunk: 1 while 256-item blocks keep every SM busy, more
+// (up to BIN_PER_MAX) when there are many items, so that the mostly empty blocks of a
+// many-view batch cost one compaction instead of a scan each.
+inline int bin_per_for(int64_t n_items, int sms) {
+    const int64_t per = n_items / ((int64_t)sms * 8 * 256 * 4);
+    return per < 1 ? 1 : (per > BIN_PER_MAX ? BIN_PER_MAX : (int)per);
+}
 void launch_tile_sort(const BinArgs &a, int sms, cudaStream_t st);
 
 // ---- densification (densify.cu) ----
