@@ -43,7 +43,8 @@
  *     TRI_ERR_OOM; "slow:MS" delays every tri_bin_sort by MS milliseconds on the host.
  *   Streams: cudaStream_t values are passed as void* (0 = legacy default stream).
  *   CUDA graphs: tri_preprocess, tri_bin_sort (with num_pairs_out = NULL),
- *     tri_render_fwd, tri_render_bwd, tri_preprocess_bwd and tri_loss_l1 may be
+ *     tri_render_fwd, tri_render_fwd_l1, tri_render_bwd, tri_preprocess_bwd and
+ *     tri_loss_l1 may be
  *     captured once the context's buffers are sized by an eager run of the same
  *     workload (a capture allocates nothing). A replay's kernels read the context's
  *     page-locked copies of its camera and output-pointer tables at run time, as written
