@@ -81,3 +81,24 @@ def test_pruning_rules_on_views():
     keep_lo = prune.keep_mask(mw, npix, tau_prune=0.1, min_views=1)
     assert keep_lo.tolist() == [True, True]
     assert prune.keep_mask(mw, npix, tau_prune=0.95).tolist() == [False, False]
+
+
+def test_running_statistics_fold_like_the_whole_array():
+    """Folding batches of views into PruneStats (torch, on the CPU) decides as
+    keep_mask over all views at once, for numpy and torch inputs alike."""
+    import torch
+    from paper_2505_19175_gb300 import prune
+    rng = np.random.default_rng(8)
+    V, n = 7, 500
+    mw = rng.uniform(0, 1, (V, n)).astype(np.float32) * (rng.uniform(size=(V, n)) < 0.6)
+    npix = rng.integers(0, 4, (V, n)).astype(np.int32)
+    want = prune.keep_mask(mw, npix, tau_prune=0.5, min_views=3)
+    st = prune.PruneStats(n, device="cpu")
+    for a, b in ((0, 3), (3, 4), (4, 7)):      # batches of 3, 1 and 3 views
+        st.update(torch.as_tensor(mw[a:b]).reshape(-1), torch.as_tensor(npix[a:b]).reshape(-1))
+    got = st.keep(0.5, min_views=3)
+    assert got.numpy().tolist() == want.tolist()
+    assert prune.keep_mask(torch.as_tensor(mw), torch.as_tensor(npix), 0.5, 3).numpy().tolist() == want.tolist()
+    assert 0 < want.sum() < n
+    st.reset()
+    assert not st.keep(0.0, min_views=1).any()
