@@ -39,7 +39,10 @@ WINDOW_POWER, WINDOW_SIGMOID = 0, 1       # Eq. indicator1 (the paper's), Eq. in
 SORT_TILE, SORT_PIXEL = 0, 1
 EXACT_CONSTS = dict(DEFAULT_CONSTS, alpha_max=1.0, alpha_min=0.0, t_eps=0.0)
 
-AMB_SKIP, AMB_STOP, AMB_ORDER, AMB_SENS, AMB_CULL = 1, 2, 4, 8, 16
+AMB_SKIP, AMB_STOP, AMB_ORDER, AMB_SENS, AMB_CULL, AMB_UNRES, AMB_GRAD = 1, 2, 4, 8, 16, 32, 64
+AMB_DECISION = AMB_SKIP | AMB_STOP | AMB_ORDER | AMB_CULL
+# one listed outcome of a pixel with a decision in the FP32 band (the C record)
+ALT_DTYPE = np.dtype([("pix", "<i4"), ("n_kept", "<i4"), ("image", "<f8", (3,)), ("T", "<f8")])
 
 _lock = threading.Lock()
 _lib = None
@@ -78,6 +81,8 @@ def _load():
             P = ctypes.c_void_p
             lib.orc_render.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, ctypes.c_int,
                                        P, P, P, P, P, P]
+            lib.orc_render_alts.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, ctypes.c_int,
+                                            P, P, P, P, P, P, P, ctypes.c_size_t, P]
             lib.orc_render_grad.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P,
                                             P, P, P, P, P, P, P]
             lib.orc_render_solid.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P, P, P]
@@ -138,10 +143,15 @@ def _const_array(consts):
                      c["tile"], c["rect_pad"], c.get("window", 0), c.get("sort", 0)], dtype=np.float64)
 
 
-def render(scene, cam, consts=None, brute: bool = False, pix_mask=None, flags: bool = False):
+def render(scene, cam, consts=None, brute: bool = False, pix_mask=None, flags: bool = False,
+           alt_capacity: int = 1 << 16):
     """Image [3,H,W], final transmittance [H,W], kept-fragment count [H,W] (FP64).
 
-    With ``flags`` also returns the per-pixel ambiguity bits and error estimate."""
+    With ``flags`` also returns the per-pixel ambiguity bits (AMB_*), the image error
+    estimate, and ``alts``: for each pixel with a decision in the FP32 band, every
+    outcome reached by taking such decisions either way (records of ALT_DTYPE: pixel
+    index y * W + x, kept count, colour, T), at most ``alt_capacity`` records (pixels
+    beyond carry AMB_UNRES)."""
     lib = _load()
     n, verts, sh, opac, sig, deg = _scene_arrays(scene)
     W, H = int(_get(cam, "W")), int(_get(cam, "H"))
@@ -151,14 +161,21 @@ def render(scene, cam, consts=None, brute: bool = False, pix_mask=None, flags: b
     fl = np.zeros((H, W), dtype=np.uint8) if flags else None
     err = np.zeros((H, W), dtype=np.float64) if flags else None
     pm = None if pix_mask is None else np.ascontiguousarray(pix_mask, dtype=np.uint8).reshape(H, W)
-    rc = lib.orc_render(n, _ptr(verts), _ptr(sh), deg, _ptr(opac), _ptr(sig), _ptr(_cam_array(cam)),
-                        _ptr(_const_array(consts)), int(bool(brute)), _ptr(pm), _ptr(img), _ptr(T),
-                        _ptr(nk), _ptr(fl), _ptr(err))
+    if flags:
+        alts = np.zeros(alt_capacity, dtype=ALT_DTYPE)
+        n_alt = ctypes.c_size_t(0)
+        rc = lib.orc_render_alts(n, _ptr(verts), _ptr(sh), deg, _ptr(opac), _ptr(sig), _ptr(_cam_array(cam)),
+                                 _ptr(_const_array(consts)), int(bool(brute)), _ptr(pm), _ptr(img), _ptr(T),
+                                 _ptr(nk), _ptr(fl), _ptr(err), _ptr(alts), alt_capacity, ctypes.byref(n_alt))
+    else:
+        rc = lib.orc_render(n, _ptr(verts), _ptr(sh), deg, _ptr(opac), _ptr(sig), _ptr(_cam_array(cam)),
+                            _ptr(_const_array(consts)), int(bool(brute)), _ptr(pm), _ptr(img), _ptr(T),
+                            _ptr(nk), None, None)
     if rc != 0:
         raise ValueError(f"orc_render failed ({rc})")
     out = dict(image=img, T_final=T, n_kept=nk)
     if flags:
-        out.update(flags=fl, err=err)
+        out.update(flags=fl, err=err, alts=alts[:min(n_alt.value, alt_capacity)].copy())
     return out
 
 

@@ -3,7 +3,7 @@
  * built together with trisplat_oracle.c by tests/test_oracle_sanitize.py with
  * -fsanitize=address,undefined and run on the CPU. It renders a small seeded scene of
  * random triangles (some behind the near plane, some degenerate, some off screen)
- * forward, with flags and statistics, and its adjoint, in both compositing orders and
+ * forward, with flags, alternative outcomes and statistics, and its adjoint, in both compositing orders and
  * both windows, and exits 0; a sanitizer report fails the run.
  */
 #include <stdint.h>
@@ -13,6 +13,10 @@
 int orc_render(int n, const double *verts, const double *sh, int sh_deg, const double *opac, const double *sigma,
                const double *cam, const double *consts, int brute, const uint8_t *pix_mask, double *image,
                double *T_final, int32_t *n_kept, uint8_t *flags, double *err_est);
+int orc_render_alts(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
+                    const double *sigma, const double *cam, const double *consts, int brute,
+                    const uint8_t *pix_mask, double *image, double *T_final, int32_t *n_kept, uint8_t *flags,
+                    double *err_est, void *alts, size_t alt_cap, size_t *alt_n);
 int orc_render_grad(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
                     const double *sigma, const double *cam, const double *consts, const double *dL_dimage,
                     const uint8_t *pix_mask, const uint8_t *tri_mask, double *dverts, double *dsh, double *dopac,
@@ -52,6 +56,7 @@ int main(void) {
     static int32_t n_kept[W * H], ids[W * H], n_pix[N];
     static uint8_t flags[W * H], amb[N];
     static double dverts[N * 9], dsh[N * NK * 3], dopac[N], dsigma[N], mw[N];
+    static double alts[5 * 256];   /* 256 outcome records of 40 bytes */
     for (int k = 0; k < 3 * W * H; ++k) dL[k] = rnd() - 0.5;
     int rc = 0;
     for (int window = 0; window < 2; ++window)
@@ -59,6 +64,12 @@ int main(void) {
             double consts[9] = {0.99, 1.0 / 255.0, 1e-4, 0.2, 1e-4, 16, 1.0 / 512.0, (double)window, (double)sort};
             rc |= orc_render(N, verts, sh, DEG, opac, sigma, cam, consts, 0, NULL, image, T, n_kept, flags, err);
             rc |= orc_render(N, verts, sh, DEG, opac, sigma, cam, consts, 1, NULL, image, T, n_kept, flags, err);
+            /* alternative outcomes, with a list too small for them all */
+            size_t nalt = 0;
+            rc |= orc_render_alts(N, verts, sh, DEG, opac, sigma, cam, consts, 0, NULL, image, T, n_kept, flags, err,
+                                  alts, sizeof alts / 40, &nalt);
+            rc |= orc_render_alts(N, verts, sh, DEG, opac, sigma, cam, consts, 0, NULL, image, T, n_kept, flags, err,
+                                  alts, 1, &nalt);
             rc |= orc_render_grad(N, verts, sh, DEG, opac, sigma, cam, consts, dL, NULL, NULL, dverts, dsh, dopac,
                                   dsigma);
             if (window == 0 && sort == 0) {

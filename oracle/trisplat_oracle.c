@@ -38,7 +38,11 @@
  * For comparisons against an FP32 implementation it also classifies each pixel whose
  * value FP32 arithmetic cannot resolve to the image tolerance: a discontinuous
  * decision (alpha vs ALPHA_MIN, the T_EPS stop, depth order, culling) that lies within
- * an FP32 error band, or a first-order error estimate above half of 1e-4.
+ * an FP32 error band, or a first-order error estimate above half of 1e-4. Where a
+ * decision lies in the band, either outcome is what the method computes in FP32, so
+ * for those pixels it also lists every outcome reached by taking each such decision
+ * both ways (and every order of depths within the band), each evaluated in FP64 by
+ * the same compositing rule.
  */
 #include <math.h>
 #include <stdint.h>
@@ -100,7 +104,14 @@ static cam_t load_cam(const double *c) {
 #define RECT_BAND 1.0e-3               /* px: FP32 error band of a rectangle bound */
 #define FLAG_TOL 5.0e-5                /* flag a pixel whose error estimate exceeds this */
 
-enum { AMB_SKIP = 1, AMB_STOP = 2, AMB_ORDER = 4, AMB_SENS = 8, AMB_CULL = 16 };
+#define GRAD_TOL 1.0e-4               /* flag (for gradients) a fragment whose derivative is this uncertain */
+
+/* Pixel flags. AMB_SKIP / STOP / ORDER / CULL: a decision within the FP32 band;
+ * AMB_SENS: image error estimate above FLAG_TOL; AMB_UNRES: outcomes not enumerated;
+ * AMB_GRAD: the image value is resolved but the pixel's gradient contribution is not
+ * (a composited fragment whose window derivative or active edge FP32 cannot fix to
+ * GRAD_TOL relative), so gradient comparisons leave the pixel out of the loss. */
+enum { AMB_SKIP = 1, AMB_STOP = 2, AMB_ORDER = 4, AMB_SENS = 8, AMB_CULL = 16, AMB_UNRES = 32, AMB_GRAD = 64 };
 
 /* ------------------------------------------------------------------ */
 /* real spherical harmonics, degree <= 3                               */
@@ -560,6 +571,32 @@ static double ratio_band(const tri2d_t *g, int am, double px, double py) {
     return EPS_LINE * (1.0 + ax + ay);
 }
 
+/* Relative FP32 uncertainty of a composited fragment's contribution to the gradient
+ * (classifier only). The window's derivative, sigma ratio^(sigma-1) for
+ * Eq. indicator1 or kappa I (1 - I) for Eq. indicator2, and the vertex derivative of
+ * the active edge's value (which vanishes with the ratio for the opposite vertex)
+ * carry the ratio's absolute error `band` relative to the ratio itself; and where two
+ * edges are within the band of the maximum, FP32 may take the other one, whose
+ * derivative differs (Sec. 3.1: phi is a max over the edges). */
+static double grad_sens(const consts_t *K, const tri_t *t, const ent_t *f, double band, double px, double py) {
+    const tri2d_t *g = &t->g;
+    double second = -INFINITY;
+    for (int i = 0; i < 3; ++i) {
+        if (i == f->argmax) continue;
+        double L = (g->n[i][0] * px + g->n[i][1] * py + g->d[i]) / g->r;
+        if (L > second) second = L;
+    }
+    /* -ratio is the largest scaled edge value */
+    if (-f->ratio - second <= 2.0 * band) return INFINITY;
+    const double ar = fabs(f->ratio);
+    if (K->window == WIN_SIGMOID) {
+        const double kap = g->r / t->sigma;
+        const double I = 1.0 / (1.0 + exp(-kap * f->ratio));
+        return band * (kap * fabs(1.0 - 2.0 * I) + (ar > 0 ? 1.0 / ar : INFINITY));
+    }
+    return band * (1.0 + fmax(t->sigma, fabs(t->sigma - 1.0))) / ar;
+}
+
 typedef struct {
     int n, sh_deg, nk;
     const double *verts, *sh, *opac, *sigma;
@@ -573,6 +610,11 @@ typedef struct {
     int32_t *n_kept;
     uint8_t *flags;
     double *err_est;
+    /* alternative outcomes of pixels with a decision in the FP32 band (nullable):
+     * a shared list of capacity alt_cap, its fill count at *alt_n */
+    struct alt_s *alts;
+    size_t alt_cap;
+    size_t *alt_n;
     /* pruning statistics per triangle (nullable, Sec. 3.3 "Pruning"): largest
      * blending weight T o over its composited fragments, number of pixels where it
      * was composited, and 1 when a pixel it took part in is flagged */
@@ -593,6 +635,165 @@ static void atomic_add(double *p, double v) {
 #pragma omp atomic
 #endif
     *p += v;
+}
+
+/* ------------------------------------------------------------------ */
+/* alternative outcomes of a pixel whose decisions lie in the FP32 band */
+/* ------------------------------------------------------------------ */
+/* One outcome: the pixel's colour (background included), final transmittance and
+ * number of composited fragments. */
+typedef struct alt_s {
+    int32_t pix, nk;
+    double C[3], T;
+} alt_t;
+
+#define ALT_PER_PIX 64   /* outcomes listed per pixel at most */
+#define ALT_RUN_MAX 3    /* longest run of depths within the band that is permuted */
+
+typedef struct {
+    const job_t *J;
+    const ent_t **ord;   /* the pixel's candidate fragments in one admissible order */
+    size_t cnt;
+    double px, py;
+    alt_t leaf[ALT_PER_PIX];
+    int nleaf, over;
+} walk_t;
+
+static void alt_leaf(walk_t *W, double T, const double C[3], int nk) {
+    if (W->nleaf == ALT_PER_PIX) { W->over = 1; return; }
+    alt_t *a = &W->leaf[W->nleaf++];
+    for (int c = 0; c < 3; ++c) a->C[c] = C[c] + T * W->J->C.bg[c];
+    a->T = T;
+    a->nk = nk;
+}
+
+/* the alpha band [alo, ahi] of fragment f, as the classifier of shade_pixel bounds it */
+static void alpha_band(const job_t *J, const ent_t *f, double px, double py, double *alo, double *ahi) {
+    const consts_t *K = &J->K;
+    const tri_t *t = &J->tris[f->id];
+    double band = ratio_band(&t->g, f->argmax, px, py);
+    double wrel = window_rel(K, t, f->ratio);
+    *ahi = t->o * window_I(K, t, f->ratio + band) * (1.0 + wrel);
+    double rlo = f->ratio - band;
+    *alo = (rlo > 0 || K->window == WIN_SIGMOID) ? t->o * window_I(K, t, rlo) * (1.0 - wrel) : 0.0;
+}
+
+/* Composite W->ord[i..] front to back from the state (T, C, nk, dTrel), taking every
+ * keep/skip and stop/continue decision that lies in the FP32 band both ways and every
+ * other decision as FP64 takes it; each path ends in one outcome. */
+static void alt_walk(walk_t *W, size_t i, double T, const double C0[3], int nk, double dTrel) {
+    const job_t *J = W->J;
+    const consts_t *K = &J->K;
+    double C[3] = {C0[0], C0[1], C0[2]};
+    for (; i < W->cnt && !W->over; ++i) {
+        const ent_t *f = W->ord[i];
+        const tri_t *t = &J->tris[f->id];
+        double alo, ahi;
+        alpha_band(J, f, W->px, W->py, &alo, &ahi);
+        const int can_keep = f->kept || ahi >= K->alpha_min;
+        const int can_skip = !f->kept || alo < K->alpha_min;
+        if (!can_keep) continue;
+        if (can_skip) alt_walk(W, i + 1, T, C, nk, dTrel);   /* the fragment skipped */
+        /* the fragment kept: its FP64 alpha (below ALPHA_MIN by rounding when FP64 skips it) */
+        const double a = f->alpha;
+        const double da = alo >= K->alpha_max ? 0.0 : fmax(fmin(ahi, K->alpha_max) - a, a - alo);
+        const double test = T * (1.0 - a);
+        if (K->t_eps > 0) {
+            const double rel = dTrel + da / (1.0 - a) + (nk + 1) * EPS_ACC;
+            const int amb = fabs(test - K->t_eps) <= 2.0 * test * rel;
+            if (test < K->t_eps || amb) alt_leaf(W, T, C, nk);   /* stopped before it */
+            if (test < K->t_eps && !amb) return;
+        }
+        for (int c = 0; c < 3; ++c) C[c] += t->rgb[c] * a * T;
+        T = test;
+        dTrel += da / (1.0 - a);
+        ++nk;
+    }
+    if (!W->over) alt_leaf(W, T, C, nk);
+}
+
+/* next permutation of p[0..n) in lexicographic order; 0 after the last one */
+static int next_perm(int *p, int n) {
+    int i = n - 2;
+    while (i >= 0 && p[i] >= p[i + 1]) --i;
+    if (i < 0) return 0;
+    int j = n - 1;
+    while (p[j] <= p[i]) --j;
+    int tmp = p[i]; p[i] = p[j]; p[j] = tmp;
+    for (int a = i + 1, b = n - 1; a < b; ++a, --b) { tmp = p[a]; p[a] = p[b]; p[b] = tmp; }
+    return 1;
+}
+
+/* List the outcomes of pixel pix into J->alts. The candidates are the fragments that
+ * FP32 may keep; runs of consecutive candidates whose depths lie within the band of
+ * one another may be composited in any order (runs longer than ALT_RUN_MAX are not
+ * enumerated). Returns AMB_UNRES when the outcomes could not all be listed: a cull
+ * decision in the band, a longer run, more than ALT_PER_PIX outcomes, or a full list. */
+static int pixel_alternatives(const job_t *J, const ent_t *e, size_t cnt, int pix, double px, double py) {
+    const consts_t *K = &J->K;
+    const ent_t **cand = (const ent_t **)malloc(sizeof(*cand) * (cnt > 0 ? cnt : 1));
+    size_t nc = 0;
+    for (size_t i = 0; i < cnt; ++i) {
+        if (e[i].kept < 0) { free(cand); return AMB_UNRES; }
+        double alo, ahi;
+        alpha_band(J, &e[i], px, py, &alo, &ahi);
+        if (e[i].kept || ahi >= K->alpha_min) cand[nc++] = &e[i];
+    }
+    /* runs of depths within the band, as run start and length */
+    size_t *rs = (size_t *)malloc(sizeof(size_t) * (nc > 0 ? nc : 1));
+    int *rl = (int *)malloc(sizeof(int) * (nc > 0 ? nc : 1));
+    size_t nr = 0;
+    for (size_t i = 0; i < nc;) {
+        size_t j = i + 1;
+        while (j < nc) {
+            const double dband = (K->sort == SORT_PIXEL ? 64.0 : 4.0) * ulp32(cand[j - 1]->depth);
+            if (fabs(cand[j]->depth - cand[j - 1]->depth) > dband) break;
+            ++j;
+        }
+        if (j - i > 1) { rs[nr] = i; rl[nr] = (int)(j - i); ++nr; }
+        i = j;
+    }
+    walk_t *W = (walk_t *)malloc(sizeof(walk_t));
+    W->J = J; W->cnt = nc; W->px = px; W->py = py; W->nleaf = 0; W->over = 0;
+    W->ord = (const ent_t **)malloc(sizeof(*W->ord) * (nc > 0 ? nc : 1));
+    int unres = 0;
+    for (size_t r = 0; r < nr; ++r)
+        if (rl[r] > ALT_RUN_MAX) unres = 1;
+    /* every combination of one permutation per run (odometer over the runs) */
+    int perm[64][ALT_RUN_MAX];
+    if (nr > 64) unres = 1;
+    for (size_t r = 0; r < nr && !unres; ++r)
+        for (int k = 0; k < rl[r]; ++k) perm[r][k] = k;
+    const double C0[3] = {0.0, 0.0, 0.0};
+    while (!unres && !W->over) {
+        for (size_t i = 0; i < nc; ++i) W->ord[i] = cand[i];
+        for (size_t r = 0; r < nr; ++r)
+            for (int k = 0; k < rl[r]; ++k) W->ord[rs[r] + k] = cand[rs[r] + perm[r][k]];
+        alt_walk(W, 0, 1.0, C0, 0, 0.0);
+        size_t r = 0;
+        while (r < nr && !next_perm(perm[r], rl[r])) ++r;   /* wrapped runs restart at identity */
+        if (r == nr) break;
+    }
+    if (W->over) unres = 1;
+    if (!unres) {
+        size_t base;
+#ifdef _OPENMP
+#pragma omp atomic capture
+#endif
+        { base = *J->alt_n; *J->alt_n += (size_t)W->nleaf; }
+        if (base + (size_t)W->nleaf > J->alt_cap) unres = 1;
+        else
+            for (int k = 0; k < W->nleaf; ++k) {
+                J->alts[base + k] = W->leaf[k];
+                J->alts[base + k].pix = pix;
+            }
+    }
+    free(W->ord);
+    free(W);
+    free(rs);
+    free(rl);
+    free(cand);
+    return unres ? AMB_UNRES : 0;
 }
 
 /* composite one pixel's sorted entries [e0, e1) */
@@ -638,6 +839,7 @@ static void shade_pixel(const job_t *J, const ent_t *e, size_t cnt, int x, int y
             if (fabs(test - K->t_eps) <= 2.0 * test * rel) amb |= AMB_STOP;
         }
         if (test < K->t_eps) break;
+        if (grad_sens(K, t, f, band, px, py) > GRAD_TOL) amb |= AMB_GRAD;
         if (J->n_pix) {
             const double wgt = T * t->o;
 #ifdef _OPENMP
@@ -699,9 +901,11 @@ static void shade_pixel(const job_t *J, const ent_t *e, size_t cnt, int x, int y
     }
     E += nk * 4.0 * EPS_ACC;
     if (E > FLAG_TOL) amb |= AMB_SENS;
+    if (J->alts && (amb & (AMB_SKIP | AMB_STOP | AMB_ORDER | AMB_CULL)))
+        amb |= pixel_alternatives(J, e, cnt, (int)pix, px, py);
     if (J->flags) J->flags[pix] = (uint8_t)amb;
     if (J->err_est) J->err_est[pix] = E;
-    if (J->tri_amb && amb)
+    if (J->tri_amb && (amb & ~AMB_GRAD))
         for (size_t i = 0; i < cnt; ++i) J->tri_amb[e[i].id] = 1;   /* benign race: all write 1 */
 }
 
@@ -859,12 +1063,17 @@ int orc_max_threads(void) {
 #endif
 }
 
-/* Forward render. image [3,H,W], T_final [H,W], n_kept [H,W]; flags / err_est nullable. */
-int orc_render(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
-               const double *sigma, const double *cam, const double *consts, int brute,
-               const uint8_t *pix_mask, double *image, double *T_final, int32_t *n_kept,
-               uint8_t *flags, double *err_est) {
+/* Forward render. image [3,H,W], T_final [H,W], n_kept [H,W]; flags / err_est nullable.
+ * alts (nullable, capacity alt_cap records of {int32 pix, int32 n_kept, double
+ * colour[3], double T}): every outcome of each pixel with a decision in the FP32
+ * band, listed in any order, their number in *alt_n (which may exceed alt_cap, the
+ * excess pixels then carry AMB_UNRES). */
+static int render_impl(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
+                       const double *sigma, const double *cam, const double *consts, int brute,
+                       const uint8_t *pix_mask, double *image, double *T_final, int32_t *n_kept,
+                       uint8_t *flags, double *err_est, alt_t *alts, size_t alt_cap, size_t *alt_n) {
     if (n < 0 || sh_deg < 0 || sh_deg > 3) return 1;
+    if (alts && (!alt_n || !flags)) return 1;
     job_t J;
     memset(&J, 0, sizeof J);
     J.n = n; J.sh_deg = sh_deg; J.nk = (sh_deg + 1) * (sh_deg + 1);
@@ -872,10 +1081,27 @@ int orc_render(int n, const double *verts, const double *sh, int sh_deg, const d
     J.C = load_cam(cam); J.K = load_consts(consts);
     J.brute = brute; J.pix_mask = pix_mask;
     J.image = image; J.T_final = T_final; J.n_kept = n_kept; J.flags = flags; J.err_est = err_est;
+    if (alts) { J.alts = alts; J.alt_cap = alt_cap; J.alt_n = alt_n; *alt_n = 0; }
     J.tris = setup_all(n, verts, sh, sh_deg, opac, sigma, &J.C, &J.K);
     run_job(&J);
     free(J.tris);
     return 0;
+}
+
+int orc_render(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
+               const double *sigma, const double *cam, const double *consts, int brute,
+               const uint8_t *pix_mask, double *image, double *T_final, int32_t *n_kept,
+               uint8_t *flags, double *err_est) {
+    return render_impl(n, verts, sh, sh_deg, opac, sigma, cam, consts, brute, pix_mask, image, T_final, n_kept,
+                       flags, err_est, NULL, 0, NULL);
+}
+
+int orc_render_alts(int n, const double *verts, const double *sh, int sh_deg, const double *opac,
+                    const double *sigma, const double *cam, const double *consts, int brute,
+                    const uint8_t *pix_mask, double *image, double *T_final, int32_t *n_kept,
+                    uint8_t *flags, double *err_est, void *alts, size_t alt_cap, size_t *alt_n) {
+    return render_impl(n, verts, sh, sh_deg, opac, sigma, cam, consts, brute, pix_mask, image, T_final, n_kept,
+                       flags, err_est, (alt_t *)alts, alt_cap, alt_n);
 }
 
 /* Pruning statistics (Sec. 3.3 "Pruning"), per triangle: max_weight = largest T o over
