@@ -99,7 +99,10 @@ struct __align__(16) Rec {
 };
 
 // Per-item gradient record, same 16-float footprint:
-//   (g_sx, g_sy, gA0, gB0, gA1, gB1, gA2, gB2, g_o, g_sigma, g_r, g_g, g_b, 0, 0, 0)
+//   (g_sx, g_sy, gA0, gB0, gA1, gB1, gA2, gB2, g_o, g_sigma, g_r, g_g, g_b, gC0, gC1, gC2)
+// with the line slopes' gradients taken about s_hi (gA_i = sum dL/dm_i (p.x - s_hi.x))
+// and gC_i = sum dL/dm_i, from which the preprocess backward moves them to the exact
+// incenter s = s_hi + s_lo: dL/dA_i = gA_i - s_lo.x gC_i.
 constexpr int GRAD_FIELDS = 16;
 
 // ---------------------------------------------------------------------------------

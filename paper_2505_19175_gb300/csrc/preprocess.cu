@@ -373,9 +373,17 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         const float sig_i = WIN == WIN_SIGMOID ? __ldg(a.sigma + i) : 0.0f;
         if constexpr (WIN == WIN_SIGMOID) gsig -= G2.y * g.r / (sig_i * sig_i);
         else gsig += G2.y;
+        // The render took the slopes' gradients about the forward's rounded incenter
+        // s_hi (its lines are m_i = C_i + A_i (p - s_hi), C_i = 1 - A_i . s_lo): moved to
+        // the exact incenter s = q0 + S = s_hi + s_lo, dL/dA_i = gA_i - s_lo.x gC_i.
+        const float2 shi = *reinterpret_cast<const float2 *>(a.recs + m);
+        const ff dxs = two_sum(g.u0.hi, -shi.x), dys = two_sum(g.v0.hi, -shi.y);
+        const float slx = __fadd_rn(__fadd_rn(dxs.hi, g.S.x), __fadd_rn(dxs.lo, g.u0.lo));
+        const float sly = __fadd_rn(__fadd_rn(dys.hi, g.S.y), __fadd_rn(dys.lo, g.v0.lo));
         // s = q0 + S
         const float gsx = G0.x, gsy = G0.y;
-        const float gA[3] = {G0.z, G1.x, G1.z}, gB[3] = {G0.w, G1.y, G1.w};
+        const float gA[3] = {fmaf(-slx, G3.y, G0.z), fmaf(-slx, G3.z, G1.x), fmaf(-slx, G3.w, G1.z)};
+        const float gB[3] = {fmaf(-sly, G3.y, G0.w), fmaf(-sly, G3.z, G1.y), fmaf(-sly, G3.w, G1.w)};
         float gq0x = gsx, gq0y = gsy;
         float gQ1x = 0.f, gQ1y = 0.f, gQ2x = 0.f, gQ2y = 0.f;
         float gell[3] = {0.f, 0.f, 0.f};

@@ -560,6 +560,10 @@ render_bwd_kernel(RenderArgs a) {
                                 gv[5] = ia == 1 ? gB : 0.f;
                                 gv[6] = ia == 2 ? gA : 0.f;
                                 gv[7] = ia == 2 ? gB : 0.f;
+                                // d/dC of the active line (the residual of the rounded incenter)
+                                gv[13] = ia == 0 ? gr : 0.f;
+                                gv[14] = ia == 1 ? gr : 0.f;
+                                gv[15] = ia == 2 ? gr : 0.f;
                             }
                         }
                     }
@@ -567,10 +571,9 @@ render_bwd_kernel(RenderArgs a) {
                 const unsigned bk = __ballot_sync(0xffffffffu, kept);
                 if (bk) {
                     group_reduce16(gv, lane);
-                    // fields 13..15 are padding and receive 0
                     float *dst = a.grad2d + (size_t)item * GRAD_FIELDS + (16 / GROUP) * gl;
                     if (GROUP == 8) {
-                        if ((bk & gmask) && gl < 7) red_add_v2(dst, gv[0], gv[1]);
+                        if (bk & gmask) red_add_v2(dst, gv[0], gv[1]);
                     } else if (GROUP == 4) {
                         if (bk & gmask) red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
                     } else if (bk & gmask) {
@@ -910,12 +913,15 @@ __global__ void __launch_bounds__(256) pps_bwd_kernel(RenderArgs a) {
                 gv[5] = ia == 1 ? gB : 0.f;
                 gv[6] = ia == 2 ? gA : 0.f;
                 gv[7] = ia == 2 ? gB : 0.f;
+                gv[13] = ia == 0 ? gr : 0.f;
+                gv[14] = ia == 1 ? gr : 0.f;
+                gv[15] = ia == 2 ? gr : 0.f;
             }
             float *dst = a.grad2d + (size_t)it * GRAD_FIELDS;
             red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
             red_add_v4(dst + 4, gv[4], gv[5], gv[6], gv[7]);
             red_add_v4(dst + 8, gv[8], gv[9], gv[10], gv[11]);
-            red_add_v4(dst + 12, gv[12], 0.f, 0.f, 0.f);
+            red_add_v4(dst + 12, gv[12], gv[13], gv[14], gv[15]);
         }
     }
 }
