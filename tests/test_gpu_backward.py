@@ -5,28 +5,39 @@ import pytest
 
 import oracle as O
 from paper_2505_19175_gb300 import synth
-from gpu_util import gpu_backward, gpu_forward
+from gpu_util import gpu_backward, gpu_forward, loss_pixels
 
 pytestmark = pytest.mark.gpu
 RTOL = 1e-3
 
 
-def _check_grads(got, want, names=("verts", "sh", "opacity", "sigma")):
+def _check_grads(got, want, names=("verts", "sh", "opacity", "sigma"), label=""):
+    """Every element within |d| <= 1e-3 |g| + 1e-3 rms(g), and each tensor within 1e-3
+    norm-wise, against the oracle adjoint."""
     for k in names:
         g, w = got[k], want[k]
         nw = np.linalg.norm(w)
         assert nw > 0, k
         rel = np.linalg.norm(g - w) / nw
-        assert rel <= RTOL, f"{k}: relative error {rel:.3e}"
         rms = np.sqrt(np.mean(w ** 2))
-        bad = np.abs(g - w) > RTOL * np.abs(w) + RTOL * rms
-        assert bad.mean() <= 1e-3, f"{k}: {bad.sum()} elements outside the element-wise bound"
+        bound = RTOL * np.abs(w) + RTOL * rms
+        excess = np.abs(g - w) / bound
+        bad = np.argwhere(excess > 1.0)
+        order = np.argsort(-excess.reshape(-1))[:5]
+        worst = [(np.unravel_index(i, g.shape), float(g.reshape(-1)[i]), float(w.reshape(-1)[i]),
+                  float(bound.reshape(-1)[i])) for i in order]
+        print(f"[grad] {label} {k}: norm-wise {rel:.3e}, worst element at {excess.max():.3f} of its bound")
+        assert rel <= RTOL, f"{k}: relative error {rel:.3e}"
+        assert len(bad) == 0, f"{k}: {len(bad)} elements outside the element-wise bound; worst {worst}"
 
 
-def _masked_grad(ref, seed, shape):
-    """Random dL/dimage, zero on pixels whose FP32 value is ill-conditioned."""
+def _masked_grad(ref, seed, shape, label=""):
+    """Random dL/dimage on the pixels whose decisions, value and gradient contribution
+    FP32 resolves (the loss is restricted to them; every gradient element is checked)."""
+    ok = loss_pixels(ref)
+    print(f"[flagged] {label}: {int((~ok).sum())} of {ok.size} pixels left out of the loss ({1 - ok.mean():.3%})")
     g = np.random.default_rng(seed).standard_normal(shape)
-    return g * (ref["flags"] == 0)[None]
+    return g * ok[None]
 
 
 @pytest.mark.parametrize("seed", [0, 1])
@@ -35,10 +46,10 @@ def test_backward_random_scene(seed):
     cam = synth.camera_identity(96, 80)
     imgs, T, nc, ctx, st = gpu_forward(scene, [cam])
     ref = O.render(scene, cam, flags=True)
-    g = _masked_grad(ref, seed, (3, cam.H, cam.W))
+    g = _masked_grad(ref, seed, (3, cam.H, cam.W), f"random scene {seed}")
     got = gpu_backward(ctx, st, [g])
     want = O.render_grad(scene, cam, g)
-    _check_grads(got, want)
+    _check_grads(got, want, label=f"random scene {seed}")
 
 
 @pytest.mark.slow
@@ -50,10 +61,12 @@ def test_backward_patch_crop_2k_triangles():
     imgs, T, nc, ctx, st = gpu_forward(crop, [cam])
     ref = O.render(crop, cam, flags=True)
     tgt = synth.target_image(cam.H, cam.W, seed=5)
-    g = np.sign(imgs[0] - tgt) / imgs[0].size * (ref["flags"] == 0)[None]
+    ok = loss_pixels(ref)
+    print(f"[flagged] 2k crop: {int((~ok).sum())} of {ok.size} pixels left out of the loss")
+    g = np.sign(imgs[0] - tgt) / imgs[0].size * ok[None]
     got = gpu_backward(ctx, st, [g])
     want = O.render_grad(crop, cam, g)
-    _check_grads(got, want)
+    _check_grads(got, want, label="2k crop")
 
 
 def test_multiview_gradients_sum_over_views():
@@ -63,11 +76,11 @@ def test_multiview_gradients_sum_over_views():
     gs, total = [], None
     for k, c in enumerate(cams):
         ref = O.render(scene, c, flags=True)
-        gs.append(_masked_grad(ref, 40 + k, (3, c.H, c.W)))
+        gs.append(_masked_grad(ref, 40 + k, (3, c.H, c.W), f"view {k}"))
         w = O.render_grad(scene, c, gs[-1])
         total = w if total is None else {n: total[n] + w[n] for n in w}
     got = gpu_backward(ctx, st, gs)
-    _check_grads(got, total)
+    _check_grads(got, total, label="three views")
 
 
 def test_autograd_function_matches_direct_calls():
@@ -138,7 +151,7 @@ def test_backward_long_tile_lists_with_empty_chunks():
     imgs, T, nc, ctx, st = gpu_forward(scene, [cam])
     assert int(nc[0][16:32, 24:32].max()) > 400
     ref = O.render(scene, cam, flags=True)
-    g = _masked_grad(ref, 8, (3, cam.H, cam.W))
+    g = _masked_grad(ref, 8, (3, cam.H, cam.W), "long lists")
     got = gpu_backward(ctx, st, [g])
     want = O.render_grad(scene, cam, g)
-    _check_grads(got, want)
+    _check_grads(got, want, label="long lists")

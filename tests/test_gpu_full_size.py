@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 from paper_2505_19175_gb300 import synth
-from gpu_util import gpu_backward, gpu_forward
+from gpu_util import UNRESOLVED_CAP, check_image, gpu_backward, gpu_forward, loss_pixels
 from test_gpu_backward import _check_grads
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -21,13 +21,13 @@ def _sample(cam, n, rng):
     return mask
 
 
-def _check_image(img, T, ref, mask):
+def _check_image(img, T, ref, mask, label):
+    """All sampled pixels against the oracle; returns the sampled pixels that may carry
+    a loss (every decision and the gradient contribution resolved in FP32)."""
     sel = mask.astype(bool)
-    ok = sel & (ref["flags"] == 0)
-    assert ok.sum() >= 0.99 * sel.sum()
-    err = np.abs(img - ref["image"])[:, ok]
-    assert err.max() <= TOL, err.max()
-    assert np.abs(T - ref["T_final"])[ok].max() <= TOL
+    check_image(img, T, ref, sel=sel, label=label)
+    ok = loss_pixels(ref, sel)
+    print(f"[flagged] {label}: {int((sel & ~ok).sum())} of {int(sel.sum())} sampled pixels left out of the loss")
     return ok
 
 
@@ -40,12 +40,12 @@ def test_full_size_patch_backward_sampled_pixels():
     mask = _sample(cam, 2000, rng)
     mask[cam.H - 1, ::7] = 1        # ragged bottom row of tiles
     ref = O.render(scene, cam, pix_mask=mask, flags=True)
-    ok = _check_image(imgs[0], T[0], ref, mask)
+    ok = _check_image(imgs[0], T[0], ref, mask, "500k patches")
     g = (rng.standard_normal((3, cam.H, cam.W)) * ok[None]).astype(np.float32)
     got = gpu_backward(ctx, st, [g])
     want = O.render_grad(scene, cam, g, pix_mask=mask)
     assert (np.abs(want["opacity"]) > 0).sum() > 10_000      # many triangles take part
-    _check_grads(got, want)
+    _check_grads(got, want, label="500k patches")
 
 
 def test_full_size_shells_16_views_sampled_pixels():
@@ -62,13 +62,13 @@ def test_full_size_shells_16_views_sampled_pixels():
         cam = cams[v]
         mask = _sample(cam, 1500, rng)
         ref = O.render(scene, cam, pix_mask=mask, flags=True)
-        ok = _check_image(imgs[v], T[v], ref, mask)
+        ok = _check_image(imgs[v], T[v], ref, mask, f"3M shells view {v}")
         dls[v] = (rng.standard_normal((3, cam.H, cam.W)) * ok[None]).astype(np.float32)
         w = O.render_grad(scene, cam, dls[v], pix_mask=mask)
         want = w if want is None else {k: want[k] + w[k] for k in w}
     del imgs, T, nc
     got = gpu_backward(ctx, st, dls)
-    _check_grads(got, want)
+    _check_grads(got, want, label="3M shells")
 
 
 def test_full_size_serving_mixed_resolutions_sampled_pixels():
@@ -94,11 +94,9 @@ def test_full_size_serving_mixed_resolutions_sampled_pixels():
         mask = _sample(cam, 600, rng)
         mask[cam.H - 1, ::11] = 1
         ref = O.render(scene, cam, pix_mask=mask, flags=True)
-        sel = mask.astype(bool)
-        ok = sel & (ref["flags"] == 0)
-        assert ok.sum() >= 0.99 * sel.sum()
-        err = np.abs(out.cpu().numpy().astype(np.float64) - ref["image"])[:, ok]
-        assert err.max() <= TOL, (cam.W, cam.H, err.max())
+        # the server returns images only
+        check_image(out.cpu().numpy().astype(np.float64), None, ref, sel=mask.astype(bool),
+                    label=f"serving {cam.W}x{cam.H}")
     assert seen == {(640, 360), (1280, 720), (1920, 1080)}
     srv.close()
 
@@ -122,7 +120,8 @@ def test_full_size_solid_1080p_sampled_pixels():
     ref = O.render_solid(scene, cam, pix_mask=mask)
     sel = mask.astype(bool)
     ok = sel & (ref["flags"] == 0)
-    assert ok.sum() >= 0.99 * sel.sum()
+    print(f"[flagged] solid 1080p: {int((sel & ~ok).sum())} of {int(sel.sum())} sampled pixels")
+    assert (sel & ~ok).sum() <= UNRESOLVED_CAP * sel.sum()
     np.testing.assert_array_equal(ids[0].cpu().numpy()[ok], ref["id"][ok])
     err = np.abs(imgs[0].cpu().numpy().astype(np.float64) - ref["image"])[:, ok]
     assert err.max() <= TOL, err.max()

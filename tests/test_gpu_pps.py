@@ -1,13 +1,14 @@
 """The per-pixel sort variant on the GPU against the oracle in the same mode (each
 pixel's fragments by the depth of their triangle's plane along its ray): images
-within 1e-4 on the pixels FP32 resolves, composited counts equal, gradients within
-1e-3; and on crossing triangles the GPU result differs from the tile sort exactly where
+within 1e-4 and composited counts equal on the pixels FP32 resolves, the others equal
+to one of the oracle's listed outcomes, gradients within 1e-3; and on crossing triangles the GPU result differs from the tile sort exactly where
 the oracle's does."""
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_2505_19175_gb300 import synth
+from gpu_util import check_image
 from test_gpu_backward import _check_grads, _masked_grad
 from test_oracle_render import one_tri_scene, stack
 
@@ -33,13 +34,8 @@ def _forward(scene, cams, sort=1):
             [x.cpu().numpy() for x in nc], ctx, st)
 
 
-def _compare(img, T, nc, ref, min_ok=0.98):
-    ok = ref["flags"] == 0
-    assert ok.mean() > min_ok, ok.mean()
-    err = np.abs(img - ref["image"])[:, ok]
-    assert err.max() <= 1e-4, err.max()
-    np.testing.assert_allclose(T[ok], ref["T_final"][ok], atol=1e-4)
-    np.testing.assert_array_equal(nc[ok], ref["n_kept"][ok])
+def _compare(img, T, nc, ref, label):
+    check_image(img, T.astype(np.float64), ref, label=label, n_kept=nc)
 
 
 @pytest.mark.parametrize("seed,W,H", [(81, 96, 80), (82, 61, 37)])
@@ -49,7 +45,7 @@ def test_per_pixel_sort_forward_matches_oracle(seed, W, H):
     cam = synth.camera_identity(W, H)
     imgs, T, nc, _, _ = _forward(scene, [cam])
     ref = O.render(scene, cam, PIXEL, flags=True)
-    _compare(imgs[0], T[0], nc[0], ref)
+    _compare(imgs[0], T[0], nc[0], ref, f"per-pixel sort {W}x{H}")
     tile = O.render(scene, cam)
     assert np.abs(tile["image"] - ref["image"]).max() > 1e-2     # the orders really differ
 
@@ -64,7 +60,7 @@ def test_crossing_triangles_follow_the_nearer_plane():
                     s["sigma"].astype(np.float32), 0)
     imgs, T, nc, _, _ = _forward(s, [cam])
     ref = O.render(s, cam, PIXEL, flags=True)
-    _compare(imgs[0], T[0], nc[0], ref, min_ok=0.95)
+    _compare(imgs[0], T[0], nc[0], ref, "crossing triangles")
     tile_gpu = _forward(s, [cam], sort=0)[0][0]
     tile_ref = O.render(s, cam)["image"]
     ok = ref["flags"] == 0
@@ -79,7 +75,7 @@ def test_per_pixel_sort_two_views():
     cams = [synth.camera_look_at((0.2 * k - 0.1, 0.0, -0.3), (0, 0, 3.5), 72, 56) for k in range(2)]
     imgs, T, nc, _, _ = _forward(scene, cams)
     for k, c in enumerate(cams):
-        _compare(imgs[k], T[k], nc[k], O.render(scene, c, PIXEL, flags=True))
+        _compare(imgs[k], T[k], nc[k], O.render(scene, c, PIXEL, flags=True), f"per-pixel sort view {k}")
 
 
 def test_per_pixel_sort_backward_matches_oracle():
@@ -88,7 +84,7 @@ def test_per_pixel_sort_backward_matches_oracle():
     cam = synth.camera_identity(80, 64)
     imgs, T, nc, ctx, st = _forward(scene, [cam])
     ref = O.render(scene, cam, PIXEL, flags=True)
-    g = _masked_grad(ref, 85, (3, cam.H, cam.W))
+    g = _masked_grad(ref, 85, (3, cam.H, cam.W), "per-pixel sort")
     got = gpu_backward(ctx, st, [g])
     want = O.render_grad(scene, cam, g, PIXEL)
-    _check_grads(got, want)
+    _check_grads(got, want, label="per-pixel sort")

@@ -6,6 +6,7 @@ import pytest
 
 import oracle as O
 from paper_2505_19175_gb300 import synth
+from gpu_util import UNRESOLVED_CAP
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +32,8 @@ def test_solid_matches_oracle(seed, W, H):
     imgs, ids, _ = _gpu_solid(scene, [cam])
     ref = O.render_solid(scene, cam)
     ok = ref["flags"] == 0
-    assert ok.mean() > 0.99
+    print(f"[flagged] solid {W}x{H}: {int((~ok).sum())} of {ok.size} pixels")
+    assert (~ok).sum() <= UNRESOLVED_CAP * ok.size
     np.testing.assert_array_equal(ids[0][ok], ref["id"][ok])
     np.testing.assert_allclose(imgs[0][:, ok], ref["image"][:, ok], atol=1e-4)
 
@@ -44,6 +46,8 @@ def test_solid_multiview_and_no_backward():
     for v, cam in enumerate(cams):
         ref = O.render_solid(scene, cam)
         ok = ref["flags"] == 0
+        print(f"[flagged] solid view {v}: {int((~ok).sum())} of {ok.size} pixels")
+        assert (~ok).sum() <= UNRESOLVED_CAP * ok.size
         np.testing.assert_array_equal(ids[v][ok], ref["id"][ok])
         np.testing.assert_allclose(imgs[v][:, ok], ref["image"][:, ok], atol=1e-4)
     import torch

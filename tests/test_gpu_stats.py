@@ -35,9 +35,13 @@ def test_stats_match_oracle(seed):
     for v, cam in enumerate(cams):
         ref = O.render_stats(scene, cam)
         ok = ref["amb"] == 0
-        assert ok.mean() > 0.5
+        # a triangle in a pixel with a decision in the FP32 band may gain or lose that pixel
+        n_flag = int(((O.render(scene, cam, flags=True)["flags"] & np.uint8(0xFF ^ O.AMB_GRAD)) != 0).sum())
+        print(f"[flagged] stats view {v}: {int((~ok).sum())} of {ok.size} triangles in {n_flag} flagged pixels")
+        assert ok.mean() >= 0.99
         np.testing.assert_array_equal(npx[v][ok], ref["n_pix"][ok])
         np.testing.assert_allclose(mw[v][ok], ref["max_weight"][ok], rtol=2e-5, atol=1e-6)
+        assert np.all(np.abs(npx[v][~ok].astype(np.int64) - ref["n_pix"][~ok]) <= n_flag)
         # every triangle, flagged or not, has consistent outputs
         assert np.all((npx[v] > 0) == (mw[v] > 0))
 
