@@ -780,7 +780,6 @@ tri_status tri_preprocess_bwd(tri_ctx *c, float *dverts, float *dsh, float *dopa
     a.nviews = c->nviews;
     a.ntiles = P<uint32_t>(c->ntiles);
     a.grad2d = P<float>(c->grad2d);
-    a.recs = P<Rec>(c->recs);
     a.dverts = dverts;
     a.dsh = dsh;
     a.dopacity = dopacity;

@@ -90,19 +90,20 @@ struct Ctl {
 };
 
 // Render record of one item: 16 floats = 4 x float4 (64 B).
-//   a = (s_hi.x, s_hi.y, A0, B0)   b = (C0, A1, B1, C1)
-//   c = (A2, B2, C2, o)             d = (sigma, r, g, b)
-// Edge line i is m_i(p) = C_i + A_i (p.x - s_hi.x) + B_i (p.y - s_hi.y); m_i = 1 at the
-// incenter, 0 on edge i, and the window ratio phi(p)/phi(s) = min_i m_i(p).
+//   a = (s_hi.x, s_hi.y, A0, B0)   b = (s_lo.x, A1, B1, s_lo.y)
+//   c = (A2, B2, 0, o)              d = (sigma, r, g, b)
+// The incenter is s = s_hi + s_lo (double-float); edge line i is
+// m_i(p) = 1 + A_i (p.x - s.x) + B_i (p.y - s.y), evaluated with p - s =
+// ((p - s_hi) - s_lo), the first difference exact; m_i = 1 at the incenter, 0 on edge
+// i, and the window ratio phi(p)/phi(s) = min_i m_i(p). The line's offset about s_hi,
+// C_i = 1 - A_i s_lo.x - B_i s_lo.y, serves the block tests.
 struct __align__(16) Rec {
     float4 a, b, c, d;
 };
 
 // Per-item gradient record, same 16-float footprint:
-//   (g_sx, g_sy, gA0, gB0, gA1, gB1, gA2, gB2, g_o, g_sigma, g_r, g_g, g_b, gC0, gC1, gC2)
-// with the line slopes' gradients taken about s_hi (gA_i = sum dL/dm_i (p.x - s_hi.x))
-// and gC_i = sum dL/dm_i, from which the preprocess backward moves them to the exact
-// incenter s = s_hi + s_lo: dL/dA_i = gA_i - s_lo.x gC_i.
+//   (g_sx, g_sy, gA0, gB0, gA1, gB1, gA2, gB2, g_o, g_sigma, g_r, g_g, g_b, 0, 0, 0)
+// with the slopes' gradients taken about the exact incenter, gA_i = sum dL/dm_i (p.x - s.x).
 constexpr int GRAD_FIELDS = 16;
 
 // ---------------------------------------------------------------------------------
@@ -180,6 +181,7 @@ __device__ __forceinline__ uint32_t wait_status(const uint32_t *p, uint32_t *err
 
 // Fragment evaluation shared by the forward and backward kernels, so that both take
 // bitwise identical decisions: edge values, window ratio and unclamped alpha.
+// dx, dy = p - s about the exact incenter.
 struct Frag {
     float dx, dy, m0, m1, m2, ratio;
 };
@@ -187,13 +189,18 @@ struct Frag {
 __device__ __forceinline__ Frag eval_lines(const float4 a, const float4 b, const float4 c, float px,
                                            float py) {
     Frag f;
-    f.dx = __fsub_rn(px, a.x);
-    f.dy = __fsub_rn(py, a.y);
-    f.m0 = fmaf(a.z, f.dx, fmaf(a.w, f.dy, b.x));
-    f.m1 = fmaf(b.y, f.dx, fmaf(b.z, f.dy, b.w));
-    f.m2 = fmaf(c.x, f.dx, fmaf(c.y, f.dy, c.z));
+    f.dx = __fsub_rn(__fsub_rn(px, a.x), b.x);
+    f.dy = __fsub_rn(__fsub_rn(py, a.y), b.w);
+    f.m0 = fmaf(a.z, f.dx, fmaf(a.w, f.dy, 1.0f));
+    f.m1 = fmaf(b.y, f.dx, fmaf(b.z, f.dy, 1.0f));
+    f.m2 = fmaf(c.x, f.dx, fmaf(c.y, f.dy, 1.0f));
     f.ratio = fminf(f.m0, fminf(f.m1, f.m2));
     return f;
+}
+
+// Offset of a record's edge line about s_hi: m_i(p) = C_i + A_i (p.x - s_hi.x) + B_i (p.y - s_hi.y).
+__device__ __forceinline__ float line_offset(float A, float B, float4 b) {
+    return fmaf(-A, b.x, fmaf(-B, b.w, 1.0f));
 }
 
 // I = ratio^sigma for ratio > 0

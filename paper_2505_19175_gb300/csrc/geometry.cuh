@@ -74,9 +74,8 @@ struct Geom {
 enum { CULL_NONE = 0, CULL_NEAR = 1, CULL_DEGENERATE = 2 };
 
 // FWD = false (the backward pass, which needs the geometry only to 1e-6 relative):
-// no edge-line slopes (A, B) and approximate reciprocals instead of divisions; vertex
-// 0 is still projected in double-float (u0, v0), from which the backward takes the
-// residual of the forward's rounded incenter.
+// no projection of vertex 0 (u0, v0) and no edge-line slopes (A, B); approximate
+// reciprocals instead of divisions.
 template <bool FWD = true>
 __device__ __forceinline__ int item_geometry(const float *v, const ViewDev &V, Geom &g) {
     ff X = dot3_add(V.R[0], V.R[1], V.R[2], v[0], v[1], v[2], V.t[0]);
@@ -97,8 +96,10 @@ __device__ __forceinline__ int item_geometry(const float *v, const ViewDev &V, G
     g.xc[2] = make_float3(X0 + e2.x, Y0 + e2.y, z2);
     g.depth = __fadd_rn(Z.hi, __fadd_rn(Z.lo, __fmul_rn(__fadd_rn(e1.z, e2.z), 1.0f / 3.0f)));
     if (Z0 < Z_NEAR || z1 < Z_NEAR || z2 < Z_NEAR) return CULL_NEAR;
-    g.u0 = project_ff(X, Z, V.fx, V.cx);
-    g.v0 = project_ff(Y, Z, V.fy, V.cy);
+    if (FWD) {
+        g.u0 = project_ff(X, Z, V.fx, V.cx);
+        g.v0 = project_ff(Y, Z, V.fy, V.cy);
+    }
     // q_k - q_0 = f (e.x z0 - x0 e.z) / (z0 z_k)
     const float i1 = FWD ? 1.0f / (Z0 * z1) : rcp_approx(Z0 * z1), i2 = FWD ? 1.0f / (Z0 * z2) : rcp_approx(Z0 * z2);
     g.Q1 = make_float2(V.fx * fmaf(e1.x, Z0, -X0 * e1.z) * i1, V.fy * fmaf(e1.y, Z0, -Y0 * e1.z) * i1);

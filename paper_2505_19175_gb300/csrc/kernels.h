@@ -32,7 +32,6 @@ struct PreBwdArgs {
     int nviews;
     const uint32_t *ntiles;
     const float *grad2d;       // [items][16]
-    const Rec *recs;           // [items] the forward's records (their rounded incenters s_hi)
     float *dverts, *dsh, *dopacity, *dsigma;
     int accumulate;
     int window = WIN_POWER;

@@ -222,13 +222,10 @@ preprocess_fwd_kernel(PreArgs a) {
         }
         uint32_t key = 0xffffffffu;   // invisible items sort after every depth
         if (nt > 0) {
-            // incenter s = q0 + S in double-float; lines re-based on s_hi
+            // incenter s = q0 + S in double-float (s_hi + s_lo)
             ff sx = two_sum(g.u0.hi, g.S.x);
             ff sy = two_sum(g.v0.hi, g.S.y);
             const float slx = sx.lo + g.u0.lo, sly = sy.lo + g.v0.lo;
-            float C[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) C[k] = fmaf(-g.A[k], slx, fmaf(-g.B[k], sly, 1.0f));
             // colour
             float w0 = cen[0] - V.campos[0], w1 = cen[1] - V.campos[1], w2 = cen[2] - V.campos[2];
             float inv = rsqrtf(fmaf(w0, w0, fmaf(w1, w1, w2 * w2)));
@@ -239,8 +236,8 @@ preprocess_fwd_kernel(PreArgs a) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c], 0.0f);
             rec.a = make_float4(sx.hi, sy.hi, g.A[0], g.B[0]);
-            rec.b = make_float4(C[0], g.A[1], g.B[1], C[1]);
-            rec.c = make_float4(g.A[2], g.B[2], C[2], a.solid ? 1.0f : o);
+            rec.b = make_float4(slx, g.A[1], g.B[1], sly);
+            rec.c = make_float4(g.A[2], g.B[2], 0.0f, a.solid ? 1.0f : o);
             rec.d = make_float4(WIN == WIN_SIGMOID ? g.r / sig : sig, col[0], col[1], col[2]);
             key = __float_as_uint(g.depth);
             ++nvis;
@@ -373,17 +370,9 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         const float sig_i = WIN == WIN_SIGMOID ? __ldg(a.sigma + i) : 0.0f;
         if constexpr (WIN == WIN_SIGMOID) gsig -= G2.y * g.r / (sig_i * sig_i);
         else gsig += G2.y;
-        // The render took the slopes' gradients about the forward's rounded incenter
-        // s_hi (its lines are m_i = C_i + A_i (p - s_hi), C_i = 1 - A_i . s_lo): moved to
-        // the exact incenter s = q0 + S = s_hi + s_lo, dL/dA_i = gA_i - s_lo.x gC_i.
-        const float2 shi = *reinterpret_cast<const float2 *>(a.recs + m);
-        const ff dxs = two_sum(g.u0.hi, -shi.x), dys = two_sum(g.v0.hi, -shi.y);
-        const float slx = __fadd_rn(__fadd_rn(dxs.hi, g.S.x), __fadd_rn(dxs.lo, g.u0.lo));
-        const float sly = __fadd_rn(__fadd_rn(dys.hi, g.S.y), __fadd_rn(dys.lo, g.v0.lo));
         // s = q0 + S
         const float gsx = G0.x, gsy = G0.y;
-        const float gA[3] = {fmaf(-slx, G3.y, G0.z), fmaf(-slx, G3.z, G1.x), fmaf(-slx, G3.w, G1.z)};
-        const float gB[3] = {fmaf(-sly, G3.y, G0.w), fmaf(-sly, G3.z, G1.y), fmaf(-sly, G3.w, G1.w)};
+        const float gA[3] = {G0.z, G1.x, G1.z}, gB[3] = {G0.w, G1.y, G1.w};
         float gq0x = gsx, gq0y = gsy;
         float gQ1x = 0.f, gQ1y = 0.f, gQ2x = 0.f, gQ2y = 0.f;
         float gell[3] = {0.f, 0.f, 0.f};

@@ -90,9 +90,9 @@ __device__ __forceinline__ bool line_reaches(float A, float B, float C, float sx
 // separating-axis test of the block against the record's support).
 __device__ __forceinline__ bool block_hit(const Rec &r, const ushort4 bx, int x0, int x1, int y0, int y1, float thr) {
     if ((int)bx.x > x1 || (int)bx.z < x0 || (int)bx.y > y1 || (int)bx.w < y0) return false;
-    return line_reaches(r.a.z, r.a.w, r.b.x, r.a.x, r.a.y, x0, x1, y0, y1, thr) &&
-           line_reaches(r.b.y, r.b.z, r.b.w, r.a.x, r.a.y, x0, x1, y0, y1, thr) &&
-           line_reaches(r.c.x, r.c.y, r.c.z, r.a.x, r.a.y, x0, x1, y0, y1, thr);
+    return line_reaches(r.a.z, r.a.w, line_offset(r.a.z, r.a.w, r.b), r.a.x, r.a.y, x0, x1, y0, y1, thr) &&
+           line_reaches(r.b.y, r.b.z, line_offset(r.b.y, r.b.z, r.b), r.a.x, r.a.y, x0, x1, y0, y1, thr) &&
+           line_reaches(r.c.x, r.c.y, line_offset(r.c.x, r.c.y, r.b), r.a.x, r.a.y, x0, x1, y0, y1, thr);
 }
 
 // The cutoff ratio below which alpha < 1/255:
@@ -560,10 +560,6 @@ render_bwd_kernel(RenderArgs a) {
                                 gv[5] = ia == 1 ? gB : 0.f;
                                 gv[6] = ia == 2 ? gA : 0.f;
                                 gv[7] = ia == 2 ? gB : 0.f;
-                                // d/dC of the active line (the residual of the rounded incenter)
-                                gv[13] = ia == 0 ? gr : 0.f;
-                                gv[14] = ia == 1 ? gr : 0.f;
-                                gv[15] = ia == 2 ? gr : 0.f;
                             }
                         }
                     }
@@ -571,9 +567,10 @@ render_bwd_kernel(RenderArgs a) {
                 const unsigned bk = __ballot_sync(0xffffffffu, kept);
                 if (bk) {
                     group_reduce16(gv, lane);
+                    // fields 13..15 are padding and receive 0
                     float *dst = a.grad2d + (size_t)item * GRAD_FIELDS + (16 / GROUP) * gl;
                     if (GROUP == 8) {
-                        if (bk & gmask) red_add_v2(dst, gv[0], gv[1]);
+                        if ((bk & gmask) && gl < 7) red_add_v2(dst, gv[0], gv[1]);
                     } else if (GROUP == 4) {
                         if (bk & gmask) red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
                     } else if (bk & gmask) {
@@ -913,15 +910,12 @@ __global__ void __launch_bounds__(256) pps_bwd_kernel(RenderArgs a) {
                 gv[5] = ia == 1 ? gB : 0.f;
                 gv[6] = ia == 2 ? gA : 0.f;
                 gv[7] = ia == 2 ? gB : 0.f;
-                gv[13] = ia == 0 ? gr : 0.f;
-                gv[14] = ia == 1 ? gr : 0.f;
-                gv[15] = ia == 2 ? gr : 0.f;
             }
             float *dst = a.grad2d + (size_t)it * GRAD_FIELDS;
             red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
             red_add_v4(dst + 4, gv[4], gv[5], gv[6], gv[7]);
             red_add_v4(dst + 8, gv[8], gv[9], gv[10], gv[11]);
-            red_add_v4(dst + 12, gv[12], gv[13], gv[14], gv[15]);
+            red_add_v4(dst + 12, gv[12], 0.f, 0.f, 0.f);
         }
     }
 }
