@@ -383,8 +383,11 @@ constexpr int TILE_BLOCKS = TILE_PIX / 32;   // 8x4 blocks of a tile
 template <int WIN>
 __global__ void __launch_bounds__(BWD_THREADS, BWD_CTAS)
 render_bwd_kernel(RenderArgs a) {
-    __shared__ uint32_t s_li[BWD_WARPS][WGROUPS][BWD_CHUNK];   // per warp and group: item ids
-    __shared__ uint8_t s_lj[BWD_WARPS][WGROUPS][BWD_CHUNK];    // and their pair index in the chunk
+    // per warp and group: item ids and their pair index in the chunk; the groups' lists
+    // sit one bank apart (padded strides), so that the groups' reads of their k-th
+    // entries are free of bank conflicts
+    __shared__ uint32_t s_li[BWD_WARPS][WGROUPS][BWD_CHUNK + 1];
+    __shared__ uint8_t s_lj[BWD_WARPS][WGROUPS][BWD_CHUNK + 4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane / GROUP, gl = lane % GROUP;
     const unsigned gmask = ((1u << GROUP) - 1u) << (GROUP * g);
     const unsigned lt_mask = lanemask_lt();
