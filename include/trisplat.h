@@ -240,6 +240,18 @@ tri_status tri_ctx_check(tri_ctx *ctx, tri_ctx_info *info, void *stream);
  *      tiles by descending half-octave bucket of their pair count */
 tri_status tri_debug_copy(tri_ctx *ctx, int which, void *dst, size_t max_bytes, size_t *bytes);
 
+/* Failure-detection test hook (the paper has no counterpart). Every wait of a kernel on
+ * another CTA (the look-back of the single-pass scans) is bounded: after a limit of
+ * device time (1 s) or a cap on its polls it sets the control block's error bit, the
+ * kernel finishes with an invalid result (every access stays within its buffers) and
+ * tri_ctx_check returns TRI_ERR_TIMEOUT. This call makes the next tri_bin_sort's
+ * tile-count scan leave the look-back status word of its CTA `cta` (0-based, 1024
+ * tiles each) unset, so that the CTA after it waits on a word nothing sets, and limits
+ * that scan's waits to `wait_ns` nanoseconds (0: the default). It applies to one
+ * tri_bin_sort; the next tri_preprocess clears the error bit. TRI_ERR_INVALID_ARG for
+ * a null context or a negative cta. */
+tri_status tri_debug_withhold_scan(tri_ctx *ctx, int32_t cta, uint64_t wait_ns);
+
 /* Window function of the context's next tri_preprocess and of the renders that use its
  * records. TRI_WINDOW_POWER (default) is the paper's Eq. indicator1, I =
  * ReLU(phi(p)/phi(s))^sigma; TRI_WINDOW_SIGMOID is Eq. indicator2, the variant the

@@ -460,6 +460,12 @@ tri_status tri_bin_sort(tri_ctx *c, int64_t *num_pairs_out, void *stream) {
     // the scan and the sort leave their tickets, queues and look-back words at zero
     // (last_cta_done), and the scan assigns the pair totals
     BinArgs b = bin_args(c);
+    if (c->test_withhold) {
+        b.withhold = c->test_withhold;
+        if (c->test_wait_ns) b.wait_ns = c->test_wait_ns;
+        c->test_withhold = 0;
+        c->test_wait_ns = 0;
+    }
     // 1. per-tile counts (from tri_preprocess), 2. ranges
     launch_bin_scan(b, st);
     if ((s = launch_check(c, "bin_scan")) != TRI_OK) return s;
@@ -812,6 +818,13 @@ tri_status tri_ctx_check(tri_ctx *c, tri_ctx_info *info, void *stream) {
     if (h.error & ERR_SPIN) return fail(c, TRI_ERR_TIMEOUT, "a bounded device wait gave up");
     if (h.error) return fail(c, TRI_ERR_DEVICE_CHECK, "device-side check failed");
     if (h.overflow) return fail(c, TRI_ERR_CAPACITY, "pair buffer overflow");
+    return TRI_OK;
+}
+
+tri_status tri_debug_withhold_scan(tri_ctx *c, int32_t cta, uint64_t wait_ns) {
+    if (!c || cta < 0) return TRI_ERR_INVALID_ARG;
+    c->test_withhold = (uint32_t)cta + 1u;
+    c->test_wait_ns = wait_ns;
     return TRI_OK;
 }
 

@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) bin_scan_kernel(BinArgs a) {
         }
         const unsigned long long total = __shfl_sync(0xffffffffu, t, SCAN_THREADS / 32 - 1);
         if (lane < SCAN_THREADS / 32) s_w[lane] = t - v;
-        const unsigned long long b = warp_lookback_excl64(a.scan_status, cta, total, &a.ctl->error);
+        const unsigned long long b =
+            warp_lookback_excl64(a.scan_status, cta, total, &a.ctl->error, a.wait_ns, a.withhold != cta + 1);
         if (lane == 0) {
             s_base = b;
             if ((int64_t)(cta + 1) * SCAN_TILE >= T) {

@@ -159,10 +159,16 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Wait for a look-back predecessor's status word to leave 0, for at most ~1 s of
-// device time; on timeout set ERR_SPIN and return 0 (the result is then invalid but
-// the kernel finishes). Waiting stops at once when an error is already set.
-__device__ __forceinline__ uint32_t wait_status(const uint32_t *p, uint32_t *err) {
+// Longest wait of a look-back on its predecessor's status word (device time), and a
+// cap on the polls of one wait in case the timer stalls.
+constexpr uint64_t WAIT_NS = 1000000000ull;
+constexpr uint32_t WAIT_POLLS_MAX = 1u << 24;
+
+// Wait for a look-back predecessor's status word to leave 0, for at most `limit_ns` of
+// device time (and WAIT_POLLS_MAX polls); on timeout set ERR_SPIN and return 0 (the
+// result is then invalid but the kernel finishes). Waiting stops at once when an error
+// is already set.
+__device__ __forceinline__ uint32_t wait_status(const uint32_t *p, uint32_t *err, uint64_t limit_ns = WAIT_NS) {
     uint32_t s = ld_relaxed(p);
     if (s != 0) return s;
     const uint64_t t0 = global_ns();
@@ -170,7 +176,7 @@ __device__ __forceinline__ uint32_t wait_status(const uint32_t *p, uint32_t *err
         s = ld_relaxed(p);
         if (s != 0) return s;
         if ((it & 63) == 63) {
-            if (ld_relaxed(err) != 0 || global_ns() - t0 > 1000000000ull) {
+            if (ld_relaxed(err) != 0 || global_ns() - t0 > limit_ns || it >= WAIT_POLLS_MAX) {
                 atomicOr(err, ERR_SPIN);
                 return LB_PREFIX;  // pretend a zero prefix so the chain ends
             }
@@ -291,8 +297,8 @@ __device__ __forceinline__ void st_relaxed64(uint64_t *p, uint64_t v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// As wait_status, for 64-bit words (bounded: 1 s, then ERR_SPIN and a zero prefix).
-__device__ __forceinline__ uint64_t wait_status64(const uint64_t *p, uint32_t *err) {
+// As wait_status, for 64-bit words (bounded: limit_ns, then ERR_SPIN and a zero prefix).
+__device__ __forceinline__ uint64_t wait_status64(const uint64_t *p, uint32_t *err, uint64_t limit_ns = WAIT_NS) {
     uint64_t s = ld_relaxed64(p);
     if (s != 0) return s;
     const uint64_t t0 = global_ns();
@@ -300,7 +306,7 @@ __device__ __forceinline__ uint64_t wait_status64(const uint64_t *p, uint32_t *e
         s = ld_relaxed64(p);
         if (s != 0) return s;
         if ((it & 63) == 63) {
-            if (ld_relaxed(err) != 0 || global_ns() - t0 > 1000000000ull) {
+            if (ld_relaxed(err) != 0 || global_ns() - t0 > limit_ns || it >= WAIT_POLLS_MAX) {
                 atomicOr(err, ERR_SPIN);
                 return LB64_PREFIX;
             }
@@ -310,20 +316,23 @@ __device__ __forceinline__ uint64_t wait_status64(const uint64_t *p, uint32_t *e
 }
 
 // Warp-parallel decoupled look-back over 64-bit words (called by one full warp):
-// publishes `agg` for tile `idx` and returns the exclusive prefix.
+// publishes `agg` for tile `idx` and returns the exclusive prefix. `publish` = false
+// leaves this tile's word unset (a failure-detection test: the successors' bounded
+// waits then give up after limit_ns).
 __device__ __forceinline__ uint64_t warp_lookback_excl64(uint64_t *status, uint32_t idx, uint64_t agg,
-                                                         uint32_t *err) {
+                                                         uint32_t *err, uint64_t limit_ns = WAIT_NS,
+                                                         bool publish = true) {
     const int lane = threadIdx.x & 31;
     if (idx == 0) {
-        if (lane == 0) st_relaxed64(&status[0], LB64_PREFIX | agg);
+        if (lane == 0 && publish) st_relaxed64(&status[0], LB64_PREFIX | agg);
         return 0;
     }
-    if (lane == 0) st_relaxed64(&status[idx], LB64_AGG | agg);
+    if (lane == 0 && publish) st_relaxed64(&status[idx], LB64_AGG | agg);
     uint64_t excl = 0;
     int base = (int)idx - 1;
     while (true) {
         const int k = base - lane;
-        const uint64_t s = k >= 0 ? wait_status64(&status[k], err) : LB64_PREFIX;
+        const uint64_t s = k >= 0 ? wait_status64(&status[k], err, limit_ns) : LB64_PREFIX;
         const unsigned pre = __ballot_sync(0xffffffffu, (s >> 62) == 2u);
         const int stop = pre ? __ffs(pre) - 1 : 31;
         uint64_t v = lane <= stop ? (s & LB64_MASK) : 0ull;
@@ -333,7 +342,7 @@ __device__ __forceinline__ uint64_t warp_lookback_excl64(uint64_t *status, uint3
         if (pre) break;
         base -= 32;
     }
-    if (lane == 0) st_relaxed64(&status[idx], LB64_PREFIX | ((excl + agg) & LB64_MASK));
+    if (lane == 0 && publish) st_relaxed64(&status[idx], LB64_PREFIX | ((excl + agg) & LB64_MASK));
     return excl;
 }
 

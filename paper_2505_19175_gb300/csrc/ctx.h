@@ -32,6 +32,8 @@ struct tri_ctx {
     int rec_sort = 0;    // compositing order of the current records
     uint64_t cand_cap = 0;   // per-pixel sort: candidate capacity
     long fault_alloc = 0, fault_slow_ms = 0, n_allocs = 0;   // TRI_FAULT injection (tests)
+    uint32_t test_withhold = 0;     // tri_debug_withhold_scan: CTA + 1 (0: none), next tri_bin_sort only
+    uint64_t test_wait_ns = 0;      // and the scan's wait limit (0: the default)
     uint64_t realloc_gen = 0;   // bumped whenever a device buffer is reallocated
     // streams of the previous and the current call: a reallocation waits for both,
     // not for the whole device

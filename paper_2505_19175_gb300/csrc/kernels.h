@@ -105,6 +105,8 @@ struct BinArgs {
     uint64_t *scan_status;          // [bin_scan_status_words] zeroed look-back words
     uint32_t *scan_ticket;          // zeroed CTA ticket of the scan
     Ctl *ctl;                       // n_pairs / n_pairs_used / overflow, work_counter[2], big_*
+    uint64_t wait_ns = WAIT_NS;     // limit of the scan's look-back waits
+    uint32_t withhold = 0;          // test: CTA withhold - 1 of the scan publishes no status
 };
 void launch_bin_scan(const BinArgs &a, cudaStream_t st);
 size_t bin_scan_status_words(int total_tiles);

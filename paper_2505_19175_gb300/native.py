@@ -94,6 +94,7 @@ def lib():
             _sig(L, "tri_densify", [vp, vp, vp, vp, vp, C.c_int, C.c_int64, C.c_int64, vp, C.c_int64, vp, C.c_float,
                                     C.c_float, vp, vp])
             _sig(L, "tri_size_reg", [vp, C.c_int64, C.c_float, vp, vp, vp])
+            _sig(L, "tri_debug_withhold_scan", [vp, C.c_int32, C.c_uint64])
             _sig(L, "tri_set_window", [vp, C.c_int])
             _sig(L, "tri_set_sort", [vp, C.c_int])
             _sig(L, "tri_set_fragment_counting", [vp, C.c_int])

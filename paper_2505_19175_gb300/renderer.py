@@ -186,6 +186,11 @@ class Context:
               "binned": (6, np.uint64, 1), "records": (7, np.float32, 16), "grad2d": (8, np.float32, 16),
               "tile_order": (9, np.uint32, 1)}
 
+    def debug_withhold_scan(self, cta: int = 0, wait_ns: int = 0) -> None:
+        """Failure-detection test hook: the next bin_sort's scan leaves the look-back
+        word of CTA ``cta`` unset and its bounded waits give up after ``wait_ns``."""
+        self._ck(self._lib.tri_debug_withhold_scan(self.h, int(cta), int(wait_ns)))
+
     def debug(self, name: str) -> np.ndarray:
         which, dt, width = self._DEBUG[name]
         info = self.info()

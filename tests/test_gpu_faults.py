@@ -72,3 +72,41 @@ def test_slow_requests_time_out_and_the_server_recovers(monkeypatch):
     t, _ = srv.submit(sid, cam)          # alone in the queue: within its deadline again
     assert srv.wait(t) == 0
     srv.close()
+
+
+def test_bounded_device_wait_gives_up_and_the_context_recovers():
+    """A scan CTA whose predecessor's look-back word nothing sets: its wait gives up
+    after the (shortened) limit, the kernel finishes, tri_ctx_check reports
+    TRI_ERR_TIMEOUT, and the next normal call on the same context renders the image the
+    oracle computes."""
+    import time
+    import torch
+    import oracle as O
+    from gpu_util import check_image
+    from paper_2505_19175_gb300 import native as N
+    from paper_2505_19175_gb300.renderer import Context, SceneTensors, new_images
+    scene = synth.random_scene(2000, seed=82, deg=1, size=(0.05, 0.4))
+    cam = synth.camera_identity(640, 480, fx=600.0)     # 1,200 tiles: two scan CTAs
+    st = SceneTensors.from_numpy(scene)
+    ctx = Context()
+    img = new_images([cam])
+    ctx.preprocess(st, [cam])
+    ctx.debug_withhold_scan(cta=0, wait_ns=2_000_000)   # CTA 1 waits on a word nothing sets
+    t0 = time.perf_counter()
+    ctx.bin_sort(sync=False)
+    ctx.render_fwd(img)
+    with pytest.raises(N.TriError) as e:
+        ctx.check()
+    waited = time.perf_counter() - t0
+    assert e.value.status == N.TRI_ERR_TIMEOUT
+    assert waited < 0.5                                  # the 2 ms limit, not the 1 s default
+    # the same context, a normal run
+    T = [torch.empty((cam.H, cam.W), device="cuda")]
+    ctx.preprocess(st, [cam])
+    ctx.bin_sort(sync=True)
+    ctx.render_fwd(img, T)
+    ctx.check()
+    torch.cuda.synchronize()
+    ref = O.render(scene, cam, flags=True)
+    check_image(img[0].cpu().numpy().astype(np.float64), T[0].cpu().numpy().astype(np.float64), ref,
+                label="after a wait gave up")
