@@ -185,7 +185,7 @@ tri_status tri_render_fwd_l1(tri_ctx *ctx, float *const *images, const float *co
  * those pixels. Both are device arrays of n_items = nviews x n entries (float /
  * int32), overwritten (zeroed first, on the stream). The pruning decisions across
  * views (largest weight below tau_prune; fewer than two views with more than one
- * pixel) are host-side reductions of these arrays. Same errors as tri_render_fwd;
+ * pixel) are device reductions of these arrays (tri_prune_fold, tri_prune_mask). Same errors as tri_render_fwd;
  * TRI_ERR_INVALID_ARG for a null output. */
 tri_status tri_render_fwd_stats(tri_ctx *ctx, float *const *images, float *const *T_final,
                                 int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels,
@@ -310,6 +310,22 @@ tri_status tri_densify(tri_ctx *ctx, float *verts, float *sh, float *opacity, fl
  * 1e-12 contribute nothing. Uses the current device; asynchronous. */
 tri_status tri_size_reg(const float *verts, int64_t n, float weight, float *loss, float *dverts,
                         void *stream);
+
+/* Pruning rule of Sec. 3.3 ("Pruning") on the device, over the statistics that
+ * tri_render_fwd_stats writes. tri_prune_fold folds one call's [nviews][n] (view-major)
+ * max_weight and n_pixels into running per-triangle state: best[n] = max(best,
+ * max_weight of every view), views[n] += the number of views with n_pixels >=
+ * min_pixels ("rendered ... with more than one pixel": min_pixels = 2). Zero best and
+ * views (or keep them from earlier folds) before the first call. tri_prune_mask writes
+ * keep[n] = 1 where best >= tau_prune and views >= min_views ("at least twice":
+ * min_views = 2), else 0. All arrays are caller-owned device memory (float32, int32,
+ * uint8); both calls are asynchronous on `stream`, use the current device, allocate
+ * nothing, and return TRI_ERR_INVALID_ARG for a negative size or a null array (when
+ * there is work: n > 0 and, for the fold, nviews > 0). */
+tri_status tri_prune_fold(const float *max_weight, const int32_t *n_pixels, int nviews, int64_t n, int min_pixels,
+                          float *best, int32_t *views, void *stream);
+tri_status tri_prune_mask(const float *best, const int32_t *views, int64_t n, float tau_prune, int min_views,
+                          uint8_t *keep, void *stream);
 
 /* L1 photometric loss helper (Sec. 3.3 lists L1 among the loss terms): loss = mean
  * |image - target| over n values, written to the device scalar `loss` (may be null),

@@ -305,3 +305,19 @@ def sh_eval(deg, dirs):
     if rc != 0:
         raise ValueError("bad degree")
     return out
+
+
+def prune_keep(max_weight, n_pix, tau_prune: float, min_views: int = 2, min_pixels: int = 2):
+    """The pruning rule of Sec. 3.3 ("Pruning") over per-view statistics max_weight
+    [V, N] (largest blending weight T o of each triangle in each view) and n_pix [V, N]
+    (pixels where it was composited): a triangle is kept when its largest weight over
+    all views reaches tau_prune and it was rendered with more than one pixel
+    (n_pix >= min_pixels) in at least min_views views ("at least twice")."""
+    mw = np.asarray(max_weight, dtype=np.float64)
+    npx = np.asarray(n_pix)
+    keep = np.zeros(mw.shape[1], dtype=bool)
+    for i in range(mw.shape[1]):
+        best = max(mw[v, i] for v in range(mw.shape[0]))
+        views = sum(1 for v in range(mw.shape[0]) if npx[v, i] >= min_pixels)
+        keep[i] = best >= tau_prune and views >= min_views
+    return keep

@@ -728,6 +728,36 @@ tri_status tri_size_reg(const float *verts, int64_t n, float weight, float *loss
     return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
 }
 
+static tri_status current_sms(int *sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return TRI_ERR_CUDA;
+    }
+    return TRI_OK;
+}
+
+tri_status tri_prune_fold(const float *max_weight, const int32_t *n_pixels, int nviews, int64_t n, int min_pixels,
+                          float *best, int32_t *views, void *stream) {
+    if (n < 0 || nviews < 0) return TRI_ERR_INVALID_ARG;
+    if (n == 0 || nviews == 0) return TRI_OK;
+    if (!max_weight || !n_pixels || !best || !views) return TRI_ERR_INVALID_ARG;
+    int sms = 1;
+    if (current_sms(&sms) != TRI_OK) return TRI_ERR_CUDA;
+    launch_prune_fold(max_weight, n_pixels, nviews, n, min_pixels, best, views, sms, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+}
+
+tri_status tri_prune_mask(const float *best, const int32_t *views, int64_t n, float tau_prune, int min_views,
+                          uint8_t *keep, void *stream) {
+    if (n < 0 || (n > 0 && (!best || !views || !keep))) return TRI_ERR_INVALID_ARG;
+    if (n == 0) return TRI_OK;
+    int sms = 1;
+    if (current_sms(&sms) != TRI_OK) return TRI_ERR_CUDA;
+    launch_prune_mask(best, views, n, tau_prune, min_views, keep, sms, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+}
+
 tri_status tri_render_fwd_stats(tri_ctx *c, float *const *images, float *const *T_final,
                                 int32_t *const *n_contrib, float *max_weight, int32_t *n_pixels, void *stream) {
     if (c && (!max_weight || !n_pixels)) return fail(c, TRI_ERR_INVALID_ARG, "statistics outputs are null");

@@ -1,5 +1,5 @@
-// Densification moves and the size regulariser (declared in trisplat.h: tri_densify,
-// tri_size_reg).
+// Densification moves, the size regulariser and the pruning rule (declared in
+// trisplat.h: tri_densify, tri_size_reg, tri_prune_fold, tri_prune_mask).
 //
 // Sec. 3.3 ("Densification"): a selected triangle is split by midpoint subdivision
 // into four that tile it (combined area and region unchanged); one whose area is
@@ -168,6 +168,50 @@ __global__ void __launch_bounds__(DENS_THREADS) size_reg_kernel(const float *__r
             atomicAdd(loss, weight * t);
         }
     }
+}
+
+// Sec. 3.3 ("Pruning"): fold the per-(view, triangle) statistics of one forward into
+// running per-triangle state, best = largest blending weight T o seen, views = number
+// of views in which the triangle was composited at >= min_pixels pixels. One thread
+// per triangle reads its column of the [nviews][n] arrays (coalesced across threads).
+__global__ void __launch_bounds__(DENS_THREADS) prune_fold_kernel(const float *__restrict__ max_weight,
+                                                                const int32_t *__restrict__ n_pixels, int nviews,
+                                                                int64_t n, int min_pixels, float *best,
+                                                                int32_t *views) {
+    for (int64_t i = (int64_t)blockIdx.x * DENS_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * DENS_THREADS) {
+        float b = best[i];
+        int32_t c = views[i];
+        for (int v = 0; v < nviews; ++v) {
+            b = fmaxf(b, __ldg(max_weight + (int64_t)v * n + i));
+            c += __ldg(n_pixels + (int64_t)v * n + i) >= min_pixels ? 1 : 0;
+        }
+        best[i] = b;
+        views[i] = c;
+    }
+}
+
+// keep = best >= tau_prune and views >= min_views (Sec. 3.3: the blending-weight
+// threshold, and "rendered at least twice with more than one pixel").
+__global__ void __launch_bounds__(DENS_THREADS) prune_mask_kernel(const float *__restrict__ best,
+                                                                const int32_t *__restrict__ views, int64_t n,
+                                                                float tau_prune, int min_views, uint8_t *keep) {
+    for (int64_t i = (int64_t)blockIdx.x * DENS_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * DENS_THREADS)
+        keep[i] = (__ldg(best + i) >= tau_prune && __ldg(views + i) >= min_views) ? 1 : 0;
+}
+
+void launch_prune_fold(const float *max_weight, const int32_t *n_pixels, int nviews, int64_t n, int min_pixels,
+                       float *best, int32_t *views, int sms, cudaStream_t st) {
+    int64_t g = (n + DENS_THREADS - 1) / DENS_THREADS;
+    if (g > (int64_t)sms * 8) g = (int64_t)sms * 8;
+    if (g > 0) prune_fold_kernel<<<(unsigned)g, DENS_THREADS, 0, st>>>(max_weight, n_pixels, nviews, n, min_pixels, best,
+                                                                     views);
+}
+
+void launch_prune_mask(const float *best, const int32_t *views, int64_t n, float tau_prune, int min_views,
+                       uint8_t *keep, int sms, cudaStream_t st) {
+    int64_t g = (n + DENS_THREADS - 1) / DENS_THREADS;
+    if (g > (int64_t)sms * 8) g = (int64_t)sms * 8;
+    if (g > 0) prune_mask_kernel<<<(unsigned)g, DENS_THREADS, 0, st>>>(best, views, n, tau_prune, min_views, keep);
 }
 
 void launch_densify(const DensifyArgs &a, cudaStream_t st) {

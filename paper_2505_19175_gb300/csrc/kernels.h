@@ -135,6 +135,10 @@ struct DensifyArgs {
     uint32_t *err;
 };
 void launch_densify(const DensifyArgs &a, cudaStream_t st);
+void launch_prune_fold(const float *max_weight, const int32_t *n_pixels, int nviews, int64_t n, int min_pixels,
+                       float *best, int32_t *views, int sms, cudaStream_t st);
+void launch_prune_mask(const float *best, const int32_t *views, int64_t n, float tau_prune, int min_views,
+                       uint8_t *keep, int sms, cudaStream_t st);
 void launch_size_reg(const float *verts, int64_t n, float weight, float *loss, float *dverts, int sms,
                      cudaStream_t st);
 

@@ -95,6 +95,8 @@ def lib():
                                     C.c_float, vp, vp])
             _sig(L, "tri_size_reg", [vp, C.c_int64, C.c_float, vp, vp, vp])
             _sig(L, "tri_debug_withhold_scan", [vp, C.c_int32, C.c_uint64])
+            _sig(L, "tri_prune_fold", [vp, vp, C.c_int, C.c_int64, C.c_int, vp, vp, vp])
+            _sig(L, "tri_prune_mask", [vp, vp, C.c_int64, C.c_float, C.c_int, vp, vp])
             _sig(L, "tri_set_window", [vp, C.c_int])
             _sig(L, "tri_set_sort", [vp, C.c_int])
             _sig(L, "tri_set_fragment_counting", [vp, C.c_int])

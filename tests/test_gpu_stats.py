@@ -58,9 +58,37 @@ def test_stats_leave_the_image_unchanged_and_drive_pruning():
         np.testing.assert_array_equal(imgs[v].cpu().numpy(), plain[v].astype(np.float32))
     refs = [O.render_stats(scene, c) for c in cams]
     amb = np.any([r["amb"] != 0 for r in refs], axis=0)
-    ref_keep = prune.keep_mask(np.stack([r["max_weight"] for r in refs]), np.stack([r["n_pix"] for r in refs]), 0.05)
+    ref_keep = O.prune_keep(np.stack([r["max_weight"] for r in refs]), np.stack([r["n_pix"] for r in refs]), 0.05)
     ps = prune.PruneStats(scene.n, device="cuda")
     ps.update(torch.as_tensor(mw).cuda(), torch.as_tensor(npx).cuda())
     keep = ps.keep(0.05).cpu().numpy()
     np.testing.assert_array_equal(keep[~amb], ref_keep[~amb])
     assert 0 < keep.sum() < scene.n
+
+
+def test_pruning_rule_on_the_device_folds_batches_of_views():
+    """tri_prune_fold over batches of 3, 1 and 3 views, then tri_prune_mask, decides as
+    the oracle's rule over all seven views at once (weights compared in FP32 on both
+    sides: the statistics are FP32)."""
+    import torch
+    from paper_2505_19175_gb300 import prune
+    rng = np.random.default_rng(8)
+    V, n = 7, 5000
+    mw = (rng.uniform(0, 1, (V, n)) * (rng.uniform(size=(V, n)) < 0.6)).astype(np.float32)
+    npix = rng.integers(0, 4, (V, n)).astype(np.int32)
+    want = O.prune_keep(mw, npix, tau_prune=np.float32(0.5), min_views=3)
+    ps = prune.PruneStats(n, device="cuda")
+    for a, b in ((0, 3), (3, 4), (4, 7)):
+        ps.update(torch.as_tensor(mw[a:b]).cuda().reshape(-1), torch.as_tensor(npix[a:b]).cuda().reshape(-1))
+    np.testing.assert_array_equal(ps.keep(0.5, min_views=3).cpu().numpy(), want)
+    np.testing.assert_array_equal(ps.max_weight.cpu().numpy(), mw.max(0))
+    np.testing.assert_array_equal(ps.views.cpu().numpy(), (npix >= 2).sum(0))
+    whole = prune.keep_mask(torch.as_tensor(mw).cuda(), torch.as_tensor(npix).cuda(), 0.5, 3)
+    np.testing.assert_array_equal(whole.cpu().numpy(), want)
+    assert 0 < want.sum() < n
+    ps.reset()
+    assert not ps.keep(0.0, min_views=1).any()
+    # ragged: one triangle, no views
+    one = prune.PruneStats(1, device="cuda")
+    one.update(torch.zeros(0, device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"))
+    assert not one.keep(0.0, min_views=1).any()

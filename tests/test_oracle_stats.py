@@ -65,7 +65,6 @@ def test_counts_sum_to_the_composited_fragments_and_culled_triangles_are_zero():
 def test_pruning_rules_on_views():
     """Two views: a triangle seen by both with more than one pixel survives the
     'twice with more than one pixel' rule; one seen by a single view does not."""
-    from paper_2505_19175_gb300 import prune
     # the second view is the left 32 columns of the first
     cams = [synth.camera_identity(48, 40, fx=40.0), synth.camera_identity(32, 40, fx=40.0, cx=24.0, cy=20.0)]
     z = np.array([3.0, 3.0, 3.0])
@@ -76,29 +75,20 @@ def test_pruning_rules_on_views():
     assert stats[0]["n_pix"][1] > 1 and stats[1]["n_pix"][1] == 0
     mw = np.stack([s["max_weight"] for s in stats])
     npix = np.stack([s["n_pix"] for s in stats])
-    keep = prune.keep_mask(mw, npix, tau_prune=0.1)
+    keep = O.prune_keep(mw, npix, tau_prune=0.1)
     assert keep.tolist() == [True, False]
-    keep_lo = prune.keep_mask(mw, npix, tau_prune=0.1, min_views=1)
+    keep_lo = O.prune_keep(mw, npix, tau_prune=0.1, min_views=1)
     assert keep_lo.tolist() == [True, True]
-    assert prune.keep_mask(mw, npix, tau_prune=0.95).tolist() == [False, False]
+    assert O.prune_keep(mw, npix, tau_prune=0.95).tolist() == [False, False]
 
 
-def test_running_statistics_fold_like_the_whole_array():
-    """Folding batches of views into PruneStats (torch, on the CPU) decides as
-    keep_mask over all views at once, for numpy and torch inputs alike."""
-    import torch
-    from paper_2505_19175_gb300 import prune
-    rng = np.random.default_rng(8)
-    V, n = 7, 500
-    mw = rng.uniform(0, 1, (V, n)).astype(np.float32) * (rng.uniform(size=(V, n)) < 0.6)
-    npix = rng.integers(0, 4, (V, n)).astype(np.int32)
-    want = prune.keep_mask(mw, npix, tau_prune=0.5, min_views=3)
-    st = prune.PruneStats(n, device="cpu")
-    for a, b in ((0, 3), (3, 4), (4, 7)):      # batches of 3, 1 and 3 views
-        st.update(torch.as_tensor(mw[a:b]).reshape(-1), torch.as_tensor(npix[a:b]).reshape(-1))
-    got = st.keep(0.5, min_views=3)
-    assert got.numpy().tolist() == want.tolist()
-    assert prune.keep_mask(torch.as_tensor(mw), torch.as_tensor(npix), 0.5, 3).numpy().tolist() == want.tolist()
-    assert 0 < want.sum() < n
-    st.reset()
-    assert not st.keep(0.0, min_views=1).any()
+def test_pruning_rule_thresholds_by_hand():
+    """Each clause on a hand-made table: weights at, below and above tau; views with
+    exactly one pixel do not count."""
+    mw = np.array([[0.5, 0.49, 0.9, 0.9, 0.0],
+                   [0.1, 0.30, 0.2, 0.9, 0.0]])
+    npix = np.array([[2, 5, 1, 2, 0],
+                     [2, 5, 7, 1, 0]])
+    assert O.prune_keep(mw, npix, 0.5).tolist() == [True, False, False, False, False]
+    assert O.prune_keep(mw, npix, 0.5, min_views=1).tolist() == [True, False, True, True, False]
+    assert O.prune_keep(mw, npix, 0.5, min_pixels=1).tolist() == [True, False, True, True, False]
