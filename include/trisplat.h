@@ -339,8 +339,10 @@ tri_status tri_loss_l1(const float *image, const float *target, int64_t n, float
  * that owns the device allocator, a real-time loop that reserved every byte up front).
  * It runs the steps of tri_preprocess + tri_bin_sort + tri_render_fwd for one view with
  * all workspace carved from one fixed array in device global memory declared by the
- * library (about 33 MB, held by every GPU that loads the library until the process
- * exits); it calls no cudaMalloc, cudaFree or other allocating routine.
+ * library (37,730,816 bytes = 36.0 MiB, held by every GPU that loads the library until
+ * the process exits); it calls no cudaMalloc, cudaFree or other allocating routine.
+ * Having no context, it always uses the paper's window (Eq. indicator1) and the
+ * per-tile centre-depth order: tri_set_window and tri_set_sort do not apply to it.
  * Limits: scene->n <= TRI_NOALLOC_MAX_TRIANGLES and width * height <=
  * TRI_NOALLOC_MAX_PIXELS (else TRI_ERR_CAPACITY, nothing runs); pairs beyond
  * TRI_NOALLOC_MAX_PAIRS are dropped and reported in *device_status.

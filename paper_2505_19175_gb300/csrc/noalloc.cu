@@ -7,9 +7,11 @@
 // tri_bin_sort + tri_render_fwd on one view, with every piece of workspace carved from
 // one fixed array in device global memory that this file declares; it calls no
 // cudaMalloc, cudaFree or other allocating routine. The caller passes the scene, the
-// camera and the output image (and, optionally, per-pixel outputs).
+// camera and the output image (and, optionally, per-pixel outputs). It takes no
+// context, so it always renders with the paper's window (Eq. indicator1) and the
+// per-tile centre-depth order, whatever tri_set_window / tri_set_sort set elsewhere.
 //
-// The array has a fixed size (about 33 MB), so the scene, pair list and image have
+// The array has a fixed size (37,730,816 bytes, 36.0 MiB), so the scene, pair list and image have
 // fixed maxima (TRI_NOALLOC_MAX_* in trisplat.h); larger inputs are rejected with
 // TRI_ERR_CAPACITY before anything runs. Every GPU that loads this library holds the
 // array until the process exits. All calls share it and it keeps the contents of the
@@ -60,6 +62,9 @@ constexpr size_t OFF_STDEPTH = OFF_NCON + align256(4 * NA_PIXELS);
 constexpr size_t OFF_STEMIT = OFF_STDEPTH + align256(4 * 4 * DEPTH_WORDS);
 constexpr size_t OFF_STPAIRS = OFF_STEMIT + align256(4 * (NA_TRIS / 256 + 2));
 constexpr size_t SCRATCH_BYTES = OFF_STPAIRS + align256(4 * NA_TILE_PASSES * PAIR_WORDS);
+// the size quoted in trisplat.h and above; a change of the limits or of the layout must
+// update both
+static_assert(SCRATCH_BYTES == 37730816, "allocation-free workspace size differs from the documented size");
 
 // The fixed workspace. Host code must not use this name as an address: its device
 // address comes from cudaGetSymbolAddress, once per device.

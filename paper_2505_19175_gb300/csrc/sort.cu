@@ -240,8 +240,11 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(EmitArgs a) {
         }
         const uint32_t k = o - s_off[lo];
         const uint32_t wx = s_wx[lo], wdt = wx >> 16, tiles_x = wx & 0xffffu;
-        // row = k / wdt: exact in FP32 (k < 2^24, the quotient's fraction >= 1 / (2 wdt))
-        const uint32_t row = (uint32_t)(((float)k + 0.5f) * s_iw[lo]);
+        // row = k / wdt: an FP32 estimate (relative error ~2^-23 of the row, so off by at
+        // most one for large rectangles), then corrected to the exact quotient
+        uint32_t row = (uint32_t)(((float)k + 0.5f) * s_iw[lo]);
+        if (row * wdt > k) --row;
+        else if ((row + 1) * wdt <= k) ++row;
         const uint32_t col = k - row * wdt;
         const uint32_t it = s_item[lo];
         const uint32_t tile = s_base_tile[lo] + row * tiles_x + col;
