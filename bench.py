@@ -36,12 +36,51 @@ FALLBACK_HBM_GBS = 6800.0
 # FP32 lanes per SM per clock on the FMA pipe of sm_10x, and MUFU (lg2, ex2, rcp) results
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
-# Algorithmic work per fragment, where a pixel's fragments are the tile-list entries up to
-# its last composited one (the "contributions per pixel" of Sec. 4's figures): forward =
-# 3 edge lines (6 FFMA), max, sigma lg2 (1 FMUL), o I, alpha T, 3 colour FFMA, T FFMA ->
-# 13 FMA-pipe ops and 2 MUFU (lg2, ex2); backward = that recomputation + ~30 FMA-pipe ops
-# of the adjoint and 1 more MUFU (the reciprocal of 1 - alpha).
-FRAG_OPS = {"render_fwd": {"fma": 13, "mufu": 2}, "render_bwd": {"fma": 43, "mufu": 3}}
+# The method's work in the render kernels, counted as the method does it (Sec. 3.1):
+# every tile-list entry a pixel visits up to its termination (the "contributions per
+# pixel", F = sum of n_contrib) costs the three edge-line evaluations, 6 FFMA; only a
+# composited fragment (alpha >= 1/255) costs the rest. Forward, per composited
+# fragment: sigma lg2, o I, 1 - alpha, alpha T, 3 colour FFMA, the T update -> 7
+# FMA-pipe ops and 2 MUFU (lg2, ex2). Backward: the same recomputation + ~30 FMA-pipe
+# ops of the adjoint (37) and 1 more MUFU (the reciprocal of 1 - alpha).
+ENTRY_OPS = {"fma": 6, "mufu": 0}
+COMPOSITED_OPS = {"render_fwd": {"fma": 7, "mufu": 2}, "render_bwd": {"fma": 37, "mufu": 3}}
+# The earlier dense count, which charged every entry up to a pixel's last composited one
+# with the full per-fragment work; kept beside the real fraction as an effective rate.
+DENSE_FRAG_OPS = {"render_fwd": {"fma": 13, "mufu": 2}, "render_bwd": {"fma": 43, "mufu": 3}}
+
+
+def stage_bytes(n: int, views: int, n_vis: int, pairs: int, pixels: int, sh_floats: int = 48,
+                loss: bool = True) -> dict:
+    """Algorithmic DRAM bytes of each stage of one step, every buffer read or written once:
+    - preprocess: parameters (verts 36 B, SH, o, sigma) read; per (view, triangle) its tile
+      count and depth key (8 B); per visible item its record and rectangle (72 B);
+    - bin_sort: per visible item its rectangle, count and key read (16 B); per pair the
+      binned (key, item) word written and read (8 + 8 B) and the sorted item id (4 B);
+    - render_fwd: per pair the item id (4 B), the record (64 B) and the group-mask words
+      (8 B); per pixel colour, T and count written (20 B), with the L1 loss the target read
+      and dL/dimage written (24 B);
+    - render_bwd: per pair the item id, the record and one mask word (72 B); per visible
+      item its gradient record accumulated (64 B); per pixel T, count and dL/dimage (20 B);
+    - preprocess_bwd: parameters read and their gradients written (2 x 236 B at SH
+      degree 3); per (view, triangle) its tile count (4 B); per visible item its gradient
+      record and rounded incenter (80 B)."""
+    params = 4 * (9 + sh_floats + 2)
+    return {"preprocess": n * params + views * n * 8 + n_vis * 72,
+            "bin_sort": n_vis * 16 + pairs * 20,
+            "render_fwd": pairs * 76 + pixels * (44 if loss else 20),
+            "render_bwd": pairs * 72 + n_vis * 64 + pixels * 20,
+            "preprocess_bwd": 2 * n * params + views * n * 4 + n_vis * 80}
+
+
+def stage_gbs(bytes_: dict, ms: dict, hbm_gbs: float) -> dict:
+    """Per stage: algorithmic GB/s over the stage's median time and its fraction of the
+    measured HBM copy rate."""
+    out = {}
+    for k, b in bytes_.items():
+        t = ms[k] / 1e3
+        out[k] = {"bytes": int(b), "gb_s": round(b / t / 1e9, 1), "frac_hbm": round(b / t / 1e9 / hbm_gbs, 4)}
+    return out
 
 
 PROFILE_FILE = os.path.join(ROOT, "profiles", "kernels_patches_500k.md")
@@ -512,21 +551,29 @@ def run_ours(args, rank, world):
     F_eval, F_kept = int(info_counted.frag_evaluated), int(info_counted.frag_composited)
 
     def pipe_roofline(kernel):
+        """The method's work (ENTRY_OPS per entry up to termination, COMPOSITED_OPS per
+        composited fragment) over the stage time, per pipe against that pipe's peak at
+        the measured maximum clock; the binding pipe is the one with the larger
+        fraction."""
         t = med[STAGES.index(kernel)] / 1e3
         best = None
         for pipe, lanes in (("fma", FP32_LANES_PER_SM), ("mufu", MUFU_PER_SM)):
             peak = sms * lanes * clock_mhz * 1e6 / 1e12
-            ach = frags * FRAG_OPS[kernel][pipe] / t / 1e12
+            ops = frags * ENTRY_OPS[pipe] + F_kept * COMPOSITED_OPS[kernel][pipe]
+            ach = ops / t / 1e12
+            dense = frags * DENSE_FRAG_OPS[kernel][pipe] / t / 1e12
             if best is None or ach / peak > best["frac"]:
                 best = {"bound": "alu", "kernel": kernel, "pipe": pipe, "achieved": round(ach, 3),
                         "peak": round(peak, 3), "unit": f"T {pipe.upper()} ops/s", "frac": round(ach / peak, 4),
-                        "units": frags, "unit_of_work": "fragment (pixel-entry up to the last composited one)",
-                        "ops_per_unit": FRAG_OPS[kernel][pipe],
+                        "units": {"entries": frags, "composited": F_kept},
+                        "unit_of_work": "entry (pixel x tile-list entry up to the pixel's termination) and "
+                                        "composited fragment (alpha >= 1/255)",
+                        "ops_per_unit": {"entry": ENTRY_OPS[pipe], "composited": COMPOSITED_OPS[kernel][pipe]},
+                        "time_ms": round(t * 1e3, 4),
+                        "frac_dense_equiv": round(dense / peak, 4),
+                        "frac_dense_equiv_note": f"every entry charged {DENSE_FRAG_OPS[kernel][pipe]} ops: an "
+                                                 "effective rate, not a fraction of executed work",
                         "peak_source": f"{sms} SMs x {lanes} lanes x {clock_mhz:.0f} MHz ({peak_src} max clock)"}
-        # the same over the entries the kernel actually evaluates (after its block culling)
-        ops_eval = F_eval * 11 + F_kept * (10 if kernel == "render_fwd" else 45)
-        fp32_peak = sms * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
-        best["frac_evaluated_entries"] = round(ops_eval / t / 1e12 / fp32_peak, 4)
         best["traffic"] = _profiled_traffic(kernel + "_kernel")
         best["traffic_unit"] = "DRAM bytes per launch (ncu)"
         return best
@@ -552,6 +599,8 @@ def run_ours(args, rank, world):
         "timing": "CUDA-graph replay of the whole step per timed iteration; stage_ms_median from eager "
                   "steps with events between the calls",
         "stage_ms_median": breakdown,
+        "stage_hbm": stage_gbs(stage_bytes(int(st.n), 1, int(info.n_visible), int(info.n_pairs), cam.W * cam.H),
+                               breakdown, float(peaks["hbm_gbs"])),
         "workload_stats": {"pairs": int(info.n_pairs), "visible": int(info.n_visible),
                            "frag_evaluated": F_eval, "frag_composited": F_kept},
         "roofline": roof,
@@ -604,16 +653,28 @@ def run_multiview(steps: int, warmup: int, n_tris: int = 3_000_000, n_views: int
     grads = [grad[v] for v in range(n_views)]
     tgts = [tgt[v] for v in range(n_views)]
 
-    def step(k, fwd_only=False):
+    def step(k, fwd_only=False, ev=None):
         cams = synth.ring_cameras(n_views, W=W, H=H, offset=float(offsets[k]))
+        if ev:
+            ev[0].record()
         ctx.preprocess(st, cams)
+        if ev:
+            ev[1].record()
         ctx.bin_sort(sync=False)
+        if ev:
+            ev[2].record()
         if fwd_only:
             ctx.render_fwd(views)
             return
         ctx.render_fwd_l1(views, tgts, grads, loss)
+        if ev:
+            ev[3].record()
         ctx.render_bwd(grads)
+        if ev:
+            ev[4].record()
         ctx.preprocess_bwd(dv, dsh, do, ds)
+        if ev:
+            ev[5].record()
 
     for k in range(warmup):
         step(k)
@@ -632,18 +693,35 @@ def run_multiview(steps: int, warmup: int, n_tris: int = 3_000_000, n_views: int
     info = ctx.check()
     ms_fwd = timed(warmup + steps, True)
     info_f = ctx.check()
+    # per stage: the same steps with events between the calls (same stream)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(steps)]
+    for i in range(steps):
+        step(warmup + i, ev=evs[i])
+    torch.cuda.synchronize()
+    info_s = ctx.check()
+    stage_ms = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(len(STAGES))] for i in range(steps)])
+    med = {k: round(float(v), 4) for k, v in zip(STAGES, np.median(stage_ms, axis=0))}
     ctx.set_fragment_counting(True)
     step(warmup + 2 * steps)
     info = ctx.check()
+    ctx.set_fragment_counting(False)
+    peaks, _ = _peaks()
+    hbm = float(peaks["hbm_gbs"])
+    nb = stage_bytes(n_tris, n_views, int(info_s.n_visible), int(info_s.n_pairs), n_views * W * H)
     return {"workload": f"{n_tris} tris SH3 on 16 shells, {n_views} ring views {W}x{H} per step, ring offset "
                         "re-drawn every step, fwd+bwd with L1 loss; params 708 MB > L2",
             "it_per_s": round(1000.0 * steps / float(ms.sum()), 3), "ms_per_step_median": round(float(np.median(ms)), 3),
             "views_per_s": round(1000.0 * steps * n_views / float(ms.sum()), 2),
             "fwd_fps_per_view": round(1000.0 * steps * n_views / float(ms_fwd.sum()), 2),
+            "stage_ms_median": med,
+            "sort_share": round(med["bin_sort"] / sum(med.values()), 4),
+            "stage_hbm": stage_gbs(nb, med, hbm),
             "pairs": int(info.n_pairs), "visible_items": int(info.n_visible),
             "frag_evaluated": int(info.frag_evaluated), "frag_composited": int(info.frag_composited),
             "overflow": bool(info.overflow or info_f.overflow), "steps": steps, "warmup": warmup,
-            "timing": "eager calls, CUDA events per step"}
+            "timing": "eager calls, CUDA events per step; stage_ms_median from steps with events between the "
+                      "calls; stage_hbm = algorithmic bytes (stage_bytes) over the stage time, against the "
+                      "measured HBM copy rate"}
 
 
 # ---------------------------------------------------------------------------------------
@@ -780,33 +858,49 @@ def replay(srv, sid, trace, max_time_s=60.0):
     return time.perf_counter() - t0
 
 
-def run_serving(n_req: int, rate_hz: float, n_tris: int):
+def serve_trace(scene, trace, warm_rate: float, **kw) -> dict:
+    """One server over one open-loop trace (after a warm-up trace of the same mix that
+    grows the workspaces and captures the graphs); its latency and throughput stats."""
     import torch
     from paper_2505_19175_gb300 import synth
-    from paper_2505_19175_gb300.renderer import SceneTensors
     from paper_2505_19175_gb300.serve import Server
+    srv = Server(max_width=1920, max_height=1080, use_graphs=True, **kw)
+    sid = srv.add_scene(scene)
+    replay(srv, sid, synth.serve_requests(512, seed=999, rate_hz=warm_rate))
+    torch.cuda.synchronize()
+    srv.reset_stats()
+    wall = replay(srv, sid, trace)
+    st = srv.stats()
+    srv.close()
+    return {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+            "max_ms": round(st["max_ms"], 3), "fps": round(st["fps"], 1),
+            "completed": int(st["completed"]), "mean_batch": round(st["mean_batch"], 2),
+            "queue_p99_ms": round(st["queue_p99_ms"], 3), "graph_replays": int(st["graph_replays"]),
+            "graph_captures": int(st["graph_captures"]), "eager_batches": int(st["eager_batches"]),
+            "reruns": int(st["reruns"]), "reallocs": int(st["reallocs"]),
+            "capture_ms": round(st["capture_ms"], 2), "eager_ms": round(st["eager_ms"], 2),
+            "wall_s": round(wall, 3), **kw}
+
+
+def run_serving(n_req: int, rate_hz: float, n_tris: int, saturation_rates=(2000.0, 8000.0, 20000.0)):
+    from paper_2505_19175_gb300 import synth
+    from paper_2505_19175_gb300.renderer import SceneTensors
     scene = SceneTensors.from_numpy(synth.scene_shells(n_tris, seed=1004))
     trace = synth.serve_requests(n_req, seed=1004, rate_hz=rate_hz)
     out = {"workload": f"{n_tris} tris SH3 shells, {n_req} requests, Poisson {rate_hz:.0f} req/s, "
                        "640x360 : 1280x720 : 1920x1080 = 2:2:1, open-loop"}
     for name, kw in (("batched", dict(max_batch=16, slots=4)), ("one_request_per_launch", dict(max_batch=1, slots=1))):
-        srv = Server(max_width=1920, max_height=1080, use_graphs=True, **kw)
-        sid = srv.add_scene(scene)
-        # warm-up on another trace of the same mix: grows workspaces, captures graphs
-        replay(srv, sid, synth.serve_requests(512, seed=999, rate_hz=rate_hz))
-        torch.cuda.synchronize()
-        srv.reset_stats()
-        wall = replay(srv, sid, trace)
-        st = srv.stats()
-        srv.close()
-        out[name] = {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
-                     "max_ms": round(st["max_ms"], 3), "fps": round(st["fps"], 1),
-                     "completed": int(st["completed"]), "mean_batch": round(st["mean_batch"], 2),
-                     "queue_p99_ms": round(st["queue_p99_ms"], 3), "graph_replays": int(st["graph_replays"]),
-                     "graph_captures": int(st["graph_captures"]), "eager_batches": int(st["eager_batches"]),
-                     "reruns": int(st["reruns"]), "reallocs": int(st["reallocs"]),
-                     "capture_ms": round(st["capture_ms"], 2), "eager_ms": round(st["eager_ms"], 2),
-                     "wall_s": round(wall, 3), **kw}
+        out[name] = serve_trace(scene, trace, rate_hz, **kw)
+    # continuous batching against one request per launch at equal concurrency (4 slots,
+    # each its own stream), at the arrival rate above and at rates beyond what one
+    # request per launch sustains; the same trace shape (seed) at each rate
+    sat = {"note": "same Poisson trace seed at each rate; both arms 4 slots; fps = completed / wall"}
+    for r in saturation_rates:
+        tr = synth.serve_requests(n_req, seed=1004, rate_hz=r)
+        sat[f"{r:.0f}_req_s"] = {name: serve_trace(scene, tr, r, **kw) for name, kw in
+                                 (("batched", dict(max_batch=16, slots=4)),
+                                  ("unbatched", dict(max_batch=1, slots=4)))}
+    out["equal_slots"] = sat
     return out
 
 
