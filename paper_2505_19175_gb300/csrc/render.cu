@@ -1,13 +1,11 @@
 // Tile rendering of the triangle-splat renderer, forward and backward.
 //
-// A tile is 16x16 pixels, one thread per pixel, cut into eight 8x4 blocks (one warp
-// each) and each block into groups of GROUP lanes (eight 2x2 groups of 4 lanes by
-// default; 2x4 groups of 8 or 2x1 groups of 2 with KM_GROUP=8 or 2, both measured
-// slower on the patches workload). Tiles are taken from device work queues by
-// persistent grids, so a launch serves any mix of views and resolutions.
+// A tile is 16x16 pixels, cut into eight 8x4 blocks and each block into eight 2x2
+// groups. Tiles are taken from device work queues by persistent grids, so a launch
+// serves any mix of views and resolutions.
 //
 // Forward (Sec. 3.1, the rendering equation of prior splatting work): one CTA of 256
-// threads per tile; the tile's depth-sorted records are staged through shared memory
+// threads per tile, one thread per pixel and one warp per block; the tile's depth-sorted records are staged through shared memory
 // 256 at a time (64 B each, one coalesced float4 x 4 gather per thread) and each warp
 // walks the list of records whose support meets its block. Per pixel,
 // ratio = min_i m_i(p) (phi(p)/phi(s) of Eq. indicator1), I = ratio^sigma, alpha = o I,
@@ -16,13 +14,16 @@
 // also records, per pair, which groups composited it (one bit per group, KM_WORDS
 // 32-bit words per pair), and per group the largest composited index.
 //
-// Backward: one warp per (tile, block) work unit, with no CTA-wide barrier. Each group
-// walks only the pairs it composited, back to front: per pixel
-// T_k = T_{k+1} / (1 - alpha_k), dL/dalpha_k = sum_c g_c (rgb_c T_k - B_c / (1 - alpha_k))
-// with B the colour behind fragment k plus T_final bg. The 13 record-field gradients
-// are summed over each group with a transposed butterfly (all the warp's groups'
-// records at once) and added to the per-item gradient record with one vector
-// reduction per lane.
+// Backward: one warp per half tile (16x8 pixels) and one lane per 2x2 group of it,
+// with no CTA-wide barrier. The warp takes the tile's pairs back to front in windows
+// of 128: the lane of pair j stages the pair's record in shared memory when any group
+// of the half tile composited it, and the window's group masks are transposed across
+// the warp so that each lane holds the bit list of the pairs its group composited.
+// Each lane walks its list back to front and evaluates its four pixels in
+// straight-line code: T_k = T_{k+1} / (1 - alpha_k),
+// dL/dalpha_k = sum_c g_c (rgb_c T_k - B_c / (1 - alpha_k)) with B the colour behind
+// fragment k plus T_final bg; the group's 13 record-field gradients go to the item's
+// gradient record with the lane's own vector reductions.
 #include "kernels.h"
 
 namespace ts {
@@ -348,238 +349,210 @@ render_fwd_kernel(RenderArgs a) {
     if (last_cta_done(&a.ctl->done[0]) && tid == 0) a.ctl->work_counter[0] = 0u;
 }
 
-// Sum 16 per-lane values over each group (transposed butterfly, all groups' records at
-// once): lane l ends with fields (16 / GROUP) (l % GROUP) + i, i < 16 / GROUP, of its
-// group's sum in v[i] (14 shuffles for groups of 8, 12 for groups of 4).
-__device__ __forceinline__ void group_reduce16(float (&v)[16], int lane) {
+// Backward, one lane per 2x2 group: a warp takes one half tile (16x8 pixels, the 32
+// groups whose bits form word h of each pair's group mask, so lane l owns bit l), and
+// each lane walks the pairs its group composited, back to front, evaluating its four
+// pixels against one record and adding the group's gradient of that record with its
+// own vector reductions (no cross-lane reduction). Lanes take their pairs from
+// windows of BW_WIN * 32 pairs: the lane of pair j stages the pair's record in shared
+// memory when any group composited it, and the window's mask words are transposed
+// across the warp (word j -> lane l's bit j), so every lane holds its own bit list of
+// the window.
+static_assert(GROUP == 4 && KM_WORDS == 2, "the backward takes one 2x2 group per lane");
+constexpr int BW_THREADS = 128;          // warps per CTA work independently
+constexpr int BW_WARPS = BW_THREADS / 32;
+constexpr int BW_WIN = 4;                // mask words per lane per window (128 pairs)
+constexpr int BW_RSTRIDE = 5;            // float4 per staged record (4 used)
+#ifndef BW_CTAS
+#define BW_CTAS 5
+#endif
+
+// 32x32 bit transpose across the warp: lane j holds row word r_j; returns the word
+// whose bit j is bit `lane` of r_j.
+__device__ __forceinline__ uint32_t warp_transpose_bits(uint32_t x, int lane) {
 #pragma unroll
-    for (int o = GROUP / 2, nf = 8; o > 0; o >>= 1, nf >>= 1) {
-        const bool up = lane & o;
-#pragma unroll
-        for (int i = 0; i < nf; ++i) {
-            const float send = up ? v[i] : v[i + nf];
-            const float keep = up ? v[i + nf] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const uint32_t m = sh == 16 ? 0x0000FFFFu : (sh == 8 ? 0x00FF00FFu : (sh == 4 ? 0x0F0F0F0Fu : (sh == 2 ? 0x33333333u : 0x55555555u)));
+        const uint32_t p = __shfl_xor_sync(0xffffffffu, x, sh);
+        x = (lane & sh) ? (((p >> sh) & m) | (x & (m << sh))) : ((x & m) | ((p & m) << sh));
     }
+    return x;
 }
 
-constexpr int BWD_CHUNK = GROUP == 8 ? 256 : (GROUP == 4 ? 128 : 64);   // pairs whose masks a warp scans per list build
-#ifndef BWD_THREADS
-#define BWD_THREADS 256          // threads of a backward CTA (its warps work independently)
-#endif
-#ifndef BWD_CTAS
-#define BWD_CTAS 3               // resident backward CTAs per SM (80 registers a thread)
-#endif
-constexpr int BWD_WARPS = BWD_THREADS / 32;
-constexpr int TILE_BLOCKS = TILE_PIX / 32;   // 8x4 blocks of a tile
+// Highest set bit of the 128-bit list (hi:lo), cleared; -1 when empty.
+__device__ __forceinline__ int pop_last(unsigned long long &hi, unsigned long long &lo) {
+    if (hi) {
+        const int b = 63 - __clzll((long long)hi);
+        hi &= ~(1ull << b);
+        return 64 + b;
+    }
+    if (lo) {
+        const int b = 63 - __clzll((long long)lo);
+        lo &= ~(1ull << b);
+        return b;
+    }
+    return -1;
+}
 
-// Backward, one warp per work unit (tile, 8x4 block of it): the warp scans the masks of
-// the tile's pairs that each of its groups composited in the forward pass,
-// builds one list per group (item ids), and walks the lists back to front with the
-// record of the next step already in flight; the warps of a CTA never wait for one
-// another. Each group's record gradient goes to the item's gradient record with one
-// vector reduction per lane per step.
 template <int WIN>
-__global__ void __launch_bounds__(BWD_THREADS, BWD_CTAS)
+__global__ void __launch_bounds__(BW_THREADS, BW_CTAS)
 render_bwd_kernel(RenderArgs a) {
-    // per warp and group: item ids and their pair index in the chunk; the groups' lists
-    // sit one bank apart (padded strides), so that the groups' reads of their k-th
-    // entries are free of bank conflicts
-    __shared__ uint32_t s_li[BWD_WARPS][WGROUPS][BWD_CHUNK + 1];
-    __shared__ uint8_t s_lj[BWD_WARPS][WGROUPS][BWD_CHUNK + 4];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane / GROUP, gl = lane % GROUP;
-    const unsigned gmask = ((1u << GROUP) - 1u) << (GROUP * g);
-    const unsigned lt_mask = lanemask_lt();
-    const uint32_t *LI = s_li[w][g];
-    const uint8_t *LJ = s_lj[w][g];
-    const uint32_t n_units = (uint32_t)a.total_tiles * TILE_BLOCKS;
+    // per warp: the window's records (stride of 5 float4 so that the lanes' reads of
+    // different records spread over the banks) and item ids
+    __shared__ float4 s_rec[BW_WARPS][32 * BW_WIN][BW_RSTRIDE];
+    __shared__ uint32_t s_it[BW_WARPS][32 * BW_WIN];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *S = s_it[w];
+    float4 (*SR)[BW_RSTRIDE] = s_rec[w];
+    const uint32_t n_units = (uint32_t)a.total_tiles * 2u;
     const Rec *__restrict__ recs = a.recs;
     for (;;) {
         uint32_t u = 0;
         if (lane == 0) u = atomicAdd(&a.ctl->work_counter[1], 1u);
         u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= n_units) break;
-        // the tiles in the forward's order (longest first), each as its 8 units
-        uint32_t tq = u / TILE_BLOCKS;
+        // tiles in the forward's order (longest first), each as its two halves
+        uint32_t tq = u >> 1;
         if (a.tile_order) {
             const uint32_t t = a.tile_order[tq];
             if (t < (uint32_t)a.total_tiles) tq = t;
             else if (lane == 0) atomicOr(&a.ctl->error, ERR_INDEX);
         }
-        const int tile = (int)tq, blk = (int)(u % TILE_BLOCKS);
+        const int tile = (int)tq, h = (int)(u & 1u);
         const int vw = find_view_warp(a.views, a.nviews, tile, lane);
         const ViewDev *V = a.views + vw;
-        const int tiles_x = V->tiles_x, W = V->W, H = V->H;
         const int lt = tile - V->tile_base;
-        int lx, ly;
-        block_pixel(blk, lane, lx, ly);
-        const int x = (lt % tiles_x) * TILE + lx, y = (lt / tiles_x) * TILE + ly;
-        const bool inside = x < W && y < H;
-        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-        const uint32_t start = a.ranges[tile].x;
-        const uint32_t gmax = a.tile_max[(size_t)tile * GROUPS + WGROUPS * blk + g];
-        const int wmax = (int)__reduce_max_sync(0xffffffffu, gmax);
-        float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
-        uint32_t last = 0;
-        if (inside) {
-            const int64_t HW = (int64_t)W * H;
-            const int64_t pix = (int64_t)y * W + x;
-            const int64_t pb = V->pix_base;
-            T = a.T_final[pb + pix];
-            last = (uint32_t)a.n_contrib[pb + pix];
-            const float *dL = view_out(a, vw).dL;
-            g0 = dL[pix];
-            g1 = dL[HW + pix];
-            g2 = dL[2 * HW + pix];
-            B0 = T * V->bg[0];
-            B1 = T * V->bg[1];
-            B2 = T * V->bg[2];
+        // this lane's group: group g of 8x4 block b of the tile
+        const int b = 4 * h + (lane >> 3), g = lane & 7;
+        const int x0 = (lt % V->tiles_x) * TILE + ((b & 1) << 3) + ((g & 3) << 1);
+        const int y0 = (lt / V->tiles_x) * TILE + ((b >> 1) << 2) + ((g >> 2) << 1);
+        const int64_t HW = (int64_t)V->W * V->H;
+        const float *dL = view_out(a, vw).dL;
+        // the four pixels: (x0 + (p & 1), y0 + (p >> 1))
+        float T[4], G0[4], G1[4], G2[4], B0[4], B1[4], B2[4];
+        uint32_t last[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int x = x0 + (p & 1), y = y0 + (p >> 1);
+            T[p] = 1.f; G0[p] = G1[p] = G2[p] = 0.f; last[p] = 0u;
+            if (x < V->W && y < V->H) {
+                const int64_t pix = (int64_t)y * V->W + x;
+                T[p] = a.T_final[V->pix_base + pix];
+                last[p] = (uint32_t)a.n_contrib[V->pix_base + pix];
+                G0[p] = dL[pix];
+                G1[p] = dL[HW + pix];
+                G2[p] = dL[2 * HW + pix];
+            }
+            B0[p] = T[p] * V->bg[0];
+            B1[p] = T[p] * V->bg[1];
+            B2[p] = T[p] * V->bg[2];
         }
-        for (int cend = wmax; cend > 0; cend -= BWD_CHUNK) {
-            const int cstart = max(0, cend - BWD_CHUNK);
-            const int nb = cend - cstart;
-            // the pairs of this chunk that each group composited, in tile order
-            uint32_t m[BWD_CHUNK / 32];
-            uint32_t itv[BWD_CHUNK / 32];
+        const uint32_t start = a.ranges[tile].x;
+        const uint32_t gmax = a.tile_max[(size_t)tile * GROUPS + 8 * b + g];
+        const int wmax = (int)__reduce_max_sync(0xffffffffu, gmax);
+        for (int wend = wmax; wend > 0; wend -= 32 * BW_WIN) {
+            const int wst = max(0, wend - 32 * BW_WIN);
+            // this lane's bits of the window: bit j of word q = pair wst + 32 q + j
+            uint32_t m[BW_WIN];
 #pragma unroll
-            for (int q = 0; q < BWD_CHUNK / 32; ++q) {
-                const int jj = 32 * q + lane;
-                m[q] = 0u;
-                itv[q] = 0u;
-                if (jj < nb) {
-                    // the word of this block's groups
-                    m[q] = a.kmask[(size_t)(start + cstart + jj) * KM_WORDS + KM_WORD(blk)];
-                    itv[q] = a.items[start + cstart + jj];
+            for (int q = 0; q < BW_WIN; ++q) {
+                const int jj = wst + 32 * q + lane;
+                uint32_t word = 0u, it = 0u;
+                if (jj < wend) {
+                    word = a.kmask[(size_t)(start + jj) * KM_WORDS + h];
+                    it = a.items[start + jj];
+                    if (word && it >= a.n_items) {
+                        atomicOr(&a.ctl->error, ERR_INDEX);
+                        word = 0u;
+                    }
                 }
+                S[32 * q + lane] = it;
+                if (word) {
+                    const float4 *rp = reinterpret_cast<const float4 *>(recs + it);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) SR[32 * q + lane][e] = __ldg(rp + e);
+                }
+                m[q] = warp_transpose_bits(word, lane);
             }
             __syncwarp();
-            int n[WGROUPS];
+            unsigned long long lo = ((unsigned long long)m[1] << 32) | m[0];
+            unsigned long long hi = ((unsigned long long)m[3] << 32) | m[2];
+            for (;;) {
+                const int cpos = pop_last(hi, lo);
+                if (!__any_sync(0xffffffffu, cpos >= 0)) break;
+                if (cpos < 0) continue;      // (the warp's next pop meets this lane at the vote)
+                const uint32_t citem = S[cpos];
+                const float4 ca = SR[cpos][0], cb = SR[cpos][1], cc = SR[cpos][2], cd = SR[cpos][3];
+                const uint32_t jt = (uint32_t)(wst + cpos);     // pair index in the tile's list
+                float gv[13];
 #pragma unroll
-            for (int e = 0; e < WGROUPS; ++e) n[e] = 0;
+                for (int q = 0; q < 13; ++q) gv[q] = 0.f;
+                // the four pixels in straight-line code (independent, so their arithmetic
+                // interleaves); a pixel that does not composite the fragment computes with
+                // safe inputs and adds zeros
+                bool any = false;
 #pragma unroll
-            for (int q = 0; q < BWD_CHUNK / 32; ++q) {
-                const uint32_t mq = (m[q] >> KM_SHIFT(blk)) & (WGROUPS == 32 ? 0xffffffffu : ((1u << WGROUPS) - 1u));
-                uint32_t it = itv[q];
-                if (mq && it >= a.n_items) {
-                    atomicOr(&a.ctl->error, ERR_INDEX);
-                    it = 0;
-                }
-#pragma unroll
-                for (int e = 0; e < WGROUPS; ++e) {
-                    const bool ke = (mq >> e) & 1u;
-                    const unsigned be = __ballot_sync(0xffffffffu, ke);
-                    if (ke) {
-                        const int pos = n[e] + __popc(be & lt_mask);
-                        s_li[w][e][pos] = it;
-                        s_lj[w][e][pos] = (uint8_t)(32 * q + lane);
+                for (int p = 0; p < 4; ++p) {
+                    const float px = (float)(x0 + (p & 1)) + 0.5f, py = (float)(y0 + (p >> 1)) + 0.5f;
+                    const Frag f = eval_lines(ca, cb, cc, px, py);
+                    const bool pos = WIN == WIN_SIGMOID || f.ratio > 0.0f;
+                    const float rs = pos ? f.ratio : 1.0f;   // the power window's ratio, kept positive
+                    const float lg = WIN == WIN_SIGMOID ? 0.0f : lg2_approx(rs);
+                    const float I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, cd.x) : ex2_approx(__fmul_rn(cd.x, lg));
+                    const float araw = __fmul_rn(cc.w, I);
+                    const bool kept = jt < last[p] && pos && araw >= ALPHA_MIN;
+                    any = any || kept;
+                    const float al = fminf(araw, ALPHA_MAX);
+                    const float om = __fsub_rn(1.0f, al);
+                    const float iom = rcp_approx(om);
+                    const float Tn = T[p] * iom;
+                    T[p] = kept ? Tn : T[p];
+                    const float wgt = kept ? al * Tn : 0.0f;
+                    gv[10] = fmaf(G0[p], wgt, gv[10]);
+                    gv[11] = fmaf(G1[p], wgt, gv[11]);
+                    gv[12] = fmaf(G2[p], wgt, gv[12]);
+                    const float gc = fmaf(G0[p], cd.y, fmaf(G1[p], cd.z, G2[p] * cd.w));
+                    const float gb = fmaf(G0[p], B0[p], fmaf(G1[p], B1[p], G2[p] * B2[p]));
+                    // dalpha/d(o I) is 0 where alpha is clamped
+                    const float galpha = (kept && araw <= ALPHA_MAX) ? Tn * gc - iom * gb : 0.0f;
+                    B0[p] = fmaf(cd.y, wgt, B0[p]);
+                    B1[p] = fmaf(cd.z, wgt, B1[p]);
+                    B2[p] = fmaf(cd.w, wgt, B2[p]);
+                    const float gI = galpha * cc.w;
+                    gv[8] = fmaf(galpha, I, gv[8]);                       // d/do
+                    float gr;                                              // d/dratio
+                    if (WIN == WIN_SIGMOID) {
+                        // I = sigmoid(kappa ratio): field 9 is d/dkappa
+                        const float s1 = I * (1.0f - I);
+                        gv[9] = fmaf(gI * s1, f.ratio, gv[9]);
+                        gr = gI * cd.x * s1;
+                    } else {
+                        // (a pixel that adds zeros may have a ratio whose lg2 or reciprocal
+                        // is infinite: those take the values of ratio 1)
+                        const float lgk = kept ? lg : 0.0f, rk = kept ? rs : 1.0f;
+                        gv[9] = fmaf(gI * I, lgk * 0.69314718055994531f, gv[9]);   // d/dsigma: I ln(ratio)
+                        gr = gI * cd.x * I * rcp_approx(rk);
                     }
-                    n[e] += __popc(be);
+                    // the active line: lowest index among the minima
+                    const int ia = (f.m0 <= f.m1 && f.m0 <= f.m2) ? 0 : (f.m1 <= f.m2 ? 1 : 2);
+                    const float Aa = ia == 0 ? ca.z : (ia == 1 ? cb.y : cc.x);
+                    const float Ba = ia == 0 ? ca.w : (ia == 1 ? cb.z : cc.y);
+                    gv[0] = fmaf(-gr, Aa, gv[0]);
+                    gv[1] = fmaf(-gr, Ba, gv[1]);
+                    const float gA = gr * f.dx, gB = gr * f.dy;
+                    gv[2] += ia == 0 ? gA : 0.f;
+                    gv[3] += ia == 0 ? gB : 0.f;
+                    gv[4] += ia == 1 ? gA : 0.f;
+                    gv[5] += ia == 1 ? gB : 0.f;
+                    gv[6] += ia == 2 ? gA : 0.f;
+                    gv[7] += ia == 2 ? gB : 0.f;
                 }
-            }
-            __syncwarp();
-            int cnt = 0, nmax = 0;
-#pragma unroll
-            for (int e = 0; e < WGROUPS; ++e) {
-                cnt = e == g ? n[e] : cnt;
-                nmax = max(nmax, n[e]);
-            }
-            // software pipeline: the record of step k - 1 loads while step k computes
-            uint32_t nit = 0;
-            int nj = 0;
-            float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb4 = na, nc = na, nd = na;
-            int k = nmax - 1;
-            if (k >= 0 && k < cnt) {
-                nit = LI[k];
-                nj = LJ[k];
-                na = __ldg(&recs[nit].a);
-                nb4 = __ldg(&recs[nit].b);
-                nc = __ldg(&recs[nit].c);
-                nd = __ldg(&recs[nit].d);
-            }
-            for (; k >= 0; --k) {
-                const float4 ra = na, rb = nb4, rc = nc, rd = nd;
-                const uint32_t item = nit;
-                const int j = nj;
-                const bool has = k < cnt;
-                if (k >= 1 && k - 1 < cnt) {
-                    nit = LI[k - 1];
-                    nj = LJ[k - 1];
-                    na = __ldg(&recs[nit].a);
-                    nb4 = __ldg(&recs[nit].b);
-                    nc = __ldg(&recs[nit].c);
-                    nd = __ldg(&recs[nit].d);
-                }
-                float gv[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) gv[q] = 0.f;
-                bool kept = false;
-                if (has && (uint32_t)(cstart + j) < last) {
-                    const Frag f = eval_lines(ra, rb, rc, px, py);
-                    if (WIN == WIN_SIGMOID || f.ratio > 0.0f) {
-                        const float lg = WIN == WIN_SIGMOID ? 0.0f : lg2_approx(f.ratio);
-                        const float I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, rd.x)
-                                                           : ex2_approx(__fmul_rn(rd.x, lg));
-                        const float araw = __fmul_rn(rc.w, I);
-                        if (araw >= ALPHA_MIN) {
-                            kept = true;
-                            const float al = fminf(araw, ALPHA_MAX);
-                            const float om = __fsub_rn(1.0f, al);
-                            const float iom = rcp_approx(om);
-                            T = T * iom;
-                            const float wgt = al * T;
-                            gv[10] = g0 * wgt;
-                            gv[11] = g1 * wgt;
-                            gv[12] = g2 * wgt;
-                            const float gc = fmaf(g0, rd.y, fmaf(g1, rd.z, g2 * rd.w));
-                            const float gb = fmaf(g0, B0, fmaf(g1, B1, g2 * B2));
-                            const float galpha = T * gc - iom * gb;
-                            B0 = fmaf(rd.y, wgt, B0);
-                            B1 = fmaf(rd.z, wgt, B1);
-                            B2 = fmaf(rd.w, wgt, B2);
-                            if (araw <= ALPHA_MAX) {
-                                const float gI = galpha * rc.w;
-                                gv[8] = galpha * I;                               // d/do
-                                float gr;                                         // d/dratio
-                                if (WIN == WIN_SIGMOID) {
-                                    // I = sigmoid(kappa ratio): field 9 is d/dkappa
-                                    const float s1 = I * (1.0f - I);
-                                    gv[9] = gI * s1 * f.ratio;
-                                    gr = gI * rd.x * s1;
-                                } else {
-                                    gv[9] = gI * I * lg * 0.69314718055994531f;   // d/dsigma: I ln(ratio)
-                                    gr = gI * rd.x * I * rcp_approx(f.ratio);
-                                }
-                                // the active line: lowest index among the minima
-                                const int ia = (f.m0 <= f.m1 && f.m0 <= f.m2) ? 0 : (f.m1 <= f.m2 ? 1 : 2);
-                                const float Aa = ia == 0 ? ra.z : (ia == 1 ? rb.y : rc.x);
-                                const float Ba = ia == 0 ? ra.w : (ia == 1 ? rb.z : rc.y);
-                                gv[0] = -gr * Aa;
-                                gv[1] = -gr * Ba;
-                                const float gA = gr * f.dx, gB = gr * f.dy;
-                                gv[2] = ia == 0 ? gA : 0.f;
-                                gv[3] = ia == 0 ? gB : 0.f;
-                                gv[4] = ia == 1 ? gA : 0.f;
-                                gv[5] = ia == 1 ? gB : 0.f;
-                                gv[6] = ia == 2 ? gA : 0.f;
-                                gv[7] = ia == 2 ? gB : 0.f;
-                            }
-                        }
-                    }
-                }
-                const unsigned bk = __ballot_sync(0xffffffffu, kept);
-                if (bk) {
-                    group_reduce16(gv, lane);
-                    // fields 13..15 are padding and receive 0
-                    float *dst = a.grad2d + (size_t)item * GRAD_FIELDS + (16 / GROUP) * gl;
-                    if (GROUP == 8) {
-                        if ((bk & gmask) && gl < 7) red_add_v2(dst, gv[0], gv[1]);
-                    } else if (GROUP == 4) {
-                        if (bk & gmask) red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
-                    } else if (bk & gmask) {
-                        red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
-                        red_add_v4(dst + 4, gv[4], gv[5], gv[6], gv[7]);
-                    }
+                if (any) {
+                    float *dst = a.grad2d + (size_t)citem * GRAD_FIELDS;
+                    red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
+                    red_add_v4(dst + 4, gv[4], gv[5], gv[6], gv[7]);
+                    red_add_v4(dst + 8, gv[8], gv[9], gv[10], gv[11]);
+                    red_add_v2(dst + 12, gv[12], 0.f);
                 }
             }
             __syncwarp();
@@ -611,13 +584,13 @@ void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st, bool soli
 }
 
 void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st) {
-    static int occ = occupancy((const void *)render_bwd_kernel<WIN_POWER>, BWD_THREADS);
+    static int occ = occupancy((const void *)render_bwd_kernel<WIN_POWER>, BW_THREADS);
     int64_t g = grid > 0 ? (int64_t)grid * occ : occ;
-    const int64_t need = ((int64_t)a.total_tiles * TILE_BLOCKS + BWD_WARPS - 1) / BWD_WARPS;
+    const int64_t need = ((int64_t)a.total_tiles * 2 + BW_WARPS - 1) / BW_WARPS;
     if (g > need) g = need;
     if (g <= 0) return;
-    if (a.window == WIN_SIGMOID) render_bwd_kernel<WIN_SIGMOID><<<(unsigned)g, BWD_THREADS, 0, st>>>(a);
-    else render_bwd_kernel<WIN_POWER><<<(unsigned)g, BWD_THREADS, 0, st>>>(a);
+    if (a.window == WIN_SIGMOID) render_bwd_kernel<WIN_SIGMOID><<<(unsigned)g, BW_THREADS, 0, st>>>(a);
+    else render_bwd_kernel<WIN_POWER><<<(unsigned)g, BW_THREADS, 0, st>>>(a);
 }
 
 // ---------------------------------------------------------------------------------
