@@ -366,6 +366,9 @@ constexpr int BW_RSTRIDE = 5;            // float4 per staged record (4 used)
 #ifndef BW_CTAS
 #define BW_CTAS 5
 #endif
+#ifndef BW_DENSE
+#define BW_DENSE 10              // groups per distinct record of a window from which adds are coalesced
+#endif
 
 // 32x32 bit transpose across the warp: lane j holds row word r_j; returns the word
 // whose bit j is bit `lane` of r_j.
@@ -392,6 +395,84 @@ __device__ __forceinline__ int pop_last(unsigned long long &hi, unsigned long lo
         return b;
     }
     return -1;
+}
+
+// The group's gradient of one record (ca..cd) at tile-list position jt, over the
+// lane's four pixels, in straight-line code (independent pixels, so their arithmetic
+// interleaves): a pixel that does not composite the fragment (or all four, when `mine`
+// is false) computes with safe inputs and adds zeros. Updates T and B back to front;
+// returns whether any pixel composited.
+template <int WIN>
+__device__ __forceinline__ bool group_grad(const float4 ca, const float4 cb, const float4 cc, const float4 cd,
+                                           uint32_t jt, bool mine, int x0, int y0, const uint32_t (&last)[4],
+                                           float (&T)[4], const float (&G0)[4], const float (&G1)[4],
+                                           const float (&G2)[4], float (&B0)[4], float (&B1)[4], float (&B2)[4],
+                                           float (&gv)[13]) {
+#pragma unroll
+    for (int q = 0; q < 13; ++q) gv[q] = 0.f;
+    bool any = false;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const float px = (float)(x0 + (p & 1)) + 0.5f, py = (float)(y0 + (p >> 1)) + 0.5f;
+        const Frag f = eval_lines(ca, cb, cc, px, py);
+        const bool pos = WIN == WIN_SIGMOID || f.ratio > 0.0f;
+        const float rs = pos ? f.ratio : 1.0f;   // the power window's ratio, kept positive
+        const float lg = WIN == WIN_SIGMOID ? 0.0f : lg2_approx(rs);
+        const float I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, cd.x) : ex2_approx(__fmul_rn(cd.x, lg));
+        const float araw = __fmul_rn(cc.w, I);
+        const bool kept = mine && jt < last[p] && pos && araw >= ALPHA_MIN;
+        any = any || kept;
+        const float al = fminf(araw, ALPHA_MAX);
+        const float om = __fsub_rn(1.0f, al);
+        const float iom = rcp_approx(om);
+        const float Tn = T[p] * iom;
+        T[p] = kept ? Tn : T[p];
+        const float wgt = kept ? al * Tn : 0.0f;
+        gv[10] = fmaf(G0[p], wgt, gv[10]);
+        gv[11] = fmaf(G1[p], wgt, gv[11]);
+        gv[12] = fmaf(G2[p], wgt, gv[12]);
+        const float gc = fmaf(G0[p], cd.y, fmaf(G1[p], cd.z, G2[p] * cd.w));
+        const float gb = fmaf(G0[p], B0[p], fmaf(G1[p], B1[p], G2[p] * B2[p]));
+        // dalpha/d(o I) is 0 where alpha is clamped
+        const float galpha = (kept && araw <= ALPHA_MAX) ? Tn * gc - iom * gb : 0.0f;
+        B0[p] = fmaf(cd.y, wgt, B0[p]);
+        B1[p] = fmaf(cd.z, wgt, B1[p]);
+        B2[p] = fmaf(cd.w, wgt, B2[p]);
+        const float gI = galpha * cc.w;
+        gv[8] = fmaf(galpha, I, gv[8]);                       // d/do
+        float gr;                                              // d/dratio
+        if (WIN == WIN_SIGMOID) {
+            // I = sigmoid(kappa ratio): field 9 is d/dkappa
+            const float s1 = I * (1.0f - I);
+            gv[9] = fmaf(gI * s1, f.ratio, gv[9]);
+            gr = gI * cd.x * s1;
+        } else {
+            // (a pixel that adds zeros may have a ratio whose lg2 or reciprocal
+            // is infinite: those take the values of ratio 1)
+            const float lgk = kept ? lg : 0.0f, rk = kept ? rs : 1.0f;
+            gv[9] = fmaf(gI * I, lgk * 0.69314718055994531f, gv[9]);   // d/dsigma: I ln(ratio)
+            gr = gI * cd.x * I * rcp_approx(rk);
+        }
+        // the active line: lowest index among the minima
+        const int ia = (f.m0 <= f.m1 && f.m0 <= f.m2) ? 0 : (f.m1 <= f.m2 ? 1 : 2);
+        const float Aa = ia == 0 ? ca.z : (ia == 1 ? cb.y : cc.x);
+        const float Ba = ia == 0 ? ca.w : (ia == 1 ? cb.z : cc.y);
+        gv[0] = fmaf(-gr, Aa, gv[0]);
+        gv[1] = fmaf(-gr, Ba, gv[1]);
+        const float gA = gr * f.dx, gB = gr * f.dy;
+        gv[2] += ia == 0 ? gA : 0.f;
+        gv[3] += ia == 0 ? gB : 0.f;
+        gv[4] += ia == 1 ? gA : 0.f;
+        gv[5] += ia == 1 ? gB : 0.f;
+        gv[6] += ia == 2 ? gA : 0.f;
+        gv[7] += ia == 2 ? gB : 0.f;
+    }
+    return any;
+}
+
+__device__ __forceinline__ float4 shfl_xor4(float4 v, int m) {
+    return make_float4(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m),
+                       __shfl_xor_sync(0xffffffffu, v.z, m), __shfl_xor_sync(0xffffffffu, v.w, m));
 }
 
 template <int WIN>
@@ -477,82 +558,78 @@ render_bwd_kernel(RenderArgs a) {
             __syncwarp();
             unsigned long long lo = ((unsigned long long)m[1] << 32) | m[0];
             unsigned long long hi = ((unsigned long long)m[3] << 32) | m[2];
-            for (;;) {
-                const int cpos = pop_last(hi, lo);
-                if (!__any_sync(0xffffffffu, cpos >= 0)) break;
-                if (cpos < 0) continue;      // (the warp's next pop meets this lane at the vote)
-                const uint32_t citem = S[cpos];
-                const float4 ca = SR[cpos][0], cb = SR[cpos][1], cc = SR[cpos][2], cd = SR[cpos][3];
-                const uint32_t jt = (uint32_t)(wst + cpos);     // pair index in the tile's list
-                float gv[13];
-#pragma unroll
-                for (int q = 0; q < 13; ++q) gv[q] = 0.f;
-                // the four pixels in straight-line code (independent, so their arithmetic
-                // interleaves); a pixel that does not composite the fragment computes with
-                // safe inputs and adds zeros
-                bool any = false;
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const float px = (float)(x0 + (p & 1)) + 0.5f, py = (float)(y0 + (p >> 1)) + 0.5f;
-                    const Frag f = eval_lines(ca, cb, cc, px, py);
-                    const bool pos = WIN == WIN_SIGMOID || f.ratio > 0.0f;
-                    const float rs = pos ? f.ratio : 1.0f;   // the power window's ratio, kept positive
-                    const float lg = WIN == WIN_SIGMOID ? 0.0f : lg2_approx(rs);
-                    const float I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, cd.x) : ex2_approx(__fmul_rn(cd.x, lg));
-                    const float araw = __fmul_rn(cc.w, I);
-                    const bool kept = jt < last[p] && pos && araw >= ALPHA_MIN;
-                    any = any || kept;
-                    const float al = fminf(araw, ALPHA_MAX);
-                    const float om = __fsub_rn(1.0f, al);
-                    const float iom = rcp_approx(om);
-                    const float Tn = T[p] * iom;
-                    T[p] = kept ? Tn : T[p];
-                    const float wgt = kept ? al * Tn : 0.0f;
-                    gv[10] = fmaf(G0[p], wgt, gv[10]);
-                    gv[11] = fmaf(G1[p], wgt, gv[11]);
-                    gv[12] = fmaf(G2[p], wgt, gv[12]);
-                    const float gc = fmaf(G0[p], cd.y, fmaf(G1[p], cd.z, G2[p] * cd.w));
-                    const float gb = fmaf(G0[p], B0[p], fmaf(G1[p], B1[p], G2[p] * B2[p]));
-                    // dalpha/d(o I) is 0 where alpha is clamped
-                    const float galpha = (kept && araw <= ALPHA_MAX) ? Tn * gc - iom * gb : 0.0f;
-                    B0[p] = fmaf(cd.y, wgt, B0[p]);
-                    B1[p] = fmaf(cd.z, wgt, B1[p]);
-                    B2[p] = fmaf(cd.w, wgt, B2[p]);
-                    const float gI = galpha * cc.w;
-                    gv[8] = fmaf(galpha, I, gv[8]);                       // d/do
-                    float gr;                                              // d/dratio
-                    if (WIN == WIN_SIGMOID) {
-                        // I = sigmoid(kappa ratio): field 9 is d/dkappa
-                        const float s1 = I * (1.0f - I);
-                        gv[9] = fmaf(gI * s1, f.ratio, gv[9]);
-                        gr = gI * cd.x * s1;
-                    } else {
-                        // (a pixel that adds zeros may have a ratio whose lg2 or reciprocal
-                        // is infinite: those take the values of ratio 1)
-                        const float lgk = kept ? lg : 0.0f, rk = kept ? rs : 1.0f;
-                        gv[9] = fmaf(gI * I, lgk * 0.69314718055994531f, gv[9]);   // d/dsigma: I ln(ratio)
-                        gr = gI * cd.x * I * rcp_approx(rk);
+            float gv[13];
+            const int k4 = lane & 3;
+            // Many groups per record (triangles wider than the groups) make the records'
+            // reductions contend in L2: then the quads' transposed, coalesced adds below;
+            // otherwise each lane adds its own record directly (fewer instructions).
+            const uint32_t nb = __reduce_add_sync(0xffffffffu, (uint32_t)(__popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3])));
+            const uint32_t nu = (uint32_t)(__popc(__reduce_or_sync(0xffffffffu, m[0])) + __popc(__reduce_or_sync(0xffffffffu, m[1])) +
+                                           __popc(__reduce_or_sync(0xffffffffu, m[2])) + __popc(__reduce_or_sync(0xffffffffu, m[3])));
+            const bool dense = nb >= BW_DENSE * nu;
+            if (!dense) {
+                for (;;) {
+                    const int cpos = pop_last(hi, lo);
+                    if (!__any_sync(0xffffffffu, cpos >= 0)) break;
+                    if (cpos < 0) continue;      // (the warp's next pop meets this lane at the vote)
+                    const uint32_t citem = S[cpos];
+                    const float4 ca = SR[cpos][0], cb = SR[cpos][1], cc = SR[cpos][2], cd = SR[cpos][3];
+                    if (group_grad<WIN>(ca, cb, cc, cd, (uint32_t)(wst + cpos), true, x0, y0, last, T, G0, G1, G2, B0, B1,
+                                        B2, gv)) {
+                        float *dst = a.grad2d + (size_t)citem * GRAD_FIELDS;
+                        red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
+                        red_add_v4(dst + 4, gv[4], gv[5], gv[6], gv[7]);
+                        red_add_v4(dst + 8, gv[8], gv[9], gv[10], gv[11]);
+                        red_add_v2(dst + 12, gv[12], 0.f);
                     }
-                    // the active line: lowest index among the minima
-                    const int ia = (f.m0 <= f.m1 && f.m0 <= f.m2) ? 0 : (f.m1 <= f.m2 ? 1 : 2);
-                    const float Aa = ia == 0 ? ca.z : (ia == 1 ? cb.y : cc.x);
-                    const float Ba = ia == 0 ? ca.w : (ia == 1 ? cb.z : cc.y);
-                    gv[0] = fmaf(-gr, Aa, gv[0]);
-                    gv[1] = fmaf(-gr, Ba, gv[1]);
-                    const float gA = gr * f.dx, gB = gr * f.dy;
-                    gv[2] += ia == 0 ? gA : 0.f;
-                    gv[3] += ia == 0 ? gB : 0.f;
-                    gv[4] += ia == 1 ? gA : 0.f;
-                    gv[5] += ia == 1 ? gB : 0.f;
-                    gv[6] += ia == 2 ? gA : 0.f;
-                    gv[7] += ia == 2 ? gB : 0.f;
                 }
-                if (any) {
-                    float *dst = a.grad2d + (size_t)citem * GRAD_FIELDS;
-                    red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
-                    red_add_v4(dst + 4, gv[4], gv[5], gv[6], gv[7]);
-                    red_add_v4(dst + 8, gv[8], gv[9], gv[10], gv[11]);
-                    red_add_v2(dst + 12, gv[12], 0.f);
+            } else {
+                for (;;) {
+                    const int cpos = pop_last(hi, lo);
+                    if (!__any_sync(0xffffffffu, cpos >= 0)) break;
+                    bool any = false;
+                    uint32_t citem = 0u;
+                    if (cpos >= 0) {
+                        citem = S[cpos];
+                        const float4 ca = SR[cpos][0], cb = SR[cpos][1], cc = SR[cpos][2], cd = SR[cpos][3];
+                        any = group_grad<WIN>(ca, cb, cc, cd, (uint32_t)(wst + cpos), true, x0, y0, last, T, G0, G1, G2,
+                                              B0, B1, B2, gv);
+                    }
+                    // The four lanes of a quad exchange their records' 16-byte chunks (a 4x4
+                    // transpose in two rounds) so that each vector reduction below writes one
+                    // whole 64-byte record from four lanes: one coalesced request instead of four.
+                    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 c0 = any ? make_float4(gv[0], gv[1], gv[2], gv[3]) : z;
+                    float4 c1 = any ? make_float4(gv[4], gv[5], gv[6], gv[7]) : z;
+                    float4 c2 = any ? make_float4(gv[8], gv[9], gv[10], gv[11]) : z;
+                    float4 c3 = any ? make_float4(gv[12], 0.f, 0.f, 0.f) : z;
+                    {
+                        // lanes 0, 1 keep chunks 0, 1 and take their partner's; lanes 2, 3 chunks 2, 3
+                        const bool low = !(k4 & 2);
+                        const float4 ra = shfl_xor4(low ? c2 : c0, 2), rb = shfl_xor4(low ? c3 : c1, 2);
+                        if (low) { c2 = ra; c3 = rb; } else { c0 = ra; c1 = rb; }
+                    }
+                    {
+                        // even lanes keep slots 0, 2, odd lanes slots 1, 3, and take the partner's
+                        const bool ev = !(k4 & 1);
+                        const float4 ra = shfl_xor4(ev ? c1 : c0, 1), rb = shfl_xor4(ev ? c3 : c2, 1);
+                        const float4 n0 = ev ? c0 : c1, n1 = ev ? c2 : c3;
+                        c0 = n0; c1 = n1; c2 = ra; c3 = rb;
+                    }
+                    // lane k now holds chunk k of the quad's records (0, 2, 1, 3) in its slots
+                    // (odd lanes (1, 3, 0, 2), put in the same order)
+                    if (k4 & 1) {
+                        const float4 t0 = c0, t1 = c1;
+                        c0 = c2; c1 = c3; c2 = t0; c3 = t1;
+                    }
+                    const int qb = lane & ~3;
+                    const uint32_t vi = any ? citem : 0xffffffffu;
+                    const uint32_t i0 = __shfl_sync(0xffffffffu, vi, qb), i1 = __shfl_sync(0xffffffffu, vi, qb + 1);
+                    const uint32_t i2 = __shfl_sync(0xffffffffu, vi, qb + 2), i3 = __shfl_sync(0xffffffffu, vi, qb + 3);
+                    if (i0 != 0xffffffffu) red_add_v4(a.grad2d + (size_t)i0 * GRAD_FIELDS + 4 * k4, c0.x, c0.y, c0.z, c0.w);
+                    if (i2 != 0xffffffffu) red_add_v4(a.grad2d + (size_t)i2 * GRAD_FIELDS + 4 * k4, c1.x, c1.y, c1.z, c1.w);
+                    if (i1 != 0xffffffffu) red_add_v4(a.grad2d + (size_t)i1 * GRAD_FIELDS + 4 * k4, c2.x, c2.y, c2.z, c2.w);
+                    if (i3 != 0xffffffffu) red_add_v4(a.grad2d + (size_t)i3 * GRAD_FIELDS + 4 * k4, c3.x, c3.y, c3.z, c3.w);
                 }
             }
             __syncwarp();
