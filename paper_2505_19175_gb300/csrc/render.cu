@@ -4,15 +4,17 @@
 // groups. Tiles are taken from device work queues by persistent grids, so a launch
 // serves any mix of views and resolutions.
 //
-// Forward (Sec. 3.1, the rendering equation of prior splatting work): one CTA of 256
-// threads per tile, one thread per pixel and one warp per block; the tile's depth-sorted records are staged through shared memory
-// 256 at a time (64 B each, one coalesced float4 x 4 gather per thread) and each warp
-// walks the list of records whose support meets its block. Per pixel,
-// ratio = min_i m_i(p) (phi(p)/phi(s) of Eq. indicator1), I = ratio^sigma, alpha = o I,
-// skip below 1/255, clamp at 0.99, stop before T drops below 1e-4, C += rgb alpha T.
-// The CTA leaves a tile as soon as every pixel has stopped (__syncthreads_count). It
-// also records, per pair, which groups composited it (one bit per group, KM_WORDS
-// 32-bit words per pair), and per group the largest composited index.
+// Forward (Sec. 3.1, the rendering equation of prior splatting work): one warp per half
+// tile (16x8 pixels) and one lane per 2x2 group of it, with no CTA-wide barrier. The warp
+// takes the tile's depth-sorted pairs front to back in windows of 64: the lane of pair j
+// gathers the pair's record (64 B) and tests it against the half tile's 32 groups, and a
+// warp bit transpose gives each lane the list of the window's pairs that may reach its
+// group. Per pixel, ratio = min_i m_i(p) (phi(p)/phi(s) of Eq. indicator1),
+// I = ratio^sigma, alpha = o I, skip below 1/255, clamp at 0.99, stop before T drops
+// below 1e-4, C += rgb alpha T. A warp leaves its half tile as soon as every pixel has
+// stopped. It also records, per pair, which groups composited it (one bit per group,
+// KM_WORDS 32-bit words per pair, word h for half tile h), and per group the largest
+// composited index.
 //
 // Backward: one warp per half tile (16x8 pixels) and one lane per 2x2 group of it,
 // with no CTA-wide barrier. The warp takes the tile's pairs back to front in windows
@@ -149,204 +151,6 @@ __device__ __forceinline__ uint32_t group_max(uint32_t v) {
 #pragma unroll
     for (int o = GROUP / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
-}
-
-// SOLID: opaque triangles (the sigma -> 0, o = 1 limit): each pixel takes the colour of
-// the first entry in depth order whose window ratio is positive. WIN: window kind.
-// The forward walks one list per warp (measured faster than per-half lists here: the
-// early exit on transmittance keeps its lists short); it records per group which pairs
-// were composited, for the backward's per-group lists.
-// COUNT: also count evaluated and composited fragments (tri_ctx_info).
-template <bool SOLID, int WIN, bool COUNT>
-__global__ void __launch_bounds__(REN_THREADS)
-render_fwd_kernel(RenderArgs a) {
-    __shared__ Rec s_rec[REN_THREADS];
-    __shared__ uint16_t s_mask[REN_THREADS];
-    __shared__ uint32_t s_km[KM_WORDS][REN_THREADS];   // groups that composited each staged record
-    __shared__ uint32_t s_sw[REN_THREADS];   // pruning statistics of each staged record:
-    __shared__ uint32_t s_sn[REN_THREADS];   // largest T o (float bits), composited pixels
-    __shared__ uint8_t s_list[REN_THREADS / 32][REN_THREADS];
-    __shared__ ViewDev s_view[MAX_VIEWS];
-    __shared__ uint32_t s_tile;
-    __shared__ float s_l1[REN_THREADS / 32];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = lane / GROUP, gl = lane % GROUP;
-    for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += REN_THREADS)
-        reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
-    int lx, ly;
-    pixel_of(tid, lx, ly);
-    float l1_acc = 0.f;               // this thread's share of the L1 loss
-#pragma unroll
-    for (int q = 0; q < KM_WORDS; ++q) s_km[q][tid] = 0u;
-    s_sw[tid] = 0u;
-    s_sn[tid] = 0u;
-    const bool stats = a.stat_n != nullptr;
-    const uint8_t *L = s_list[w];
-    for (;;) {
-        if (tid == 0) {
-            uint32_t q = atomicAdd(&a.ctl->work_counter[0], 1u);
-            if (a.tile_order && q < (uint32_t)a.total_tiles) {
-                const uint32_t t = a.tile_order[q];
-                if (t < (uint32_t)a.total_tiles) q = t;
-                else atomicOr(&a.ctl->error, ERR_INDEX);
-            }
-            s_tile = q;
-        }
-        __syncthreads();
-        const int tile = (int)s_tile;
-        if (tile >= a.total_tiles) break;
-        const int vw = find_view(s_view, a.nviews, tile);
-        const ViewDev &V = s_view[vw];
-        const int lt = tile - V.tile_base;
-        const int ox = (lt % V.tiles_x) * TILE, oy = (lt / V.tiles_x) * TILE;
-        const int x = ox + lx, y = oy + ly;
-        const bool inside = x < V.W && y < V.H;
-        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-        const uint2 rg = a.ranges[tile];
-        const uint32_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
-        float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-        uint32_t last = 0, n_eval = 0, n_kept = 0;
-        bool done = !inside;
-        for (uint32_t b0 = start; b0 < end; b0 += REN_THREADS) {
-            if (__syncthreads_count(done) == REN_THREADS) break;
-            const uint32_t idx = b0 + tid;
-            uint32_t it = 0;
-            if (idx < end) {
-                it = a.items[idx];
-                if (it >= a.n_items) {
-                    atomicOr(&a.ctl->error, ERR_INDEX);
-                    it = 0;
-                }
-                const Rec r = a.recs[it];
-                s_rec[tid] = r;
-                s_mask[tid] = (uint16_t)warp_mask(r, a.rects[it], ox, oy, cutoff_ratio<WIN>(r, SOLID));
-            } else {
-                s_mask[tid] = 0;
-            }
-            __syncthreads();
-            const int cnt = warp_list(s_mask, s_list[w], w, lane);
-            // chunks of 32 list entries; bit k of `kept` marks the entries this lane
-            // composited, and each group's OR of them marks the pairs for the backward
-            for (int c = 0; c < cnt; c += 32) {
-                if (__all_sync(0xffffffffu, done)) break;
-                const int kend = min(cnt, c + 32);
-                uint32_t kept = 0;
-                for (int k = c; k < kend; ++k) {
-                    if (done) break;
-                    const int j = L[k];
-                    if (COUNT) ++n_eval;
-                    const float4 ra = s_rec[j].a, rb = s_rec[j].b, rc = s_rec[j].c;
-                    const Frag f = eval_lines(ra, rb, rc, px, py);
-                    if ((SOLID || WIN == WIN_POWER) && f.ratio <= 0.0f) continue;
-                    const float4 rd = s_rec[j].d;
-                    if (SOLID) {
-                        C0 = rd.y;
-                        C1 = rd.z;
-                        C2 = rd.w;
-                        T = 0.0f;
-                        last = b0 - start + (uint32_t)j + 1u;
-                        if (COUNT) ++n_kept;
-                        done = true;
-                        break;
-                    }
-                    const float I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, rd.x) : window_pow(f.ratio, rd.x);
-                    float al = __fmul_rn(rc.w, I);
-                    if (al < ALPHA_MIN) continue;
-                    al = fminf(al, ALPHA_MAX);
-                    const float tT = __fmul_rn(T, __fsub_rn(1.0f, al));
-                    if (tT < T_EPS) {
-                        done = true;
-                        break;
-                    }
-                    const float wgt = __fmul_rn(al, T);
-                    if (stats) {
-                        // Sec. 3.3 "Pruning": blending weight T o of this fragment
-                        atomicMax(&s_sw[j], __float_as_uint(__fmul_rn(T, rc.w)));
-                        atomicAdd(&s_sn[j], 1u);
-                    }
-                    C0 = fmaf(rd.y, wgt, C0);
-                    C1 = fmaf(rd.z, wgt, C1);
-                    C2 = fmaf(rd.w, wgt, C2);
-                    T = tT;
-                    last = b0 - start + (uint32_t)j + 1u;
-                    if (COUNT) ++n_kept;
-                    kept |= 1u << (k - c);
-                }
-                if (a.kmask) {
-                    // lane b gathers which groups of the warp composited entry c + b
-                    const uint32_t gk = group_or(kept);
-                    uint32_t mb = 0;
-#pragma unroll
-                    for (int e = 0; e < WGROUPS; ++e) mb |= ((__shfl_sync(0xffffffffu, gk, e * GROUP) >> lane) & 1u) << e;
-                    if (mb && c + lane < cnt) atomicOr(&s_km[KM_WORD(w)][L[c + lane]], mb << KM_SHIFT(w));
-                }
-            }
-            if (a.kmask || stats) {
-                __syncthreads();
-                if (a.kmask) {
-                    if (idx < end) {
-#pragma unroll
-                        for (int q = 0; q < KM_WORDS; ++q) a.kmask[(size_t)idx * KM_WORDS + q] = s_km[q][tid];
-                    }
-#pragma unroll
-                    for (int q = 0; q < KM_WORDS; ++q) s_km[q][tid] = 0u;
-                }
-                if (stats) {
-                    if (s_sn[tid]) {
-                        atomicAdd(&a.stat_n[it], s_sn[tid]);
-                        atomicMax(&a.stat_w[it], s_sw[tid]);
-                    }
-                    s_sn[tid] = 0u;
-                    s_sw[tid] = 0u;
-                }
-            }
-        }
-        if (inside) {
-            const int64_t HW = (int64_t)V.W * V.H;
-            const int64_t pix = (int64_t)y * V.W + x;
-            const ViewOut vo = view_out(a, vw);
-            const float c[3] = {fmaf(T, V.bg[0], C0), fmaf(T, V.bg[1], C1), fmaf(T, V.bg[2], C2)};
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) vo.image[ch * HW + pix] = c[ch];
-            if (vo.target) {
-                // the L1 loss of the pixel and its gradient, while the colour is in registers
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    const float d = c[ch] - vo.target[ch * HW + pix];
-                    l1_acc += fabsf(d);
-                    vo.grad[ch * HW + pix] = l1_sign(d, a.loss_scale);
-                }
-            }
-            a.T_final[V.pix_base + pix] = T;
-            a.n_contrib[V.pix_base + pix] = (int32_t)last;
-            if (SOLID && a.ids)
-                a.ids[V.pix_base + pix] = last ? (int32_t)((int64_t)a.items[start + last - 1] - (int64_t)vw * a.n_per_view)
-                                               : -1;
-        }
-        const uint32_t gm = group_max(last);
-        const uint32_t we = COUNT ? __reduce_add_sync(0xffffffffu, n_eval) : 0u;
-        const uint32_t wk = COUNT ? __reduce_add_sync(0xffffffffu, n_kept) : 0u;
-        if (gl == 0) a.tile_max[(size_t)tile * GROUPS + WGROUPS * w + g] = gm;
-        if (lane == 0) {
-            atomicAdd(&a.ctl->frag_eval, (unsigned long long)we);
-            atomicAdd(&a.ctl->frag_kept, (unsigned long long)wk);
-        }
-        __syncthreads();
-    }
-    if (a.loss) {
-        // one reduction per CTA
-        float v = l1_acc;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_l1[w] = v;
-        __syncthreads();
-        if (tid == 0) {
-            float t = 0.f;
-#pragma unroll
-            for (int k = 0; k < REN_THREADS / 32; ++k) t += s_l1[k];
-            atomicAdd(a.loss, t * a.loss_scale);
-        }
-    }
-    if (last_cta_done(&a.ctl->done[0]) && tid == 0) a.ctl->work_counter[0] = 0u;
 }
 
 // Backward, one lane per 2x2 group: a warp takes one half tile (16x8 pixels, the 32
@@ -638,26 +442,363 @@ render_bwd_kernel(RenderArgs a) {
     if (last_cta_done(&a.ctl->done[1]) && threadIdx.x == 0) a.ctl->work_counter[1] = 0u;
 }
 
+// ---------------------------------------------------------------------------------
+// Forward, one lane per 2x2 group (the backward's layout): a warp takes one half tile
+// (16x8 pixels, the 32 groups of word h of the pairs' group masks; lane l owns group l)
+// and composites the tile's records front to back in windows of FW_WIN * 32 pairs. The
+// lane of pair j gathers the pair's record, tests it against the 32 groups (group_cover)
+// and stages it in shared memory when any group may see it; the window's coverage words
+// are transposed across the warp so that each lane holds the bit list of the pairs its
+// group may see, and walks it in order, compositing its four pixels in straight-line code
+// with the arithmetic of one pixel per thread. The kept bits go back through the same
+// transpose as the pairs' group masks for the backward. No CTA-wide barrier: a warp
+// leaves its half tile when its 32 groups have stopped.
+constexpr int FW_THREADS = 128;
+constexpr int FW_WARPS = FW_THREADS / 32;
+#ifndef FW_WIN
+#define FW_WIN 2                 // mask words per lane per window (64 pairs)
+#endif
+#ifndef FW_CTAS
+#define FW_CTAS 5
+#endif
+
+// One edge line's bound on the group column of each of the half tile's 4 group rows:
+// line (A, B, C) about s = (sx, sy) can reach `t` at a pixel centre of group column c of
+// row r only if c >= lo[r] (A > 0) or c <= hi[r] (A < 0). Each row takes its best
+// pixel row (the lower one when B >= 0) and the column bound from one division, widened
+// by a slack that covers its rounding; ex bounds |p.x - sx| over the half tile.
+__device__ __forceinline__ void line_cols(float A, float B, float C, float sx, float sy, int X0, int Y0, float ex,
+                                          float t, int (&lo)[4], int (&hi)[4]) {
+    const float dy0 = __fsub_rn((float)Y0 + (B >= 0.f ? 1.5f : 0.5f), sy);
+    const float dxs = __fsub_rn(sx, (float)X0);
+    if (fabsf(A) < 1e-6f) {
+        // (nearly) horizontal line: the row passes where its best value can reach t
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float need = t - C - B * (dy0 + 2.0f * (float)r);
+            if (need > fabsf(A) * ex) lo[r] = 8;
+        }
+        return;
+    }
+    const float rA = rcp_approx(A);
+    const float num = t - C - B * dy0;
+    // column bound of row r: 0.5 (sx - X0 - off) + 0.5 (t - C - B dy_r) / A
+    const float al = fmaf(0.5f, dxs - (A > 0.f ? 1.5f : 0.5f), 0.5f * num * rA);
+    const float be = B * rA;
+    const float sl = 0.05f + 1e-6f * (fabsf(dxs) + fabsf(rA) * (fabsf(t) + fabsf(C) + fabsf(B * dy0)) + 4.0f * fabsf(be));
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float v = fminf(fmaxf(fmaf(-(float)r, be, al), -4.0f), 12.0f);
+        if (A > 0.f) lo[r] = max(lo[r], (int)ceilf(v - sl));
+        else hi[r] = min(hi[r], (int)floorf(v + sl));
+    }
+}
+
+// Bit l set when the record (cutoff ratio thr) may composite at a pixel centre of 2x2
+// group l of the half tile with pixel origin (X0, Y0): group l sits at column
+// c = 4 ((l >> 3) & 1) + (l & 3) and row r = 2 (l >> 4) + ((l >> 2) & 1), pixels
+// (X0 + 2c + {0, 1}, Y0 + 2r + {0, 1}). The record's pixel rectangle and each edge
+// line bound the columns of each row; the margin covers the FP32 rounding of the
+// per-pixel evaluation, as in line_reaches.
+__device__ __forceinline__ uint32_t group_cover(const Rec &r, const ushort4 bx, int X0, int Y0, float thr) {
+    const float sx = r.a.x, sy = r.a.y;
+    const float ex = fmaxf(fabsf((float)X0 + 0.5f - sx), fabsf((float)X0 + 15.5f - sx));
+    const float ey = fmaxf(fabsf((float)Y0 + 0.5f - sy), fabsf((float)Y0 + 7.5f - sy));
+    const int clo = ((int)bx.x - X0) >> 1, chi = ((int)bx.z - X0) >> 1;
+    int lo[4], hi[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool rows = (int)bx.y <= Y0 + 2 * q + 1 && (int)bx.w >= Y0 + 2 * q;
+        lo[q] = rows ? max(clo, 0) : 8;
+        hi[q] = min(chi, 7);
+    }
+    const float C0 = line_offset(r.a.z, r.a.w, r.b), C1 = line_offset(r.b.y, r.b.z, r.b),
+                C2 = line_offset(r.c.x, r.c.y, r.b);
+    line_cols(r.a.z, r.a.w, C0, sx, sy, X0, Y0, ex,
+              thr - (1e-3f + 4e-7f * (fabsf(r.a.z) * ex + fabsf(r.a.w) * ey + fabsf(C0))), lo, hi);
+    line_cols(r.b.y, r.b.z, C1, sx, sy, X0, Y0, ex,
+              thr - (1e-3f + 4e-7f * (fabsf(r.b.y) * ex + fabsf(r.b.z) * ey + fabsf(C1))), lo, hi);
+    line_cols(r.c.x, r.c.y, C2, sx, sy, X0, Y0, ex,
+              thr - (1e-3f + 4e-7f * (fabsf(r.c.x) * ex + fabsf(r.c.y) * ey + fabsf(C2))), lo, hi);
+    uint32_t word = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int l = min(max(lo[q], 0), 8), h = min(max(hi[q], -1), 7);
+        const uint32_t M = (0xFFu << l) & (0xFFu >> (7 - h));
+        const int base = 16 * (q >> 1) + 4 * (q & 1);
+        word |= ((M & 0xFu) << base) | (((M >> 4) & 0xFu) << (base + 8));
+    }
+    return word;
+}
+
+// Composite one record (ca..cd, tile-list position jt1 - 1) at the lane's four pixels
+// (x0 + (p & 1), y0 + (p >> 1)), front to back, in straight-line code with the per-pixel
+// arithmetic of the rendering equation: bit p of `done` marks a pixel that has stopped.
+// Returns whether any pixel composited; STATS: the largest T o of those and their count.
+template <bool SOLID, int WIN, bool STATS, bool COUNT>
+__device__ __forceinline__ bool group_fwd(const float4 ca, const float4 cb, const float4 cc, const float4 cd,
+                                          uint32_t jt1, int x0, int y0, float (&T)[4], float (&C0)[4],
+                                          float (&C1)[4], float (&C2)[4], uint32_t (&last)[4], uint32_t &done,
+                                          float &sw, uint32_t &sn, uint32_t &n_eval, uint32_t &n_kept) {
+    bool any = false;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const float px = (float)(x0 + (p & 1)) + 0.5f, py = (float)(y0 + (p >> 1)) + 0.5f;
+        const bool live = !((done >> p) & 1u);
+        if (COUNT) n_eval += live ? 1u : 0u;
+        const Frag f = eval_lines(ca, cb, cc, px, py);
+        if (SOLID) {
+            const bool hit = live && f.ratio > 0.0f;
+            C0[p] = hit ? cd.y : C0[p];
+            C1[p] = hit ? cd.z : C1[p];
+            C2[p] = hit ? cd.w : C2[p];
+            T[p] = hit ? 0.0f : T[p];
+            last[p] = hit ? jt1 : last[p];
+            done |= hit ? 1u << p : 0u;
+            if (COUNT) n_kept += hit ? 1u : 0u;
+            any = any || hit;
+            continue;
+        }
+        const bool pos = WIN == WIN_SIGMOID || f.ratio > 0.0f;
+        const float I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, cd.x) : window_pow(pos ? f.ratio : 1.0f, cd.x);
+        const float araw = __fmul_rn(cc.w, I);
+        const bool act = live && pos && araw >= ALPHA_MIN;
+        const float al = fminf(araw, ALPHA_MAX);
+        const float tT = __fmul_rn(T[p], __fsub_rn(1.0f, al));
+        const bool stop = act && tT < T_EPS;
+        const bool comp = act && !stop;
+        done |= stop ? 1u << p : 0u;
+        const float wgt = __fmul_rn(al, T[p]);
+        if (STATS && comp) {
+            // Sec. 3.3 "Pruning": blending weight T o of this fragment
+            sw = fmaxf(sw, __fmul_rn(T[p], cc.w));
+            ++sn;
+        }
+        C0[p] = comp ? fmaf(cd.y, wgt, C0[p]) : C0[p];
+        C1[p] = comp ? fmaf(cd.z, wgt, C1[p]) : C1[p];
+        C2[p] = comp ? fmaf(cd.w, wgt, C2[p]) : C2[p];
+        T[p] = comp ? tT : T[p];
+        last[p] = comp ? jt1 : last[p];
+        if (COUNT) n_kept += comp ? 1u : 0u;
+        any = any || comp;
+    }
+    return any;
+}
+
+// Lowest set bit of the list (hi:lo), cleared; -1 when empty.
+__device__ __forceinline__ int pop_first(unsigned long long &hi, unsigned long long &lo) {
+    if (lo) {
+        const int b = __ffsll((long long)lo) - 1;
+        lo &= lo - 1ull;
+        return b;
+    }
+    if (hi) {
+        const int b = __ffsll((long long)hi) - 1;
+        hi &= hi - 1ull;
+        return 64 + b;
+    }
+    return -1;
+}
+
+template <bool SOLID, int WIN, bool STATS, bool COUNT>
+__global__ void __launch_bounds__(FW_THREADS, FW_CTAS)
+render_fwd_kernel(RenderArgs a) {
+    // per warp: the window's records (stride of 5 float4: lanes reading different
+    // records spread over the banks), item ids and the pruning statistics of each pair
+    __shared__ float4 s_rec[FW_WARPS][32 * FW_WIN][BW_RSTRIDE];
+    __shared__ uint32_t s_it[FW_WARPS][32 * FW_WIN];
+    __shared__ uint32_t s_sw[STATS ? FW_WARPS : 1][32 * FW_WIN];
+    __shared__ uint32_t s_sn[STATS ? FW_WARPS : 1][32 * FW_WIN];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *S = s_it[w];
+    float4 (*SR)[BW_RSTRIDE] = s_rec[w];
+    if (STATS) {
+#pragma unroll
+        for (int q = 0; q < FW_WIN; ++q) s_sw[w][32 * q + lane] = s_sn[w][32 * q + lane] = 0u;
+    }
+    const uint32_t n_units = (uint32_t)a.total_tiles * 2u;
+    const Rec *__restrict__ recs = a.recs;
+    float l1_acc = 0.f;                 // this lane's share of the L1 loss
+    uint32_t n_eval = 0, n_kept = 0;
+    for (;;) {
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(&a.ctl->work_counter[0], 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= n_units) break;
+        // tiles in the binning's order (longest first), each as its two halves
+        uint32_t tq = u >> 1;
+        if (a.tile_order) {
+            const uint32_t t = a.tile_order[tq];
+            if (t < (uint32_t)a.total_tiles) tq = t;
+            else if (lane == 0) atomicOr(&a.ctl->error, ERR_INDEX);
+        }
+        const int tile = (int)tq, h = (int)(u & 1u);
+        const int vw = find_view_warp(a.views, a.nviews, tile, lane);
+        const ViewDev *V = a.views + vw;
+        const int lt = tile - V->tile_base;
+        const int X0 = (lt % V->tiles_x) * TILE, Y0 = (lt / V->tiles_x) * TILE + 8 * h;
+        // this lane's group: column c = 4 ((lane >> 3) & 1) + (lane & 3), row
+        // r = 2 (lane >> 4) + ((lane >> 2) & 1) of the half tile
+        const int x0 = X0 + 8 * ((lane >> 3) & 1) + 2 * (lane & 3);
+        const int y0 = Y0 + 4 * (lane >> 4) + 2 * ((lane >> 2) & 1);
+        const int W = V->W, H = V->H;
+        float T[4], C0[4], C1[4], C2[4];
+        uint32_t last[4], done = 0u;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            T[p] = 1.0f;
+            C0[p] = C1[p] = C2[p] = 0.0f;
+            last[p] = 0u;
+            if (x0 + (p & 1) >= W || y0 + (p >> 1) >= H) done |= 1u << p;
+        }
+        const uint2 rg = a.ranges[tile];
+        const uint32_t start = rg.x;
+        const int n = rg.y > rg.x ? (int)(rg.y - rg.x) : 0;
+        for (int wst = 0; wst < n; wst += 32 * FW_WIN) {
+            if (__all_sync(0xffffffffu, done == 0xFu)) break;
+            // this lane's bits of the window: bit j of word q = pair wst + 32 q + j
+            uint32_t m[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int q = 0; q < FW_WIN; ++q) {
+                const int jj = wst + 32 * q + lane;
+                uint32_t word = 0u, it = 0u;
+                if (jj < n) {
+                    it = a.items[start + jj];
+                    if (it >= a.n_items) {
+                        atomicOr(&a.ctl->error, ERR_INDEX);
+                        it = 0u;
+                    } else {
+                        const Rec r = recs[it];
+                        word = group_cover(r, a.rects[it], X0, Y0, cutoff_ratio<WIN>(r, SOLID));
+                        if (word) {
+                            SR[32 * q + lane][0] = r.a;
+                            SR[32 * q + lane][1] = r.b;
+                            SR[32 * q + lane][2] = r.c;
+                            SR[32 * q + lane][3] = r.d;
+                        }
+                    }
+                }
+                S[32 * q + lane] = it;
+                m[q] = warp_transpose_bits(word, lane);
+            }
+            __syncwarp();
+            unsigned long long lo = ((unsigned long long)m[1] << 32) | m[0];
+            unsigned long long hi = ((unsigned long long)m[3] << 32) | m[2];
+            unsigned long long klo = 0ull, khi = 0ull;   // pairs this lane's group composited
+            for (;;) {
+                const int cpos = done == 0xFu ? -1 : pop_first(hi, lo);
+                if (!__any_sync(0xffffffffu, cpos >= 0)) break;
+                if (cpos < 0) continue;      // (the warp's next pop meets this lane at the vote)
+                const float4 ca = SR[cpos][0], cb = SR[cpos][1], cc = SR[cpos][2], cd = SR[cpos][3];
+                float sw = 0.0f;
+                uint32_t sn = 0u;
+                if (group_fwd<SOLID, WIN, STATS, COUNT>(ca, cb, cc, cd, (uint32_t)(wst + cpos + 1), x0, y0, T, C0, C1,
+                                                        C2, last, done, sw, sn, n_eval, n_kept)) {
+                    if (cpos < 64) klo |= 1ull << cpos;
+                    else khi |= 1ull << (cpos - 64);
+                    if (STATS) {
+                        atomicMax(&s_sw[w][cpos], __float_as_uint(sw));
+                        atomicAdd(&s_sn[w][cpos], sn);
+                    }
+                }
+            }
+            if (a.kmask) {
+                // back through the transpose: lane j gets the groups that composited pair j
+#pragma unroll
+                for (int q = 0; q < FW_WIN; ++q) {
+                    const unsigned long long src = q < 2 ? klo : khi;
+                    const uint32_t kw = (uint32_t)(src >> (32 * (q & 1)));
+                    const uint32_t word = warp_transpose_bits(kw, lane);
+                    const int jj = wst + 32 * q + lane;
+                    if (jj < n) a.kmask[(size_t)(start + jj) * KM_WORDS + h] = word;
+                }
+            }
+            if (STATS) {
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < FW_WIN; ++q) {
+                    const int k = 32 * q + lane;
+                    const uint32_t sn = s_sn[w][k];
+                    if (sn) {
+                        atomicAdd(&a.stat_n[S[k]], sn);
+                        atomicMax(&a.stat_w[S[k]], s_sw[w][k]);
+                    }
+                    s_sn[w][k] = 0u;
+                    s_sw[w][k] = 0u;
+                }
+            }
+            __syncwarp();
+        }
+        const int64_t HW = (int64_t)W * H;
+        const ViewOut vo = view_out(a, vw);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int x = x0 + (p & 1), y = y0 + (p >> 1);
+            if (x >= W || y >= H) continue;
+            const int64_t pix = (int64_t)y * W + x;
+            const float c[3] = {fmaf(T[p], V->bg[0], C0[p]), fmaf(T[p], V->bg[1], C1[p]), fmaf(T[p], V->bg[2], C2[p])};
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) vo.image[ch * HW + pix] = c[ch];
+            if (vo.target) {
+                // the L1 loss of the pixel and its gradient, while the colour is in registers
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float d = c[ch] - vo.target[ch * HW + pix];
+                    l1_acc += fabsf(d);
+                    vo.grad[ch * HW + pix] = l1_sign(d, a.loss_scale);
+                }
+            }
+            a.T_final[V->pix_base + pix] = T[p];
+            a.n_contrib[V->pix_base + pix] = (int32_t)last[p];
+            if (SOLID && a.ids)
+                a.ids[V->pix_base + pix] =
+                    last[p] ? (int32_t)((int64_t)a.items[start + last[p] - 1] - (int64_t)vw * a.n_per_view) : -1;
+        }
+        a.tile_max[(size_t)tile * GROUPS + 32 * h + lane] = max(max(last[0], last[1]), max(last[2], last[3]));
+    }
+    if (COUNT) {
+        const uint32_t we = __reduce_add_sync(0xffffffffu, n_eval), wk = __reduce_add_sync(0xffffffffu, n_kept);
+        if (lane == 0) {
+            atomicAdd(&a.ctl->frag_eval, (unsigned long long)we);
+            atomicAdd(&a.ctl->frag_kept, (unsigned long long)wk);
+        }
+    }
+    if (a.loss) {
+        float v = l1_acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) atomicAdd(a.loss, v * a.loss_scale);
+    }
+    if (last_cta_done(&a.ctl->done[0]) && threadIdx.x == 0) a.ctl->work_counter[0] = 0u;
+}
+
 static int occupancy(const void *fn, int threads) {
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0) != cudaSuccess || occ < 1) occ = 1;
     return occ;
 }
 
-template <bool COUNT>
-static void launch_fwd_count(const RenderArgs &a, int g, cudaStream_t st, bool solid) {
-    if (solid) render_fwd_kernel<true, WIN_POWER, COUNT><<<g, REN_THREADS, 0, st>>>(a);
-    else if (a.window == WIN_SIGMOID) render_fwd_kernel<false, WIN_SIGMOID, COUNT><<<g, REN_THREADS, 0, st>>>(a);
-    else render_fwd_kernel<false, WIN_POWER, COUNT><<<g, REN_THREADS, 0, st>>>(a);
+template <bool STATS, bool COUNT>
+static void launch_fwd_kind(const RenderArgs &a, unsigned g, cudaStream_t st, bool solid) {
+    if (solid) render_fwd_kernel<true, WIN_POWER, false, COUNT><<<g, FW_THREADS, 0, st>>>(a);
+    else if (a.window == WIN_SIGMOID) render_fwd_kernel<false, WIN_SIGMOID, STATS, COUNT><<<g, FW_THREADS, 0, st>>>(a);
+    else render_fwd_kernel<false, WIN_POWER, STATS, COUNT><<<g, FW_THREADS, 0, st>>>(a);
 }
 
 void launch_render_fwd(const RenderArgs &a, int grid, cudaStream_t st, bool solid) {
-    static int occ = occupancy((const void *)render_fwd_kernel<false, WIN_POWER, false>, REN_THREADS);
-    int g = grid > 0 ? grid * occ : occ;
-    if (g > a.total_tiles) g = a.total_tiles;
+    static int occ = occupancy((const void *)render_fwd_kernel<false, WIN_POWER, false, false>, FW_THREADS);
+    int64_t g = grid > 0 ? (int64_t)grid * occ : occ;
+    const int64_t need = ((int64_t)a.total_tiles * 2 + FW_WARPS - 1) / FW_WARPS;
+    if (g > need) g = need;
     if (g <= 0) return;
-    if (a.count_frags) launch_fwd_count<true>(a, g, st, solid);
-    else launch_fwd_count<false>(a, g, st, solid);
+    const bool stats = a.stat_n != nullptr && !solid;
+    if (stats) {
+        if (a.count_frags) launch_fwd_kind<true, true>(a, (unsigned)g, st, solid);
+        else launch_fwd_kind<true, false>(a, (unsigned)g, st, solid);
+    } else {
+        if (a.count_frags) launch_fwd_kind<false, true>(a, (unsigned)g, st, solid);
+        else launch_fwd_kind<false, false>(a, (unsigned)g, st, solid);
+    }
 }
 
 void launch_render_bwd(const RenderArgs &a, int grid, cudaStream_t st) {
