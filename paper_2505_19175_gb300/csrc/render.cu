@@ -559,24 +559,25 @@ __device__ __forceinline__ bool group_fwd(const float4 ca, const float4 cb, cons
             any = any || hit;
             continue;
         }
-        const bool pos = WIN == WIN_SIGMOID || f.ratio > 0.0f;
-        const float I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, cd.x) : window_pow(pos ? f.ratio : 1.0f, cd.x);
+        // (a power-window ratio <= 0 gives alpha 0 or NaN, which the threshold test skips)
+        const float I = WIN == WIN_SIGMOID ? window_sigmoid(f.ratio, cd.x) : window_pow(f.ratio, cd.x);
         const float araw = __fmul_rn(cc.w, I);
-        const bool act = live && pos && araw >= ALPHA_MIN;
+        const bool act = live && araw >= ALPHA_MIN;
         const float al = fminf(araw, ALPHA_MAX);
         const float tT = __fmul_rn(T[p], __fsub_rn(1.0f, al));
         const bool stop = act && tT < T_EPS;
         const bool comp = act && !stop;
         done |= stop ? 1u << p : 0u;
-        const float wgt = __fmul_rn(al, T[p]);
+        // a pixel that does not composite adds rgb x 0 (colours are finite and >= 0)
+        const float wgt = comp ? __fmul_rn(al, T[p]) : 0.0f;
         if (STATS && comp) {
             // Sec. 3.3 "Pruning": blending weight T o of this fragment
             sw = fmaxf(sw, __fmul_rn(T[p], cc.w));
             ++sn;
         }
-        C0[p] = comp ? fmaf(cd.y, wgt, C0[p]) : C0[p];
-        C1[p] = comp ? fmaf(cd.z, wgt, C1[p]) : C1[p];
-        C2[p] = comp ? fmaf(cd.w, wgt, C2[p]) : C2[p];
+        C0[p] = fmaf(cd.y, wgt, C0[p]);
+        C1[p] = fmaf(cd.z, wgt, C1[p]);
+        C2[p] = fmaf(cd.w, wgt, C2[p]);
         T[p] = comp ? tT : T[p];
         last[p] = comp ? jt1 : last[p];
         if (COUNT) n_kept += comp ? 1u : 0u;
@@ -686,7 +687,8 @@ render_fwd_kernel(RenderArgs a) {
             unsigned long long hi = ((unsigned long long)m[3] << 32) | m[2];
             unsigned long long klo = 0ull, khi = 0ull;   // pairs this lane's group composited
             for (;;) {
-                const int cpos = done == 0xFu ? -1 : pop_first(hi, lo);
+                int cpos = pop_first(hi, lo);
+                if (done == 0xFu) cpos = -1;     // (a lane whose pixels have all stopped drops its list)
                 if (!__any_sync(0xffffffffu, cpos >= 0)) break;
                 if (cpos < 0) continue;      // (the warp's next pop meets this lane at the vote)
                 const float4 ca = SR[cpos][0], cb = SR[cpos][1], cc = SR[cpos][2], cd = SR[cpos][3];
