@@ -31,11 +31,7 @@
 namespace ts {
 
 constexpr int REN_THREADS = TILE_PIX;
-constexpr int WGROUPS = 32 / GROUP;               // groups per warp
 constexpr int GROUPS = GROUPS_PER_TILE;           // groups per tile
-// word and bit offset of warp w's groups in the pair's group mask
-#define KM_WORD(w) ((w) / (32 / WGROUPS))
-#define KM_SHIFT(w) (WGROUPS * ((w) % (32 / WGROUPS)))
 
 // View of a tile from the views' first tile ids, by one warp (all lanes get it): the
 // last view whose first tile is <= tile.
@@ -139,18 +135,6 @@ __device__ __forceinline__ int warp_list(const uint16_t *s_mask, uint8_t *list, 
     }
     __syncwarp();
     return cnt;
-}
-
-// OR / max across the 8 lanes of a group (full-warp shuffles that stay in the group).
-__device__ __forceinline__ uint32_t group_or(uint32_t v) {
-#pragma unroll
-    for (int o = GROUP / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ uint32_t group_max(uint32_t v) {
-#pragma unroll
-    for (int o = GROUP / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
 }
 
 // Backward, one lane per 2x2 group: a warp takes one half tile (16x8 pixels, the 32
@@ -655,6 +639,10 @@ render_fwd_kernel(RenderArgs a) {
         const uint2 rg = a.ranges[tile];
         const uint32_t start = rg.x;
         const int n = rg.y > rg.x ? (int)(rg.y - rg.x) : 0;
+        // item ids of the window, loaded one window ahead
+        uint32_t nit[FW_WIN];
+#pragma unroll
+        for (int q = 0; q < FW_WIN; ++q) nit[q] = 32 * q + lane < n ? a.items[start + 32 * q + lane] : 0u;
         for (int wst = 0; wst < n; wst += 32 * FW_WIN) {
             if (__all_sync(0xffffffffu, done == 0xFu)) break;
             // this lane's bits of the window: bit j of word q = pair wst + 32 q + j
@@ -664,7 +652,7 @@ render_fwd_kernel(RenderArgs a) {
                 const int jj = wst + 32 * q + lane;
                 uint32_t word = 0u, it = 0u;
                 if (jj < n) {
-                    it = a.items[start + jj];
+                    it = nit[q];
                     if (it >= a.n_items) {
                         atomicOr(&a.ctl->error, ERR_INDEX);
                         it = 0u;
@@ -683,6 +671,11 @@ render_fwd_kernel(RenderArgs a) {
                 m[q] = warp_transpose_bits(word, lane);
             }
             __syncwarp();
+#pragma unroll
+            for (int q = 0; q < FW_WIN; ++q) {
+                const int jn = wst + 32 * FW_WIN + 32 * q + lane;
+                nit[q] = jn < n ? a.items[start + jn] : 0u;
+            }
             unsigned long long lo = ((unsigned long long)m[1] << 32) | m[0];
             unsigned long long hi = ((unsigned long long)m[3] << 32) | m[2];
             unsigned long long klo = 0ull, khi = 0ull;   // pairs this lane's group composited
