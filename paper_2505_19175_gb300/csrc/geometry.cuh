@@ -151,28 +151,33 @@ constexpr float c3d = 0.3731763325901154f;   // sqrt(7/(16 pi))
 constexpr float c3e = 1.445305721320277f;    // sqrt(105/(16 pi))
 }  // namespace shc
 
+// Real SH basis up to degree 3 at the unit direction (x, y, z). Every operation is an
+// explicit round-to-nearest multiply, subtract or fused multiply-add, so that all the
+// kernels that inline it (forward, backward, one view or many) compute the same bits.
 __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float *Y) {
     using namespace shc;
     Y[0] = c0;
     if (deg < 1) return;
-    Y[1] = c1 * y;
-    Y[2] = c1 * z;
-    Y[3] = c1 * x;
+    Y[1] = __fmul_rn(c1, y);
+    Y[2] = __fmul_rn(c1, z);
+    Y[3] = __fmul_rn(c1, x);
     if (deg < 2) return;
-    const float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = c2a * x * y;
-    Y[5] = c2a * y * z;
-    Y[6] = c2b * (3.0f * zz - 1.0f);
-    Y[7] = c2a * x * z;
-    Y[8] = c2c * (xx - yy);
+    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    const float dxy = __fsub_rn(xx, yy);
+    Y[4] = __fmul_rn(__fmul_rn(c2a, x), y);
+    Y[5] = __fmul_rn(__fmul_rn(c2a, y), z);
+    Y[6] = __fmul_rn(c2b, fmaf(3.0f, zz, -1.0f));
+    Y[7] = __fmul_rn(__fmul_rn(c2a, x), z);
+    Y[8] = __fmul_rn(c2c, dxy);
     if (deg < 3) return;
-    Y[9] = c3a * y * (3.0f * xx - yy);
-    Y[10] = c3b * x * y * z;
-    Y[11] = c3c * y * (5.0f * zz - 1.0f);
-    Y[12] = c3d * z * (5.0f * zz - 3.0f);
-    Y[13] = c3c * x * (5.0f * zz - 1.0f);
-    Y[14] = c3e * z * (xx - yy);
-    Y[15] = c3a * x * (xx - 3.0f * yy);
+    const float z5 = fmaf(5.0f, zz, -1.0f);
+    Y[9] = __fmul_rn(__fmul_rn(c3a, y), fmaf(3.0f, xx, -yy));
+    Y[10] = __fmul_rn(__fmul_rn(__fmul_rn(c3b, x), y), z);
+    Y[11] = __fmul_rn(__fmul_rn(c3c, y), z5);
+    Y[12] = __fmul_rn(__fmul_rn(c3d, z), fmaf(5.0f, zz, -3.0f));
+    Y[13] = __fmul_rn(__fmul_rn(c3c, x), z5);
+    Y[14] = __fmul_rn(__fmul_rn(c3e, z), dxy);
+    Y[15] = __fmul_rn(__fmul_rn(c3a, x), fmaf(-3.0f, yy, xx));
 }
 
 // sum_k gY[k] dY_k/d(x, y, z), the basis taken as polynomials in free x, y, z
