@@ -189,20 +189,27 @@ __device__ __forceinline__ int pop_last(unsigned long long &hi, unsigned long lo
 // lane's four pixels, in straight-line code (independent pixels, so their arithmetic
 // interleaves): a pixel that does not composite the fragment (or all four, when `mine`
 // is false) computes with safe inputs and adds zeros. Updates T and B back to front;
-// returns whether any pixel composited.
+// returns whether any pixel composited. dL/dratio of each pixel goes to its active
+// line i: W[i] sums it, and with the pixel offsets dx_p = dx_0 + (p & 1),
+// dy_p = dy_0 + (p >> 1), dL/dA_i = dx_0 W[i] + (sum over odd p) and dL/dB_i likewise,
+// dL/ds = -(sum_i W[i] (A_i, B_i)).
 template <int WIN>
 __device__ __forceinline__ bool group_grad(const float4 ca, const float4 cb, const float4 cc, const float4 cd,
                                            uint32_t jt, bool mine, int x0, int y0, const uint32_t (&last)[4],
                                            float (&T)[4], const float (&G0)[4], const float (&G1)[4],
                                            const float (&G2)[4], float (&B0)[4], float (&B1)[4], float (&B2)[4],
                                            float (&gv)[13]) {
-#pragma unroll
-    for (int q = 0; q < 13; ++q) gv[q] = 0.f;
+    float W[3] = {0.f, 0.f, 0.f}, Wx[3] = {0.f, 0.f, 0.f}, Wy[3] = {0.f, 0.f, 0.f};
+    float go = 0.f, gs = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, dx0 = 0.f, dy0 = 0.f;
     bool any = false;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const float px = (float)(x0 + (p & 1)) + 0.5f, py = (float)(y0 + (p >> 1)) + 0.5f;
         const Frag f = eval_lines(ca, cb, cc, px, py);
+        if (p == 0) {
+            dx0 = f.dx;
+            dy0 = f.dy;
+        }
         const bool pos = WIN == WIN_SIGMOID || f.ratio > 0.0f;
         const float rs = pos ? f.ratio : 1.0f;   // the power window's ratio, kept positive
         const float lg = WIN == WIN_SIGMOID ? 0.0f : lg2_approx(rs);
@@ -216,9 +223,9 @@ __device__ __forceinline__ bool group_grad(const float4 ca, const float4 cb, con
         const float Tn = T[p] * iom;
         T[p] = kept ? Tn : T[p];
         const float wgt = kept ? al * Tn : 0.0f;
-        gv[10] = fmaf(G0[p], wgt, gv[10]);
-        gv[11] = fmaf(G1[p], wgt, gv[11]);
-        gv[12] = fmaf(G2[p], wgt, gv[12]);
+        gc0 = fmaf(G0[p], wgt, gc0);
+        gc1 = fmaf(G1[p], wgt, gc1);
+        gc2 = fmaf(G2[p], wgt, gc2);
         const float gc = fmaf(G0[p], cd.y, fmaf(G1[p], cd.z, G2[p] * cd.w));
         const float gb = fmaf(G0[p], B0[p], fmaf(G1[p], B1[p], G2[p] * B2[p]));
         // dalpha/d(o I) is 0 where alpha is clamped
@@ -227,34 +234,50 @@ __device__ __forceinline__ bool group_grad(const float4 ca, const float4 cb, con
         B1[p] = fmaf(cd.z, wgt, B1[p]);
         B2[p] = fmaf(cd.w, wgt, B2[p]);
         const float gI = galpha * cc.w;
-        gv[8] = fmaf(galpha, I, gv[8]);                       // d/do
+        go = fmaf(galpha, I, go);                             // d/do
         float gr;                                              // d/dratio
         if (WIN == WIN_SIGMOID) {
             // I = sigmoid(kappa ratio): field 9 is d/dkappa
             const float s1 = I * (1.0f - I);
-            gv[9] = fmaf(gI * s1, f.ratio, gv[9]);
+            gs = fmaf(gI * s1, f.ratio, gs);
             gr = gI * cd.x * s1;
         } else {
             // (a pixel that adds zeros may have a ratio whose lg2 or reciprocal
             // is infinite: those take the values of ratio 1)
             const float lgk = kept ? lg : 0.0f, rk = kept ? rs : 1.0f;
-            gv[9] = fmaf(gI * I, lgk * 0.69314718055994531f, gv[9]);   // d/dsigma: I ln(ratio)
+            gs = fmaf(gI * I, lgk, gs);                        // d/dsigma / ln 2: I lg2(ratio)
             gr = gI * cd.x * I * rcp_approx(rk);
         }
         // the active line: lowest index among the minima
-        const int ia = (f.m0 <= f.m1 && f.m0 <= f.m2) ? 0 : (f.m1 <= f.m2 ? 1 : 2);
-        const float Aa = ia == 0 ? ca.z : (ia == 1 ? cb.y : cc.x);
-        const float Ba = ia == 0 ? ca.w : (ia == 1 ? cb.z : cc.y);
-        gv[0] = fmaf(-gr, Aa, gv[0]);
-        gv[1] = fmaf(-gr, Ba, gv[1]);
-        const float gA = gr * f.dx, gB = gr * f.dy;
-        gv[2] += ia == 0 ? gA : 0.f;
-        gv[3] += ia == 0 ? gB : 0.f;
-        gv[4] += ia == 1 ? gA : 0.f;
-        gv[5] += ia == 1 ? gB : 0.f;
-        gv[6] += ia == 2 ? gA : 0.f;
-        gv[7] += ia == 2 ? gB : 0.f;
+        const bool a0 = f.m0 <= f.m1 && f.m0 <= f.m2, a1 = !a0 && f.m1 <= f.m2;
+        const float w0 = a0 ? gr : 0.f, w1 = a1 ? gr : 0.f, w2 = gr - w0 - w1;
+        W[0] += w0;
+        W[1] += w1;
+        W[2] += w2;
+        if (p & 1) {
+            Wx[0] += w0;
+            Wx[1] += w1;
+            Wx[2] += w2;
+        }
+        if (p >> 1) {
+            Wy[0] += w0;
+            Wy[1] += w1;
+            Wy[2] += w2;
+        }
     }
+    gv[0] = -fmaf(ca.z, W[0], fmaf(cb.y, W[1], cc.x * W[2]));
+    gv[1] = -fmaf(ca.w, W[0], fmaf(cb.z, W[1], cc.y * W[2]));
+    gv[2] = fmaf(dx0, W[0], Wx[0]);
+    gv[3] = fmaf(dy0, W[0], Wy[0]);
+    gv[4] = fmaf(dx0, W[1], Wx[1]);
+    gv[5] = fmaf(dy0, W[1], Wy[1]);
+    gv[6] = fmaf(dx0, W[2], Wx[2]);
+    gv[7] = fmaf(dy0, W[2], Wy[2]);
+    gv[8] = go;
+    gv[9] = WIN == WIN_SIGMOID ? gs : gs * 0.69314718055994531f;
+    gv[10] = gc0;
+    gv[11] = gc1;
+    gv[12] = gc2;
     return any;
 }
 
