@@ -144,7 +144,8 @@ tri_status tri_preprocess(tri_ctx *ctx, const tri_scene *scene, const tri_camera
 
 /* Step 2 (Supp. "Depth sorting", "Tile assignment"): duplication of every visible item
  * into the tiles of its rectangle, binned by tile (per-tile counts, their scan into
- * [start, end) ranges, a scatter into the ranges), then each tile's range sorted by
+ * [start, end) ranges, a scatter of the preprocess's list of visible items into the
+ * ranges), then each tile's range sorted by
  * (32-bit centroid-depth key, item id). The result equals a stable sort of the 64-bit
  * keys (tile << 32 | depth bits) emitted in item order.
  * If `num_pairs_out` is non-null the call synchronises after the counts, returns the
@@ -227,10 +228,11 @@ tri_status tri_ctx_check(tri_ctx *ctx, tri_ctx_info *info, void *stream);
 /* Internal buffers, for tests and diagnostics: copies buffer `which` to host memory
  * `dst` (at most `max_bytes`), synchronously; `*bytes` receives the byte count used.
  *   0: sorted pair tile keys (uint32 [n_pairs])   1: sorted pair item ids (uint32)
- *   2: tile ranges (uint32 [total_tiles][2])       3: item depth keys (uint32 [n_items])
+ *   2: tile ranges (uint32 [total_tiles][2])       3: item depth keys (uint32 [n_items];
+ *      0xffffffff for items that touch no tile; assembled from the visible-item list)
  *   4: item pixel rectangles (uint16 [n_items][4]: x0, y0, x1, y1 inclusive; written
  *      only for items with a non-zero tile count, as are the records of 7)
- *   5: item tile counts (uint32 [n_items])
+ *   5: item tile counts (uint32 [n_items]; assembled from the visible-item list)
  *   6: binned pairs (uint64 [n_pairs]: depth key << 32 | item id), grouped by tile;
  *      within a tile in scatter order, except tiles of more than 2048 pairs, whose
  *      ranges hold the sort's intermediate runs

@@ -216,9 +216,9 @@ BinArgs bin_args(tri_ctx *c) {
     b.nviews = c->nviews;
     b.n = c->scene.n;
     b.n_items = c->n_items;
-    b.ntiles = P<uint32_t>(c->ntiles);
     b.rects = P<ushort4>(c->rects);
-    b.dkeys = P<uint32_t>(c->dkeys);
+    b.vislist = P<uint4>(c->vislist);
+    b.vis_cap = (uint32_t)c->n_items;
     b.tile_count = P<uint32_t>(c->tile_count);
     b.tile_cursor = P<uint32_t>(c->tile_cursor);
     b.ranges = P<uint2>(c->ranges);
@@ -231,21 +231,6 @@ BinArgs bin_args(tri_ctx *c) {
     b.scan_ticket = &ctl_of(c)->cta_counter[3];
     b.cap = (uint32_t)c->pair_cap;
     b.total_tiles = c->total_tiles;
-    // a stride near 0.618 of the block count and coprime with it: a permutation
-    b.bin_per = bin_per_for(c->n_items, c->sms);
-    const uint64_t chunk = 256ull * (uint64_t)b.bin_per;
-    const uint64_t nblk = (uint64_t)(c->n_items + chunk - 1) / chunk;
-    uint64_t stride = nblk > 2 ? (uint64_t)((double)nblk * 0.6180339887) | 1u : 1u;
-    auto gcd = [](uint64_t x, uint64_t y) {
-        while (y) {
-            const uint64_t t = x % y;
-            x = y;
-            y = t;
-        }
-        return x;
-    };
-    while (nblk > 1 && gcd(stride, nblk) != 1) stride += 2;
-    b.blk_stride = nblk > 1 ? stride % nblk : 0;
     b.ctl = ctl_of(c);
     return b;
 }
@@ -383,9 +368,9 @@ static tri_status preprocess_impl(tri_ctx *c, const tri_scene *scene, const tri_
     ENSURE(c->outs_fwd, sizeof(ViewOut) * nviews);
     ENSURE(c->outs_bwd, sizeof(ViewOut) * nviews);
     ENSURE(c->recs, sizeof(Rec) * (size_t)M);
-    ENSURE(c->ntiles, 4 * (size_t)M);
     ENSURE(c->rects, 8 * (size_t)M);
-    ENSURE(c->dkeys, 4 * (size_t)M);
+    ENSURE(c->vislist, 16 * (size_t)M);
+    ENSURE(c->vmask, 8 * (size_t)scene->n);
     ENSURE(c->tile_count, 4 * (size_t)tiles);
     ENSURE(c->tile_cursor, 4 * (size_t)tiles);
     ENSURE(c->big_tiles, 4 * (size_t)tiles);
@@ -420,9 +405,10 @@ static tri_status preprocess_impl(tri_ctx *c, const tri_scene *scene, const tri_
         a.views = P<ViewDev>(c->views_d);
         a.nviews = nviews;
         a.recs = P<Rec>(c->recs);
-        a.ntiles = P<uint32_t>(c->ntiles);
         a.rects = P<ushort4>(c->rects);
-        a.dkeys = P<uint32_t>(c->dkeys);
+        a.vislist = P<uint4>(c->vislist);
+        a.vmask = P<uint64_t>(c->vmask);
+        a.vis_cap = (uint32_t)M;
         a.ctl = ctl_of(c);
         a.tile_count = P<uint32_t>(c->tile_count);
         a.solid = solid ? 1 : 0;
@@ -814,7 +800,8 @@ tri_status tri_preprocess_bwd(tri_ctx *c, float *dverts, float *dsh, float *dopa
     a.sh_degree = c->scene.sh_degree;
     a.views = P<ViewDev>(c->views_d);
     a.nviews = c->nviews;
-    a.ntiles = P<uint32_t>(c->ntiles);
+    a.ntiles = nullptr;
+    a.vmask = P<uint64_t>(c->vmask);
     a.grad2d = P<float>(c->grad2d);
     a.dverts = dverts;
     a.dsh = dsh;
@@ -885,9 +872,26 @@ tri_status tri_debug_copy(tri_ctx *c, int which, void *dst, size_t max_bytes, si
         }
         case 1: src = c->items.p; n = 4 * np; break;
         case 2: src = c->ranges.p; n = sizeof(uint2) * (size_t)c->total_tiles; break;
-        case 3: src = c->dkeys.p; n = 4 * M; break;
+        case 3:
+        case 5: {
+            // per-item depth keys / tile counts, from the visible-item list (items without
+            // an entry: key 0xffffffff, count 0)
+            n = 4 * M;
+            if (n > max_bytes) return fail(c, TRI_ERR_CAPACITY, "destination too small");
+            std::vector<uint4> L(std::min((size_t)h.vis_count, M));
+            if (!L.empty()) CK(cudaMemcpy(L.data(), c->vislist.p, sizeof(uint4) * L.size(), cudaMemcpyDeviceToHost));
+            uint32_t *out = (uint32_t *)dst;
+            for (size_t k = 0; k < M; ++k) out[k] = which == 3 ? 0xffffffffu : 0u;
+            for (const uint4 &e : L) {
+                if (e.x == VIS_HOLE || e.x >= M) continue;
+                const uint32_t tw = (e.w & 0xffffu) / TILE - (e.z & 0xffffu) / TILE + 1;
+                const uint32_t th = (e.w >> 16) / TILE - (e.z >> 16) / TILE + 1;
+                out[e.x] = which == 3 ? e.y : tw * th;
+            }
+            if (bytes) *bytes = n;
+            return TRI_OK;
+        }
         case 4: src = c->rects.p; n = 8 * M; break;
-        case 5: src = c->ntiles.p; n = 4 * M; break;
         case 6: src = c->kv.p; n = 8 * np; break;
         case 7: src = c->recs.p; n = sizeof(Rec) * M; break;
         case 8: src = c->grad2d.p; n = sizeof(float) * GRAD_FIELDS * M; break;

@@ -25,11 +25,12 @@ constexpr int TSORT_THREADS = 256;
 constexpr int WS_MAX = 512;               // words one warp sorts; longer ranges take a CTA
 constexpr int MERGE_PER_THREAD = 8;
 
-// Per-item expansion into (item, tile) pairs. A CTA takes chunks of bin_per x 256
-// items, compacts the items with a non-zero tile count into shared memory, and expands
-// them 256 at a time: f(valid, item, tile) is called for every pair, in rounds of
-// BIN_THREADS pairs in which all threads of the block take part (so that f may use warp
-// collectives).
+// Expansion of the visible items into (item, tile) pairs. A CTA takes chunks of 256
+// entries of the visible-item list (coalesced 16-byte loads: item, depth key, pixel
+// rectangle; holes skipped) and expands them in rounds of 2 x BIN_THREADS pairs in which all threads
+// of the block take part (so that f may use warp collectives): each thread decodes two
+// pairs, o and o + BIN_THREADS, and f(ok, item, tile, depth key) is called with both
+// (so that their memory operations overlap).
 template <class F>
 __device__ __forceinline__ void for_each_pair(const BinArgs &a, F &&f) {
     __shared__ uint32_t s_off[BIN_THREADS];
@@ -37,93 +38,109 @@ __device__ __forceinline__ void for_each_pair(const BinArgs &a, F &&f) {
     __shared__ uint32_t s_base_tile[BIN_THREADS];   // global id of the rectangle's first tile
     __shared__ uint32_t s_wx[BIN_THREADS];          // (rect width in tiles << 16) | view tiles_x
     __shared__ float s_iw[BIN_THREADS];             // 1 / rect width
+    __shared__ uint32_t s_key[BIN_THREADS];         // depth key
     __shared__ uint32_t s_tmp[33];
-    __shared__ uint32_t s_vis[BIN_THREADS * BIN_PER_MAX];   // the chunk's items that touch a tile
     __shared__ int2 s_vt[MAX_VIEWS];                // (tiles_x, tile_base)
     const int tid = threadIdx.x;
     for (int k = tid; k < a.nviews; k += BIN_THREADS) s_vt[k] = make_int2(a.views[k].tiles_x, a.views[k].tile_base);
     __syncthreads();
-    const int per = a.bin_per < 1 ? 1 : (a.bin_per > BIN_PER_MAX ? BIN_PER_MAX : a.bin_per);
-    const int64_t chunk = (int64_t)BIN_THREADS * per;
-    const uint64_t nchunk = (uint64_t)((a.n_items + chunk - 1) / chunk);
-    for (uint64_t ci = blockIdx.x; ci < nchunk; ci += gridDim.x) {
-        // chunks in a strided order: neighbouring items (often neighbours on screen) go
-        // to CTAs far apart in time, which spreads the atomics over many tiles
-        const int64_t c0 = (int64_t)((ci * a.blk_stride) % nchunk) * chunk;
-        uint32_t nvis;
-        if (per == 1) {
-            // one round over the chunk itself (items without tiles expand to nothing)
-            nvis = (uint32_t)(a.n_items - c0 < BIN_THREADS ? a.n_items - c0 : BIN_THREADS);
-        } else {
-            uint32_t flags = 0;
-            for (int k = 0; k < per; ++k) {
-                const int64_t m = c0 + (int64_t)k * BIN_THREADS + tid;
-                if (m < a.n_items && a.ntiles[m]) flags |= 1u << k;
-            }
-            uint32_t p = block_excl_scan((uint32_t)__popc(flags), s_tmp, nvis);
-            for (int k = 0; k < per; ++k)
-                if ((flags >> k) & 1u) s_vis[p++] = (uint32_t)(c0 + (int64_t)k * BIN_THREADS + tid);
-            __syncthreads();
+    const uint32_t K = min(a.ctl->vis_count, a.vis_cap);
+    const uint32_t nchunk = (K + BIN_THREADS - 1) / BIN_THREADS;
+    // chunks in a strided order (a stride near 0.618 of the chunk count, coprime with
+    // it): neighbouring entries (often neighbours on screen) go to CTAs far apart in
+    // time, which spreads the atomics over many tiles
+    uint32_t stride = nchunk > 2 ? ((uint32_t)((float)nchunk * 0.618034f) | 1u) : 1u;
+    auto gcd = [](uint32_t x, uint32_t y) {
+        while (y) {
+            const uint32_t t = x % y;
+            x = y;
+            y = t;
         }
-        for (uint32_t v0 = 0; v0 < nvis; v0 += BIN_THREADS) {
-            const bool valid = v0 + tid < nvis;
-            const uint32_t m = !valid ? 0u : (per == 1 ? (uint32_t)(c0 + tid) : s_vis[v0 + tid]);
-            const uint32_t nt = valid ? a.ntiles[m] : 0u;
-            uint32_t total;
-            const uint32_t local = block_excl_scan(nt, s_tmp, total);
-            s_off[tid] = local;
-            s_item[tid] = m;
-            if (nt) {
-                const ushort4 pr = a.rects[m];
-                const uint32_t tx0 = pr.x / TILE, ty0 = pr.y / TILE, wdt = pr.z / TILE - tx0 + 1;
-                const int2 vt = s_vt[a.nviews > 1 ? (int)((int64_t)m / a.n) : 0];
-                s_base_tile[tid] = (uint32_t)vt.y + ty0 * (uint32_t)vt.x + tx0;
-                s_wx[tid] = (wdt << 16) | (uint32_t)vt.x;
-                s_iw[tid] = 1.0f / (float)wdt;
-            }
-            __syncthreads();
-            for (uint32_t r0 = 0; r0 < total; r0 += BIN_THREADS) {
-                const uint32_t o = r0 + tid;
-                const bool ok = o < total;
-                uint32_t item = 0, tile = 0xffffffffu;
-                if (ok) {
-                    // owner: the last thread whose offset is <= o (threads with no tile
-                    // share their successor's offset and lose the search)
-                    int lo = 0, hi = BIN_THREADS - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_off[mid] <= o) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    const uint32_t k = o - s_off[lo];
-                    const uint32_t wx = s_wx[lo], wdt = wx >> 16, tiles_x = wx & 0xffffu;
-                    uint32_t row = (uint32_t)(((float)k + 0.5f) * s_iw[lo]);
-                    if (row * wdt > k) --row;                 // guard the FP32 quotient
-                    else if ((row + 1) * wdt <= k) ++row;
-                    const uint32_t col = k - row * wdt;
-                    item = s_item[lo];
-                    tile = s_base_tile[lo] + row * tiles_x + col;
-                    if (tile >= (uint32_t)a.total_tiles) {
-                        atomicOr(&a.ctl->error, ERR_INDEX);
-                        tile = 0xffffffffu;
-                    }
-                }
-                f(ok && tile != 0xffffffffu, item, tile);
-            }
-            __syncthreads();
+        return x;
+    };
+    while (nchunk > 1 && gcd(stride, nchunk) != 1u) stride += 2u;
+    // pair o of the current chunk: (item, tile, key), tile 0xffffffff when invalid
+    auto decode = [&](uint32_t o, uint32_t total, uint32_t &item, uint32_t &tile, uint32_t &key) {
+        item = 0u;
+        tile = 0xffffffffu;
+        key = 0u;
+        if (o >= total) return;
+        // owner: the last thread whose offset is <= o (threads with no tile share their
+        // successor's offset and lose the search)
+        int lo = 0, hi = BIN_THREADS - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= o) lo = mid;
+            else hi = mid - 1;
         }
+        const uint32_t k = o - s_off[lo];
+        const uint32_t wx = s_wx[lo], wdt = wx >> 16, tiles_x = wx & 0xffffu;
+        uint32_t row = (uint32_t)(((float)k + 0.5f) * s_iw[lo]);
+        if (row * wdt > k) --row;                 // guard the FP32 quotient
+        else if ((row + 1) * wdt <= k) ++row;
+        const uint32_t col = k - row * wdt;
+        item = s_item[lo];
+        key = s_key[lo];
+        tile = s_base_tile[lo] + row * tiles_x + col;
+        if (tile >= (uint32_t)a.total_tiles) {
+            atomicOr(&a.ctl->error, ERR_INDEX);
+            tile = 0xffffffffu;
+        }
+    };
+    for (uint32_t ci = blockIdx.x; ci < nchunk; ci += gridDim.x) {
+        const uint32_t j = (uint32_t)(((uint64_t)ci * stride) % nchunk) * BIN_THREADS + tid;
+        uint4 e = make_uint4(0u, 0u, 0u, 0u);
+        bool valid = j < K;
+        if (valid) {
+            e = a.vislist[j];
+            if (e.x == VIS_HOLE) {
+                valid = false;
+            } else if ((int64_t)e.x >= a.n_items) {
+                atomicOr(&a.ctl->error, ERR_INDEX);
+                valid = false;
+            }
+        }
+        const uint32_t tx0 = (e.z & 0xffffu) / TILE, ty0 = (e.z >> 16) / TILE;
+        const uint32_t wdt = (e.w & 0xffffu) / TILE - tx0 + 1, hgt = (e.w >> 16) / TILE - ty0 + 1;
+        const uint32_t nt = valid ? wdt * hgt : 0u;
+        uint32_t total;
+        const uint32_t local = block_excl_scan(nt, s_tmp, total);
+        s_off[tid] = local;
+        s_item[tid] = e.x;
+        if (nt) {
+            const int2 vt = s_vt[a.nviews > 1 ? (int)((int64_t)e.x / a.n) : 0];
+            s_base_tile[tid] = (uint32_t)vt.y + ty0 * (uint32_t)vt.x + tx0;
+            s_wx[tid] = (wdt << 16) | (uint32_t)vt.x;
+            s_iw[tid] = 1.0f / (float)wdt;
+            s_key[tid] = e.y;
+        }
+        __syncthreads();
+        for (uint32_t r0 = 0; r0 < total; r0 += 2 * BIN_THREADS) {
+            uint32_t i0, t0, k0, i1, t1, k1;
+            decode(r0 + tid, total, i0, t0, k0);
+            decode(r0 + BIN_THREADS + tid, total, i1, t1, k1);
+            f(t0 != 0xffffffffu, i0, t0, k0, t1 != 0xffffffffu, i1, t1, k1);
+        }
+        __syncthreads();
     }
 }
 
 __global__ void __launch_bounds__(BIN_THREADS) bin_scatter_kernel(BinArgs a) {
     const unsigned lt = lanemask_lt();
-    for_each_pair(a, [&](bool ok, uint32_t item, uint32_t tile) {
-        const unsigned peers = __match_any_sync(0xffffffffu, ok ? tile : 0xffffffffu);
-        const int leader = __ffs(peers) - 1;
-        uint32_t slot = 0;
-        if (ok && (int)(threadIdx.x & 31) == leader) slot = atomicAdd(&a.tile_cursor[tile], (uint32_t)__popc(peers));
-        slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(peers & lt);
-        if (ok && slot < a.cap) a.kv[slot] = ((unsigned long long)a.dkeys[item] << 32) | item;
+    const int lane = (int)(threadIdx.x & 31);
+    for_each_pair(a, [&](bool ok0, uint32_t item0, uint32_t tile0, uint32_t key0, bool ok1, uint32_t item1,
+                         uint32_t tile1, uint32_t key1) {
+        // one slot reservation per tile among the warp's pairs (both atomics in flight)
+        const unsigned p0 = __match_any_sync(0xffffffffu, ok0 ? tile0 : 0xffffffffu);
+        const unsigned p1 = __match_any_sync(0xffffffffu, ok1 ? tile1 : 0xffffffffu);
+        const int l0 = __ffs(p0) - 1, l1 = __ffs(p1) - 1;
+        uint32_t s0 = 0, s1 = 0;
+        if (ok0 && lane == l0) s0 = atomicAdd(&a.tile_cursor[tile0], (uint32_t)__popc(p0));
+        if (ok1 && lane == l1) s1 = atomicAdd(&a.tile_cursor[tile1], (uint32_t)__popc(p1));
+        s0 = __shfl_sync(0xffffffffu, s0, l0) + __popc(p0 & lt);
+        s1 = __shfl_sync(0xffffffffu, s1, l1) + __popc(p1 & lt);
+        if (ok0 && s0 < a.cap) a.kv[s0] = ((unsigned long long)key0 << 32) | item0;
+        if (ok1 && s1 < a.cap) a.kv[s1] = ((unsigned long long)key1 << 32) | item1;
     });
 }
 
@@ -482,8 +499,8 @@ void launch_bin_scan(const BinArgs &a, cudaStream_t st) {
 size_t bin_scan_status_words(int total_tiles) { return (size_t)((total_tiles + SCAN_TILE - 1) / SCAN_TILE) + 1; }
 
 void launch_bin_scatter(const BinArgs &a, int sms, cudaStream_t st) {
-    const int64_t chunk = (int64_t)BIN_THREADS * (a.bin_per < 1 ? 1 : a.bin_per);
-    int64_t g = (a.n_items + chunk - 1) / chunk;
+    // (the list's length is known on the device only: enough CTAs for every item, at most 16 per SM)
+    int64_t g = (a.n_items + BIN_THREADS - 1) / BIN_THREADS;
     if (g > (int64_t)sms * 16) g = (int64_t)sms * 16;
     if (g > 0) bin_scatter_kernel<<<(unsigned)g, BIN_THREADS, 0, st>>>(a);
 }

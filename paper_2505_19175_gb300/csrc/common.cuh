@@ -80,6 +80,7 @@ struct Ctl {
     uint32_t big_count;        // tiles queued for the CTA-wide sort
     uint32_t big_next;         // next queued tile to sort
     uint32_t done[8];          // CTAs finished, per self-cleaning kernel (see last_cta_done)
+    uint32_t vis_count;        // entries appended to the visible-item list (may exceed its capacity)
     unsigned long long frag_eval;   // forward: (pixel, entry) evaluations
     unsigned long long frag_kept;   // forward: composited fragments
     unsigned long long pps_total;   // per-pixel sort: candidates of all pixels

@@ -41,13 +41,13 @@ struct tri_ctx {
     // pinned copies of the small per-call tables, used while the stream is captured
     ts::ViewDev *h_views = nullptr;
     ts::ViewOut *h_outs_fwd = nullptr, *h_outs_bwd = nullptr;
-    TsDevBuf views_d, outs_fwd, outs_bwd, ctl, recs, ntiles, rects, dkeys, tile_count, tile_cursor, big_tiles, tile_order,
+    TsDevBuf views_d, outs_fwd, outs_bwd, ctl, recs, rects, tile_count, tile_cursor, big_tiles, tile_order,
         kv, kv_tmp, items, kmask, ids, dens_status, scan_status, ranges, tile_max, Tfin, ncontrib, grad2d, zplane, pcount,
-        poff, cand, pscan_status;
+        poff, cand, pscan_status, vislist, vmask;
     std::vector<TsDevBuf *> all() {
-        return {&views_d, &outs_fwd, &outs_bwd, &ctl, &recs, &ntiles, &rects, &dkeys, &tile_count, &tile_cursor,
+        return {&views_d, &outs_fwd, &outs_bwd, &ctl, &recs, &rects, &tile_count, &tile_cursor,
                 &big_tiles, &tile_order, &kv, &kv_tmp, &items, &kmask, &ids, &dens_status, &scan_status, &ranges, &tile_max, &Tfin, &ncontrib, &grad2d,
-                &zplane, &pcount, &poff, &cand, &pscan_status};
+                &zplane, &pcount, &poff, &cand, &pscan_status, &vislist, &vmask};
     }
 };
 

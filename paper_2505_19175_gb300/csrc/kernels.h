@@ -5,6 +5,11 @@
 
 namespace ts {
 
+// Entry of the visible-item list, written by the preprocess for each item that passes
+// its view's frustum test (CTA by CTA, in no particular order): (item id, depth key,
+// x0 | y0 << 16, x1 | y1 << 16), the inclusive pixel rectangle; item id VIS_HOLE for an
+// item that then touches no tile.
+constexpr uint32_t VIS_HOLE = 0xffffffffu;
 struct PreArgs {
     const float *verts, *sh, *opacity, *sigma;
     int64_t n;
@@ -21,6 +26,11 @@ struct PreArgs {
     int solid = 0;                   // opaque-triangle records: full triangle, o = 1
     int window = WIN_POWER;          // window kind of the records
     float4 *zplane = nullptr;        // if set: [items] (a, b, c, 0), 1/z(p) = a (p.x - cx) + b (p.y - cy) + c
+    uint4 *vislist = nullptr;        // if set: the visible-item list (entries as above)
+    uint32_t vis_cap = 0;
+    // if set: [triangles] bit v = the triangle's item of view v touches a tile; the
+    // per-item ntiles and dkeys are then not written
+    uint64_t *vmask = nullptr;
 };
 
 struct PreBwdArgs {
@@ -31,6 +41,7 @@ struct PreBwdArgs {
     const ViewDev *views;
     int nviews;
     const uint32_t *ntiles;
+    const uint64_t *vmask = nullptr;   // if set: read instead of ntiles (see PreArgs)
     const float *grad2d;       // [items][16]
     float *dverts, *dsh, *dopacity, *dsigma;
     int accumulate;
@@ -87,9 +98,7 @@ struct BinArgs {
     int nviews;
     int64_t n;                      // triangles per view
     int64_t n_items;                // views x triangles
-    const uint32_t *ntiles;         // per item
     const ushort4 *rects;           // per-item pixel rectangles
-    const uint32_t *dkeys;          // per-item depth keys
     uint32_t *tile_count;           // [total_tiles] pairs per tile (counted by the preprocess)
     uint32_t *tile_cursor;          // [total_tiles]
     uint2 *ranges;                  // [total_tiles]
@@ -100,8 +109,8 @@ struct BinArgs {
     uint32_t *tile_order = nullptr; // [total_tiles] if set: tiles by descending pair count
     uint32_t cap;
     int total_tiles;
-    uint64_t blk_stride;            // visiting order of the item chunks: c * stride mod chunks
-    int bin_per = 1;                // chunk = bin_per x 256 items (1..BIN_PER_MAX)
+    const uint4 *vislist;           // [min(ctl->vis_count, vis_cap)] visible-item list (see PreArgs)
+    uint32_t vis_cap;
     uint64_t *scan_status;          // [bin_scan_status_words] zeroed look-back words
     uint32_t *scan_ticket;          // zeroed CTA ticket of the scan
     Ctl *ctl;                       // n_pairs / n_pairs_used / overflow, work_counter[2], big_*
@@ -111,14 +120,6 @@ struct BinArgs {
 void launch_bin_scan(const BinArgs &a, cudaStream_t st);
 size_t bin_scan_status_words(int total_tiles);
 void launch_bin_scatter(const BinArgs &a, int sms, cudaStream_t st);
-constexpr int BIN_PER_MAX = 8;
-// Items per thread of a scatter chunk: 1 while 256-item blocks keep every SM busy, more
-// (up to BIN_PER_MAX) when there are many items, so that the mostly empty blocks of a
-// many-view batch cost one compaction instead of a scan each.
-inline int bin_per_for(int64_t n_items, int sms) {
-    const int64_t per = n_items / ((int64_t)sms * 8 * 256 * 4);
-    return per < 1 ? 1 : (per > BIN_PER_MAX ? BIN_PER_MAX : (int)per);
-}
 void launch_tile_sort(const BinArgs &a, int sms, cudaStream_t st);
 
 // ---- densification (densify.cu) ----

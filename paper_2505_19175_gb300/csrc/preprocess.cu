@@ -178,8 +178,10 @@ preprocess_fwd_kernel(PreArgs a) {
                 continue;
             }
             const int64_t m = (int64_t)vw * a.n + i;
-            a.ntiles[m] = 0u;
-            a.dkeys[m] = 0xffffffffu;
+            if (!a.vmask) {
+                a.ntiles[m] = 0u;
+                a.dkeys[m] = 0xffffffffu;
+            }
             if (a.depth_hist) {
 #pragma unroll
                 for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][255], 1u);
@@ -187,7 +189,23 @@ preprocess_fwd_kernel(PreArgs a) {
         }
     }
 
+    // list slots of this thread's candidate items: one reservation per warp
+    uint32_t lslot = 0;
+    if (a.vislist) {
+        const uint32_t c = (uint32_t)__popcll(vis);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((tid & 31) >= o) incl += y;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t base = 0;
+        if ((tid & 31) == 0 && tot) base = atomicAdd(&a.ctl->vis_count, tot);
+        lslot = __shfl_sync(0xffffffffu, base, 0) + incl - c;
+    }
     uint32_t nvis = 0;
+    uint64_t vm = 0;    // views in which the triangle touches a tile
 #pragma unroll 1
     for (; vis; vis &= vis - 1) {
         const int vw = __ffsll((long long)vis) - 1;
@@ -265,8 +283,18 @@ preprocess_fwd_kernel(PreArgs a) {
             a.recs[m] = rec;
             a.rects[m] = rect;
         }
-        a.ntiles[m] = nt;
-        a.dkeys[m] = key;
+        if (!a.vmask) {
+            a.ntiles[m] = nt;
+            a.dkeys[m] = key;
+        }
+        vm |= nt ? 1ull << vw : 0ull;
+        if (a.vislist && lslot < a.vis_cap) {
+            // this candidate's list entry (a hole when the item touches no tile)
+            a.vislist[lslot] = nt ? make_uint4((uint32_t)m, key, (uint32_t)rect.x | ((uint32_t)rect.y << 16),
+                                               (uint32_t)rect.z | ((uint32_t)rect.w << 16))
+                                  : make_uint4(VIS_HOLE, 0u, 0u, 0u);
+        }
+        ++lslot;
         if (a.tile_count && nt) {
             // per-tile pair counts of the binning (fire-and-forget reductions)
             const uint32_t tx0 = rect.x / TILE, tx1 = rect.z / TILE, ty0 = rect.y / TILE, ty1 = rect.w / TILE;
@@ -279,6 +307,7 @@ preprocess_fwd_kernel(PreArgs a) {
         for (int p = 0; p < 4; ++p)
             if (a.depth_hist) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
     }
+    if (a.vmask && alive) a.vmask[i] = vm;
     const uint32_t wv = __reduce_add_sync(0xffffffffu, nvis);
     if ((tid & 31) == 0 && wv) atomicAdd(&s_nvis, wv);
     __syncthreads();
@@ -312,7 +341,7 @@ preprocess_bwd_kernel(PreBwdArgs a) {
     uint32_t nt1 = 0;
     float4 R0 = make_float4(0.f, 0.f, 0.f, 0.f), R1 = R0, R2 = R0, R3 = R0;
     if (!MULTI && alive) {
-        nt1 = __ldg(a.ntiles + i);
+        nt1 = a.vmask ? (uint32_t)(__ldg(a.vmask + i) & 1ull) : __ldg(a.ntiles + i);
         const float4 *gp = reinterpret_cast<const float4 *>(a.grad2d + i * GRAD_FIELDS);
         R0 = __ldg(gp);
         R1 = __ldg(gp + 1);
@@ -340,12 +369,14 @@ preprocess_bwd_kernel(PreBwdArgs a) {
         for (int k = 0; k < nk * 3; ++k) gsh[k] = 0.f;
     }
 
-    // views in which the triangle was binned: with several views the tile counts of all
-    // views are loaded back to back (one latency) into a bit mask, then only those views
-    // are visited
+    // views in which the triangle was binned: its view mask, or with several views the
+    // tile counts of all views loaded back to back (one latency) into a bit mask; then
+    // only those views are visited
     uint64_t vis = 0;
     if (!MULTI) {
         vis = nt1 != 0u ? 1ull : 0ull;
+    } else if (alive && a.vmask) {
+        vis = __ldg(a.vmask + i);
     } else if (alive) {
         for (int v0 = 0; v0 < a.nviews; v0 += 8) {
             uint32_t nt[8];
