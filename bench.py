@@ -53,24 +53,25 @@ DENSE_FRAG_OPS = {"render_fwd": {"fma": 13, "mufu": 2}, "render_bwd": {"fma": 43
 def stage_bytes(n: int, views: int, n_vis: int, pairs: int, pixels: int, sh_floats: int = 48,
                 loss: bool = True) -> dict:
     """Algorithmic DRAM bytes of each stage of one step, every buffer read or written once:
-    - preprocess: parameters (verts 36 B, SH, o, sigma) read; per (view, triangle) its tile
-      count and depth key (8 B); per visible item its record and rectangle (72 B);
-    - bin_sort: per visible item its rectangle, count and key read (16 B); per pair the
-      binned (key, item) word written and read (8 + 8 B) and the sorted item id (4 B);
+    - preprocess: parameters (verts 36 B, SH, o, sigma) read; per triangle its view mask
+      (8 B); per visible item its record and rectangle (72 B) and its entry of the
+      visible-item list (16 B);
+    - bin_sort: per visible item its list entry read (16 B); per pair the binned (key,
+      item) word written and read (8 + 8 B) and the sorted item id (4 B);
     - render_fwd: per pair the item id (4 B), the record (64 B) and the group-mask words
       (8 B); per pixel colour, T and count written (20 B), with the L1 loss the target read
       and dL/dimage written (24 B);
     - render_bwd: per pair the item id, the record and one mask word (72 B); per visible
       item its gradient record accumulated (64 B); per pixel T, count and dL/dimage (20 B);
     - preprocess_bwd: parameters read and their gradients written (2 x 236 B at SH
-      degree 3); per (view, triangle) its tile count (4 B); per visible item its gradient
-      record and rounded incenter (80 B)."""
+      degree 3); per triangle its view mask (8 B); per visible item its gradient record
+      and rounded incenter (80 B)."""
     params = 4 * (9 + sh_floats + 2)
-    return {"preprocess": n * params + views * n * 8 + n_vis * 72,
+    return {"preprocess": n * params + n * 8 + n_vis * 88,
             "bin_sort": n_vis * 16 + pairs * 20,
             "render_fwd": pairs * 76 + pixels * (44 if loss else 20),
             "render_bwd": pairs * 72 + n_vis * 64 + pixels * 20,
-            "preprocess_bwd": 2 * n * params + views * n * 4 + n_vis * 80}
+            "preprocess_bwd": 2 * n * params + n * 8 + n_vis * 80}
 
 
 def stage_gbs(bytes_: dict, ms: dict, hbm_gbs: float) -> dict:
