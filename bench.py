@@ -113,7 +113,10 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region: the
+    sampler (100 ms period) is running before the region starts, and the samples kept
+    are those taken inside it plus the first one after it (which covers its last
+    100 ms)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -122,28 +125,50 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
+        self.lines = []          # (time, line)
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+            deadline = time.perf_counter() + 5.0
+            while not self.lines and time.perf_counter() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
+        self.t0 = time.perf_counter()
         return self
 
     def __exit__(self, *a):
-        self.out = ""
+        self.t1 = time.perf_counter()
         if self.proc is not None:
+            deadline = self.t1 + 0.5
+            while time.perf_counter() < deadline and not any(t >= self.t1 for t, _ in self.lines):
+                time.sleep(0.01)
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
 
     def summary(self):
         rows = []
-        for line in (getattr(self, "out", "") or "").splitlines():
+        after = False
+        for t, line in list(self.lines):
+            if self.t0 is None or t < self.t0:
+                continue
+            if self.t1 is not None and t >= self.t1:
+                if after:
+                    break
+                after = True
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -216,9 +241,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     scene, cam, target = make_workload()
-    rows = cam.H   # whole frames: a step is the oracle's fwd+bwd of the workload (~2 s)
-    for _ in range(max(args.warmup, 0) and 1):
-        oracle_sample(scene, cam, target, rows)
+    # a step is the oracle's fwd+bwd over a band of pixel rows of the workload's frame,
+    # sized from one whole-frame warm-up so that the K steps take about two minutes
+    t_frame, _, _ = oracle_sample(scene, cam, target, cam.H)
+    rows = max(8, min(cam.H, int(cam.H * 120.0 / (max(args.steps, 1) * t_frame))))
     times, fracs, threads = [], [], 1
     for _ in range(args.steps):
         dt, frac, threads = oracle_sample(scene, cam, target, rows)
@@ -230,7 +256,7 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample_rows_per_step": rows},
             "cpu_baseline": {"value": its, "unit": "it/s", "cores": threads, "kind": "oracle",
-                             "sample": f"whole {cam.W}x{cam.H} frame per step, fwd+bwd"},
+                             "sample": f"{rows} of {cam.H} pixel rows of the {cam.W}x{cam.H} frame per step, fwd+bwd"},
             "e2e": {"value": its, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -1023,7 +1049,7 @@ def run_multiscene(n_req: int, rate_hz: float = 2000.0, budget_gb: float = 60.0)
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
