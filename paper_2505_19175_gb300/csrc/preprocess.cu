@@ -105,13 +105,25 @@ preprocess_fwd_kernel(PreArgs a) {
     __shared__ __align__(16) float s_sh[PRE_THREADS * 52];
     __shared__ uint32_t s_hist[4][256];
     __shared__ uint32_t s_nvis;
-    extern __shared__ ViewDev s_view[];   // nviews entries
+    // dynamic: per view, the frustum test's side-plane offsets (left, right, top,
+    // bottom) and the reciprocal lengths of the planes' normals, then the view table
+    extern __shared__ float4 s_dyn[];
+    float4 *s_pofs = s_dyn, *s_pinv = s_dyn + a.nviews;
+    ViewDev *s_view = reinterpret_cast<ViewDev *>(s_dyn + 2 * a.nviews);
 
     const int tid = threadIdx.x;
     for (int k = tid; k < 4 * 256; k += PRE_THREADS) (&s_hist[0][0])[k] = 0u;
     if (tid == 0) s_nvis = 0;
     for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += PRE_THREADS)
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
+    for (int k = tid; k < a.nviews; k += PRE_THREADS) {
+        const ViewDev &V = a.views[k];
+        const float ul = V.cx + FRUSTUM_PAD, ur = (float)V.W + FRUSTUM_PAD - V.cx;
+        const float vt = V.cy + FRUSTUM_PAD, vb = (float)V.H + FRUSTUM_PAD - V.cy;
+        s_pofs[k] = make_float4(ul, ur, vt, vb);
+        s_pinv[k] = make_float4(rsqrtf(fmaf(V.fx, V.fx, ul * ul)), rsqrtf(fmaf(V.fx, V.fx, ur * ur)),
+                                rsqrtf(fmaf(V.fy, V.fy, vt * vt)), rsqrtf(fmaf(V.fy, V.fy, vb * vb)));
+    }
     const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
     const int cnt = (int)(a.n - i0 < PRE_THREADS ? a.n - i0 : PRE_THREADS);
     constexpr int nk = (DEG + 1) * (DEG + 1);
@@ -163,15 +175,12 @@ preprocess_fwd_kernel(PreArgs a) {
                 const float xc = fmaf(V.R[0], cen[0], fmaf(V.R[1], cen[1], fmaf(V.R[2], cen[2], V.t[0])));
                 const float yc = fmaf(V.R[3], cen[0], fmaf(V.R[4], cen[1], fmaf(V.R[5], cen[2], V.t[1])));
                 const float zc = fmaf(V.R[6], cen[0], fmaf(V.R[7], cen[1], fmaf(V.R[8], cen[2], V.t[2])));
-                const float ul = V.cx + FRUSTUM_PAD, ur = (float)V.W + FRUSTUM_PAD - V.cx;
-                const float vt = V.cy + FRUSTUM_PAD, vb = (float)V.H + FRUSTUM_PAD - V.cy;
+                const float4 po = s_pofs[vw], pi = s_pinv[vw];
                 // (the near test keeps half the plane distance as slack for the FP32
                 // vertex depths of the exact test)
-                out = zc + rad < 0.5f * Z_NEAR ||
-                      fmaf(V.fx, xc, ul * zc) * rsqrtf(fmaf(V.fx, V.fx, ul * ul)) < -rad ||
-                      fmaf(-V.fx, xc, ur * zc) * rsqrtf(fmaf(V.fx, V.fx, ur * ur)) < -rad ||
-                      fmaf(V.fy, yc, vt * zc) * rsqrtf(fmaf(V.fy, V.fy, vt * vt)) < -rad ||
-                      fmaf(-V.fy, yc, vb * zc) * rsqrtf(fmaf(V.fy, V.fy, vb * vb)) < -rad;
+                out = zc + rad < 0.5f * Z_NEAR || fmaf(V.fx, xc, po.x * zc) * pi.x < -rad ||
+                      fmaf(-V.fx, xc, po.y * zc) * pi.y < -rad || fmaf(V.fy, yc, po.z * zc) * pi.z < -rad ||
+                      fmaf(-V.fy, yc, po.w * zc) * pi.w < -rad;
             }
             if (!out) {
                 vis |= 1ull << vw;
@@ -605,7 +614,7 @@ static void launch_fwd_zp(const PreArgs &a, int grid, size_t smem, cudaStream_t 
 void launch_preprocess_fwd(const PreArgs &a, cudaStream_t st) {
     const int grid = (int)((a.n + PRE_THREADS - 1) / PRE_THREADS);
     if (grid <= 0) return;
-    const size_t smem = sizeof(ViewDev) * a.nviews;
+    const size_t smem = (2 * sizeof(float4) + sizeof(ViewDev)) * a.nviews;
     if (a.zplane) launch_fwd_zp<true>(a, grid, smem, st);
     else launch_fwd_zp<false>(a, grid, smem, st);
 }
