@@ -151,6 +151,14 @@ constexpr float c3d = 0.3731763325901154f;   // sqrt(7/(16 pi))
 constexpr float c3e = 1.445305721320277f;    // sqrt(105/(16 pi))
 }  // namespace shc
 
+// Centroid of the triangle's vertices v[0..8], in explicit round-to-nearest operations
+// (so that no kernel fuses it into a later subtraction: the colour's view direction has
+// the same bits in every kernel).
+__device__ __forceinline__ void centroid(const float (&v)[9], float (&cen)[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) cen[k] = __fmul_rn(__fadd_rn(__fadd_rn(v[k], v[3 + k]), v[6 + k]), 1.0f / 3.0f);
+}
+
 // Real SH basis up to degree 3 at the unit direction (x, y, z). Every operation is an
 // explicit round-to-nearest multiply, subtract or fused multiply-add, so that all the
 // kernels that inline it (forward, backward, one view or many) compute the same bits.

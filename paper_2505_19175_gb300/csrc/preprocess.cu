@@ -97,22 +97,151 @@ __device__ __forceinline__ int clamp_pix(float v, int n) {
     return (int)v;
 }
 
-// ZP: also write the items' inverse-depth planes (per-pixel sort).
+// One item (view vw, triangle i) of the forward: geometry and culling, rectangle,
+// record, depth key, its entry `lslot` of the visible-item list, and the binning's tile
+// counts. Returns the item's tile count.
 template <int DEG, int WIN, bool ZP>
+__device__ __forceinline__ uint32_t preprocess_item(const PreArgs &a, const ViewDev &V, int vw, int64_t i,
+                                                    uint32_t lslot, const float (&v)[9], const float *shp,
+                                                    const float (&cen)[3], float o, float sig, float fshrink_pow,
+                                                    float lgt, uint32_t (*s_hist)[256]) {
+    constexpr int nk = (DEG + 1) * (DEG + 1);
+    const int64_t m = (int64_t)vw * a.n + i;
+    Geom g;
+    int cull = item_geometry(v, V, g);
+    uint32_t nt = 0;
+    ushort4 rect = make_ushort4(0, 0, 0, 0);
+    Rec rec;
+    float fshrink = fshrink_pow;
+    if (WIN == WIN_SIGMOID && !a.solid && cull == CULL_NONE)
+        fshrink = o > ALPHA_MIN ? 1.0f - sig * lgt / g.r : 0.0f;   // > 1: support beyond the triangle
+    if (cull == CULL_NONE && fshrink > 0.0f) {
+        // shrunk triangle: S + f (Q_k - S), Q_0 = 0
+        const float wx0 = g.S.x - fshrink * g.S.x, wy0 = g.S.y - fshrink * g.S.y;
+        const float wx1 = fmaf(fshrink, g.Q1.x - g.S.x, g.S.x), wy1 = fmaf(fshrink, g.Q1.y - g.S.y, g.S.y);
+        const float wx2 = fmaf(fshrink, g.Q2.x - g.S.x, g.S.x), wy2 = fmaf(fshrink, g.Q2.y - g.S.y, g.S.y);
+        const float xmin = g.u0.hi + fminf(wx0, fminf(wx1, wx2)) - RECT_PAD;
+        const float xmax = g.u0.hi + fmaxf(wx0, fmaxf(wx1, wx2)) + RECT_PAD;
+        const float ymin = g.v0.hi + fminf(wy0, fminf(wy1, wy2)) - RECT_PAD;
+        const float ymax = g.v0.hi + fmaxf(wy0, fmaxf(wy1, wy2)) + RECT_PAD;
+        // pixels whose centres x + 0.5 lie in [min, max]
+        int px0 = max(clamp_pix(ceilf(fminf(fmaxf(xmin, -2.f), V.W + 2.f) - 0.5f), V.W), 0);
+        int px1 = min(clamp_pix(floorf(fminf(fmaxf(xmax, -2.f), V.W + 2.f) - 0.5f), V.W), V.W - 1);
+        int py0 = max(clamp_pix(ceilf(fminf(fmaxf(ymin, -2.f), V.H + 2.f) - 0.5f), V.H), 0);
+        int py1 = min(clamp_pix(floorf(fminf(fmaxf(ymax, -2.f), V.H + 2.f) - 0.5f), V.H), V.H - 1);
+        if (px0 <= px1 && py0 <= py1) {
+            rect = make_ushort4(px0, py0, px1, py1);
+            nt = (uint32_t)(px1 / TILE - px0 / TILE + 1) * (uint32_t)(py1 / TILE - py0 / TILE + 1);
+        }
+    }
+    uint32_t key = 0xffffffffu;   // invisible items sort after every depth
+    if (nt > 0) {
+        // incenter s = q0 + S in double-float (s_hi + s_lo)
+        ff sx = two_sum(g.u0.hi, g.S.x);
+        ff sy = two_sum(g.v0.hi, g.S.y);
+        const float slx = sx.lo + g.u0.lo, sly = sy.lo + g.v0.lo;
+        // colour
+        float w0 = cen[0] - V.campos[0], w1 = cen[1] - V.campos[1], w2 = cen[2] - V.campos[2];
+        float inv = rsqrtf(fmaf(w0, w0, fmaf(w1, w1, w2 * w2)));
+        float Y[16];
+        sh_basis(DEG, w0 * inv, w1 * inv, w2 * inv, Y);
+        float col[3] = {0.5f, 0.5f, 0.5f};
+        sh_accumulate<nk>(shp, Y, col);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c], 0.0f);
+        rec.a = make_float4(sx.hi, sy.hi, g.A[0], g.B[0]);
+        rec.b = make_float4(slx, g.A[1], g.B[1], sly);
+        rec.c = make_float4(g.A[2], g.B[2], 0.0f, a.solid ? 1.0f : o);
+        rec.d = make_float4(WIN == WIN_SIGMOID ? g.r / sig : sig, col[0], col[1], col[2]);
+        key = __float_as_uint(g.depth);
+        if (ZP) {
+            // inverse depth along the ray through p: (n . d) / (n . x0), n the plane
+            // normal (x1 - x0) x (x2 - x0), d = ((p.x - cx) / fx, (p.y - cy) / fy, 1)
+            float e[2][3];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float dx = v[3 * q + 3] - v[0], dy = v[3 * q + 4] - v[1], dz = v[3 * q + 5] - v[2];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) e[q][r] = fmaf(V.R[3 * r], dx, fmaf(V.R[3 * r + 1], dy, V.R[3 * r + 2] * dz));
+            }
+            const float nx = e[0][1] * e[1][2] - e[0][2] * e[1][1];
+            const float ny = e[0][2] * e[1][0] - e[0][0] * e[1][2];
+            const float nz = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+            const float D = fmaf(nx, g.xc[0].x, fmaf(ny, g.xc[0].y, nz * g.xc[0].z));
+            a.zplane[m] = D != 0.0f ? make_float4(nx / (V.fx * D), ny / (V.fy * D), nz / D, 0.0f)
+                                    : make_float4(0.0f, 0.0f, 1.0f / g.depth, 0.0f);
+        }
+    }
+    // records and rectangles are read only through the tile lists: an item that
+    // touches no tile skips them (most items of a many-view batch are off screen)
+    if (nt > 0) {
+        a.recs[m] = rec;
+        a.rects[m] = rect;
+    }
+    if (!a.vmask) {
+        a.ntiles[m] = nt;
+        a.dkeys[m] = key;
+    }
+    if (a.vislist && lslot < a.vis_cap) {
+        // this candidate's list entry (a hole when the item touches no tile)
+        a.vislist[lslot] = nt ? make_uint4((uint32_t)m, key, (uint32_t)rect.x | ((uint32_t)rect.y << 16),
+                                           (uint32_t)rect.z | ((uint32_t)rect.w << 16))
+                              : make_uint4(VIS_HOLE, 0u, 0u, 0u);
+    }
+    if (a.tile_count && nt) {
+        // per-tile pair counts of the binning (fire-and-forget reductions)
+        const uint32_t tx0 = rect.x / TILE, tx1 = rect.z / TILE, ty0 = rect.y / TILE, ty1 = rect.w / TILE;
+        for (uint32_t ty = ty0; ty <= ty1; ++ty) {
+            uint32_t *row = a.tile_count + V.tile_base + ty * (uint32_t)V.tiles_x;
+            for (uint32_t tx = tx0; tx <= tx1; ++tx) atomicAdd(row + tx, 1u);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        if (a.depth_hist) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
+    return nt;
+}
+
+// Position of the j-th (from 0) set bit of m (which has more than j).
+__device__ __forceinline__ int nth_set_bit(uint64_t m, int j) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 32; w > 0; w >>= 1) {
+        const int c = __popcll(m & ((1ull << w) - 1ull));
+        if (j >= c) {
+            j -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+// ZP: also write the items' inverse-depth planes (per-pixel sort). MULTI: several views,
+// whose candidate items each warp deals out to its lanes.
+template <int DEG, int WIN, bool ZP, bool MULTI>
 __global__ void __launch_bounds__(PRE_THREADS, 6)
 preprocess_fwd_kernel(PreArgs a) {
     __shared__ __align__(16) float s_v[PRE_THREADS * 9];
     __shared__ __align__(16) float s_sh[PRE_THREADS * 52];
-    __shared__ uint32_t s_hist[4][256];
     __shared__ uint32_t s_nvis;
+    // several views: per warp, each lane's candidate views and its first item; per
+    // triangle, its view mask and (o, sigma, shrink factor, sigmoid log term)
+    __shared__ uint64_t s_wvis[MULTI ? PRE_THREADS / 32 : 1][32];
+    __shared__ uint32_t s_wofs[MULTI ? PRE_THREADS / 32 : 1][33];
+    __shared__ uint64_t s_vm[MULTI ? PRE_THREADS : 1];
+    __shared__ float4 s_tri[MULTI ? PRE_THREADS : 1];
     // dynamic: per view, the frustum test's side-plane offsets (left, right, top,
-    // bottom) and the reciprocal lengths of the planes' normals, then the view table
+    // bottom) and the reciprocal lengths of the planes' normals, the view table, and
+    // (depth_hist only) the 4 digit histograms of the depth keys
     extern __shared__ float4 s_dyn[];
     float4 *s_pofs = s_dyn, *s_pinv = s_dyn + a.nviews;
     ViewDev *s_view = reinterpret_cast<ViewDev *>(s_dyn + 2 * a.nviews);
+    uint32_t (*s_hist)[256] = reinterpret_cast<uint32_t (*)[256]>(s_view + a.nviews);
 
     const int tid = threadIdx.x;
-    for (int k = tid; k < 4 * 256; k += PRE_THREADS) (&s_hist[0][0])[k] = 0u;
+    if (a.depth_hist)
+        for (int k = tid; k < 4 * 256; k += PRE_THREADS) (&s_hist[0][0])[k] = 0u;
     if (tid == 0) s_nvis = 0;
     for (int k = tid; k < a.nviews * (int)(sizeof(ViewDev) / 4); k += PRE_THREADS)
         reinterpret_cast<uint32_t *>(s_view)[k] = reinterpret_cast<const uint32_t *>(a.views)[k];
@@ -146,8 +275,8 @@ preprocess_fwd_kernel(PreArgs a) {
     const float fshrink_pow = a.solid ? 1.0f : (WIN == WIN_POWER ? 1.0f - powf(ALPHA_MIN / o, 1.0f / sig) : 0.0f);
     // sigmoid window: o I >= tau where kappa ratio >= ln(tau / (o - tau))
     const float lgt = (WIN == WIN_SIGMOID && o > ALPHA_MIN) ? logf(ALPHA_MIN / (o - ALPHA_MIN)) : 0.0f;
-    const float cen[3] = {(v[0] + v[3] + v[6]) * (1.0f / 3.0f), (v[1] + v[4] + v[7]) * (1.0f / 3.0f),
-                          (v[2] + v[5] + v[8]) * (1.0f / 3.0f)};
+    float cen[3];
+    centroid(v, cen);
 
     // views the triangle may touch: its bounding sphere (centroid, largest vertex
     // distance) against the near plane and the four side planes of each view's frustum
@@ -198,9 +327,10 @@ preprocess_fwd_kernel(PreArgs a) {
         }
     }
 
-    // list slots of this thread's candidate items: one reservation per warp
-    uint32_t lslot = 0;
-    if (a.vislist) {
+    // the warp's candidate items (this thread's first at woff of wtot) and their list
+    // slots from wbase: one reservation per warp
+    uint32_t woff, wtot, wbase = 0;
+    {
         const uint32_t c = (uint32_t)__popcll(vis);
         uint32_t incl = c;
 #pragma unroll
@@ -208,113 +338,56 @@ preprocess_fwd_kernel(PreArgs a) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if ((tid & 31) >= o) incl += y;
         }
-        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-        uint32_t base = 0;
-        if ((tid & 31) == 0 && tot) base = atomicAdd(&a.ctl->vis_count, tot);
-        lslot = __shfl_sync(0xffffffffu, base, 0) + incl - c;
+        wtot = __shfl_sync(0xffffffffu, incl, 31);
+        woff = incl - c;
+        if (a.vislist) {
+            if ((tid & 31) == 0 && wtot) wbase = atomicAdd(&a.ctl->vis_count, wtot);
+            wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        }
     }
+    uint32_t lslot = wbase + woff;
     uint32_t nvis = 0;
     uint64_t vm = 0;    // views in which the triangle touches a tile
+    if (!MULTI) {
 #pragma unroll 1
-    for (; vis; vis &= vis - 1) {
-        const int vw = __ffsll((long long)vis) - 1;
-        const ViewDev &V = s_view[vw];
-        const int64_t m = (int64_t)vw * a.n + i;
-        Geom g;
-        int cull = item_geometry(v, V, g);
-        uint32_t nt = 0;
-        ushort4 rect = make_ushort4(0, 0, 0, 0);
-        Rec rec;
-        float fshrink = fshrink_pow;
-        if (WIN == WIN_SIGMOID && !a.solid && cull == CULL_NONE)
-            fshrink = o > ALPHA_MIN ? 1.0f - sig * lgt / g.r : 0.0f;   // > 1: support beyond the triangle
-        if (cull == CULL_NONE && fshrink > 0.0f) {
-            // shrunk triangle: S + f (Q_k - S), Q_0 = 0
-            const float wx0 = g.S.x - fshrink * g.S.x, wy0 = g.S.y - fshrink * g.S.y;
-            const float wx1 = fmaf(fshrink, g.Q1.x - g.S.x, g.S.x), wy1 = fmaf(fshrink, g.Q1.y - g.S.y, g.S.y);
-            const float wx2 = fmaf(fshrink, g.Q2.x - g.S.x, g.S.x), wy2 = fmaf(fshrink, g.Q2.y - g.S.y, g.S.y);
-            const float xmin = g.u0.hi + fminf(wx0, fminf(wx1, wx2)) - RECT_PAD;
-            const float xmax = g.u0.hi + fmaxf(wx0, fmaxf(wx1, wx2)) + RECT_PAD;
-            const float ymin = g.v0.hi + fminf(wy0, fminf(wy1, wy2)) - RECT_PAD;
-            const float ymax = g.v0.hi + fmaxf(wy0, fmaxf(wy1, wy2)) + RECT_PAD;
-            // pixels whose centres x + 0.5 lie in [min, max]
-            int px0 = max(clamp_pix(ceilf(fminf(fmaxf(xmin, -2.f), V.W + 2.f) - 0.5f), V.W), 0);
-            int px1 = min(clamp_pix(floorf(fminf(fmaxf(xmax, -2.f), V.W + 2.f) - 0.5f), V.W), V.W - 1);
-            int py0 = max(clamp_pix(ceilf(fminf(fmaxf(ymin, -2.f), V.H + 2.f) - 0.5f), V.H), 0);
-            int py1 = min(clamp_pix(floorf(fminf(fmaxf(ymax, -2.f), V.H + 2.f) - 0.5f), V.H), V.H - 1);
-            if (px0 <= px1 && py0 <= py1) {
-                rect = make_ushort4(px0, py0, px1, py1);
-                nt = (uint32_t)(px1 / TILE - px0 / TILE + 1) * (uint32_t)(py1 / TILE - py0 / TILE + 1);
-            }
+        for (; vis; vis &= vis - 1) {
+            const int vw = __ffsll((long long)vis) - 1;
+            const uint32_t nt =
+                preprocess_item<DEG, WIN, ZP>(a, s_view[vw], vw, i, lslot++, v, shp, cen, o, sig, fshrink_pow, lgt, s_hist);
+            nvis += nt ? 1u : 0u;
+            vm |= nt ? 1ull << vw : 0ull;
         }
-        uint32_t key = 0xffffffffu;   // invisible items sort after every depth
-        if (nt > 0) {
-            // incenter s = q0 + S in double-float (s_hi + s_lo)
-            ff sx = two_sum(g.u0.hi, g.S.x);
-            ff sy = two_sum(g.v0.hi, g.S.y);
-            const float slx = sx.lo + g.u0.lo, sly = sy.lo + g.v0.lo;
-            // colour
-            float w0 = cen[0] - V.campos[0], w1 = cen[1] - V.campos[1], w2 = cen[2] - V.campos[2];
-            float inv = rsqrtf(fmaf(w0, w0, fmaf(w1, w1, w2 * w2)));
-            float Y[16];
-            sh_basis(DEG, w0 * inv, w1 * inv, w2 * inv, Y);
-            float col[3] = {0.5f, 0.5f, 0.5f};
-            sh_accumulate<nk>(shp, Y, col);
+    } else {
+        // the warp's candidate items are dealt out to its lanes in rounds (a lane per
+        // triangle looping over its views would leave about half of them idle): item c
+        // of the warp belongs to the last lane whose first item is <= c
+        const int lane = tid & 31, w = tid >> 5;
+        s_wvis[w][lane] = vis;
+        s_wofs[w][lane] = woff;
+        s_vm[tid] = 0ull;
+        s_tri[tid] = make_float4(o, sig, fshrink_pow, lgt);
+        __syncwarp();
+        for (uint32_t c = (uint32_t)lane; c < wtot; c += 32u) {
+            int lo = 0;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c], 0.0f);
-            rec.a = make_float4(sx.hi, sy.hi, g.A[0], g.B[0]);
-            rec.b = make_float4(slx, g.A[1], g.B[1], sly);
-            rec.c = make_float4(g.A[2], g.B[2], 0.0f, a.solid ? 1.0f : o);
-            rec.d = make_float4(WIN == WIN_SIGMOID ? g.r / sig : sig, col[0], col[1], col[2]);
-            key = __float_as_uint(g.depth);
-            ++nvis;
-            if (ZP) {
-                // inverse depth along the ray through p: (n . d) / (n . x0), n the plane
-                // normal (x1 - x0) x (x2 - x0), d = ((p.x - cx) / fx, (p.y - cy) / fy, 1)
-                float e[2][3];
+            for (int st = 16; st > 0; st >>= 1)
+                if (s_wofs[w][lo + st] <= c) lo += st;
+            const int t = 32 * w + lo;       // the owner's thread
+            const int vw = nth_set_bit(s_wvis[w][lo], (int)(c - s_wofs[w][lo]));
+            float vt[9];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const float dx = v[3 * q + 3] - v[0], dy = v[3 * q + 4] - v[1], dz = v[3 * q + 5] - v[2];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) e[q][r] = fmaf(V.R[3 * r], dx, fmaf(V.R[3 * r + 1], dy, V.R[3 * r + 2] * dz));
-                }
-                const float nx = e[0][1] * e[1][2] - e[0][2] * e[1][1];
-                const float ny = e[0][2] * e[1][0] - e[0][0] * e[1][2];
-                const float nz = e[0][0] * e[1][1] - e[0][1] * e[1][0];
-                const float D = fmaf(nx, g.xc[0].x, fmaf(ny, g.xc[0].y, nz * g.xc[0].z));
-                a.zplane[m] = D != 0.0f ? make_float4(nx / (V.fx * D), ny / (V.fy * D), nz / D, 0.0f)
-                                        : make_float4(0.0f, 0.0f, 1.0f / g.depth, 0.0f);
-            }
+            for (int q = 0; q < 9; ++q) vt[q] = s_v[t * 9 + q];
+            float ct[3];
+            centroid(vt, ct);
+            const float4 tp = s_tri[t];
+            const uint32_t nt = preprocess_item<DEG, WIN, ZP>(a, s_view[vw], vw, i0 + t, wbase + c, vt,
+                                                              s_sh + t * RecLayout<nk * 3>::stride, ct, tp.x, tp.y, tp.z,
+                                                              tp.w, s_hist);
+            nvis += nt ? 1u : 0u;
+            if (nt) atomicOr(reinterpret_cast<unsigned long long *>(&s_vm[t]), 1ull << vw);
         }
-        // records and rectangles are read only through the tile lists: an item that
-        // touches no tile skips them (most items of a many-view batch are off screen)
-        if (nt > 0) {
-            a.recs[m] = rec;
-            a.rects[m] = rect;
-        }
-        if (!a.vmask) {
-            a.ntiles[m] = nt;
-            a.dkeys[m] = key;
-        }
-        vm |= nt ? 1ull << vw : 0ull;
-        if (a.vislist && lslot < a.vis_cap) {
-            // this candidate's list entry (a hole when the item touches no tile)
-            a.vislist[lslot] = nt ? make_uint4((uint32_t)m, key, (uint32_t)rect.x | ((uint32_t)rect.y << 16),
-                                               (uint32_t)rect.z | ((uint32_t)rect.w << 16))
-                                  : make_uint4(VIS_HOLE, 0u, 0u, 0u);
-        }
-        ++lslot;
-        if (a.tile_count && nt) {
-            // per-tile pair counts of the binning (fire-and-forget reductions)
-            const uint32_t tx0 = rect.x / TILE, tx1 = rect.z / TILE, ty0 = rect.y / TILE, ty1 = rect.w / TILE;
-            for (uint32_t ty = ty0; ty <= ty1; ++ty) {
-                uint32_t *row = a.tile_count + V.tile_base + ty * (uint32_t)V.tiles_x;
-                for (uint32_t tx = tx0; tx <= tx1; ++tx) atomicAdd(row + tx, 1u);
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-            if (a.depth_hist) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
+        __syncwarp();
+        vm = s_vm[tid];
     }
     if (a.vmask && alive) a.vmask[i] = vm;
     const uint32_t wv = __reduce_add_sync(0xffffffffu, nvis);
@@ -364,8 +437,8 @@ preprocess_bwd_kernel(PreBwdArgs a) {
     for (int k = 0; k < 9; ++k) v[k] = s_v[tid * 9 + k];
     constexpr int sstride = RecLayout<nk * 3>::stride;
     float *shp = s_sh + tid * sstride;
-    const float cen[3] = {(v[0] + v[3] + v[6]) * (1.0f / 3.0f), (v[1] + v[4] + v[7]) * (1.0f / 3.0f),
-                          (v[2] + v[5] + v[8]) * (1.0f / 3.0f)};
+    float cen[3];
+    centroid(v, cen);
     float gv[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) gv[k] = 0.f;
@@ -596,27 +669,32 @@ void launch_step_init(const ViewDev *views, const ViewDev *pinned, int nviews, V
     else step_init<MAX_VIEWS>(views, pinned, nviews, views_d, ctl, tile_count, tiles, st);
 }
 
-template <bool ZP>
+template <bool ZP, bool MULTI>
 static void launch_fwd_zp(const PreArgs &a, int grid, size_t smem, cudaStream_t st) {
     const bool sg = a.window == WIN_SIGMOID;
     switch (a.sh_degree) {
-        case 0: sg ? preprocess_fwd_kernel<0, 1, ZP><<<grid, PRE_THREADS, smem, st>>>(a)
-                   : preprocess_fwd_kernel<0, 0, ZP><<<grid, PRE_THREADS, smem, st>>>(a); break;
-        case 1: sg ? preprocess_fwd_kernel<1, 1, ZP><<<grid, PRE_THREADS, smem, st>>>(a)
-                   : preprocess_fwd_kernel<1, 0, ZP><<<grid, PRE_THREADS, smem, st>>>(a); break;
-        case 2: sg ? preprocess_fwd_kernel<2, 1, ZP><<<grid, PRE_THREADS, smem, st>>>(a)
-                   : preprocess_fwd_kernel<2, 0, ZP><<<grid, PRE_THREADS, smem, st>>>(a); break;
-        default: sg ? preprocess_fwd_kernel<3, 1, ZP><<<grid, PRE_THREADS, smem, st>>>(a)
-                    : preprocess_fwd_kernel<3, 0, ZP><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        case 0: sg ? preprocess_fwd_kernel<0, 1, ZP, MULTI><<<grid, PRE_THREADS, smem, st>>>(a)
+                   : preprocess_fwd_kernel<0, 0, ZP, MULTI><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        case 1: sg ? preprocess_fwd_kernel<1, 1, ZP, MULTI><<<grid, PRE_THREADS, smem, st>>>(a)
+                   : preprocess_fwd_kernel<1, 0, ZP, MULTI><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        case 2: sg ? preprocess_fwd_kernel<2, 1, ZP, MULTI><<<grid, PRE_THREADS, smem, st>>>(a)
+                   : preprocess_fwd_kernel<2, 0, ZP, MULTI><<<grid, PRE_THREADS, smem, st>>>(a); break;
+        default: sg ? preprocess_fwd_kernel<3, 1, ZP, MULTI><<<grid, PRE_THREADS, smem, st>>>(a)
+                    : preprocess_fwd_kernel<3, 0, ZP, MULTI><<<grid, PRE_THREADS, smem, st>>>(a); break;
     }
 }
 
 void launch_preprocess_fwd(const PreArgs &a, cudaStream_t st) {
     const int grid = (int)((a.n + PRE_THREADS - 1) / PRE_THREADS);
     if (grid <= 0) return;
-    const size_t smem = (2 * sizeof(float4) + sizeof(ViewDev)) * a.nviews;
-    if (a.zplane) launch_fwd_zp<true>(a, grid, smem, st);
-    else launch_fwd_zp<false>(a, grid, smem, st);
+    const size_t smem = (2 * sizeof(float4) + sizeof(ViewDev)) * a.nviews + (a.depth_hist ? 4 * 256 * 4 : 0);
+    if (a.nviews > 1) {
+        if (a.zplane) launch_fwd_zp<true, true>(a, grid, smem, st);
+        else launch_fwd_zp<false, true>(a, grid, smem, st);
+    } else {
+        if (a.zplane) launch_fwd_zp<true, false>(a, grid, smem, st);
+        else launch_fwd_zp<false, false>(a, grid, smem, st);
+    }
 }
 
 template <bool MULTI>
