@@ -81,6 +81,29 @@ def test_crowded_tile_sorted_by_chunks_and_merges(n):
     _compare(imgs[0], T[0], ref, f"crowded tile, {n} triangles")
 
 
+def test_tile_lists_order_equal_depth_keys_by_item():
+    """Triangles in one fronto-parallel plane share their centroid depth key exactly: the
+    tile lists must hold them in item order (the stable sort of the 64-bit keys). (The
+    images are not compared: with equal depths the oracle lists the compositing order as
+    undecided.)"""
+    base = synth.random_scene(3000, seed=33, deg=0, size=(0.05, 0.5))
+    rng = np.random.default_rng(33)
+    v = np.array(base.verts, copy=True)
+    flat = rng.random(len(v)) < 0.5
+    v[flat, :, 2] = 3.0
+    scene = synth.Scene(v, base.sh, base.opacity, base.sigma, base.sh_degree)
+    cam = synth.camera_identity(257, 129)
+    _, _, _, ctx, _ = gpu_forward(scene, [cam])
+    nt = ctx.debug("ntiles")
+    dk = ctx.debug("depth_keys")[nt > 0]
+    assert len(np.unique(dk)) < len(dk) - 100          # many shared keys
+    tiles = ctx.debug("pair_tiles").astype(np.uint64)
+    items = ctx.debug("pair_items").astype(np.uint64)
+    et, ei = expected_pairs_from_items(ctx, [cam])
+    np.testing.assert_array_equal(tiles, et)
+    np.testing.assert_array_equal(items, ei)
+
+
 def test_binned_pairs_hold_each_tiles_items():
     """The scatter puts exactly the tile's items into its range; the sort only reorders."""
     scene = synth.random_scene(1500, seed=21, deg=0, size=(0.05, 0.8))
