@@ -548,7 +548,33 @@ def run_ours(args, rank, world):
     e1.record(cs)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    del sets
+    # the host link's rate for the same copies (in alone, out alone, both at once)
+    b0 = sets[0]
+
+    def copy_in():
+        with torch.cuda.stream(up):
+            for key in ("verts", "sh", "opacity", "sigma"):
+                getattr(b0["st"], key).copy_(host[key], non_blocking=True)
+            b0["tgt"].copy_(host["target"], non_blocking=True)
+
+    def copy_out():
+        with torch.cuda.stream(down):
+            for key, x in zip(("dv", "dsh", "do", "ds"), b0["g"]):
+                hout[key].copy_(x, non_blocking=True)
+            hout["loss"].copy_(b0["loss"], non_blocking=True)
+
+    def link_gbs(fn, nbytes, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return nbytes * reps / (time.perf_counter() - t0) / 1e9
+
+    link = {"h2d_gbs": link_gbs(copy_in, h2d), "d2h_gbs": link_gbs(copy_out, d2h),
+            "both_gbs": link_gbs(lambda: (copy_in(), copy_out()), h2d + d2h)}
+    del sets, b0
     if world > 1:
         e2e_ms = max_over_ranks(e2e_ms, "cuda")
     # the same step with the sigmoid window (Eq. indicator2): supports beyond the triangles
@@ -560,7 +586,13 @@ def run_ours(args, rank, world):
         pixel_sort_line = run_pixel_sort_step(args, dev, st, cam, imgs, grad, loss, tgt, dv, dsh, do, ds, capture,
                                               timed)
 
-    e2e = {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "it/s", "h2d_bytes_per_step": h2d,           "d2h_bytes_per_step": d2h}
+    e2e = {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "it/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+    # the copies' rate in the timed steps against the link's own with both directions busy
+    e2e_gbs = (h2d + d2h) * args.steps / (e2e_ms / 1000.0) / 1e9
+    e2e["link"] = {"achieved_gbs": round(e2e_gbs, 1), **{k: round(v, 1) for k, v in link.items()},
+                   "frac_of_both": round(e2e_gbs / link["both_gbs"], 3),
+                   "note": "pinned host <-> HBM copies of the step's inputs and outputs, timed alone"}
 
     if rank != 0:
         return
