@@ -281,6 +281,17 @@ __device__ __forceinline__ bool group_grad(const float4 ca, const float4 cb, con
     return any;
 }
 
+// A record no pixel composites, for the forward's lanes with no pair of their own in a
+// walk step (so that they take the step's straight-line code with the others instead of
+// a path of their own): its first edge line is at 1e30 (ratio < 0 everywhere), its opacity,
+// sigma and colour 0, so every term it adds is a finite zero.
+__device__ __forceinline__ void put_null_record(float4 *r) {
+    r[0] = make_float4(1e30f, 1e30f, 1.0f, 0.0f);
+    r[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    r[2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    r[3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
 __device__ __forceinline__ float4 shfl_xor4(float4 v, int m) {
     return make_float4(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m),
                        __shfl_xor_sync(0xffffffffu, v.z, m), __shfl_xor_sync(0xffffffffu, v.w, m));
@@ -613,13 +624,16 @@ __global__ void __launch_bounds__(FW_THREADS, FW_CTAS)
 render_fwd_kernel(RenderArgs a) {
     // per warp: the window's records (stride of 5 float4: lanes reading different
     // records spread over the banks), item ids and the pruning statistics of each pair
-    __shared__ float4 s_rec[FW_WARPS][32 * FW_WIN][BW_RSTRIDE];
+    // (slot 32 FW_WIN: the null record)
+    __shared__ float4 s_rec[FW_WARPS][32 * FW_WIN + 1][BW_RSTRIDE];
     __shared__ uint32_t s_it[FW_WARPS][32 * FW_WIN];
     __shared__ uint32_t s_sw[STATS ? FW_WARPS : 1][32 * FW_WIN];
     __shared__ uint32_t s_sn[STATS ? FW_WARPS : 1][32 * FW_WIN];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t *S = s_it[w];
     float4 (*SR)[BW_RSTRIDE] = s_rec[w];
+    if (lane == 0) put_null_record(SR[32 * FW_WIN]);
+    __syncwarp();
     if (STATS) {
 #pragma unroll
         for (int q = 0; q < FW_WIN; ++q) s_sw[w][32 * q + lane] = s_sn[w][32 * q + lane] = 0u;
@@ -706,11 +720,14 @@ render_fwd_kernel(RenderArgs a) {
                 int cpos = pop_first(hi, lo);
                 if (done == 0xFu) cpos = -1;     // (a lane whose pixels have all stopped drops its list)
                 if (!__any_sync(0xffffffffu, cpos >= 0)) break;
-                if (cpos < 0) continue;      // (the warp's next pop meets this lane at the vote)
-                const float4 ca = SR[cpos][0], cb = SR[cpos][1], cc = SR[cpos][2], cd = SR[cpos][3];
+                // (a lane with no pair takes the null record, or, when counting fragments,
+                // meets the others at the next vote)
+                if (COUNT && cpos < 0) continue;
+                const int slot = cpos >= 0 ? cpos : 32 * FW_WIN;
+                const float4 ca = SR[slot][0], cb = SR[slot][1], cc = SR[slot][2], cd = SR[slot][3];
                 float sw = 0.0f;
                 uint32_t sn = 0u;
-                if (group_fwd<SOLID, WIN, STATS, COUNT>(ca, cb, cc, cd, (uint32_t)(wst + cpos + 1), x0, y0, T, C0, C1,
+                if (group_fwd<SOLID, WIN, STATS, COUNT>(ca, cb, cc, cd, (uint32_t)(wst + slot + 1), x0, y0, T, C0, C1,
                                                         C2, last, done, sw, sn, n_eval, n_kept)) {
                     if (cpos < 64) klo |= 1ull << cpos;
                     else khi |= 1ull << (cpos - 64);
