@@ -676,6 +676,8 @@ def run_ours(args, rank, world):
         line["densify_3m"] = run_densify(max(3, min(args.steps, 20)))
     if not args.no_solid and world == 1:
         line["solid_2m"] = run_solid(max(3, min(args.steps, 20)))
+    if not args.no_noalloc and world == 1:
+        line["noalloc_60k"] = run_noalloc(max(3, min(args.steps, 50)))
     if not args.no_serving:
         line["serving"] = run_serving(args.serve_requests, 2000.0, 1_000_000)
     if not args.no_multiscene and world == 1:
@@ -824,6 +826,64 @@ def run_solid(steps: int, n_tris: int = 2_000_000):
                            "ms_median": round(float(np.median(ms)), 4), "pairs": int(info.n_pairs),
                            "visible": int(info.n_visible), "overflow": bool(info.overflow)}
         del g
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# the allocation-free forward (its own fixed workspace; preprocess, onesweep radix sort
+# of the 64-bit tile|depth keys, render) against the regular entry points on one scene
+# ---------------------------------------------------------------------------------------
+def run_noalloc(steps: int, n_tris: int = 60_000):
+    import ctypes as C
+    import torch
+    from paper_2505_19175_gb300 import native as N, synth
+    from paper_2505_19175_gb300.renderer import Context, SceneTensors, new_images
+    scene, _, _ = synth.scene_patches(n=n_tris, n_patch=40)
+    cam = synth.camera_patches()
+    st = SceneTensors.from_numpy(scene)
+    f = N.lib().tri_render_fwd_noalloc
+    f.argtypes = [C.POINTER(N.tri_scene), C.POINTER(N.tri_camera), C.c_void_p, C.c_void_p, C.c_void_p,
+                  C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    img = torch.empty((3, cam.H, cam.W), device="cuda")
+    T = torch.empty((cam.H, cam.W), device="cuda")
+    nc = torch.empty((cam.H, cam.W), device="cuda", dtype=torch.int32)
+    status = torch.zeros((1,), device="cuda", dtype=torch.int32)
+    abi_scene, abi_cam = st.as_abi(), N.make_camera(cam)
+    stream = int(torch.cuda.current_stream().cuda_stream)
+
+    def noalloc():
+        if f(C.byref(abi_scene), C.byref(abi_cam), img.data_ptr(), T.data_ptr(), nc.data_ptr(),
+             status.data_ptr(), stream) != 0:
+            raise RuntimeError("tri_render_fwd_noalloc failed")
+
+    ctx = Context()
+    imgs = new_images([cam])
+
+    def regular():
+        ctx.preprocess(st, [cam])
+        ctx.bin_sort(sync=False)
+        ctx.render_fwd(imgs)
+
+    ctx.preprocess(st, [cam])
+    ctx.reserve(int(ctx.bin_sort(sync=True) * 1.25) + 1024)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {"workload": f"{n_tris} tris SH3 on 40 planar patches, 1297x840, forward only, eager calls, "
+                       "L2 flushed between frames"}
+    for name, fn in (("noalloc", noalloc), ("regular", regular)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record()
+            fn()
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        out[name + "_ms_median"] = round(float(np.median([a.elapsed_time(b) for a, b in ev])), 4)
+    out["status"] = int(status.item())
+    out["pairs"] = int(ctx.check().n_pairs)
     return out
 
 
@@ -1093,6 +1153,7 @@ def main():
     ap.add_argument("--no-sigmoid", action="store_true")
     ap.add_argument("--no-pixel-sort", action="store_true")
     ap.add_argument("--no-multiscene", action="store_true")
+    ap.add_argument("--no-noalloc", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4096)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
