@@ -216,7 +216,6 @@ BinArgs bin_args(tri_ctx *c) {
     b.nviews = c->nviews;
     b.n = c->scene.n;
     b.n_items = c->n_items;
-    b.rects = P<ushort4>(c->rects);
     b.vislist = P<uint4>(c->vislist);
     b.vis_cap = (uint32_t)c->n_items;
     b.tile_count = P<uint32_t>(c->tile_count);

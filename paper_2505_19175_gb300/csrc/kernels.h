@@ -98,7 +98,6 @@ struct BinArgs {
     int nviews;
     int64_t n;                      // triangles per view
     int64_t n_items;                // views x triangles
-    const ushort4 *rects;           // per-item pixel rectangles
     uint32_t *tile_count;           // [total_tiles] pairs per tile (counted by the preprocess)
     uint32_t *tile_cursor;          // [total_tiles]
     uint2 *ranges;                  // [total_tiles]
